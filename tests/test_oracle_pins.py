@@ -1,0 +1,410 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test is chosen so that a plausible mistake in the oracle (a dropped term, a
+wrong sign, a transposed operand) fails it.  CPU only.
+"""
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate, special, stats
+
+from tests import analytic as A
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------------- RNG
+def test_philox_known_answers(orc):
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(t, 16) for t in r]
+        out = orc.philox(v[0:4], v[4:6])
+        assert [int(o) for o in out] == v[6:10]
+
+
+def test_stream_counter_layout(orc):
+    # photon stream = Philox(key=seed, ctr=(photon lo, photon hi, block lo, block hi))
+    seed, pid = 0x0123456789ABCDEF, 0xFEDCBA9876543210
+    w = orc.stream_words(seed, pid, 12)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for blk in range(3):
+        ref = orc.philox([pid & 0xFFFFFFFF, pid >> 32, blk, 0], key)
+        assert list(w[4 * blk:4 * blk + 4]) == list(ref)
+
+
+def test_stream_uniformity(orc):
+    w = orc.stream_words(7, 3, 200000).astype(np.float64)
+    u = (w + 0.5) / 2 ** 32
+    assert stats.kstest(u, "uniform").pvalue > 1e-3
+
+
+# ------------------------------------------------------------ special functions
+def test_dawson_against_scipy_and_mpmath(orc):
+    import mpmath as mp
+    mp.mp.dps = 30
+    xs = np.concatenate([np.linspace(-9, 9, 721), [1e-6, 0.1999, 0.2, 0.2001, 3.0]])
+    d = np.array([orc.dawson(x) for x in xs])
+    ref = special.dawsn(xs)
+    nz = xs != 0
+    assert np.max(np.abs(d[nz] - ref[nz]) / np.abs(ref[nz])) < 1e-13
+    assert orc.dawson(0.0) == 0.0
+    for x in [0.05, 0.5, 0.92413887, 2.0, 5.5]:
+        t = float(mp.sqrt(mp.pi) / 2 * mp.exp(-x * x) * mp.erfi(x))
+        assert abs(orc.dawson(x) - t) <= 1e-14 * abs(t)
+
+
+def _H_mp(a, x):
+    import mpmath as mp
+    z = mp.mpc(x, a)
+    return float(mp.re(mp.exp(-z * z) * mp.erfc(-1j * z)))
+
+
+def test_voigt_against_faddeeva_high_precision(orc):
+    """App. A.3: the truth is Re w(x + i a); compare to 40-digit mpmath."""
+    import mpmath as mp
+    mp.mp.dps = 40
+    worst = 0.0
+    for a in [1e-5, 5e-5, 4.7e-4, 2e-3, 1.05e-2, 0.1, 0.5]:
+        for x in list(np.linspace(0, 10, 41)) + [6.99, 7.0, 7.01, 12.0, 30.0, 100.0, 300.0, 2000.0]:
+            h = float(orc.voigt(a, x))
+            t = _H_mp(a, x)
+            worst = max(worst, abs(h - t) / t)
+    assert worst < 1e-12
+
+
+def test_voigt_special_cases(orc):
+    x = np.linspace(-6, 6, 121)
+    assert np.allclose(orc.voigt(0.0, x), np.exp(-x * x), rtol=1e-13, atol=0)
+    for a in [1e-4, 1e-3, 1e-2, 0.3]:
+        assert abs(orc.voigt(a, 0.0) - np.exp(a * a) * special.erfc(a)) < 1e-13
+    # symmetric in x
+    assert np.allclose(orc.voigt(1e-3, x), orc.voigt(1e-3, -x), rtol=0, atol=0)
+    # Lorentzian wing: H -> a / (sqrt(pi) x^2) (1 + 3/(2 x^2))
+    for x0 in [50.0, 500.0]:
+        a = 1e-3
+        assert abs(orc.voigt(a, x0) / (a / (np.sqrt(np.pi) * x0 ** 2) * (1 + 1.5 / x0 ** 2)) - 1) < 1e-6
+
+
+def test_voigt_normalisation(orc):
+    # int H dx = sqrt(pi); integrate to |x| = X and add the Lorentzian tails analytically
+    a, X = 1e-3, 200.0
+    val = integrate.quad(lambda t: float(orc.voigt(a, t)), -X, X, points=[0.0], limit=400, epsrel=1e-11)[0]
+    tail = 2 * a / np.sqrt(np.pi) * (1 / X + 0.5 / X ** 3)
+    assert abs(val + tail - np.sqrt(np.pi)) < 1e-8
+
+
+def test_line_parameters(orc):
+    # check values quoted throughout the Lya literature (e.g. Dijkstra 2017 review):
+    # v_th = 12.85 km/s, a = 4.7e-4, sigma_0 = 5.9e-14 cm^2 at 1e4 K, scaling T^(1/2), T^(-1/2)
+    p = orc.line_params(1e4)
+    assert abs(p["vth_kms"] - 12.85) < 0.01
+    assert abs(p["a"] - 4.7e-4) < 0.05e-4
+    assert abs(p["sigma0"] - 5.9e-14) < 0.05e-14
+    q = orc.line_params(4e4)
+    assert abs(q["vth_kms"] / p["vth_kms"] - 2) < 1e-12
+    assert abs(q["a"] / p["a"] - 0.5) < 1e-12
+    assert abs(q["sigma0"] / p["sigma0"] - 0.5) < 1e-12
+    # Lorentz half width in velocity a*v_th = A21 lambda0 / (4 pi) is T independent
+    assert abs(p["a"] * p["vth_kms"] - q["a"] * q["vth_kms"]) < 1e-15
+
+
+# ------------------------------------------------------------------ samplers
+@pytest.mark.parametrize("a", [1e-2, 1e-3, 1e-4])
+@pytest.mark.parametrize("x", [0.0, 1.0, 2.0, 3.0, 4.0, 6.0, 10.0, -2.5])
+def test_upar_distribution_matches_eq6(orc, x, a):
+    n = 40000
+    u, iters = orc.sample_upar(x, a, n, seed=11)
+    grid, cdf = A.upar_cdf_table(x, a)
+    res = stats.kstest(u, lambda t: np.interp(t, grid, cdf))
+    assert res.pvalue > 1e-4, (x, a, res)
+    m = A.upar_mean(x, a)
+    sd = np.std(u) / np.sqrt(n)
+    assert abs(u.mean() - m) < 5 * sd + 1e-6
+
+
+def test_upar_degenerate_a_zero(orc):
+    # a -> 0: the absorbing atom is exactly resonant, u_par = x
+    u, _ = orc.sample_upar(1.7, 0.0, 100, seed=1)
+    assert np.all(u == 1.7)
+
+
+def test_phase_function_samplers(orc):
+    n = 200000
+    mu = orc.sample_mu("isotropic", n, seed=1)
+    assert stats.kstest(mu, "uniform", args=(-1, 2)).pvalue > 1e-3
+    mu = orc.sample_mu("dipole", n, seed=2)
+    assert abs(np.mean(mu ** 2) - 0.4) < 5 * np.std(mu ** 2) / np.sqrt(n)
+    assert stats.kstest(mu, lambda t: (t ** 3 + 3 * t + 4) / 8).pvalue > 1e-3
+    g = 0.73
+    mu = orc.sample_mu("hg", n, g=g, seed=3)
+    assert abs(mu.mean() - g) < 5 * mu.std() / np.sqrt(n)
+    hg_cdf = lambda t: (1 - g * g) / (2 * g) * (1 / np.sqrt(1 + g * g - 2 * g * t) - 1 / (1 + g))
+    assert stats.kstest(mu, hg_cdf).pvalue > 1e-3
+
+
+@pytest.mark.parametrize("x_in", [0.3, 1.0, 2.0])
+def test_single_scatter_isotropic_matches_hummer_RIA(orc, x_in):
+    """Eq. 5-7 (no recoil) + isotropic phase function in the a -> 0 limit."""
+    xo, mu = orc.scatter_once(x_in, 1e-8, 0, 200000, seed=5)
+    cdf_grid = np.linspace(-6, 6, 24001)
+    pdf = A.hummer_RIA_conditional(cdf_grid, x_in)
+    cdf = np.concatenate([[0], np.cumsum(0.5 * (pdf[1:] + pdf[:-1]) * np.diff(cdf_grid))])
+    assert stats.kstest(xo, lambda t: np.interp(t, cdf_grid, cdf)).pvalue > 1e-4
+
+
+@pytest.mark.parametrize("x_in", [0.5, 1.5])
+def test_single_scatter_dipole_redistribution(orc, x_in):
+    xo, mu = orc.scatter_once(x_in, 1e-8, 1, 200000, seed=6)
+    g = np.linspace(-6, 6, 6001)
+    pdf = A.dipole_redistribution(g, x_in)
+    cdf = np.concatenate([[0], np.cumsum(0.5 * (pdf[1:] + pdf[:-1]) * np.diff(g))])
+    assert abs(cdf[-1] - 1) < 1e-6
+    assert stats.kstest(xo, lambda t: np.interp(t, g, cdf)).pvalue > 1e-4
+    assert abs(np.mean(mu ** 2) - 0.4) < 0.005
+
+
+def test_wing_scattering_restoring_drift(orc):
+    # far-wing scattering: <x_out - x_in> = -<u_par> = -1/x to leading order
+    x = 12.0
+    xo, _ = orc.scatter_once(x, 4.7e-4, 1, 400000, seed=8)
+    d = xo - x
+    assert abs(d.mean() + 1 / x) < 5 * d.std() / np.sqrt(d.size)
+
+
+# ----------------------------------------------------------- optical depth
+@pytest.mark.parametrize("x0,gam", [(0.3, 15.6), (-14.0, 15.6), (3.0, 0.5), (-40.0, 200.0)])
+def test_segment_tau_integral(orc, x0, gam):
+    """tau = kap0 int H(a, x0 - gam s) ds + kapd S (Eq. 4) against scipy quad on wofz."""
+    a, kap0, kapd, S = 4.7e-4, 1e3, 2.0, 0.1
+    ref = integrate.quad(lambda s: kap0 * A.voigt_scipy(a, x0 - gam * s) + kapd, 0, S,
+                         limit=500, epsrel=1e-12, points=[x0 / gam] if 0 < x0 / gam < S else None)[0]
+    tot, _ = orc.segment_tau(x0, gam, kap0, kapd, a, S)
+    assert abs(tot - ref) < 1e-9 * ref
+    # crossing point reproduces half of the total
+    _, s = orc.segment_tau(x0, gam, kap0, kapd, a, S, tau_rem=0.5 * ref)
+    half = integrate.quad(lambda t: kap0 * A.voigt_scipy(a, x0 - gam * t) + kapd, 0, s, limit=500,
+                          epsrel=1e-12)[0]
+    assert abs(half - 0.5 * ref) < 1e-8 * ref
+
+
+# ----------------------------------------------------------------- cell walk
+def test_dda_against_brute_force(orc):
+    rng = np.random.default_rng(0)
+    dims = np.array([5, 4, 6])
+    n = 300
+    org = rng.uniform(0, 1, (n, 3)) * dims
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    d = d.astype(np.float32)
+    cells, seg, cnt = orc.dda_trace(dims, org, d, 64)
+    for r in range(n):
+        dd = d[r].astype(np.float64)
+        # chord length to the box
+        t_exit = np.inf
+        for ax in range(3):
+            if dd[ax] > 0:
+                t_exit = min(t_exit, (dims[ax] - org[r, ax]) / dd[ax])
+            elif dd[ax] < 0:
+                t_exit = min(t_exit, -org[r, ax] / dd[ax])
+        assert abs(seg[r, :cnt[r]].sum() - t_exit) < 1e-12 * max(1, t_exit)
+        # distinct cells visited by dense sampling of the segment
+        ts = np.linspace(0, t_exit, 200001)[:-1] + 0.5 * t_exit / 200000
+        pts = org[r][None, :] + ts[:, None] * dd[None, :]
+        idx = np.floor(pts).astype(int)
+        lin = idx[:, 0] + dims[0] * (idx[:, 1] + dims[1] * idx[:, 2])
+        seq = lin[np.concatenate([[True], lin[1:] != lin[:-1]])]
+        got = cells[r, :cnt[r]]
+        got = got[seg[r, :cnt[r]] > 1e-4]  # skip corner grazes shorter than the sampling step
+        assert list(seq) == list(got)
+
+
+def test_dda_tie_break_and_faces(orc):
+    dims = [4, 4, 4]
+    # exact diagonal through a corner: x steps before y (lowest axis first)
+    o = np.array([[0.5, 0.5, 0.5]])
+    d = np.array([[np.sqrt(0.5), np.sqrt(0.5), 0.0]], dtype=np.float32)
+    cells, seg, cnt = orc.dda_trace(dims, o, d, 16)
+    lin = list(cells[0, :cnt[0]])
+    assert lin[:3] == [0, 1, 5]
+    # starting on a face and leaving through it starts in the lower cell
+    o = np.array([[2.0, 1.5, 1.5]])
+    d = np.array([[-1.0, 0.0, 0.0]], dtype=np.float32)
+    cells, seg, cnt = orc.dda_trace(dims, o, d, 16)
+    assert list(cells[0, :cnt[0]]) == [1 + 4 * (1 + 4 * 1), 0 + 4 * (1 + 4 * 1)]
+
+
+# ---------------------------------------------------------- transport pins
+def test_dust_only_escape_fraction(orc):
+    # no HI: f_esc = exp(-tau_d) exactly for a central source (Eq. 3)
+    n = 20000
+    r = orc.run_shell(tau0=0.0, T=1e4, R_in=0.5, tau_dust=0.7, n_photons=n, seed=3)
+    f = r["n_escaped"] / n
+    assert abs(f - np.exp(-0.7)) < 4 * np.sqrt(f * (1 - f) / n)
+    assert r["n_escaped"] + r["n_absorbed"] == n
+
+
+def test_optically_thin_direct_escape(orc):
+    # static sphere, source at line centre: P(no scattering) = exp(-tau0 H(a,0))
+    n, tau0 = 20000, 0.3
+    p = orc.line_params(1e4)
+    r = orc.run_shell(tau0=tau0, T=1e4, n_photons=n, seed=4, raw=True)
+    f = np.mean(r["nscat"] == 0)
+    e = np.exp(-tau0 * np.exp(p["a"] ** 2) * special.erfc(p["a"]))
+    assert abs(f - e) < 4 * np.sqrt(e * (1 - e) / n)
+    assert r["n_escaped"] == n
+
+
+def test_outflow_shell_first_flight(orc):
+    """Homologous outflow v = v_max r / R_out: a photon emitted radially at lab X sees
+    x(s) = (X - v_max r(s)/R_out)/v_th; P(no interaction) = exp(-tau_line(X))."""
+    n, T, vmax, Rin, tau0 = 20000, 1e4, 200.0, 0.9, 200.0
+    p = orc.line_params(T)
+    X0 = 190.0  # resonant inside the shell
+    r = orc.run_shell(tau0=tau0, T=T, R_in=Rin, v_max=vmax, X0=X0, n_photons=n, seed=5, raw=True)
+    f = np.mean(r["nscat"] == 0)
+    kap0 = tau0 / (1 - Rin)
+    xs = lambda rr: (X0 - vmax * rr) / p["vth_kms"]
+    tau = kap0 * integrate.quad(lambda rr: A.voigt_scipy(p["a"], xs(rr)), Rin, 1.0, limit=400,
+                                points=[X0 / vmax])[0]
+    e = np.exp(-tau)
+    assert abs(f - e) < 4 * np.sqrt(e * (1 - e) / n) + 1e-4
+    # inverted velocity sign would make the photon see x < -13 everywhere: tau ~ 0.01
+    assert tau > 1.0
+
+
+def test_static_sphere_symmetry_and_conservation(orc):
+    n = 4000
+    p = orc.line_params(1e4)
+    lim = 10 * p["vth_kms"]
+    r = orc.run_shell(tau0=1e3, T=1e4, n_photons=n, seed=6, n_bins=40, X_min=-lim, X_max=lim)
+    assert r["n_escaped"] == n
+    c = r["counts"].astype(float)
+    lhs, rhs = c[:20], c[20:][::-1]
+    chi2 = np.sum((lhs - rhs) ** 2 / np.maximum(lhs + rhs, 1)) / 20
+    assert chi2 < 2.5
+
+
+def _neufeld_check(orc, geometry, shape, n, seed):
+    """Static sphere / slab, T = 10 K, tau0 = 1e5 (a tau0 = 1.5e3), central source at
+    line centre, against the analytic spectrum valid for a tau0 >> 1 (Sec. 4; Neufeld
+    1990, Dijkstra et al. 2006).  At this a tau0 the analytic wings are known to be a
+    little too steep, so the pin is (i) the mean |x| / (a tau0)^(1/3) within 4 per cent
+    (a factor-2 error in the frequency redistribution moves it by ~25 per cent) and
+    (ii) chi^2 over the well-populated bins around the two peaks."""
+    T, tau0 = 10.0, 1e5
+    p = orc.line_params(T)
+    at = p["a"] * tau0
+    vt = p["vth_kms"]
+    r = orc.run_shell(tau0=tau0, T=T, geometry=geometry, n_photons=n, seed=seed, raw=True,
+                      n_bins=4, X_min=-1.0, X_max=1.0)
+    assert r["n_escaped"] == n
+    x = r["X"] / vt
+    s = at ** (1 / 3)
+    norm = integrate.quad(lambda t: shape(t, a_tau0=1.0), -8, 8, limit=200)[0]
+    mean_abs = integrate.quad(lambda t: abs(t) * shape(t, a_tau0=1.0), -8, 8, limit=200)[0] / norm
+    assert abs(np.mean(np.abs(x)) / s / mean_abs - 1) < 0.04
+    edges = np.linspace(-4 * s, 4 * s, 25)
+    c, _ = np.histogram(x, edges)
+    e = A.binned_expectation(shape, edges, c.sum(), a_tau0=at)
+    m = e > 50
+    chi2 = np.sum((c[m] - e[m]) ** 2 / e[m]) / m.sum()
+    assert chi2 < 3.0, chi2
+    # static medium: the spectrum is symmetric
+    assert abs(np.mean(x > 0) - 0.5) < 4 * 0.5 / np.sqrt(n)
+
+
+def test_neufeld_sphere_analytic(orc):
+    _neufeld_check(orc, "shell", A.neufeld_sphere_shape, 1000, 7)
+
+
+def test_neufeld_slab_analytic(orc):
+    _neufeld_check(orc, "slab", A.neufeld_slab_shape, 700, 8)
+
+
+def test_slab_dust_escape_fraction(orc):
+    """Dusty slab (Sec. 4, Laursen et al. 2009): f_esc(b), b = (a tau0)^(1/3) tau_a,
+    an approximation fitted to Monte Carlo runs; agreement within 15 per cent."""
+    T, tau0 = 20.0, 1e5
+    p = orc.line_params(T)
+    at = p["a"] * tau0
+    for tau_a, n in [(0.02, 600), (0.1, 600)]:
+        r = orc.run_shell(tau0=tau0, T=T, geometry="slab", tau_dust=tau_a, albedo=0.0, n_photons=n, seed=9)
+        f = r["n_escaped"] / n
+        e = A.laursen_fesc(at, tau_a)
+        assert abs(f / e - 1) < 0.15 + 3 * np.sqrt(f * (1 - f) / n) / e, (tau_a, f, e)
+
+
+# ------------------------------------------------------------------ peeling
+def _uniform_fields(n, nHI, kd, T=1e4):
+    shape = (n, n, n)
+    return {"n_HI": np.full(shape, nHI, np.float32), "T": np.full(shape, T, np.float32),
+            "vx": np.zeros(shape, np.float32), "vy": np.zeros(shape, np.float32),
+            "vz": np.zeros(shape, np.float32), "kd": np.full(shape, kd, np.float32)}
+
+
+def test_peel_empty_grid(orc):
+    # no gas: every photon escapes, each emission peel deposits exactly 1/(4 pi)
+    f = _uniform_fields(8, 0.0, 0.0)
+    f["n_HI"][...] = 0.0
+    # emission needs n_HI > 0 somewhere: give the gas no opacity through T-independent zero cross
+    f = _uniform_fields(8, 1e-30, 0.0)
+    n = 2000
+    r = orc.run_grid(f, cell_cm=3.086e20, n_photons=n, seed=1, n_bins=16, X_min=-200, X_max=200)
+    assert r["n_escaped"] == n and r["sum_scat"] == 0
+    assert abs(r["cube"].sum() - 3 * n / (4 * np.pi)) < 1e-9 * n
+
+
+def test_peel_dust_attenuation(orc):
+    # uniform absorbing dust, no HI opacity: E[exp(-k (L - z))] = (1 - exp(-k L)) / (k L)
+    L, n = 8, 6000
+    kcell = 0.25
+    cell_cm = 1.0
+    f = _uniform_fields(L, 1e-30, kcell / cell_cm)
+    r = orc.run_grid(f, cell_cm=cell_cm, n_photons=n, seed=2, albedo=0.0, n_bins=16, X_min=-200, X_max=200)
+    per_obs = r["cube"].sum(axis=(1, 2, 3)) * 4 * np.pi / n
+    e = (1 - np.exp(-kcell * L)) / (kcell * L)
+    assert np.all(np.abs(per_obs - e) < 0.02)
+    fesc = r["n_escaped"] / n
+    assert r["n_escaped"] + r["n_absorbed"] == n and 0.2 < fesc < 0.8
+
+
+# ------------------------------------------------------------------- forest
+def test_forest_column_against_scipy(orc):
+    rng = np.random.default_rng(4)
+    nz = 64
+    nHI = (1e-10 * np.exp(rng.normal(0, 1.5, (nz, 2, 2)))).astype(np.float32)
+    T = (1e4 * np.exp(rng.normal(0, 0.5, (nz, 2, 2)))).astype(np.float32)
+    v = rng.normal(0, 30, (nz, 2, 2)).astype(np.float32)
+    ds, dvc, nb = 3.03e22, 2.0, 128
+    tau = orc.forest(nHI, T, v, [1], [0], ds_cm=ds, dv_cell=dvc, n_bins=nb, dv_bin=1.0)[0]
+    ref = np.zeros(nb)
+    V = nz * dvc
+    vb = (np.arange(nb) + 0.5) * 1.0
+    for k in range(nz):
+        p = orc.line_params(float(T[k, 0, 1]))
+        vk = (k + 0.5) * dvc + float(v[k, 0, 1])
+        dv = vb - vk
+        dv -= V * np.floor(dv / V + 0.5)
+        ref += float(nHI[k, 0, 1]) * p["sigma0"] * ds * A.voigt_scipy(p["a"], dv / p["vth_kms"])
+    assert np.max(np.abs(tau - ref) / ref) < 1e-10
+
+
+def test_forest_line_integral_identity(orc):
+    # optically thin identity: sum_b tau_b dv = sum_k n sigma_0 ds b sqrt(pi) minus far wings
+    rng = np.random.default_rng(5)
+    nz, nb, dvc = 256, 512, 2.0
+    nHI = (1e-10 * np.exp(rng.normal(0, 1.0, (nz, 1, 1)))).astype(np.float32)
+    T = np.full((nz, 1, 1), 1e4, np.float32)
+    v = rng.normal(0, 30, (nz, 1, 1)).astype(np.float32)
+    ds = 3.03e22
+    tau = orc.forest(nHI, T, v, [0], [0], ds_cm=ds, dv_cell=dvc, n_bins=nb, dv_bin=1.0)[0]
+    p = orc.line_params(1e4)
+    V = nz * dvc
+    b, a = p["vth_kms"], p["a"]
+    x_edge = V / 2 / b
+    per = b * (np.sqrt(np.pi) - 2 * a / np.sqrt(np.pi) / x_edge)
+    expect = np.sum(nHI.astype(float)) * p["sigma0"] * ds * per
+    assert abs(tau.sum() * 1.0 / expect - 1) < 2e-4
