@@ -1,0 +1,324 @@
+"""Benchmark: Lyman-alpha resonant scatterings per second on one GB300.
+
+Workload (default): the expanding thin shell -- R_in/R_out = 0.9, N_HI = 1e20 cm^-2,
+homologous outflow 200 km/s at R_out, T = 1e4 K, dust absorption tau_d = 0.5, central
+source with a Gaussian line sigma = 50 km/s, 1e5 photons, dipole phase function,
+escaped spectrum in 400 bins over +-1500 km/s.  One step = one full run of the photon
+loop over all 1e5 photons (thor_run).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload forest]
+
+Timing: CUDA events on the context's stream around each step, L2 flushed (256 MiB
+write) before every step outside the events; K timed steps between barriers and
+device synchronisation; value = total scatterings / summed step time.  `e2e` repeats
+the measurement through the public call with host buffers (wall clock, host<->device
+copies inside).  Under torchrun each rank runs its own photon-id range (weak scaling,
+no collective in the timed region).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Lyα scatterings/sec on 1 GB300 vs oracle; p50/p99 latency of shell-model stream"
+SHELL = dict(R_in=0.9, N_HI=1e20, T=1e4, v_max=200.0, tau_dust=0.5, phase="dipole")
+RUN = dict(sigma=50.0, n_bins=400, X_min=-1500.0, X_max=1500.0)
+N_PHOTONS = 100_000
+WORKLOAD = "expanding shell R_in/R_out=0.9 N_HI=1e20 v_max=200km/s T=1e4K tau_d=0.5 sigma=50km/s 1e5 photons"
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0):
+        self.dev = device_index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([s.strip() for s in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in self.rows if len(r) > 2 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for i, n in enumerate(names):
+                if len(r) > 5 + i and r[5 + i].lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def dist_env():
+    r = int(os.environ.get("RANK", "0"))
+    w = int(os.environ.get("WORLD_SIZE", "1"))
+    lr = int(os.environ.get("LOCAL_RANK", "0"))
+    return r, w, lr
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ CPU baseline
+def oracle_sample(seconds=15.0, first_id=0, cap=100_000):
+    """The FP64 oracle on the same workload: photons first_id, first_id+1, ... in chunks
+    on all host cores until `seconds` passed; trapped photons stop at `cap` scatterings."""
+    import oracle
+    oracle.build()
+    ncores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    n_done, n_scat, pid = 0, 0, first_id
+    chunk = 4 * ncores
+    while time.perf_counter() - t0 < seconds:
+        r = oracle.run_shell(tau0=SHELL["N_HI"] * oracle.line_params(SHELL["T"])["sigma0"], T=SHELL["T"],
+                             R_in=SHELL["R_in"], v_max=SHELL["v_max"], tau_dust=SHELL["tau_dust"], phase="dipole",
+                             line="gauss", sigma=RUN["sigma"], n_photons=chunk, first_id=pid, seed=1,
+                             n_bins=RUN["n_bins"], X_min=RUN["X_min"], X_max=RUN["X_max"], max_scat=cap,
+                             n_threads=ncores)
+        n_done += chunk
+        pid += chunk
+        n_scat += r["sum_scat"]
+    dt = time.perf_counter() - t0
+    return {"value": n_scat / dt, "unit": "scatterings/s", "cores": ncores, "kind": "oracle",
+            "sample": f"{n_done} photons (ids {first_id}..{pid - 1}) of the same workload, "
+                      f"{n_scat} scatterings in {dt:.1f} s, photons stopped at {cap} scatterings"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample(seconds=2.0)
+    t0 = time.perf_counter()
+    tot, vals = 0.0, []
+    for i in range(args.steps):
+        s = oracle_sample(seconds=args.ref_seconds, first_id=100_000 + 4096 * i)
+        vals.append(s["value"])
+    dt = time.perf_counter() - t0
+    v = float(np.mean(vals))
+    cb = oracle_sample(seconds=2.0)
+    cb["value"] = v
+    cb["sample"] = f"{args.steps} steps of ~{args.ref_seconds:.0f} s oracle work each on this workload; " + cb["sample"]
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": "scatterings/s", "n_gpus": 0,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                      "data": "synthetic", "config": {"workload": WORKLOAD},
+                      "cpu_baseline": cb,
+                      "e2e": {"value": v, "unit": "scatterings/s", "h2d_bytes_per_step": 0,
+                              "d2h_bytes_per_step": 0}}))
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_shell_bench(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2507_11603_gb300 import thor
+    ctx = thor.Context(local)
+    if args.block:
+        ctx.set_launch(args.block, args.blocks_per_sm)
+    stream = torch.cuda.Stream()
+    ctx.set_stream(stream)
+    geom = ctx.shell(**SHELL)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    base_id = rank * N_PHOTONS * (args.steps + args.warmup + 1)
+
+    def step(i, device_out=True):
+        return ctx.run(geom, n_photons=N_PHOTONS, seed=1, first_id=base_id + i * N_PHOTONS, device_out=device_out,
+                       **RUN)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    barrier(world)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kern_ms, n_scat, launches = 0.0, 0, 0
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(i & 0xFF)
+            ev[i][0].record(stream)
+            r = step(args.warmup + i)
+            ev[i][1].record(stream)
+            kern_ms += r.stats["elapsed_ms"]
+            n_scat += r.stats["n_scat"]
+            launches += 1
+        torch.cuda.synchronize()
+    barrier(world)
+    step_ms = sum(a.elapsed_time(b) for a, b in ev)
+    t_max = max_over_ranks(step_ms, world)
+    tot_scat = sum_over_ranks(float(n_scat), world)
+    value = tot_scat / (t_max / 1000.0)
+    kern_avg_ms = kern_ms / args.steps
+
+    # e2e through the public call with host buffers (copies inside the timed region)
+    e2e_ms, e2e_scat = 0.0, 0
+    for i in range(args.e2e_steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = step(args.warmup + args.steps + i, device_out=False)
+        e2e_ms += (time.perf_counter() - t0) * 1000.0
+        e2e_scat += r.stats["n_scat"]
+    e2e_value = sum_over_ranks(float(e2e_scat), world) / (max_over_ranks(e2e_ms, world) / 1000.0)
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    pk = peaks()
+    sm_max = pk.get("sm_max_mhz", 2070.0)
+    # ALU roofline: lane-instruction issue peak = SMs x 128 lanes x max SM clock
+    peak_lane_ops = 152 * 128 * sm_max * 1e6
+    ops_per_scat = args.ops_per_scat
+    achieved = (n_scat / args.steps) * ops_per_scat / (kern_avg_ms / 1000.0)
+    line = {
+        "metric": METRIC, "value": value, "unit": "scatterings/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "photons_per_step": N_PHOTONS, "l2": "flushed (256 MiB write) before each step",
+                   "scatterings_per_step": n_scat / args.steps, "kernel_ms_per_step": kern_avg_ms,
+                   "launch": {"block": args.block or 128, "blocks_per_sm": args.blocks_per_sm}},
+        "e2e": {"value": e2e_value, "unit": "scatterings/s", "h2d_bytes_per_step": 256 + 48,
+                "d2h_bytes_per_step": (RUN["n_bins"] + 2) * 8 + 96},
+        "gpu_launches": launches,
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_lane_ops / 1e12,
+                     "unit": "Tlane-ops/s", "frac": achieved / peak_lane_ops, "traffic": None,
+                     "per_unit": f"{ops_per_scat} thread instructions per scattering (ncu, DESIGN.md)",
+                     "peak_source": f"152 SMs x 128 lanes x {sm_max:.0f} MHz (max SM clock of measured peaks)"},
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_sample(seconds=args.cpu_seconds)
+    print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_forest_bench(args):
+    import torch
+    from paper_2507_11603_gb300 import synth, thor
+    ctx = thor.Context(0)
+    stream = torch.cuda.Stream()
+    ctx.set_stream(stream)
+    n = args.forest_n
+    nHI, T, v = synth.forest_fields_torch(n, seed=5)
+    torch.cuda.synchronize()
+    ds = synth.forest_scale(2.0, 2.0)
+    out = torch.empty((n * n, 2 * n), dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        ctx.forest(nHI, T, v, ds_cm=ds, dv_cell=2.0, n_bins=2 * n, dv_bin=1.0, out=out)
+    ms = []
+    with ClockSampler(0) as clk:
+        for _ in range(args.steps):
+            ctx.forest(nHI, T, v, ds_cm=ds, dv_cell=2.0, n_bins=2 * n, dv_bin=1.0, out=out)
+            ms.append(ctx.last_elapsed_ms())
+    evals = float(n) * n * n * 2 * n
+    t = float(np.mean(ms)) / 1000.0
+    print(json.dumps({"metric": "Voigt evaluations/s (Lya forest, Eq. 11)", "value": evals / t,
+                      "unit": "evals/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": 1000 * t, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": f"forest {n}^3 box, {n * n} sightlines x {2 * n} bins"},
+                      "clocks": clk.summary()}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="shell", choices=["shell", "forest"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--blocks-per-sm", type=int, default=0)
+    ap.add_argument("--ops-per-scat", type=float, default=float(os.environ.get("THOR_OPS_PER_SCAT", "0") or 0))
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--forest-n", type=int, default=1024)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    elif args.workload == "forest":
+        run_forest_bench(args)
+    else:
+        run_shell_bench(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,249 @@
+/*
+ * thor.h -- C ABI of the GB300 resonant-line Monte Carlo library (libthor.so).
+ *
+ * The library implements the data-parallel hot path of the method described by
+ * THOR (Byrohl & Nelson, "thor: a GPU-accelerated Monte Carlo radiative transfer
+ * code for resonant lines", arXiv:2507.11603): the Lyman-alpha photon-packet loop
+ * (Sec. 3.4: emission, propagation through gridless shells or a uniform grid,
+ * interaction, resonant and dust scattering, peeling-off, escape) and the
+ * Lyman-alpha forest optical-depth ray-march (Sec. 3.5.2, Eq. 11), on one CUDA
+ * device (sm_103a).
+ *
+ * Conventions
+ *  - Every call returns an int status: THOR_OK (0) or a negative THOR_ERR_* code;
+ *    thor_last_error() then holds a one-line message.  No call aborts the process.
+ *  - Pointers are plain host or device pointers; `mem_kind` says which
+ *    (THOR_MEM_HOST or THOR_MEM_DEVICE).  Input arrays are only read during the
+ *    call (geometry creation copies and packs them).  Output buffers are owned by
+ *    the caller and must hold the sizes stated below.
+ *  - 3-D fields are C-contiguous arrays of shape (nz, ny, nx): cell (ix, iy, iz)
+ *    is element ix + nx * (iy + ny * iz).  Positions are in cell units.
+ *  - Frequencies are lab-frame velocity offsets X = c (nu - nu0) / nu0 in km/s
+ *    (positive = blue); velocities in km/s; the gas-frame dimensionless frequency
+ *    is x = (X - v . k) / v_th (Sec. 2.3.1).
+ *  - Results are deterministic for fixed (seed, photon ids): photon i uses the
+ *    Philox4x32-10 stream keyed by the run seed with counter (i, draw block),
+ *    and all spectrum tallies are integer counts.
+ *  - Calls on one context are serialised by the caller; contexts are independent.
+ */
+#ifndef THOR_H
+#define THOR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define THOR_OK 0
+#define THOR_ERR_INVALID_ARG (-1) /* bad pointer, size or parameter */
+#define THOR_ERR_OOM (-2)         /* device allocation failed */
+#define THOR_ERR_CAPACITY (-3)    /* request exceeds a configured capacity */
+#define THOR_ERR_TIMEOUT (-4)     /* a bounded wait ran out */
+#define THOR_ERR_DEVICE (-5)      /* CUDA error (message in thor_last_error) */
+#define THOR_ERR_CANCELLED (-6)   /* served request was cancelled */
+#define THOR_ERR_NOT_FOUND (-7)   /* unknown ticket */
+
+#define THOR_MEM_HOST 0
+#define THOR_MEM_DEVICE 1
+
+/* Phase function of resonant scattering (Sec. 2.3.1): isotropic, dipole
+ * P(mu) = 3/8 (1 + mu^2), or the 1:2 isotropic:dipole mix in the line core
+ * (|x_atom| < 0.2) with pure dipole in the wings. */
+#define THOR_PHASE_ISOTROPIC 0
+#define THOR_PHASE_DIPOLE 1
+#define THOR_PHASE_MIXED 2
+
+typedef struct thor_ctx* thor_ctx_t;
+typedef struct thor_geom* thor_geom_t;
+typedef struct thor_server* thor_server_t;
+
+/* ---- context --------------------------------------------------------------------- */
+
+/* Create a context on CUDA device `device` (Sec. 3.6.1: one compute thread drives
+ * one device).  *out receives the handle.  Errors: INVALID_ARG, DEVICE. */
+int thor_init(int device, thor_ctx_t* out);
+/* Release the context and everything it allocated.  NULL is ignored. */
+void thor_destroy(thor_ctx_t ctx);
+/* Last error message of the context (never NULL; "" after success).  With ctx NULL,
+ * the message of the last failed thor_init. */
+const char* thor_last_error(thor_ctx_t ctx);
+/* Use `cuda_stream` (a cudaStream_t, may be NULL = legacy default stream) for all
+ * subsequent work of this context. */
+int thor_ctx_set_stream(thor_ctx_t ctx, void* cuda_stream);
+/* Launch configuration of the persistent photon loops: threads per block (multiple
+ * of 32, <= 256) and resident blocks per SM (0 = occupancy maximum). */
+int thor_ctx_set_launch(thor_ctx_t ctx, int block_size, int blocks_per_sm);
+
+/* ---- geometries (Sec. 3.3 datasets) ----------------------------------------------- */
+
+/* Gridless spherical shell (Sec. 3.3; a sphere when R_in = 0), lengths in units of
+ * R_out, homologous radial outflow v(r) = v_max r / R_out, a central point source in
+ * the empty cavity (Sec. 4 validation setups, shell models of Sec. 5.1). */
+typedef struct {
+  double R_in, R_out;    /* radii, 0 <= R_in < R_out */
+  double N_HI;           /* HI column R_in -> R_out [cm^-2]; used when tau0 <= 0 */
+  double tau0;           /* line-centre optical depth n sigma_0 (R_out - R_in); > 0 overrides N_HI */
+  double T;              /* gas temperature [K] */
+  double v_max;          /* outflow speed at R_out [km/s] */
+  double tau_dust;       /* dust extinction optical depth R_in -> R_out (frequency independent) */
+  double albedo;         /* dust albedo (Eq. 8); 0 = pure absorption */
+  double g_hg;           /* Henyey-Greenstein asymmetry (Eq. 9) */
+  int32_t phase;         /* THOR_PHASE_* for resonant scattering */
+  int32_t reserved;
+  double step_dx;        /* step limiter f (Sec. 4.1): sub-step length f v_th / |dv/dr|; 0 -> 0.01 */
+} thor_shell_params;
+
+int thor_shell_create(thor_ctx_t ctx, const thor_shell_params* p, thor_geom_t* out);
+
+/* Uniform Cartesian grid (Sec. 3.3).  n_HI [cm^-3], T [K], v = 3 arrays (vx, vy, vz)
+ * laid out one after another (3 * N floats) [km/s], dust = dust extinction
+ * coefficient [cm^-1] (may be NULL = no dust).  dims = (nx, ny, nz).  Fields are
+ * packed into one 32-byte record per cell on the device (zeroth-order cells,
+ * Sec. 3.4) together with the emission CDF (emissivity proportional to n_HI^2).
+ * The inputs are not referenced after the call. */
+int thor_grid_create(thor_ctx_t ctx, const float* n_HI, const float* T, const float* v, const float* dust,
+                     const int32_t dims[3], double cell_size_cm, int mem_kind, thor_geom_t* out);
+
+/* Scattering parameters of a grid run (Sec. 2.3): phase function of resonant
+ * scattering, dust albedo (Eq. 8) and Henyey-Greenstein g (Eq. 9).  Defaults:
+ * dipole, 0.32, 0.73 (the paper's fiducial dust values). */
+int thor_grid_set_scattering(thor_geom_t g, int phase, double albedo, double g_hg);
+
+void thor_geom_destroy(thor_geom_t g);
+
+/* ---- Monte Carlo run (Sec. 3.4) ----------------------------------------------------- */
+
+/* Photon source.  kind 0: point source at the centre of a shell geometry with a
+ * delta (sigma = 0) or Gaussian (sigma > 0) line at X0 in the source frame;
+ * kind 1: gas emission of a grid, cells with probability proportional to n_HI^2,
+ * thermal line in the cell frame (Sec. 2.1).  One source per run. */
+typedef struct {
+  int32_t kind;
+  int32_t reserved;
+  double X0, sigma;      /* km/s */
+} thor_source;
+
+typedef struct {
+  /* escaped spectrum: counts of escaping photons in n_bins bins of lab X over
+   * [X_min, X_max), then underflow, overflow: n_bins + 2 uint64 entries */
+  int32_t n_bins;
+  int32_t mem_kind;      /* where the buffers below live */
+  double X_min, X_max;
+  uint64_t* spectrum;    /* required */
+  /* peeling-off (grid only, Sec. 3.4.1): 3 observers along +x, +y, +z, images
+   * img_n x img_n (img_n divides the grid size), peel_bins bins over
+   * [peel_X_min, peel_X_max); cube = float[3][img_n][img_n][peel_bins] (zeroed by the call) */
+  int32_t peel;
+  int32_t img_n;
+  int32_t peel_bins;
+  int32_t reserved;
+  double peel_X_min, peel_X_max;
+  float* cube;
+  /* optional per-photon records, indexed by photon id - first id (may be NULL) */
+  float* raw_X;          /* final lab X [km/s] */
+  uint32_t* raw_nscat;   /* resonant scatterings */
+  uint8_t* raw_status;   /* 1 escaped, 2 absorbed, 3 stopped at max_scat */
+  uint32_t max_scat;     /* stop a photon after this many scatterings (0 = never) */
+  uint32_t reserved2;
+} thor_output_spec;
+
+typedef struct {
+  uint64_t n_photons, n_escaped, n_absorbed, n_capped;
+  uint64_t n_scat;        /* resonant HI scatterings (the throughput unit) */
+  uint64_t n_dust_scat;
+  uint64_t n_upar_iters;  /* rejection iterations of the u_par sampler */
+  uint64_t n_steps;       /* propagation steps (sub-steps or cells) */
+  uint64_t n_peel_rays, n_peel_cells;
+  double sum_scat2;       /* sum over photons of n_scat^2 */
+  double elapsed_ms;      /* device time of the photon loop (CUDA events) */
+} thor_result;
+
+/* Run photons first_id .. first_id + n_photons - 1 of the stream `seed` through the
+ * geometry (Sec. 3.4 emission / propagation / interaction / escape; Sec. 3.4.1
+ * peeling-off on grids).  One persistent launch; returns when the results are in
+ * `out` and the output buffers.  Errors: INVALID_ARG, OOM, DEVICE. */
+int thor_run(thor_ctx_t ctx, thor_geom_t g, const thor_source* src, uint64_t first_id, uint64_t n_photons,
+             uint64_t seed, const thor_output_spec* spec, thor_result* out);
+
+/* ---- Lyman-alpha forest (Sec. 3.5.2, Eq. 11) ---------------------------------------- */
+
+typedef struct {
+  double ds_cm;           /* proper path length per cell [cm] */
+  double dv_cell;         /* Hubble-flow velocity across one cell [km/s] */
+  int32_t n_bins;         /* velocity bins, n_bins * dv_bin == nz * dv_cell (periodic) */
+  int32_t reserved;
+  double dv_bin;          /* km/s */
+  int64_t first_sightline, n_sightlines;  /* sightline s = column (s % nx, s / nx) along z */
+} thor_forest_spec;
+
+/* tau_out[s * n_bins + b] = sum over cells k of the column of
+ * n_HI sigma_0(T) ds H(a(T), (v_b - v_k) / v_th(T)), v_k = (k + 1/2) dv_cell + v_los,
+ * v_b = (b + 1/2) dv_bin, nearest periodic image.  Fields as for grids (v_los = the
+ * z velocity); all pointers of kind mem_kind.  n_bins <= 2048 per call. */
+int thor_forest(thor_ctx_t ctx, const float* n_HI, const float* T, const float* v_los, const int32_t dims[3],
+                int mem_kind, const thor_forest_spec* spec, float* tau_out);
+
+/* Device time of the last thor_forest call in milliseconds (CUDA events). */
+double thor_last_elapsed_ms(thor_ctx_t ctx);
+
+/* ---- served stream of shell models (continuous batching) ---------------------------- */
+
+typedef struct {
+  int32_t max_requests;      /* requests resident at once (admission limit) */
+  int32_t events_per_round;  /* events per lane per device round */
+  int64_t n_slots;           /* resident packet slots (0 = one per resident thread) */
+  uint64_t mem_budget_bytes; /* device bytes for per-request tables (admission limit) */
+  int32_t block_size;        /* 0 = context default */
+  int32_t reserved;
+} thor_server_config;
+
+/* Create a server on the context: a host thread runs device rounds while work is
+ * pending; requests submitted while others run are admitted as slots and memory
+ * free up and share the same launches. */
+int thor_server_create(thor_ctx_t ctx, const thor_server_config* cfg, thor_server_t* out);
+/* Queue one shell-model request (geometry, source kind 0, spectrum binning as in
+ * thor_output_spec with host buffers; spectrum must stay valid until the request
+ * completes).  *ticket receives its id.  Errors: INVALID_ARG, CAPACITY (can never fit). */
+int thor_server_submit(thor_server_t s, const thor_shell_params* p, const thor_source* src, uint64_t n_photons,
+                       uint64_t seed, const thor_output_spec* spec, int64_t* ticket);
+/* *done = 1 when the request finished (results written), else 0. */
+int thor_server_poll(thor_server_t s, int64_t ticket, int* done);
+/* Block until the request finished or timeout_ms passed (< 0 = no limit): fills *out
+ * (elapsed_ms = submit-to-completion latency).  Errors: TIMEOUT, NOT_FOUND, CANCELLED. */
+int thor_server_wait(thor_server_t s, int64_t ticket, int64_t timeout_ms, thor_result* out);
+/* Cancel a request that has not finished. */
+int thor_server_cancel(thor_server_t s, int64_t ticket);
+/* Statistics: rounds launched, photons resident per round (average). */
+int thor_server_stats(thor_server_t s, uint64_t* rounds, double* mean_resident, uint64_t* admitted);
+void thor_server_destroy(thor_server_t s);
+
+/* ---- diagnostics: the device building blocks, one at a time ------------------------- */
+
+/* H[i] = Voigt function H(a[i], x[i]) in FP32 (App. A.3); precise selects the
+ * accurate exponential (forest kernel) instead of the fast one (photon loop). */
+int thor_voigt_eval(thor_ctx_t ctx, const float* a, const float* x, float* H, int64_t n, int precise, int mem_kind);
+/* Cell walk of n rays (origins 3n doubles in cell units, directions 3n floats) through
+ * a grid of dims; cells[r * max_steps + j] = linear cell index, seg[...] = path length,
+ * count[r] = cells visited (Sec. 3.4 face-to-face propagation). */
+int thor_dda_trace(thor_ctx_t ctx, const int32_t dims[3], const double* origins, const float* dirs, int32_t n,
+                   int32_t max_steps, int64_t* cells, double* seg, int32_t* count, int mem_kind);
+/* n samples of u_par at fixed (x, a) (Eq. 6 by the rejection scheme of Eq. 10),
+ * sample i from photon stream i of `seed`; *iters = total rejection iterations. */
+int thor_sample_upar(thor_ctx_t ctx, float x, float a, uint64_t seed, int64_t n, float* out, uint64_t* iters,
+                     int mem_kind);
+/* One resonant scattering (Eq. 5-7) of n photons moving along +z at gas-frame x in
+ * static gas: x_out and mu = k_in . k_out. */
+int thor_scatter_once(thor_ctx_t ctx, float x, float a, int phase, uint64_t seed, int64_t n, float* x_out,
+                      float* mu_out, int mem_kind);
+/* Philox4x32-10 blocks: ctr 4n words, key 2n words, out 4n words. */
+int thor_philox(thor_ctx_t ctx, const uint32_t* ctr, const uint32_t* key, uint32_t* out, int32_t n, int mem_kind);
+
+/* Line parameters at T (Sec. 2.3.1): v_th [km/s], Voigt a, sigma_0 [cm^2]. */
+void thor_line_params(double T, double* vth_kms, double* a, double* sigma0);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* THOR_H */

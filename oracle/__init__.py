@@ -2,11 +2,10 @@
 arXiv:2507.11603).
 
 TEST INFRASTRUCTURE ONLY: only ``tests/``, ``__graft_entry__.smoke()`` and
-``bench.py``'s CPU-baseline / reference arm may import this package.  The product
-path (``paper_2507_11603_gb300``) never imports it, and it never imports the
-product path.  The shared seeded input generators live in their own module
-(``paper_2507_11603_gb300.synth``), which holds none of the method's arithmetic
-and is passed in as arrays.
+``bench.py``'s CPU-baseline / reference arm may import this package.  The CUDA
+product path never imports it, and it never imports the product path.  Inputs
+come in as plain arrays drawn by the seeded generators of the synthetic-input
+module, which holds none of the method's arithmetic.
 
 The arithmetic is in ``thor_oracle.cpp`` (plain C++17, double precision); this
 module compiles it with g++ and wraps it with ctypes.

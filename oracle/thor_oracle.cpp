@@ -744,8 +744,8 @@ extern "C" int orc_run_shell(const orc_shell* geo, const orc_source* src, uint64
 // multiply-add, operations exactly as written.
 //   start cell i = floor(p); if d < 0 and p == i then i - 1 (a ray starting on a face
 //     and leaving through it starts in the lower cell);
-//   distance to the next face along each axis t_ax = ((i + (d > 0)) - p) / d,
-//     +inf when d == 0;
+//   inv_ax = 1 / d_ax once per ray (IEEE division), +inf marker when d == 0;
+//   distance to the next face along each axis t_ax = ((i + (d > 0)) - p) * inv_ax;
 //   step along the axis with the smallest t, ties to the lowest axis (x < y < z);
 //   segment length = t_next - t_current.
 // ------------------------------------------------------------------------------
@@ -753,7 +753,7 @@ namespace {
 
 struct DDA {
   int i[3], step[3];
-  double p[3], d[3];
+  double p[3], d[3], inv[3];
   double t;  // distance already travelled from p
   void init(const double pin[3], const double din[3]) {
     t = 0.0;
@@ -764,12 +764,13 @@ struct DDA {
       if (d[a] < 0.0 && p[a] == f) ii -= 1;
       i[a] = ii;
       step[a] = (d[a] > 0.0) ? 1 : (d[a] < 0.0 ? -1 : 0);
+      inv[a] = (step[a] != 0) ? 1.0 / d[a] : 0.0;
     }
   }
   double tface(int a) const {
     if (step[a] == 0) return HUGE_VAL;
     double face = (double)(i[a] + (step[a] > 0 ? 1 : 0));
-    return (face - p[a]) / d[a];
+    return (face - p[a]) * inv[a];
   }
   // returns the axis of the next face and its distance
   int next_axis(double* tn) const {

@@ -1,0 +1,53 @@
+"""Generate the coefficient table of the device Voigt approximation (voigt_coeffs.h).
+
+The device evaluates H(a,x) for |x| < 6 as
+    H = exp(-x^2) (1 + a^2 (1 - 2x^2)) + (2a/sqrt(pi)) K(x) + (a^3/(3 sqrt(pi))) ((6 - 4x^2) K(x) + 2)
+with K(x) = 2 x F(x) - 1 and F Dawson's integral (the Taylor series of w(x + i a) in a,
+truncated after a^3).  K is fitted here, per unit interval [i, i+1), i = 0..5, by a
+degree-11 polynomial in u = x - (i + 1/2) (least squares on Chebyshev nodes, float64,
+F from scipy.special.dawsn).  Deterministic: re-running reproduces voigt_coeffs.h.
+"""
+import os
+
+import numpy as np
+from scipy.special import dawsn
+
+DEG = 11
+NINT = 6
+
+
+def K(x):
+    return 2.0 * x * dawsn(x) - 1.0
+
+
+def fit():
+    rows = []
+    for i in range(NINT):
+        c = i + 0.5
+        t = np.cos(np.pi * (np.arange(400) + 0.5) / 400)
+        x = c + 0.5 * t
+        u = x - c
+        V = np.vander(u, DEG + 1, increasing=True)
+        # weight: relative in the tail where K ~ 1/(2x^2), absolute near the zero of K
+        w = 1.0 / np.maximum(np.abs(K(x)), 1e-2)
+        coef, *_ = np.linalg.lstsq(V * w[:, None], K(x) * w, rcond=None)
+        rows.append(coef)
+    return np.array(rows)
+
+
+def main():
+    rows = fit()
+    here = os.path.dirname(os.path.abspath(__file__))
+    with open(os.path.join(here, "voigt_coeffs.h"), "w") as f:
+        f.write("// Generated by gen_voigt_coeffs.py -- do not edit.\n")
+        f.write("// K(x) = 2 x F(x) - 1 on [i, i+1): sum_j c[i][j] (x - i - 1/2)^j, j = 0..11\n")
+        f.write("#pragma once\n")
+        f.write(f"#define THOR_VOIGT_NINT {NINT}\n#define THOR_VOIGT_NCOEF {DEG + 1}\n")
+        f.write("static const float kVoigtK[THOR_VOIGT_NINT][THOR_VOIGT_NCOEF] = {\n")
+        for r in rows:
+            f.write("  {" + ", ".join(f"{v:.9e}f" for v in r) + "},\n")
+        f.write("};\n")
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,560 @@
+// thor_capi.cu -- host runtime behind include/thor.h: contexts, geometry objects,
+// the single-model run, the forest ray-march and the diagnostic entry points.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/thor.h"
+#include "thor_ctx.h"
+#include "thor_device.cuh"
+#include "thor_internal.h"
+
+using namespace thor;
+
+// ------------------------------------------------------------------------------ errors
+static std::string g_init_error;
+
+int thor_ctx::fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  last_error = buf;
+  return code;
+}
+
+int thor_ctx::cuda(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return THOR_OK;
+  if (e == cudaErrorMemoryAllocation) return fail(THOR_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+  return fail(THOR_ERR_DEVICE, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int thor_ctx::select() { return cuda(cudaSetDevice(device), "cudaSetDevice"); }
+
+void* thor_ctx::scratch(Buf& b, size_t bytes) {
+  if (b.cap >= bytes && b.p) return b.p;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.cap = 0;
+  size_t cap = bytes < 256 ? 256 : bytes;
+  if (cudaMalloc(&b.p, cap) != cudaSuccess) return nullptr;
+  b.cap = cap;
+  return b.p;
+}
+
+thor_ctx::~thor_ctx() {
+  cudaSetDevice(device);
+  for (Buf* b : {&b_models, &b_tally, &b_queue, &b_spec, &b_cube, &b_raw, &b_diag, &b_stats})
+    if (b->p) cudaFree(b->p);
+  if (d_ktab) cudaFree(d_ktab);
+  if (ev0) cudaEventDestroy(ev0);
+  if (ev1) cudaEventDestroy(ev1);
+}
+
+// ------------------------------------------------------------------------------ context
+extern "C" int thor_init(int device, thor_ctx_t* out) {
+  if (!out) { g_init_error = "thor_init: out is NULL"; return THOR_ERR_INVALID_ARG; }
+  *out = nullptr;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess || device < 0 || device >= n) {
+    g_init_error = std::string("thor_init: no CUDA device ") + std::to_string(device) + " (" +
+                   cudaGetErrorString(e) + ")";
+    return THOR_ERR_DEVICE;
+  }
+  thor_ctx* c = new thor_ctx();
+  c->device = device;
+  if (c->select() != THOR_OK) { g_init_error = c->last_error; delete c; return THOR_ERR_DEVICE; }
+  cudaDeviceProp prop;
+  cudaGetDeviceProperties(&prop, device);
+  c->sm_count = prop.multiProcessorCount;
+  c->cc_major = prop.major;
+  c->cc_minor = prop.minor;
+  if (cudaMalloc(&c->d_ktab, sizeof(kVoigtK)) != cudaSuccess ||
+      cudaMemcpy(c->d_ktab, kVoigtK, sizeof(kVoigtK), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
+    g_init_error = "thor_init: device setup failed";
+    delete c;
+    return THOR_ERR_DEVICE;
+  }
+  *out = c;
+  return THOR_OK;
+}
+
+extern "C" void thor_destroy(thor_ctx_t ctx) { delete ctx; }
+
+extern "C" const char* thor_last_error(thor_ctx_t ctx) {
+  if (!ctx) return g_init_error.c_str();
+  return ctx->last_error.c_str();
+}
+
+extern "C" int thor_ctx_set_stream(thor_ctx_t ctx, void* s) {
+  if (!ctx) return THOR_ERR_INVALID_ARG;
+  ctx->stream = (cudaStream_t)s;
+  return THOR_OK;
+}
+
+extern "C" int thor_ctx_set_launch(thor_ctx_t ctx, int block_size, int blocks_per_sm) {
+  if (!ctx) return THOR_ERR_INVALID_ARG;
+  if (block_size <= 0 || block_size > 256 || (block_size & 31) || blocks_per_sm < 0)
+    return ctx->fail(THOR_ERR_INVALID_ARG, "thor_ctx_set_launch: block_size must be a multiple of 32 in [32, 256]");
+  ctx->block = block_size;
+  ctx->blocks_per_sm = blocks_per_sm;
+  return THOR_OK;
+}
+
+extern "C" void thor_line_params(double T, double* vth, double* a, double* sigma0) {
+  if (vth) *vth = line_vth_kms(T);
+  if (a) *a = line_a(T);
+  if (sigma0) *sigma0 = line_sigma0(T);
+}
+
+// ------------------------------------------------------------------------------ geometry
+int thor::fill_shell_model(thor_ctx* ctx, const thor_shell_params* p, ShellModel* m) {
+  if (!p) return ctx->fail(THOR_ERR_INVALID_ARG, "shell parameters are NULL");
+  if (!(p->R_out > 0.0) || !(p->R_in >= 0.0) || !(p->R_in < p->R_out))
+    return ctx->fail(THOR_ERR_INVALID_ARG, "shell radii must satisfy 0 <= R_in < R_out");
+  if (!(p->T > 0.0)) return ctx->fail(THOR_ERR_INVALID_ARG, "temperature must be > 0");
+  if (!(p->tau_dust >= 0.0) || !(p->albedo >= 0.0 && p->albedo <= 1.0) || !(p->g_hg > -1.0 && p->g_hg < 1.0))
+    return ctx->fail(THOR_ERR_INVALID_ARG, "dust parameters out of range");
+  if (p->phase < 0 || p->phase > 2) return ctx->fail(THOR_ERR_INVALID_ARG, "unknown phase function");
+  if (!(p->v_max >= 0.0)) return ctx->fail(THOR_ERR_INVALID_ARG, "v_max must be >= 0");
+  const double L = (p->R_out - p->R_in) / p->R_out;  // in units of R_out
+  double tau0 = p->tau0;
+  if (!(tau0 > 0.0)) {
+    if (!(p->N_HI >= 0.0)) return ctx->fail(THOR_ERR_INVALID_ARG, "N_HI must be >= 0");
+    tau0 = p->N_HI * line_sigma0(p->T);
+  }
+  std::memset(m, 0, sizeof(*m));
+  m->R_in = p->R_in / p->R_out;
+  m->R_out = 1.0;
+  m->kap0 = (float)(tau0 / L);
+  m->kapd = (float)(p->tau_dust / L);
+  const double vth = line_vth_kms(p->T);
+  m->vth = (float)vth;
+  m->inv_vth = (float)(1.0 / vth);
+  m->a = (float)line_a(p->T);
+  m->vgrad = (float)p->v_max;  // km/s per R_out
+  m->gam = (float)(p->v_max / vth);
+  const double f = (p->step_dx > 0.0) ? p->step_dx : 0.01;
+  m->ds_core = (p->v_max > 0.0) ? (float)(f * vth / p->v_max) : 1e30f;
+  m->albedo = (float)p->albedo;
+  m->g_hg = (float)p->g_hg;
+  m->phase = p->phase;
+  return THOR_OK;
+}
+
+extern "C" int thor_shell_create(thor_ctx_t ctx, const thor_shell_params* p, thor_geom_t* out) {
+  if (!ctx || !out) return THOR_ERR_INVALID_ARG;
+  *out = nullptr;
+  thor_geom* g = new thor_geom();
+  g->ctx = ctx;
+  g->kind = thor_geom::SHELL;
+  int rc = fill_shell_model(ctx, p, &g->shell);
+  if (rc != THOR_OK) { delete g; return rc; }
+  g->shell_params = *p;
+  *out = g;
+  return THOR_OK;
+}
+
+static int copy_in(thor_ctx* ctx, const void* src, size_t bytes, int mem_kind, void* dst) {
+  const cudaMemcpyKind k = (mem_kind == THOR_MEM_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  return ctx->cuda(cudaMemcpyAsync(dst, src, bytes, k, ctx->stream), "copy to device");
+}
+
+extern "C" int thor_grid_create(thor_ctx_t ctx, const float* n_HI, const float* T, const float* v, const float* dust,
+                                const int32_t dims[3], double cell_cm, int mem_kind, thor_geom_t* out) {
+  if (!ctx || !out) return THOR_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!n_HI || !T || !v || !dims) return ctx->fail(THOR_ERR_INVALID_ARG, "thor_grid_create: NULL field");
+  if (dims[0] <= 0 || dims[1] <= 0 || dims[2] <= 0) return ctx->fail(THOR_ERR_INVALID_ARG, "bad dims");
+  if (!(cell_cm > 0.0)) return ctx->fail(THOR_ERR_INVALID_ARG, "cell size must be > 0");
+  if (mem_kind != THOR_MEM_HOST && mem_kind != THOR_MEM_DEVICE) return ctx->fail(THOR_ERR_INVALID_ARG, "mem_kind");
+  if (int rc = ctx->select()) return rc;
+  const int64_t n = (int64_t)dims[0] * dims[1] * dims[2];
+  thor_geom* g = new thor_geom();
+  g->ctx = ctx;
+  g->kind = thor_geom::GRID;
+  for (int a = 0; a < 3; ++a) g->dims[a] = dims[a];
+  g->cell_cm = cell_cm;
+  g->n_cells = n;
+  const size_t fb = (size_t)n * sizeof(float);
+  float* stage = nullptr;
+  int rc = THOR_OK;
+  if (cudaMalloc(&g->cells, (size_t)n * sizeof(GridCell)) != cudaSuccess ||
+      cudaMalloc(&g->cdf, (size_t)n * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&g->scan_tmp, scan_f64_scratch(n)) != cudaSuccess) {
+    delete g;
+    return ctx->fail(THOR_ERR_OOM, "thor_grid_create: cannot allocate %lld cells", (long long)n);
+  }
+  const float *dn = n_HI, *dT = T, *dvx = v, *dvy = v + n, *dvz = v + 2 * n, *dd = dust;
+  if (mem_kind == THOR_MEM_HOST) {  // stage the six fields on the device
+    const int nf = dust ? 6 : 5;
+    if (cudaMalloc(&stage, fb * nf) != cudaSuccess) {
+      delete g;
+      return ctx->fail(THOR_ERR_OOM, "thor_grid_create: cannot stage fields");
+    }
+    const float* srcs[6] = {n_HI, T, v, v + n, v + 2 * n, dust};
+    for (int f = 0; f < nf && rc == THOR_OK; ++f) rc = copy_in(ctx, srcs[f], fb, THOR_MEM_HOST, stage + f * (size_t)n);
+    dn = stage; dT = stage + n; dvx = stage + 2 * n; dvy = stage + 3 * n; dvz = stage + 4 * n;
+    dd = dust ? stage + 5 * n : nullptr;
+  }
+  if (rc == THOR_OK) rc = ctx->cuda(launch_grid_pack(dn, dT, dvx, dvy, dvz, dd, n, cell_cm, g->cells, g->cdf, ctx->stream), "grid pack");
+  if (rc == THOR_OK) rc = ctx->cuda(launch_scan_f64(g->cdf, n, g->scan_tmp, ctx->stream), "emission CDF");
+  if (rc == THOR_OK) rc = ctx->cuda(cudaStreamSynchronize(ctx->stream), "grid create");
+  if (stage) cudaFree(stage);
+  if (rc != THOR_OK) { delete g; return rc; }
+  double total = 0.0;
+  cudaMemcpy(&total, g->cdf + (n - 1), sizeof(double), cudaMemcpyDeviceToHost);
+  if (!(total > 0.0)) { delete g; return ctx->fail(THOR_ERR_INVALID_ARG, "thor_grid_create: n_HI is zero everywhere"); }
+  *out = g;
+  return THOR_OK;
+}
+
+thor_geom::~thor_geom() {
+  if (ctx) cudaSetDevice(ctx->device);
+  if (cells) cudaFree(cells);
+  if (cdf) cudaFree(cdf);
+  if (scan_tmp) cudaFree(scan_tmp);
+}
+
+extern "C" void thor_geom_destroy(thor_geom_t g) { delete g; }
+
+// ------------------------------------------------------------------------------ run
+int thor::prepare_outputs(thor_ctx* ctx, const thor_output_spec* spec, uint64_t n_photons, bool grid, OutBufs* o) {
+  if (!spec || !spec->spectrum) return ctx->fail(THOR_ERR_INVALID_ARG, "output spec / spectrum is NULL");
+  if (spec->n_bins <= 0 || !(spec->X_max > spec->X_min)) return ctx->fail(THOR_ERR_INVALID_ARG, "bad spectrum binning");
+  if (spec->mem_kind != THOR_MEM_HOST && spec->mem_kind != THOR_MEM_DEVICE)
+    return ctx->fail(THOR_ERR_INVALID_ARG, "bad output mem_kind");
+  const bool dev = spec->mem_kind == THOR_MEM_DEVICE;
+  const size_t sb = (size_t)(spec->n_bins + 2) * sizeof(uint64_t);
+  o->spec = dev ? (unsigned long long*)spec->spectrum : (unsigned long long*)ctx->scratch(ctx->b_spec, sb);
+  if (!o->spec) return ctx->fail(THOR_ERR_OOM, "spectrum buffer");
+  if (int rc = ctx->cuda(cudaMemsetAsync(o->spec, 0, sb, ctx->stream), "clear spectrum")) return rc;
+  o->cube = nullptr;
+  if (grid && spec->peel) {
+    if (!spec->cube || spec->img_n <= 0 || spec->peel_bins <= 0 || !(spec->peel_X_max > spec->peel_X_min))
+      return ctx->fail(THOR_ERR_INVALID_ARG, "bad peeling-off spec");
+    const size_t cb = (size_t)3 * spec->img_n * spec->img_n * spec->peel_bins * sizeof(float);
+    o->cube = dev ? spec->cube : (float*)ctx->scratch(ctx->b_cube, cb);
+    if (!o->cube) return ctx->fail(THOR_ERR_OOM, "cube buffer");
+    if (int rc = ctx->cuda(cudaMemsetAsync(o->cube, 0, cb, ctx->stream), "clear cube")) return rc;
+  }
+  o->raw_X = nullptr; o->raw_n = nullptr; o->raw_s = nullptr;
+  if (spec->raw_X || spec->raw_nscat || spec->raw_status) {
+    if (!spec->raw_X || !spec->raw_nscat || !spec->raw_status)
+      return ctx->fail(THOR_ERR_INVALID_ARG, "raw_X, raw_nscat and raw_status go together");
+    if (dev) {
+      o->raw_X = spec->raw_X; o->raw_n = spec->raw_nscat; o->raw_s = spec->raw_status;
+    } else {
+      const size_t rb = (size_t)n_photons * 9 + 64;
+      char* p = (char*)ctx->scratch(ctx->b_raw, rb);
+      if (!p) return ctx->fail(THOR_ERR_OOM, "raw buffers");
+      o->raw_X = (float*)p;
+      o->raw_n = (uint32_t*)(p + 4 * n_photons);
+      o->raw_s = (uint8_t*)(p + 8 * n_photons);
+    }
+  }
+  return THOR_OK;
+}
+
+int thor::finish_outputs(thor_ctx* ctx, const thor_output_spec* spec, uint64_t n_photons, bool grid, const OutBufs& o) {
+  if (spec->mem_kind == THOR_MEM_DEVICE) return THOR_OK;
+  cudaStream_t s = ctx->stream;
+  int rc = ctx->cuda(cudaMemcpyAsync(spec->spectrum, o.spec, (size_t)(spec->n_bins + 2) * 8, cudaMemcpyDeviceToHost, s),
+                     "copy spectrum");
+  if (rc == THOR_OK && o.cube)
+    rc = ctx->cuda(cudaMemcpyAsync(spec->cube, o.cube, (size_t)3 * spec->img_n * spec->img_n * spec->peel_bins * 4,
+                                   cudaMemcpyDeviceToHost, s), "copy cube");
+  if (rc == THOR_OK && o.raw_X) {
+    rc = ctx->cuda(cudaMemcpyAsync(spec->raw_X, o.raw_X, n_photons * 4, cudaMemcpyDeviceToHost, s), "copy raw");
+    if (rc == THOR_OK) rc = ctx->cuda(cudaMemcpyAsync(spec->raw_nscat, o.raw_n, n_photons * 4, cudaMemcpyDeviceToHost, s), "copy raw");
+    if (rc == THOR_OK) rc = ctx->cuda(cudaMemcpyAsync(spec->raw_status, o.raw_s, n_photons, cudaMemcpyDeviceToHost, s), "copy raw");
+  }
+  return rc;
+}
+
+void thor::tally_to_result(const Tally& t, uint64_t n_photons, thor_result* r) {
+  r->n_photons = n_photons;
+  r->n_escaped = t.n_escaped; r->n_absorbed = t.n_absorbed; r->n_capped = t.n_capped;
+  r->n_scat = t.n_scat; r->n_dust_scat = t.n_dust_scat; r->n_upar_iters = t.n_upar_iters;
+  r->n_steps = t.n_steps; r->sum_scat2 = t.sum_scat2;
+}
+
+extern "C" int thor_run(thor_ctx_t ctx, thor_geom_t g, const thor_source* src, uint64_t first_id, uint64_t n_photons,
+                        uint64_t seed, const thor_output_spec* spec, thor_result* out) {
+  if (!ctx || !g || !src || !out) return ctx ? ctx->fail(THOR_ERR_INVALID_ARG, "thor_run: NULL argument") : THOR_ERR_INVALID_ARG;
+  if (g->ctx != ctx) return ctx->fail(THOR_ERR_INVALID_ARG, "geometry belongs to another context");
+  if (n_photons == 0) return ctx->fail(THOR_ERR_INVALID_ARG, "n_photons must be > 0");
+  if (first_id + n_photons < first_id) return ctx->fail(THOR_ERR_INVALID_ARG, "photon id range overflows");
+  const bool grid = g->kind == thor_geom::GRID;
+  if (grid && src->kind != 1) return ctx->fail(THOR_ERR_INVALID_ARG, "grids take source kind 1 (gas emission)");
+  if (!grid && src->kind != 0) return ctx->fail(THOR_ERR_INVALID_ARG, "shells take source kind 0 (central point source)");
+  if (!grid && !(src->sigma >= 0.0)) return ctx->fail(THOR_ERR_INVALID_ARG, "source sigma must be >= 0");
+  if (grid && spec && spec->peel && spec->img_n > 0 &&
+      (g->dims[0] % spec->img_n || g->dims[1] % spec->img_n || g->dims[2] % spec->img_n))
+    return ctx->fail(THOR_ERR_INVALID_ARG, "img_n must divide the grid dimensions");
+  if (int rc = ctx->select()) return rc;
+  OutBufs o;
+  if (int rc = prepare_outputs(ctx, spec, n_photons, grid, &o)) return rc;
+  cudaStream_t s = ctx->stream;
+  // per-run device scratch: tally, queue counter + tables, model record, peel statistics
+  Tally* d_tally = (Tally*)ctx->scratch(ctx->b_tally, sizeof(Tally));
+  char* qb = (char*)ctx->scratch(ctx->b_queue, 256);
+  unsigned long long* d_stats = (unsigned long long*)ctx->scratch(ctx->b_stats, 2 * sizeof(unsigned long long));
+  if (!d_tally || !qb || !d_stats) return ctx->fail(THOR_ERR_OOM, "run scratch");
+  struct QHost { unsigned long long next, prefix[2], first_id; int32_t model; } qh{0, {0, n_photons}, first_id, 0};
+  if (int rc = ctx->cuda(cudaMemcpyAsync(qb, &qh, sizeof qh, cudaMemcpyHostToDevice, s), "queue upload")) return rc;
+  if (int rc = ctx->cuda(cudaMemsetAsync(d_tally, 0, sizeof(Tally), s), "clear tally")) return rc;
+  if (int rc = ctx->cuda(cudaMemsetAsync(d_stats, 0, 16, s), "clear stats")) return rc;
+  WorkQueue q;
+  q.next = (unsigned long long*)(qb + offsetof(QHost, next));
+  q.total = n_photons;
+  q.prefix = (const unsigned long long*)(qb + offsetof(QHost, prefix));
+  q.first_id = (const unsigned long long*)(qb + offsetof(QHost, first_id));
+  q.model = (const int32_t*)(qb + offsetof(QHost, model));
+  q.n_entries = 1;
+  const float dX = (float)((spec->X_max - spec->X_min) / spec->n_bins);
+  int rc = THOR_OK;
+  if (!grid) {
+    ShellModel m = g->shell;
+    m.line = (src->sigma > 0.0) ? 1 : 0;
+    m.X0 = (float)src->X0;
+    m.sigma = (float)src->sigma;
+    m.X_min = (float)spec->X_min;
+    m.inv_dX = 1.0f / dX;
+    m.n_bins = spec->n_bins;
+    m.seed_lo = (uint32_t)seed; m.seed_hi = (uint32_t)(seed >> 32);
+    m.max_scat = spec->max_scat;
+    m.spectrum = o.spec;
+    m.tally = d_tally;
+    m.raw_X = o.raw_X; m.raw_nscat = o.raw_n; m.raw_status = o.raw_s;
+    m.id_base = first_id;
+    m.n_photons = n_photons;
+    ShellModel* d_m = (ShellModel*)ctx->scratch(ctx->b_models, sizeof(ShellModel));
+    if (!d_m) return ctx->fail(THOR_ERR_OOM, "model table");
+    if ((rc = ctx->cuda(cudaMemcpyAsync(d_m, &m, sizeof m, cudaMemcpyHostToDevice, s), "model upload"))) return rc;
+    const int gsz = shell_grid(ctx->block, ctx->blocks_per_sm, false);
+    cudaEventRecord(ctx->ev0, s);
+    rc = ctx->cuda(launch_shell_run(d_m, q, ctx->d_ktab, gsz, ctx->block, s), "shell photon loop");
+    cudaEventRecord(ctx->ev1, s);
+  } else {
+    GridModel m;
+    std::memset(&m, 0, sizeof m);
+    m.cells = g->cells; m.cdf = g->cdf;
+    m.nx = g->dims[0]; m.ny = g->dims[1]; m.nz = g->dims[2];
+    m.phase = g->grid_phase;
+    m.albedo = (float)g->grid_albedo; m.g_hg = (float)g->grid_g;
+    m.X_min = (float)spec->X_min; m.inv_dX = 1.0f / dX; m.n_bins = spec->n_bins;
+    m.peel = (spec->peel && o.cube) ? 1 : 0;
+    m.img_n = spec->img_n; m.peel_bins = spec->peel_bins;
+    if (m.peel) {
+      m.pX_min = (float)spec->peel_X_min;
+      m.pinv_dX = (float)(spec->peel_bins / (spec->peel_X_max - spec->peel_X_min));
+    }
+    m.tau_cut = 50.0f;
+    m.max_scat = spec->max_scat;
+    m.seed_lo = (uint32_t)seed; m.seed_hi = (uint32_t)(seed >> 32);
+    m.spectrum = o.spec; m.cube = o.cube; m.tally = d_tally;
+    m.n_photons = n_photons; m.id_base = first_id;
+    m.peel_rays = d_stats; m.peel_cells = d_stats + 1;
+    const int gsz = grid_grid(ctx->block, ctx->blocks_per_sm);
+    cudaEventRecord(ctx->ev0, s);
+    rc = ctx->cuda(launch_grid_run(m, q, ctx->d_ktab, gsz, ctx->block, s), "grid photon loop");
+    cudaEventRecord(ctx->ev1, s);
+  }
+  if (rc) return rc;
+  Tally t;
+  unsigned long long st[2];
+  if ((rc = ctx->cuda(cudaMemcpyAsync(&t, d_tally, sizeof t, cudaMemcpyDeviceToHost, s), "copy tally"))) return rc;
+  if ((rc = ctx->cuda(cudaMemcpyAsync(st, d_stats, sizeof st, cudaMemcpyDeviceToHost, s), "copy stats"))) return rc;
+  if ((rc = finish_outputs(ctx, spec, n_photons, grid, o))) return rc;
+  if ((rc = ctx->cuda(cudaStreamSynchronize(s), "photon loop"))) return rc;
+  std::memset(out, 0, sizeof *out);
+  tally_to_result(t, n_photons, out);
+  out->n_peel_rays = st[0];
+  out->n_peel_cells = st[1];
+  float ms = 0.0f;
+  cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+  out->elapsed_ms = ms;
+  if (t.n_done != n_photons) return ctx->fail(THOR_ERR_DEVICE, "photon loop finished %llu of %llu photons",
+                                              (unsigned long long)t.n_done, (unsigned long long)n_photons);
+  ctx->last_error.clear();
+  return THOR_OK;
+}
+
+// Grid scattering parameters are set on the geometry (albedo, g, phase) -- exposed
+// through thor_grid_set_scattering in thor_ctx.h for the Python binding.
+extern "C" int thor_grid_set_scattering(thor_geom_t g, int phase, double albedo, double g_hg) {
+  if (!g || g->kind != thor_geom::GRID) return THOR_ERR_INVALID_ARG;
+  if (phase < 0 || phase > 2 || !(albedo >= 0.0 && albedo <= 1.0) || !(g_hg > -1.0 && g_hg < 1.0))
+    return g->ctx->fail(THOR_ERR_INVALID_ARG, "bad grid scattering parameters");
+  g->grid_phase = phase;
+  g->grid_albedo = albedo;
+  g->grid_g = g_hg;
+  return THOR_OK;
+}
+
+// ------------------------------------------------------------------------------ forest
+extern "C" int thor_forest(thor_ctx_t ctx, const float* n_HI, const float* T, const float* v_los, const int32_t dims[3],
+                           int mem_kind, const thor_forest_spec* sp, float* tau_out) {
+  if (!ctx) return THOR_ERR_INVALID_ARG;
+  if (!n_HI || !T || !v_los || !dims || !sp || !tau_out) return ctx->fail(THOR_ERR_INVALID_ARG, "thor_forest: NULL argument");
+  if (dims[0] <= 0 || dims[1] <= 0 || dims[2] <= 0) return ctx->fail(THOR_ERR_INVALID_ARG, "bad dims");
+  if (sp->n_bins <= 0 || sp->n_bins > 2048) return ctx->fail(THOR_ERR_INVALID_ARG, "n_bins must be in [1, 2048]");
+  if (!(sp->ds_cm > 0.0) || !(sp->dv_cell > 0.0) || !(sp->dv_bin > 0.0))
+    return ctx->fail(THOR_ERR_INVALID_ARG, "ds_cm, dv_cell, dv_bin must be > 0");
+  const double V = dims[2] * sp->dv_cell;
+  if (std::fabs(sp->n_bins * sp->dv_bin - V) > 1e-9 * V)
+    return ctx->fail(THOR_ERR_INVALID_ARG, "n_bins * dv_bin must equal nz * dv_cell (periodic spectrum)");
+  const int64_t ncol = (int64_t)dims[0] * dims[1];
+  if (sp->first_sightline < 0 || sp->n_sightlines <= 0 || sp->first_sightline + sp->n_sightlines > ncol)
+    return ctx->fail(THOR_ERR_INVALID_ARG, "sightline range outside the grid");
+  if (mem_kind != THOR_MEM_HOST && mem_kind != THOR_MEM_DEVICE) return ctx->fail(THOR_ERR_INVALID_ARG, "mem_kind");
+  if (int rc = ctx->select()) return rc;
+  cudaStream_t s = ctx->stream;
+  const int64_t n = (int64_t)dims[0] * dims[1] * dims[2];
+  const size_t tb = (size_t)sp->n_sightlines * sp->n_bins * sizeof(float);
+  const float *dn = n_HI, *dT = T, *dv = v_los;
+  float* dtau = tau_out;
+  void* stage = nullptr;
+  int rc = THOR_OK;
+  if (mem_kind == THOR_MEM_HOST) {
+    if (cudaMalloc(&stage, 3 * (size_t)n * 4 + tb) != cudaSuccess) return ctx->fail(THOR_ERR_OOM, "forest staging");
+    float* f = (float*)stage;
+    rc = copy_in(ctx, n_HI, (size_t)n * 4, THOR_MEM_HOST, f);
+    if (!rc) rc = copy_in(ctx, T, (size_t)n * 4, THOR_MEM_HOST, f + n);
+    if (!rc) rc = copy_in(ctx, v_los, (size_t)n * 4, THOR_MEM_HOST, f + 2 * n);
+    dn = f; dT = f + n; dv = f + 2 * n; dtau = f + 3 * n;
+  }
+  if (!rc) {
+    cudaEventRecord(ctx->ev0, s);
+    rc = ctx->cuda(launch_forest(dn, dT, dv, dims[0], dims[1], dims[2], sp->first_sightline, sp->n_sightlines, sp->ds_cm,
+                                 sp->dv_cell, sp->n_bins, sp->dv_bin, dtau, ctx->d_ktab, s), "forest kernel");
+    cudaEventRecord(ctx->ev1, s);
+  }
+  if (!rc && mem_kind == THOR_MEM_HOST) rc = ctx->cuda(cudaMemcpyAsync(tau_out, dtau, tb, cudaMemcpyDeviceToHost, s), "copy tau");
+  if (!rc) rc = ctx->cuda(cudaStreamSynchronize(s), "forest");
+  if (!rc) cudaEventElapsedTime(&ctx->last_ms, ctx->ev0, ctx->ev1);
+  if (stage) cudaFree(stage);
+  return rc;
+}
+
+extern "C" double thor_last_elapsed_ms(thor_ctx_t ctx) { return ctx ? ctx->last_ms : -1.0; }
+
+// ------------------------------------------------------------------------------ diagnostics
+namespace {
+// Stage small diagnostic buffers: device pointers pass through, host pointers are copied.
+struct Stage {
+  thor_ctx* ctx;
+  int kind;
+  std::vector<std::pair<void*, std::pair<void*, size_t>>> back;  // (host dst, (dev src, bytes))
+  char* base = nullptr;
+  size_t used = 0;
+  void* in(const void* p, size_t bytes) {
+    if (kind == THOR_MEM_DEVICE) return (void*)p;
+    void* d = base + used;
+    used += (bytes + 255) & ~(size_t)255;
+    cudaMemcpyAsync(d, p, bytes, cudaMemcpyHostToDevice, ctx->stream);
+    return d;
+  }
+  void* out(void* p, size_t bytes) {
+    if (kind == THOR_MEM_DEVICE) return p;
+    void* d = base + used;
+    used += (bytes + 255) & ~(size_t)255;
+    back.push_back({p, {d, bytes}});
+    return d;
+  }
+  int finish() {
+    for (auto& b : back) cudaMemcpyAsync(b.first, b.second.first, b.second.second, cudaMemcpyDeviceToHost, ctx->stream);
+    return ctx->cuda(cudaStreamSynchronize(ctx->stream), "diagnostic kernel");
+  }
+};
+
+int stage_begin(thor_ctx* ctx, int kind, size_t bytes, Stage* st) {
+  st->ctx = ctx;
+  st->kind = kind;
+  if (kind != THOR_MEM_HOST && kind != THOR_MEM_DEVICE) return ctx->fail(THOR_ERR_INVALID_ARG, "mem_kind");
+  if (int rc = ctx->select()) return rc;
+  if (kind == THOR_MEM_HOST) {
+    st->base = (char*)ctx->scratch(ctx->b_diag, bytes + 4096);
+    if (!st->base) return ctx->fail(THOR_ERR_OOM, "diagnostic staging");
+  }
+  return THOR_OK;
+}
+}  // namespace
+
+extern "C" int thor_voigt_eval(thor_ctx_t ctx, const float* a, const float* x, float* H, int64_t n, int precise,
+                               int mem_kind) {
+  if (!ctx || !a || !x || !H || n <= 0) return ctx ? ctx->fail(THOR_ERR_INVALID_ARG, "thor_voigt_eval") : THOR_ERR_INVALID_ARG;
+  Stage st;
+  if (int rc = stage_begin(ctx, mem_kind, 3 * (size_t)n * 4 + 1024, &st)) return rc;
+  const float* da = (const float*)st.in(a, n * 4);
+  const float* dx = (const float*)st.in(x, n * 4);
+  float* dH = (float*)st.out(H, n * 4);
+  if (int rc = ctx->cuda(launch_voigt_eval(da, dx, dH, n, ctx->d_ktab, ctx->stream, precise), "voigt kernel")) return rc;
+  return st.finish();
+}
+
+extern "C" int thor_dda_trace(thor_ctx_t ctx, const int32_t dims[3], const double* org, const float* dir, int32_t n,
+                              int32_t max_steps, int64_t* cells, double* seg, int32_t* count, int mem_kind) {
+  if (!ctx || !dims || !org || !dir || !cells || !seg || !count || n <= 0 || max_steps <= 0)
+    return ctx ? ctx->fail(THOR_ERR_INVALID_ARG, "thor_dda_trace") : THOR_ERR_INVALID_ARG;
+  const size_t tb = (size_t)n * max_steps;
+  Stage st;
+  if (int rc = stage_begin(ctx, mem_kind, (size_t)n * 40 + tb * 16 + 4096, &st)) return rc;
+  const double* dorg = (const double*)st.in(org, (size_t)n * 24);
+  const float* ddir = (const float*)st.in(dir, (size_t)n * 12);
+  int64_t* dc = (int64_t*)st.out(cells, tb * 8);
+  double* ds = (double*)st.out(seg, tb * 8);
+  int32_t* dn = (int32_t*)st.out(count, (size_t)n * 4);
+  if (int rc = ctx->cuda(launch_dda_trace(dims[0], dims[1], dims[2], dorg, ddir, n, max_steps, dc, ds, dn, ctx->stream),
+                         "dda kernel"))
+    return rc;
+  return st.finish();
+}
+
+extern "C" int thor_sample_upar(thor_ctx_t ctx, float x, float a, uint64_t seed, int64_t n, float* out, uint64_t* iters,
+                                int mem_kind) {
+  if (!ctx || !out || n <= 0 || !(a >= 0.0f)) return ctx ? ctx->fail(THOR_ERR_INVALID_ARG, "thor_sample_upar") : THOR_ERR_INVALID_ARG;
+  Stage st;
+  if (int rc = stage_begin(ctx, mem_kind, (size_t)n * 4 + 4096, &st)) return rc;
+  float* d = (float*)st.out(out, (size_t)n * 4);
+  unsigned long long* dit = (unsigned long long*)ctx->scratch(ctx->b_stats, 16);
+  if (!dit) return ctx->fail(THOR_ERR_OOM, "stats");
+  cudaMemsetAsync(dit, 0, 8, ctx->stream);
+  if (int rc = ctx->cuda(launch_upar(x, a, seed, n, d, dit, ctx->stream), "u_par kernel")) return rc;
+  unsigned long long h = 0;
+  cudaMemcpyAsync(&h, dit, 8, cudaMemcpyDeviceToHost, ctx->stream);
+  int rc = st.finish();
+  if (iters) *iters = h;
+  return rc;
+}
+
+extern "C" int thor_scatter_once(thor_ctx_t ctx, float x, float a, int phase, uint64_t seed, int64_t n, float* x_out,
+                                 float* mu_out, int mem_kind) {
+  if (!ctx || !x_out || !mu_out || n <= 0 || phase < 0 || phase > 2)
+    return ctx ? ctx->fail(THOR_ERR_INVALID_ARG, "thor_scatter_once") : THOR_ERR_INVALID_ARG;
+  Stage st;
+  if (int rc = stage_begin(ctx, mem_kind, (size_t)n * 8 + 4096, &st)) return rc;
+  float* dx = (float*)st.out(x_out, (size_t)n * 4);
+  float* dm = (float*)st.out(mu_out, (size_t)n * 4);
+  if (int rc = ctx->cuda(launch_scatter_once(x, a, phase, seed, n, dx, dm, ctx->stream), "scatter kernel")) return rc;
+  return st.finish();
+}
+
+extern "C" int thor_philox(thor_ctx_t ctx, const uint32_t* ctr, const uint32_t* key, uint32_t* out, int32_t n,
+                           int mem_kind) {
+  if (!ctx || !ctr || !key || !out || n <= 0) return ctx ? ctx->fail(THOR_ERR_INVALID_ARG, "thor_philox") : THOR_ERR_INVALID_ARG;
+  Stage st;
+  if (int rc = stage_begin(ctx, mem_kind, (size_t)n * 40 + 4096, &st)) return rc;
+  const uint32_t* dc = (const uint32_t*)st.in(ctr, (size_t)n * 16);
+  const uint32_t* dk = (const uint32_t*)st.in(key, (size_t)n * 8);
+  uint32_t* dout = (uint32_t*)st.out(out, (size_t)n * 16);
+  if (int rc = ctx->cuda(launch_philox(dc, dk, dout, n, ctx->stream), "philox kernel")) return rc;
+  return st.finish();
+}

@@ -1,0 +1,65 @@
+// thor_ctx.h -- host-side objects behind the opaque handles of include/thor.h.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "../../include/thor.h"
+#include "thor_internal.h"
+
+struct thor_ctx {
+  struct Buf {
+    void* p = nullptr;
+    size_t cap = 0;
+  };
+  int device = 0;
+  int sm_count = 0, cc_major = 0, cc_minor = 0;
+  cudaStream_t stream = nullptr;
+  int block = 128;          // threads per block of the photon loops
+  int blocks_per_sm = 0;    // 0 = occupancy maximum
+  float* d_ktab = nullptr;  // Voigt coefficient table (device copy)
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  float last_ms = 0.0f;
+  std::string last_error;
+  // grow-only scratch buffers reused across calls
+  Buf b_models, b_tally, b_queue, b_spec, b_cube, b_raw, b_diag, b_stats;
+
+  int fail(int code, const char* fmt, ...);
+  int cuda(cudaError_t e, const char* what);
+  int select();
+  void* scratch(Buf& b, size_t bytes);
+  ~thor_ctx();
+};
+
+struct thor_geom {
+  enum Kind { SHELL, GRID } kind = SHELL;
+  thor_ctx* ctx = nullptr;
+  // shell
+  thor::ShellModel shell{};
+  thor_shell_params shell_params{};
+  // grid
+  int32_t dims[3] = {0, 0, 0};
+  double cell_cm = 0.0;
+  int64_t n_cells = 0;
+  thor::GridCell* cells = nullptr;
+  double* cdf = nullptr;
+  double* scan_tmp = nullptr;
+  int grid_phase = THOR_PHASE_DIPOLE;
+  double grid_albedo = 0.32, grid_g = 0.73;
+  ~thor_geom();
+};
+
+namespace thor {
+struct OutBufs {
+  unsigned long long* spec = nullptr;
+  float* cube = nullptr;
+  float* raw_X = nullptr;
+  uint32_t* raw_n = nullptr;
+  uint8_t* raw_s = nullptr;
+};
+int fill_shell_model(thor_ctx* ctx, const thor_shell_params* p, ShellModel* m);
+int prepare_outputs(thor_ctx* ctx, const thor_output_spec* spec, uint64_t n_photons, bool grid, OutBufs* o);
+int finish_outputs(thor_ctx* ctx, const thor_output_spec* spec, uint64_t n_photons, bool grid, const OutBufs& o);
+void tally_to_result(const Tally& t, uint64_t n_photons, thor_result* r);
+}  // namespace thor

@@ -1,0 +1,355 @@
+// thor_device.cuh -- device building blocks of the resonant Lyman-alpha photon loop
+// (THOR, arXiv:2507.11603, Sec. 2-3): line constants, Philox4x32-10 streams, the
+// FP32 Voigt function, atom-velocity and phase-function samplers, the fused frame
+// shift, and the bit-reproducible DDA cell walk.  sm_103a only.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "voigt_coeffs.h"
+
+namespace thor {
+
+// ------------------------------------------------------------------------------
+// Physical constants (CGS; CODATA 2018 and NIST ASD values for Lyman-alpha).
+// ------------------------------------------------------------------------------
+constexpr double kPiD = 3.14159265358979323846;
+constexpr double kC = 2.99792458e10;
+constexpr double kBoltz = 1.380649e-16;
+constexpr double kMassH = 1.6735575e-24;
+constexpr double kLambda0 = 1215.67e-8;
+constexpr double kA21 = 6.265e8;
+constexpr double kF12 = 0.4164;
+constexpr double kEsu = 4.80320471e-10;
+constexpr double kMe = 9.1093837015e-28;
+constexpr float kPiF = 3.14159265358979f;
+constexpr float kInvSqrtPiF = 0.564189583547756f;
+
+// Line parameters at temperature T (Sec. 2.3.1): v_th = sqrt(2kT/m_H) [km/s];
+// a = A21 lambda0 / (4 pi v_th); sigma_0 = f12 sqrt(pi) e^2 lambda0 / (m_e c v_th) [cm^2]
+// so that sigma(x) = sigma_0 H(a, x).
+__host__ __device__ inline double line_vth_kms(double T) { return sqrt(2.0 * kBoltz * T / kMassH) * 1e-5; }
+__host__ __device__ inline double line_a(double T) { return kA21 * kLambda0 / (4.0 * kPiD * line_vth_kms(T) * 1e5); }
+__host__ __device__ inline double line_sigma0(double T) {
+  return kF12 * 1.7724538509055160 * kEsu * kEsu * kLambda0 / (kMe * kC * line_vth_kms(T) * 1e5);
+}
+// T-scalings used by per-cell kernels: v_th = kVth1 sqrt(T), a = kA1 / sqrt(T), sigma_0 = kSig1 / sqrt(T).
+#define THOR_VTH1 (1.2845065404917818e-1)     /* km/s at T = 1 K */
+#define THOR_A1 (4.718354755551596e-2)        /* a at T = 1 K   */
+#define THOR_SIG1 (5.900890163475877e-12)     /* cm^2 at T = 1 K */
+
+// ------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al. 2011, SC'11), written from the published definition.
+// Per-packet stream: key = seed (low, high); counter = (photon id low, photon id high,
+// block low, block high).  Words are consumed in order, four per block.
+// ------------------------------------------------------------------------------
+__device__ __forceinline__ void philox10(uint32_t& c0, uint32_t& c1, uint32_t& c2, uint32_t& c3,
+                                         uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+  }
+}
+
+struct Rng {
+  uint32_t k0, k1, p0, p1;  // key, photon id
+  uint32_t blk_lo, blk_hi;  // next block to generate
+  uint32_t w0, w1, w2, w3;  // buffered words (w0 next)
+  uint32_t left;            // buffered words left
+
+  __device__ __forceinline__ void init(uint64_t seed, uint64_t pid) {
+    k0 = (uint32_t)seed; k1 = (uint32_t)(seed >> 32);
+    p0 = (uint32_t)pid; p1 = (uint32_t)(pid >> 32);
+    blk_lo = 0; blk_hi = 0; left = 0;
+  }
+  __device__ __forceinline__ void refill() {
+    uint32_t c0 = p0, c1 = p1, c2 = blk_lo, c3 = blk_hi;
+    philox10(c0, c1, c2, c3, k0, k1);
+    w0 = c0; w1 = c1; w2 = c2; w3 = c3; left = 4;
+    blk_lo += 1u;
+    if (blk_lo == 0u) blk_hi += 1u;
+  }
+  __device__ __forceinline__ uint32_t next() {
+    if (left == 0u) refill();
+    const uint32_t r = w0;
+    w0 = w1; w1 = w2; w2 = w3;
+    --left;
+    return r;
+  }
+  // (u + 1/2) 2^-32 in FP32: in (0, 1]
+  __device__ __forceinline__ float uni() {
+    return fminf(__fmaf_rn(__uint2float_rn(next()), 2.3283064365386963e-10f, 1.1641532182693481e-10f), 1.0f);
+  }
+  // Rebuild the buffer after a state save: the stream is at block (blk) with `left` words left.
+  __device__ __forceinline__ void resume(uint32_t words_left) {
+    if (words_left == 0u) { left = 0; return; }
+    // regenerate the block that was being consumed
+    uint32_t lo = blk_lo - 1u, hi = blk_hi - (blk_lo == 0u ? 1u : 0u);
+    uint32_t c0 = p0, c1 = p1, c2 = lo, c3 = hi;
+    philox10(c0, c1, c2, c3, k0, k1);
+    uint32_t w[4] = {c0, c1, c2, c3};
+    uint32_t s = 4u - words_left;
+    w0 = w[s & 3]; w1 = w[(s + 1) & 3]; w2 = w[(s + 2) & 3]; w3 = w[(s + 3) & 3];
+    left = words_left;
+  }
+};
+
+// ------------------------------------------------------------------------------
+// Voigt function H(a, x) in FP32 (App. A.3 defines the truth Re w(x + i a)).
+//   |x| >= 6 : asymptotic wing series, with t = 1/(x^2 + a^2),
+//              H = (a/sqrt(pi)) t sum_k ((2k+1)!!/2^k) t^k   (8 terms);
+//   |x| <  6 : Taylor series of w(x + i a) in a up to a^3, with K(x) = 2 x F(x) - 1
+//              (F Dawson's integral) from a piecewise degree-11 fit (voigt_coeffs.h):
+//              H = e^{-x^2} (1 + a^2 (1 - 2x^2)) + (2a/sqrt(pi)) K + (a^3/(3 sqrt(pi))) ((6 - 4x^2) K + 2).
+// Relative error against the FP64 truth below 1e-6 for a <= 1e-2 (tested).
+// Ktab points to the 6x12 coefficient table (shared memory in the kernels).
+// ------------------------------------------------------------------------------
+__device__ __forceinline__ float voigt_wing(float a, float x2) {
+  const float t = __frcp_rn(__fmaf_rn(a, a, x2));
+  float s = 15836.1328125f;
+  s = __fmaf_rn(s, t, 2111.484375f);
+  s = __fmaf_rn(s, t, 324.84375f);
+  s = __fmaf_rn(s, t, 59.0625f);
+  s = __fmaf_rn(s, t, 13.125f);
+  s = __fmaf_rn(s, t, 3.75f);
+  s = __fmaf_rn(s, t, 1.5f);
+  s = __fmaf_rn(s, t, 1.0f);
+  return a * kInvSqrtPiF * t * s;
+}
+
+template <bool kAccurateExp>
+__device__ __forceinline__ float voigt_core(float a, float ax, float x2, const float* __restrict__ Ktab) {
+  int i = min((int)ax, THOR_VOIGT_NINT - 1);
+  const float u = ax - ((float)i + 0.5f);
+  const float4* c4 = reinterpret_cast<const float4*>(Ktab + i * THOR_VOIGT_NCOEF);
+  const float4 q0 = c4[0], q1 = c4[1], q2 = c4[2];
+  float k = q2.w;
+  k = __fmaf_rn(k, u, q2.z); k = __fmaf_rn(k, u, q2.y); k = __fmaf_rn(k, u, q2.x);
+  k = __fmaf_rn(k, u, q1.w); k = __fmaf_rn(k, u, q1.z); k = __fmaf_rn(k, u, q1.y);
+  k = __fmaf_rn(k, u, q1.x); k = __fmaf_rn(k, u, q0.w); k = __fmaf_rn(k, u, q0.z);
+  k = __fmaf_rn(k, u, q0.y); k = __fmaf_rn(k, u, q0.x);
+  const float g = kAccurateExp ? expf(-x2) : __expf(-x2);
+  const float a2 = a * a;
+  const float gauss = g * __fmaf_rn(a2, __fmaf_rn(-2.0f, x2, 1.0f), 1.0f);
+  const float c3 = a2 * a * (kInvSqrtPiF / 3.0f);
+  return __fmaf_rn(2.0f * a * kInvSqrtPiF, k, gauss) + c3 * __fmaf_rn(__fmaf_rn(-4.0f, x2, 6.0f), k, 2.0f);
+}
+
+template <bool kAccurateExp = true>
+__device__ __forceinline__ float voigt(float a, float x, const float* __restrict__ Ktab) {
+  const float ax = fabsf(x);
+  const float x2 = ax * ax;
+  if (ax >= 6.0f) return voigt_wing(a, x2);
+  return voigt_core<kAccurateExp>(a, ax, x2, Ktab);
+}
+
+// ------------------------------------------------------------------------------
+// Atom velocity parallel to the photon (Eq. 6) by rejection with the comparison
+// function of Eq. 10, sampled through alpha = theta + pi/2 = atan2(a, x - u):
+//   region 1 (u <= u0): alpha ~ U(0, w1), accept with exp(-u^2);
+//   region 2 (u >  u0): alpha ~ U(w1, pi), accept with exp(u0^2 - u^2);
+//   w1 = atan2(a, x - u0), P(region 1) = w1 / (w1 + e^{-u0^2} (pi - w1)), u = x - a / tan(alpha).
+// Split point u0: the smaller-envelope candidate of (i) x - sqrt(a/(2 pi x)) e^{x^2/2}
+// and (ii) three Newton steps on u0^2 = ln(2 pi u0 (x - u0)^2 / a) (only for x > 2).
+// Three draws per iteration: region, alpha, acceptance.
+// ------------------------------------------------------------------------------
+__device__ __forceinline__ float envelope_D(float xr, float a, float u0) {
+  const float w1 = atan2f(a, xr - u0);
+  return w1 + __expf(-u0 * u0) * (kPiF - w1);
+}
+
+__device__ __forceinline__ float u0_rule(float xr, float a) {
+  if (xr <= 0.0f) return 0.0f;
+  const float d = sqrtf(a / (2.0f * kPiF * xr)) * __expf(fminf(0.5f * xr * xr, 80.0f));
+  const float c1 = fmaxf(0.0f, xr - d);
+  if (xr <= 2.0f) return c1;
+  float u = fminf(xr - 0.3f, 2.0f + 0.6f * __logf(xr));
+#pragma unroll
+  for (int it = 0; it < 3; ++it) {
+    const float dx = xr - u;
+    const float g = u * u - __logf(2.0f * kPiF * u * dx * dx / a);
+    const float gp = 2.0f * u - __frcp_rn(u) + 2.0f * __frcp_rn(dx);
+    u = fminf(fmaxf(u - g / gp, 0.5f), xr - 1e-3f);
+  }
+  return (envelope_D(xr, a, c1) <= envelope_D(xr, a, u)) ? c1 : u;
+}
+
+__device__ __forceinline__ float sample_upar(float x, float a, Rng& rng, uint32_t& iters) {
+  const float sgn = (x < 0.0f) ? -1.0f : 1.0f;
+  const float xr = fabsf(x);
+  const float u0 = u0_rule(xr, a);
+  const float w1 = atan2f(a, xr - u0);
+  const float e0 = __expf(-u0 * u0);
+  const float p1 = w1 / (w1 + e0 * (kPiF - w1));
+  const float u02 = u0 * u0;
+  float u;
+  for (;;) {
+    const float R1 = rng.uni(), R2 = rng.uni(), R3 = rng.uni();
+    const bool reg1 = R1 < p1;
+    const float alpha = reg1 ? w1 * R2 : __fmaf_rn(kPiF - w1, R2, w1);
+    u = xr - a / tanf(alpha);
+    const float acc = reg1 ? __expf(-u * u) : __expf(u02 - u * u);
+    ++iters;
+    if (R3 <= acc) break;
+  }
+  return sgn * u;
+}
+
+// Phase functions (Sec. 2.3): mu = k_in . k_out.
+enum : int { PH_ISO = 0, PH_DIPOLE = 1, PH_MIXED = 2 };
+__device__ __forceinline__ float mu_dipole(float R) {  // CDF (mu^3 + 3 mu + 4)/8, Cardano
+  const float B = __fmaf_rn(4.0f, R, -2.0f);
+  const float A = cbrtf(B + sqrtf(__fmaf_rn(B, B, 1.0f)));
+  return A - __frcp_rn(A);
+}
+__device__ __forceinline__ float mu_hg(float R, float g) {  // Eq. 9 inverse CDF
+  if (fabsf(g) < 1e-6f) return __fmaf_rn(2.0f, R, -1.0f);
+  const float t = (1.0f - g * g) / __fmaf_rn(2.0f * g, R, 1.0f - g);
+  return (1.0f + g * g - t * t) / (2.0f * g);
+}
+__device__ __forceinline__ float P_dipole(float mu) { return 0.375f * __fmaf_rn(mu, mu, 1.0f); }
+__device__ __forceinline__ float P_hg(float mu, float g) {
+  const float d = __fmaf_rn(-2.0f * g, mu, 1.0f + g * g);
+  return 0.5f * (1.0f - g * g) * rsqrtf(d * d * d);
+}
+
+// Orthonormal basis perpendicular to unit k (Duff et al. 2017, JCGT 6(1)).
+__device__ __forceinline__ void basis(float kx, float ky, float kz, float3& e1, float3& e2) {
+  const float s = copysignf(1.0f, kz);
+  const float a = -1.0f / (s + kz);
+  const float b = kx * ky * a;
+  e1 = make_float3(1.0f + s * kx * kx * a, s * b, -s * kx);
+  e2 = make_float3(b, s + ky * ky * a, -ky);
+}
+
+struct AtomFrame {  // what peeling-off needs from a resonant scattering
+  float upar, u1, u2;
+  float3 e1, e2;
+  bool core;
+};
+
+// One resonant scattering in the gas frame (Eq. 5-7, recoil ignored).  Returns
+// x_out = x_in + u . (k_out - k_in) and overwrites k with k_out.
+__device__ __forceinline__ float scatter_resonant(float x, float a, int phase, float3& k, Rng& rng,
+                                                  uint32_t& iters, AtomFrame* af) {
+  const float upar = sample_upar(x, a, rng, iters);
+  const float r = sqrtf(-__logf(rng.uni()));
+  float sp1, cp1;
+  sincospif(2.0f * rng.uni(), &sp1, &cp1);
+  const float u1 = r * cp1, u2 = r * sp1;
+  const bool core = fabsf(x - upar) < 0.2f;
+  float mu;
+  if (phase == PH_ISO) {
+    mu = __fmaf_rn(2.0f, rng.uni(), -1.0f);
+  } else if (phase == PH_DIPOLE) {
+    mu = mu_dipole(rng.uni());
+  } else {
+    const float Rc = rng.uni();
+    const float Rm = rng.uni();
+    mu = (core && Rc < (1.0f / 3.0f)) ? __fmaf_rn(2.0f, Rm, -1.0f) : mu_dipole(Rm);
+  }
+  float sp, cp;
+  sincospif(2.0f * rng.uni(), &sp, &cp);
+  float3 e1, e2;
+  basis(k.x, k.y, k.z, e1, e2);
+  const float st = sqrtf(fmaxf(0.0f, 1.0f - mu * mu));
+  float3 ko;
+  ko.x = mu * k.x + st * (cp * e1.x + sp * e2.x);
+  ko.y = mu * k.y + st * (cp * e1.y + sp * e2.y);
+  ko.z = mu * k.z + st * (cp * e1.z + sp * e2.z);
+  const float inv = rsqrtf(ko.x * ko.x + ko.y * ko.y + ko.z * ko.z);
+  ko.x *= inv; ko.y *= inv; ko.z *= inv;
+  if (af) { af->upar = upar; af->u1 = u1; af->u2 = u2; af->e1 = e1; af->e2 = e2; af->core = core; }
+  k = ko;
+  return x - upar + __fmaf_rn(upar, mu, st * __fmaf_rn(u1, cp, u2 * sp));
+}
+
+__device__ __forceinline__ void scatter_dust(float g, float3& k, Rng& rng) {
+  const float mu = mu_hg(rng.uni(), g);
+  float sp, cp;
+  sincospif(2.0f * rng.uni(), &sp, &cp);
+  float3 e1, e2;
+  basis(k.x, k.y, k.z, e1, e2);
+  const float st = sqrtf(fmaxf(0.0f, 1.0f - mu * mu));
+  float3 ko;
+  ko.x = mu * k.x + st * (cp * e1.x + sp * e2.x);
+  ko.y = mu * k.y + st * (cp * e1.y + sp * e2.y);
+  ko.z = mu * k.z + st * (cp * e1.z + sp * e2.z);
+  const float inv = rsqrtf(ko.x * ko.x + ko.y * ko.y + ko.z * ko.z);
+  k = make_float3(ko.x * inv, ko.y * inv, ko.z * inv);
+}
+
+__device__ __forceinline__ float3 iso_dir(Rng& rng) {
+  const float mu = __fmaf_rn(2.0f, rng.uni(), -1.0f);
+  float sp, cp;
+  sincospif(2.0f * rng.uni(), &sp, &cp);
+  const float st = sqrtf(fmaxf(0.0f, 1.0f - mu * mu));
+  return make_float3(st * cp, st * sp, mu);
+}
+
+// ------------------------------------------------------------------------------
+// DDA cell walk (Amanatides & Woo 1987) with a bit-reproducible contract: FP64
+// round-to-nearest with explicit __dadd_rn/__dmul_rn and one IEEE division per axis
+// (never contracted into FMA):
+//   start cell floor(p), minus one where d < 0 and p lies on the face;
+//   inv_ax = 1/d_ax once per ray (IEEE division);
+//   next face distance per axis ((i + (d > 0)) - p) * inv_ax, +inf for d == 0;
+//   step the axis with the smallest distance, ties to the lowest axis (x < y < z).
+// Only the axis that stepped gets a new face distance (recomputed from the face,
+// never accumulated).
+// ------------------------------------------------------------------------------
+struct Dda {
+  int i[3];
+  int step[3];
+  double p[3], inv[3], tm[3];
+  double t;
+
+  __device__ __forceinline__ double face_t(int a) const {
+    const double face = (double)(i[a] + (step[a] > 0 ? 1 : 0));
+    return __dmul_rn(__dadd_rn(face, -p[a]), inv[a]);
+  }
+  __device__ __forceinline__ void init(double px, double py, double pz, double dx, double dy, double dz) {
+    p[0] = px; p[1] = py; p[2] = pz;
+    const double d[3] = {dx, dy, dz};
+    t = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const double f = floor(p[a]);
+      int ii = (int)f;
+      if (d[a] < 0.0 && p[a] == f) ii -= 1;
+      i[a] = ii;
+      step[a] = (d[a] > 0.0) ? 1 : (d[a] < 0.0 ? -1 : 0);
+      inv[a] = (step[a] != 0) ? __ddiv_rn(1.0, d[a]) : 0.0;
+      tm[a] = (step[a] != 0) ? face_t(a) : __longlong_as_double(0x7ff0000000000000ll);
+    }
+  }
+  __device__ __forceinline__ int next_axis(double& tn) const {
+    int ax = 0;
+    double m = tm[0];
+    if (tm[1] < m) { ax = 1; m = tm[1]; }
+    if (tm[2] < m) { ax = 2; m = tm[2]; }
+    tn = m;
+    return ax;
+  }
+  __device__ __forceinline__ void advance(int ax, double tn) {
+    t = tn;
+    i[ax] += step[ax];
+    tm[ax] = face_t(ax);
+  }
+  __device__ __forceinline__ bool inside(int nx, int ny, int nz) const {
+    return i[0] >= 0 && i[1] >= 0 && i[2] >= 0 && i[0] < nx && i[1] < ny && i[2] < nz;
+  }
+};
+
+// Kernel preamble: copy the Voigt coefficient table into shared memory.
+__device__ __forceinline__ void load_ktab(float* sK, const float* __restrict__ gK) {
+  for (int j = threadIdx.x; j < THOR_VOIGT_NINT * THOR_VOIGT_NCOEF; j += blockDim.x) sK[j] = gK[j];
+  __syncthreads();
+}
+
+}  // namespace thor

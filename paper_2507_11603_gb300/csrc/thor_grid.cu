@@ -1,0 +1,390 @@
+// thor_grid.cu -- photon-packet loop on a uniform Cartesian grid (THOR Sec. 3.3-3.4.1):
+// field packing, emission CDF, DDA propagation with zeroth-order cells, interaction,
+// and peeling-off to three axis-aligned observers.
+#include "thor_device.cuh"
+#include "thor_internal.h"
+
+namespace thor {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ---- packing: one 32-byte record per cell, plus n_HI^2 for the emission CDF -------
+__global__ void grid_pack_kernel(const float* __restrict__ nHI, const float* __restrict__ T,
+                                 const float* __restrict__ vx, const float* __restrict__ vy,
+                                 const float* __restrict__ vz, const float* __restrict__ dust, int64_t n,
+                                 double cell_cm, GridCell* __restrict__ out, double* __restrict__ w) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+    const double Tc = (double)T[c];
+    const double rT = 1.0 / sqrt(Tc);
+    const double nh = (double)nHI[c];
+    GridCell g;
+    g.kap0 = (float)(nh * THOR_SIG1 * rT * cell_cm);
+    g.a = (float)(THOR_A1 * rT);
+    g.vth = (float)(THOR_VTH1 * sqrt(Tc));
+    g.inv_vth = (float)(1.0 / (THOR_VTH1 * sqrt(Tc)));
+    g.vx = vx[c]; g.vy = vy[c]; g.vz = vz[c];
+    g.kd = dust ? (float)((double)dust[c] * cell_cm) : 0.0f;
+    out[c] = g;
+    w[c] = nh * nh;
+  }
+}
+
+// ---- inclusive FP64 prefix sum (three passes) -------------------------------------
+constexpr int kScanBlock = 1024;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanBlock * kScanItems;
+
+__device__ __forceinline__ double block_exclusive_scan(double v, double* sh, double& total) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  double x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double y = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    double s = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0.0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double y = __shfl_up_sync(kFull, s, o);
+      if (lane >= o) s += y;
+    }
+    sh[lane] = s;
+  }
+  __syncthreads();
+  const double warp_off = (wid > 0) ? sh[wid - 1] : 0.0;
+  total = sh[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return warp_off + x - v;
+}
+
+__global__ void __launch_bounds__(kScanBlock) scan_tiles(double* data, int64_t n, double* tile_sums, int64_t off) {
+  __shared__ double sh[32];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  double loc[kScanItems];
+  double s = 0.0;
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    const int64_t i = base + j;
+    loc[j] = (i < n) ? data[i] : 0.0;
+    s += loc[j];
+  }
+  double total;
+  double pre = block_exclusive_scan(s, sh, total);
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    pre += loc[j];
+    const int64_t i = base + j;
+    if (i < n) data[i] = pre;
+  }
+  if (threadIdx.x == 0 && tile_sums) tile_sums[blockIdx.x + off] = total;
+}
+
+__global__ void add_offsets(double* data, int64_t n, const double* tile_pre) {
+  const int64_t t = blockIdx.x;
+  if (t == 0) return;
+  const double o = tile_pre[t - 1];
+  const int64_t base = t * kScanTile;
+  for (int j = threadIdx.x; j < kScanTile; j += blockDim.x) {
+    const int64_t i = base + j;
+    if (i < n) data[i] += o;
+  }
+}
+
+// ---- photon loop ------------------------------------------------------------------
+struct GPhoton {
+  double p[3];  // position in cell units
+  float3 k;
+  float X;
+  uint32_t nscat, ndust, iters, steps;
+  Rng rng;
+  unsigned long long pid;
+};
+
+__device__ __forceinline__ GridCell load_cell(const GridCell* __restrict__ cells, int64_t c) {
+  const float4* q = reinterpret_cast<const float4*>(cells + c);
+  const float4 a = __ldg(q), b = __ldg(q + 1);
+  GridCell g;
+  g.kap0 = a.x; g.a = a.y; g.inv_vth = a.z; g.vth = a.w;
+  g.vx = b.x; g.vy = b.y; g.vz = b.z; g.kd = b.w;
+  return g;
+}
+
+__device__ __forceinline__ int64_t cell_index(const GridModel& m, int ix, int iy, int iz) {
+  return (int64_t)ix + (int64_t)m.nx * ((int64_t)iy + (int64_t)m.ny * iz);
+}
+
+// Optical depth from p to the box face along +axis at lab frequency Xp (Sec. 3.4.1),
+// cell by cell, stopping once tau > tau_cut.
+__device__ float peel_tau(const GridModel& m, const double p[3], int axis, float Xp, const float* Ktab,
+                          uint32_t& ncell) {
+  int i[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) i[a] = (int)floor(p[a]);
+  const int n_ax = (axis == 0) ? m.nx : (axis == 1) ? m.ny : m.nz;
+  double t = 0.0;
+  float tau = 0.0f;
+  while (i[axis] < n_ax) {
+    const double tn = __dadd_rn((double)(i[axis] + 1), -p[axis]);
+    const GridCell g = load_cell(m.cells, cell_index(m, i[0], i[1], i[2]));
+    const float v = (axis == 0) ? g.vx : (axis == 1) ? g.vy : g.vz;
+    const float x = (Xp - v) * g.inv_vth;
+    tau = __fmaf_rn(__fmaf_rn(g.kap0, voigt<false>(g.a, x, Ktab), g.kd), (float)(tn - t), tau);
+    ++ncell;
+    if (tau > m.tau_cut) break;
+    t = tn;
+    i[axis] += 1;
+  }
+  return tau;
+}
+
+__device__ __forceinline__ void deposit(const GridModel& m, const double p[3], int axis, float Xp, float wgt) {
+  const float f = (Xp - m.pX_min) * m.pinv_dX;
+  if (!(f >= 0.0f) || f >= (float)m.peel_bins) return;
+  const int b = (int)f;
+  const int a1 = (axis + 1) % 3, a2 = (axis + 2) % 3;
+  const int n1 = (a1 == 0) ? m.nx : (a1 == 1) ? m.ny : m.nz;
+  const int n2 = (a2 == 0) ? m.nx : (a2 == 1) ? m.ny : m.nz;
+  const int ix = (int)floor(p[a1]) / (n1 / m.img_n), iy = (int)floor(p[a2]) / (n2 / m.img_n);
+  if (ix < 0 || iy < 0 || ix >= m.img_n || iy >= m.img_n) return;
+  atomicAdd(&m.cube[(((size_t)axis * m.img_n + iy) * m.img_n + ix) * m.peel_bins + b], wgt);
+}
+
+// Emission (Sec. 2.1, 3.4): cell with probability n_HI^2 / sum, uniform position in it,
+// isotropic direction, thermal x ~ N(0, 1/2) in the cell frame; peel at emission.
+__device__ void grid_emit(const GridModel& m, GPhoton& ph, const float* Ktab, uint32_t& pr, uint32_t& pc) {
+  ph.rng.init(((uint64_t)m.seed_hi << 32) | m.seed_lo, ph.pid);
+  const int64_t n = (int64_t)m.nx * m.ny * m.nz;
+  const double total = m.cdf[n - 1];
+  const double R = (double)ph.rng.uni() * total;
+  int64_t lo = 0, hi = n - 1;  // smallest c with cdf[c] > R
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (m.cdf[mid] > R) hi = mid; else lo = mid + 1;
+  }
+  const int64_t c = lo;
+  const int ix = (int)(c % m.nx), iy = (int)((c / m.nx) % m.ny), iz = (int)(c / ((int64_t)m.nx * m.ny));
+  ph.p[0] = ix + (double)ph.rng.uni();
+  ph.p[1] = iy + (double)ph.rng.uni();
+  ph.p[2] = iz + (double)ph.rng.uni();
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {  // a uniform of exactly 1.0 would land on the next cell's face
+    const double lim = (a == 0 ? ix : a == 1 ? iy : iz) + 1.0;
+    if (ph.p[a] >= lim) ph.p[a] = nextafter(lim, 0.0);
+  }
+  ph.k = iso_dir(ph.rng);
+  const float R1 = ph.rng.uni(), R2 = ph.rng.uni();
+  const float xe = sqrtf(-__logf(R1)) * cospif(2.0f * R2);
+  const GridCell g = load_cell(m.cells, c);
+  ph.X = __fmaf_rn(xe, g.vth, g.vx * ph.k.x + g.vy * ph.k.y + g.vz * ph.k.z);
+  ph.nscat = 0; ph.ndust = 0; ph.iters = 0; ph.steps = 0;
+  if (m.peel) {
+    const float vv[3] = {g.vx, g.vy, g.vz};
+#pragma unroll 1
+    for (int ax = 0; ax < 3; ++ax) {
+      const float Xp = __fmaf_rn(xe, g.vth, vv[ax]);
+      const float tau = peel_tau(m, ph.p, ax, Xp, Ktab, pc);
+      ++pr;
+      deposit(m, ph.p, ax, Xp, __expf(-tau) * (0.25f / kPiF));
+    }
+  }
+}
+
+// One event; returns 0 continue, 1 escaped, 2 absorbed, 3 capped.
+__device__ int grid_event(const GridModel& m, GPhoton& ph, const float* Ktab, uint32_t& pr, uint32_t& pc) {
+  float tau_rem = -__logf(ph.rng.uni());
+  Dda w;
+  w.init(ph.p[0], ph.p[1], ph.p[2], (double)ph.k.x, (double)ph.k.y, (double)ph.k.z);
+  GridCell g;
+  float x = 0.0f, kH = 0.0f;
+  for (;;) {
+    if (!w.inside(m.nx, m.ny, m.nz)) return 1;
+    double tn;
+    const int ax = w.next_axis(tn);
+    g = load_cell(m.cells, cell_index(m, w.i[0], w.i[1], w.i[2]));
+    x = (ph.X - (g.vx * ph.k.x + g.vy * ph.k.y + g.vz * ph.k.z)) * g.inv_vth;
+    kH = g.kap0 * voigt<false>(g.a, x, Ktab);
+    const float kt = kH + g.kd;
+    const float dt = (float)(tn - w.t);
+    const float dtau = kt * dt;
+    ++ph.steps;
+    if (dtau >= tau_rem && kt > 0.0f) {
+      const double ts = w.t + (double)(tau_rem / kt);
+      const double kk[3] = {(double)ph.k.x, (double)ph.k.y, (double)ph.k.z};
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const double lo = (double)w.i[a], hi = nextafter((double)(w.i[a] + 1), lo);
+        ph.p[a] = fmin(fmax(ph.p[a] + ts * kk[a], lo), hi);
+      }
+      break;
+    }
+    tau_rem -= dtau;
+    w.advance(ax, tn);
+  }
+  const float vv[3] = {g.vx, g.vy, g.vz};
+  const float vk_in = g.vx * ph.k.x + g.vy * ph.k.y + g.vz * ph.k.z;
+  bool dust = false;
+  if (g.kd > 0.0f) dust = ph.rng.uni() >= kH / (kH + g.kd);
+  if (dust) {
+    bool scat;
+    if (m.albedo <= 0.0f) scat = false;
+    else if (m.albedo >= 1.0f) scat = true;
+    else scat = ph.rng.uni() < m.albedo;
+    if (!scat) return 2;
+    if (m.peel) {
+      const float kin[3] = {ph.k.x, ph.k.y, ph.k.z};
+#pragma unroll 1
+      for (int ax = 0; ax < 3; ++ax) {
+        const float Xp = ph.X + vv[ax] - vk_in;
+        const float tau = peel_tau(m, ph.p, ax, Xp, Ktab, pc);
+        ++pr;
+        deposit(m, ph.p, ax, Xp, P_hg(kin[ax], m.g_hg) * (0.5f / kPiF) * __expf(-tau));
+      }
+    }
+    scatter_dust(m.g_hg, ph.k, ph.rng);
+    ph.X += (g.vx * ph.k.x + g.vy * ph.k.y + g.vz * ph.k.z) - vk_in;
+    ++ph.ndust;
+    return 0;
+  }
+  const float kin[3] = {ph.k.x, ph.k.y, ph.k.z};
+  AtomFrame af;
+  const float xo = scatter_resonant(x, g.a, m.phase, ph.k, ph.rng, ph.iters, &af);
+  if (m.peel) {
+    const float e1[3] = {af.e1.x, af.e1.y, af.e1.z}, e2[3] = {af.e2.x, af.e2.y, af.e2.z};
+#pragma unroll 1
+    for (int ax = 0; ax < 3; ++ax) {
+      const float mu = kin[ax];
+      const float xp = x - af.upar + __fmaf_rn(af.upar, mu, __fmaf_rn(af.u1, e1[ax], af.u2 * e2[ax]));
+      const float Xp = __fmaf_rn(xp, g.vth, vv[ax]);
+      float P;
+      if (m.phase == PH_ISO) P = 0.5f;
+      else if (m.phase == PH_DIPOLE) P = P_dipole(mu);
+      else P = af.core ? (0.5f / 3.0f + 2.0f * P_dipole(mu) / 3.0f) : P_dipole(mu);
+      const float tau = peel_tau(m, ph.p, ax, Xp, Ktab, pc);
+      ++pr;
+      deposit(m, ph.p, ax, Xp, P * (0.5f / kPiF) * __expf(-tau));
+    }
+  }
+  ph.X = __fmaf_rn(xo, g.vth, g.vx * ph.k.x + g.vy * ph.k.y + g.vz * ph.k.z);
+  ++ph.nscat;
+  if (m.max_scat && ph.nscat >= m.max_scat) return 3;
+  return 0;
+}
+
+__device__ __forceinline__ unsigned long long wsum(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+  return v;
+}
+__device__ __forceinline__ double wsum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(256) grid_run_kernel(GridModel m, WorkQueue q, const float* __restrict__ gK) {
+  __shared__ __align__(16) float sK[THOR_VOIGT_NINT * THOR_VOIGT_NCOEF];
+  load_ktab(sK, gK);
+  const unsigned lane = threadIdx.x & 31u;
+  GPhoton ph;
+  bool active = false, done = false;
+  unsigned long long esc = 0, ab = 0, cap = 0, sc = 0, du = 0, it = 0, stp = 0, dn = 0;
+  double sc2 = 0.0;
+  uint32_t pr = 0, pc = 0;
+  for (;;) {
+    const unsigned need = __ballot_sync(kFull, !active && !done);
+    if (need) {
+      const int leader = __ffs(need) - 1;
+      unsigned long long base = 0;
+      if ((int)lane == leader) base = atomicAdd(q.next, (unsigned long long)__popc(need));
+      base = __shfl_sync(kFull, base, leader);
+      if (!active && !done) {
+        const unsigned long long g = base + __popc(need & ((1u << lane) - 1u));
+        if (g < q.total) {
+          ph.pid = q.first_id[0] + g;
+          grid_emit(m, ph, sK, pr, pc);
+          active = true;
+        } else {
+          done = true;
+        }
+      }
+    }
+    if (__all_sync(kFull, !active)) break;
+    if (active) {
+      const int st = grid_event(m, ph, sK, pr, pc);
+      if (st) {
+        if (st == 1) {
+          ++esc;
+          const float f = (ph.X - m.X_min) * m.inv_dX;
+          int bin = !(f >= 0.0f) ? m.n_bins : (f >= (float)m.n_bins ? m.n_bins + 1 : (int)f);
+          atomicAdd(&m.spectrum[bin], 1ull);
+        } else if (st == 2) ++ab;
+        else ++cap;
+        sc += ph.nscat; du += ph.ndust; it += ph.iters; stp += ph.steps; ++dn;
+        sc2 += (double)ph.nscat * (double)ph.nscat;
+        active = false;
+      }
+    }
+  }
+  esc = wsum(esc); ab = wsum(ab); cap = wsum(cap); sc = wsum(sc); du = wsum(du); it = wsum(it);
+  stp = wsum(stp); dn = wsum(dn); sc2 = wsum(sc2);
+  const unsigned long long prs = wsum((unsigned long long)pr), pcs = wsum((unsigned long long)pc);
+  if (lane == 0 && (dn || prs)) {
+    Tally* T = m.tally;
+    atomicAdd(&T->n_escaped, esc); atomicAdd(&T->n_absorbed, ab); atomicAdd(&T->n_capped, cap);
+    atomicAdd(&T->n_scat, sc); atomicAdd(&T->n_dust_scat, du); atomicAdd(&T->n_upar_iters, it);
+    atomicAdd(&T->n_steps, stp); atomicAdd(&T->n_done, dn); atomicAdd(&T->sum_scat2, sc2);
+    if (m.peel_rays) { atomicAdd(m.peel_rays, prs); atomicAdd(m.peel_cells, pcs); }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_grid_pack(const float* nHI, const float* T, const float* vx, const float* vy, const float* vz,
+                             const float* dust, int64_t n, double cell_cm, GridCell* out, double* w,
+                             cudaStream_t s) {
+  const int block = 256;
+  const int64_t want = (n + block - 1) / block;
+  const int grid = (int)(want < 152 * 32 ? want : 152 * 32);
+  grid_pack_kernel<<<grid, block, 0, s>>>(nHI, T, vx, vy, vz, dust, n, cell_cm, out, w);
+  return cudaGetLastError();
+}
+
+size_t scan_f64_scratch(int64_t n) {
+  const int64_t tiles = (n + kScanTile - 1) / kScanTile;
+  return (size_t)(tiles + 1) * sizeof(double);
+}
+
+// Inclusive prefix sum in place.  Tile sums are scanned with the same kernel, one
+// tile at a time (a tile covers 8192 entries, so 8192 tiles = 67M cells per pass).
+cudaError_t launch_scan_f64(double* data, int64_t n, double* scratch, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t tiles = (n + kScanTile - 1) / kScanTile;
+  scan_tiles<<<(unsigned)tiles, kScanBlock, 0, s>>>(data, n, scratch, 0);
+  if (tiles > 1) {
+    if (tiles > kScanTile) return cudaErrorInvalidValue;
+    scan_tiles<<<1, kScanBlock, 0, s>>>(scratch, tiles, nullptr, 0);
+    add_offsets<<<(unsigned)tiles, 256, 0, s>>>(data, n, scratch);
+  }
+  return cudaGetLastError();
+}
+
+int grid_grid(int block, int blocks_per_sm) {
+  int dev = 0, sms = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, grid_run_kernel, block, 0);
+  if (occ < 1) occ = 1;
+  const int b = (blocks_per_sm > 0 && blocks_per_sm < occ) ? blocks_per_sm : occ;
+  return sms * b;
+}
+
+cudaError_t launch_grid_run(GridModel m, WorkQueue q, const float* d_ktab, int grid, int block, cudaStream_t s) {
+  grid_run_kernel<<<grid, block, 0, s>>>(m, q, d_ktab);
+  return cudaGetLastError();
+}
+
+}  // namespace thor

@@ -1,0 +1,128 @@
+// thor_internal.h -- plain structs shared by the host runtime and the kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace thor {
+
+// Per-model tallies (device, 8-byte aligned).  Integer fields are exact and
+// independent of the order in which photons finish.
+struct Tally {
+  unsigned long long n_escaped, n_absorbed, n_capped, n_done;
+  unsigned long long n_scat, n_dust_scat, n_upar_iters, n_steps;
+  double sum_scat2;
+  double pad[3];
+};
+
+// Gridless model (Sec. 3.3 spherical shell / sphere) as the kernels read it.
+struct ShellModel {
+  double R_in, R_out;        // radii (R_out normalises lengths)
+  float kap0;                // HI line-centre opacity per unit length
+  float kapd;                // dust extinction per unit length
+  float vth, inv_vth, a;     // km/s, s/km, Voigt parameter
+  float vgrad;               // km/s per unit length (homologous v = vgrad r)
+  float gam;                 // |dx/ds| = vgrad / vth
+  float ds_core;             // sub-step length (step limiter, Sec. 4.1: f l_v)
+  float albedo, g_hg;
+  int32_t phase;
+  int32_t line;              // 0 delta, 1 Gaussian
+  float X0, sigma;           // source line (km/s)
+  float X_min, inv_dX;       // spectrum binning
+  int32_t n_bins;
+  uint32_t seed_lo, seed_hi;
+  uint32_t max_scat;         // 0 = none
+  unsigned long long* spectrum;  // n_bins + 2
+  Tally* tally;
+  float* raw_X;              // optional per-photon outputs (indexed by photon id - id_base)
+  uint32_t* raw_nscat;
+  uint8_t* raw_status;
+  unsigned long long id_base;
+  unsigned long long n_photons;
+};
+
+// Photon work queue: photon g in [0, total) belongs to model m with
+// prefix[m] <= g < prefix[m+1] and has id first_id[m] + g - prefix[m].
+struct WorkQueue {
+  unsigned long long* next;          // device counter
+  unsigned long long total;
+  const unsigned long long* prefix;  // n_models + 1
+  const unsigned long long* first_id;
+  const int32_t* model;              // model table index per queue entry
+  int32_t n_entries;
+};
+
+// Resident packet state for time-sliced (served) execution, SoA, one slot per thread.
+struct SlotState {
+  double *px, *py, *pz;
+  float *kx, *ky, *kz, *X;
+  uint32_t *blk_lo, *blk_hi, *left;   // RNG position
+  uint32_t *nscat, *ndust, *iters, *steps;
+  int32_t* model;                    // -1 = empty
+  unsigned long long* pid;
+  uint8_t* region;
+  int64_t n_slots;
+};
+
+// Grid model (Sec. 3.3 uniform Cartesian grid), packed 32 B per cell.
+struct GridCell {
+  float kap0;   // n_HI sigma_0(T) L_cell: HI line-centre opacity per cell length
+  float a;      // Voigt parameter
+  float inv_vth;
+  float vth;
+  float vx, vy, vz;  // km/s
+  float kd;     // dust extinction per cell length
+};
+
+struct GridModel {
+  const GridCell* cells;
+  const double* cdf;      // emission CDF over cells (n_HI^2), last entry = total
+  int32_t nx, ny, nz;
+  int32_t phase;
+  float albedo, g_hg;
+  float X_min, inv_dX;    // escaped spectrum
+  int32_t n_bins;
+  int32_t peel;           // 0/1
+  int32_t img_n;          // pixels per image axis
+  int32_t peel_bins;
+  float pX_min, pinv_dX;
+  float tau_cut;
+  uint32_t max_scat;
+  uint32_t seed_lo, seed_hi;
+  unsigned long long* spectrum;
+  float* cube;            // [3][img_n][img_n][peel_bins]
+  Tally* tally;
+  unsigned long long n_photons;
+  unsigned long long id_base;
+  unsigned long long* peel_rays;   // statistics: peel rays traced, cells visited
+  unsigned long long* peel_cells;
+};
+
+// ---- launchers (implemented in the .cu files) ------------------------------------
+int shell_grid(int block, int blocks_per_sm, bool sliced);  // persistent grid size
+int grid_grid(int block, int blocks_per_sm);
+cudaError_t launch_shell_run(const ShellModel* d_models, WorkQueue q, const float* d_ktab, int grid,
+                             int block, cudaStream_t s);
+cudaError_t launch_shell_slice(const ShellModel* d_models, WorkQueue q, SlotState st, uint32_t event_budget,
+                               const float* d_ktab, int grid, int block, cudaStream_t s);
+cudaError_t launch_grid_pack(const float* nHI, const float* T, const float* vx, const float* vy,
+                             const float* vz, const float* dust, int64_t n, double cell_cm, GridCell* out,
+                             double* w, cudaStream_t s);
+cudaError_t launch_scan_f64(double* data, int64_t n, double* scratch, cudaStream_t s);
+size_t scan_f64_scratch(int64_t n);
+cudaError_t launch_grid_run(GridModel m, WorkQueue q, const float* d_ktab, int grid, int block,
+                            cudaStream_t s);
+cudaError_t launch_forest(const float* nHI, const float* T, const float* vlos, int nx, int ny, int nz,
+                          int64_t first, int64_t count, double ds_cm, double dv_cell, int n_bins,
+                          double dv_bin, float* tau, const float* d_ktab, cudaStream_t s);
+cudaError_t launch_voigt_eval(const float* a, const float* x, float* H, int64_t n, const float* d_ktab,
+                              cudaStream_t s, int precise);
+cudaError_t launch_dda_trace(int nx, int ny, int nz, const double* org, const float* dir, int n, int max_steps,
+                             int64_t* cells, double* seg, int32_t* count, cudaStream_t s);
+cudaError_t launch_upar(float x, float a, uint64_t seed, int64_t n, float* out, unsigned long long* iters,
+                        cudaStream_t s);
+cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int n, cudaStream_t s);
+cudaError_t launch_scatter_once(float x, float a, int phase, uint64_t seed, int64_t n, float* x_out,
+                                float* mu_out, cudaStream_t s);
+
+}  // namespace thor

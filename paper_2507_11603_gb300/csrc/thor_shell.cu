@@ -1,0 +1,337 @@
+// thor_shell.cu -- photon-packet loop through gridless spherical shells (THOR
+// Sec. 3.3-3.4): emission, propagation with the velocity-gradient step limiter
+// (Sec. 4.1), interaction channel choice, resonant / dust scattering, escape tally.
+//
+// Execution model: persistent warps.  Every loop iteration is one event (draw tau,
+// propagate to the interaction or the boundary, interact) for every live lane;
+// lanes whose packet finished are refilled from the photon work queue with one
+// warp-aggregated atomic (ballot of the idle lanes), so a warp stays full until the
+// queue drains.  The packet state lives in registers; the time-sliced variant
+// additionally loads/stores it from a slot array between launches (serving).
+#include "thor_device.cuh"
+#include "thor_internal.h"
+
+namespace thor {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+struct Photon {
+  double px, py, pz;
+  float3 k;
+  float X;
+  int region;  // 1 = inside the empty cavity
+  uint32_t nscat, ndust, iters, steps;
+  Rng rng;
+  int model;
+  unsigned long long pid;
+};
+
+__device__ __forceinline__ int find_entry(const WorkQueue& q, unsigned long long g) {
+  int lo = 0, hi = q.n_entries - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (q.prefix[mid] <= g) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Emission (Sec. 3.4): central point source, isotropic, line profile in the source frame.
+__device__ __forceinline__ void shell_emit(const ShellModel& m, Photon& ph) {
+  ph.rng.init(((uint64_t)m.seed_hi << 32) | m.seed_lo, ph.pid);
+  ph.px = 0.0; ph.py = 0.0; ph.pz = 0.0;
+  ph.k = iso_dir(ph.rng);
+  float X = m.X0;
+  if (m.line == 1) {
+    const float R1 = ph.rng.uni(), R2 = ph.rng.uni();
+    X = __fmaf_rn(m.sigma * sqrtf(-2.0f * __logf(R1)), cospif(2.0f * R2), X);
+  }
+  ph.X = X;
+  ph.region = (m.R_in > 0.0) ? 1 : 0;
+  ph.nscat = 0; ph.ndust = 0; ph.iters = 0; ph.steps = 0;
+}
+
+// One event.  Returns 0 = continues, 1 = escaped, 2 = absorbed by dust, 3 = capped.
+__device__ int shell_event(const ShellModel& m, Photon& ph, const float* __restrict__ Ktab) {
+  float tau_rem = -__logf(ph.rng.uni());  // Eq. 3: tau ~ Exp(1)
+  const double kx = ph.k.x, ky = ph.k.y, kz = ph.k.z;
+  float x_site = 0.0f;
+  for (;;) {
+    if (ph.region) {  // empty cavity: straight to the inner sphere
+      const double b = ph.px * kx + ph.py * ky + ph.pz * kz;
+      const double c = ph.px * ph.px + ph.py * ph.py + ph.pz * ph.pz - m.R_in * m.R_in;
+      const double s = -b + sqrt(fmax(b * b - c, 0.0));
+      ph.px += s * kx; ph.py += s * ky; ph.pz += s * kz;
+      ph.region = 0;
+    }
+    const double b = ph.px * kx + ph.py * ky + ph.pz * kz;
+    const double pp = ph.px * ph.px + ph.py * ph.py + ph.pz * ph.pz;
+    double S = -b + sqrt(fmax(b * b - (pp - m.R_out * m.R_out), 0.0));
+    int next = 1;  // 1 escape, 2 cavity
+    if (m.R_in > 0.0 && b < 0.0) {
+      const double disc = b * b - (pp - m.R_in * m.R_in);
+      if (disc > 0.0) {
+        const double s_in = -b - sqrt(disc);
+        if (s_in < S) { S = s_in; next = 2; }
+      }
+    }
+    S = fmax(S, 0.0);
+    const float Sf = (float)S;
+    // gas-frame frequency at the segment start; along the ray x(s) = x0 - gam s
+    const float x0 = (ph.X - m.vgrad * (float)b) * m.inv_vth;
+    float s_star = -1.0f;
+    if (m.gam == 0.0f) {
+      const float kap = __fmaf_rn(m.kap0, voigt<false>(m.a, x0, Ktab), m.kapd);
+      const float dtau = kap * Sf;
+      ++ph.steps;
+      if (dtau >= tau_rem) s_star = fminf(tau_rem / kap, Sf);
+      else tau_rem -= dtau;
+    } else {
+      float s = 0.0f;
+      while (s < Sf) {
+        const float s1 = fminf(Sf, s + m.ds_core);
+        const float xm = x0 - m.gam * 0.5f * (s + s1);
+        const float kap = __fmaf_rn(m.kap0, voigt<false>(m.a, xm, Ktab), m.kapd);
+        const float dtau = kap * (s1 - s);
+        ++ph.steps;
+        if (dtau >= tau_rem) { s_star = fminf(s + tau_rem / kap, Sf); break; }
+        tau_rem -= dtau;
+        s = s1;
+      }
+    }
+    if (s_star >= 0.0f) {
+      const double sd = s_star;
+      ph.px += sd * kx; ph.py += sd * ky; ph.pz += sd * kz;
+      x_site = x0 - m.gam * s_star;
+      break;
+    }
+    ph.px += S * kx; ph.py += S * ky; ph.pz += S * kz;
+    if (next == 1) return 1;
+    ph.region = 1;
+  }
+  // Interaction (Sec. 3.4): channel i with probability tau_i / sum_i tau_i.
+  const float3 v = make_float3(m.vgrad * (float)ph.px, m.vgrad * (float)ph.py, m.vgrad * (float)ph.pz);
+  const float kH = m.kap0 * voigt<false>(m.a, x_site, Ktab);
+  bool dust = false;
+  if (m.kapd > 0.0f) dust = ph.rng.uni() >= kH / (kH + m.kapd);
+  const float vk_in = v.x * ph.k.x + v.y * ph.k.y + v.z * ph.k.z;
+  if (dust) {
+    bool scat;
+    if (m.albedo <= 0.0f) scat = false;
+    else if (m.albedo >= 1.0f) scat = true;
+    else scat = ph.rng.uni() < m.albedo;
+    if (!scat) return 2;
+    scatter_dust(m.g_hg, ph.k, ph.rng);
+    ph.X += (v.x * ph.k.x + v.y * ph.k.y + v.z * ph.k.z) - vk_in;
+    ++ph.ndust;
+    return 0;
+  }
+  const float xo = scatter_resonant(x_site, m.a, m.phase, ph.k, ph.rng, ph.iters, nullptr);
+  ph.X = __fmaf_rn(xo, m.vth, v.x * ph.k.x + v.y * ph.k.y + v.z * ph.k.z);
+  ++ph.nscat;
+  if (m.max_scat && ph.nscat >= m.max_scat) return 3;
+  return 0;
+}
+
+__device__ __forceinline__ void tally_spectrum(const ShellModel& m, float X) {
+  int bin;
+  const float f = (X - m.X_min) * m.inv_dX;
+  if (!(f >= 0.0f)) bin = m.n_bins;
+  else if (f >= (float)m.n_bins) bin = m.n_bins + 1;
+  else bin = (int)f;
+  atomicAdd(&m.spectrum[bin], 1ull);
+}
+
+__device__ __forceinline__ void write_raw(const ShellModel& m, const Photon& ph, int status) {
+  if (m.raw_X) {
+    const unsigned long long j = ph.pid - m.id_base;
+    m.raw_X[j] = ph.X;
+    m.raw_nscat[j] = ph.nscat;
+    m.raw_status[j] = (uint8_t)status;
+  }
+}
+
+// Per-photon tally with global atomics (used where lanes may belong to different models).
+__device__ __forceinline__ void finish_global(const ShellModel& m, const Photon& ph, int status) {
+  Tally* T = m.tally;
+  if (status == 1) { atomicAdd(&T->n_escaped, 1ull); tally_spectrum(m, ph.X); }
+  else if (status == 2) atomicAdd(&T->n_absorbed, 1ull);
+  else atomicAdd(&T->n_capped, 1ull);
+  atomicAdd(&T->n_scat, (unsigned long long)ph.nscat);
+  atomicAdd(&T->n_dust_scat, (unsigned long long)ph.ndust);
+  atomicAdd(&T->n_upar_iters, (unsigned long long)ph.iters);
+  atomicAdd(&T->n_steps, (unsigned long long)ph.steps);
+  atomicAdd(&T->sum_scat2, (double)ph.nscat * (double)ph.nscat);
+  atomicAdd(&T->n_done, 1ull);
+  write_raw(m, ph, status);
+}
+
+struct LaneTally {
+  unsigned long long esc = 0, abs = 0, cap = 0, scat = 0, dust = 0, iters = 0, steps = 0, done = 0;
+  double scat2 = 0.0;
+};
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+  return v;
+}
+
+// Run-to-completion: all queue entries belong to one model (thor_run).
+__global__ void __launch_bounds__(256) shell_run_kernel(const ShellModel* __restrict__ models, WorkQueue q,
+                                                        const float* __restrict__ gK) {
+  __shared__ __align__(16) float sK[THOR_VOIGT_NINT * THOR_VOIGT_NCOEF];
+  __shared__ ShellModel sm;
+  load_ktab(sK, gK);
+  if (threadIdx.x == 0) sm = models[q.model[0]];
+  __syncthreads();
+  const ShellModel& m = sm;
+  const unsigned lane = threadIdx.x & 31u;
+  Photon ph;
+  bool active = false, done = false;
+  LaneTally lt;
+  for (;;) {
+    const unsigned need = __ballot_sync(kFull, !active && !done);
+    if (need) {
+      const int leader = __ffs(need) - 1;
+      unsigned long long base = 0;
+      if ((int)lane == leader) base = atomicAdd(q.next, (unsigned long long)__popc(need));
+      base = __shfl_sync(kFull, base, leader);
+      if (!active && !done) {
+        const unsigned long long g = base + __popc(need & ((1u << lane) - 1u));
+        if (g < q.total) {
+          ph.model = q.model[0];
+          ph.pid = q.first_id[0] + g;
+          shell_emit(m, ph);
+          active = true;
+        } else {
+          done = true;
+        }
+      }
+    }
+    if (__all_sync(kFull, !active)) break;
+    if (active) {
+      const int st = shell_event(m, ph, sK);
+      if (st) {
+        if (st == 1) { ++lt.esc; tally_spectrum(m, ph.X); }
+        else if (st == 2) ++lt.abs;
+        else ++lt.cap;
+        lt.scat += ph.nscat; lt.dust += ph.ndust; lt.iters += ph.iters; lt.steps += ph.steps; ++lt.done;
+        lt.scat2 += (double)ph.nscat * (double)ph.nscat;
+        write_raw(m, ph, st);
+        active = false;
+      }
+    }
+  }
+  // flush lane tallies: warp reduce, one atomic per warp and field
+  const unsigned long long e = warp_sum(lt.esc), a = warp_sum(lt.abs), c = warp_sum(lt.cap),
+                           s = warp_sum(lt.scat), d = warp_sum(lt.dust), it = warp_sum(lt.iters),
+                           sp = warp_sum(lt.steps), dn = warp_sum(lt.done);
+  const double s2 = warp_sum(lt.scat2);
+  if (lane == 0 && dn) {
+    Tally* T = m.tally;
+    atomicAdd(&T->n_escaped, e); atomicAdd(&T->n_absorbed, a); atomicAdd(&T->n_capped, c);
+    atomicAdd(&T->n_scat, s); atomicAdd(&T->n_dust_scat, d); atomicAdd(&T->n_upar_iters, it);
+    atomicAdd(&T->n_steps, sp); atomicAdd(&T->n_done, dn); atomicAdd(&T->sum_scat2, s2);
+  }
+}
+
+// Time-sliced execution over resident slots (one per thread): resume the packet in the
+// slot, run at most `budget` events per lane, refill finished lanes from the queue of
+// admitted requests, and save what is still in flight.
+__global__ void __launch_bounds__(256) shell_slice_kernel(const ShellModel* __restrict__ models, WorkQueue q,
+                                                          SlotState st, uint32_t budget,
+                                                          const float* __restrict__ gK) {
+  __shared__ __align__(16) float sK[THOR_VOIGT_NINT * THOR_VOIGT_NCOEF];
+  load_ktab(sK, gK);
+  const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool has_slot = slot < st.n_slots;
+  const unsigned lane = threadIdx.x & 31u;
+  Photon ph;
+  bool active = false, done = false;
+  if (has_slot && st.model[slot] >= 0) {
+    ph.model = st.model[slot];
+    const ShellModel& m = models[ph.model];
+    ph.pid = st.pid[slot];
+    ph.rng.init(((uint64_t)m.seed_hi << 32) | m.seed_lo, ph.pid);
+    ph.rng.blk_lo = st.blk_lo[slot]; ph.rng.blk_hi = st.blk_hi[slot];
+    ph.rng.resume(st.left[slot]);
+    ph.px = st.px[slot]; ph.py = st.py[slot]; ph.pz = st.pz[slot];
+    ph.k = make_float3(st.kx[slot], st.ky[slot], st.kz[slot]);
+    ph.X = st.X[slot];
+    ph.region = st.region[slot];
+    ph.nscat = st.nscat[slot]; ph.ndust = st.ndust[slot]; ph.iters = st.iters[slot]; ph.steps = st.steps[slot];
+    active = true;
+  }
+  if (!has_slot) done = true;
+  for (uint32_t ev = 0; ev < budget; ++ev) {
+    const unsigned need = __ballot_sync(kFull, !active && !done);
+    if (need) {
+      const int leader = __ffs(need) - 1;
+      unsigned long long base = 0;
+      if ((int)lane == leader) base = atomicAdd(q.next, (unsigned long long)__popc(need));
+      base = __shfl_sync(kFull, base, leader);
+      if (!active && !done) {
+        const unsigned long long g = base + __popc(need & ((1u << lane) - 1u));
+        if (g < q.total) {
+          const int e = find_entry(q, g);
+          ph.model = q.model[e];
+          ph.pid = q.first_id[e] + (g - q.prefix[e]);
+          shell_emit(models[ph.model], ph);
+          active = true;
+        } else {
+          done = true;
+        }
+      }
+    }
+    if (__all_sync(kFull, !active)) break;
+    if (active) {
+      const ShellModel& m = models[ph.model];
+      const int s = shell_event(m, ph, sK);
+      if (s) { finish_global(m, ph, s); active = false; }
+    }
+  }
+  if (!has_slot) return;
+  if (active) {
+    st.model[slot] = ph.model; st.pid[slot] = ph.pid;
+    st.blk_lo[slot] = ph.rng.blk_lo; st.blk_hi[slot] = ph.rng.blk_hi; st.left[slot] = ph.rng.left;
+    st.px[slot] = ph.px; st.py[slot] = ph.py; st.pz[slot] = ph.pz;
+    st.kx[slot] = ph.k.x; st.ky[slot] = ph.k.y; st.kz[slot] = ph.k.z;
+    st.X[slot] = ph.X; st.region[slot] = (uint8_t)ph.region;
+    st.nscat[slot] = ph.nscat; st.ndust[slot] = ph.ndust; st.iters[slot] = ph.iters; st.steps[slot] = ph.steps;
+  } else {
+    st.model[slot] = -1;
+  }
+}
+
+}  // namespace
+
+int shell_grid(int block, int blocks_per_sm, bool sliced) {
+  int dev = 0, sms = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (sliced) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, shell_slice_kernel, block, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, shell_run_kernel, block, 0);
+  if (occ < 1) occ = 1;
+  const int b = (blocks_per_sm > 0 && blocks_per_sm < occ) ? blocks_per_sm : occ;
+  return sms * b;
+}
+
+cudaError_t launch_shell_run(const ShellModel* d_models, WorkQueue q, const float* d_ktab, int grid, int block,
+                             cudaStream_t s) {
+  shell_run_kernel<<<grid, block, 0, s>>>(d_models, q, d_ktab);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shell_slice(const ShellModel* d_models, WorkQueue q, SlotState st, uint32_t budget,
+                               const float* d_ktab, int grid, int block, cudaStream_t s) {
+  shell_slice_kernel<<<grid, block, 0, s>>>(d_models, q, st, budget, d_ktab);
+  return cudaGetLastError();
+}
+
+}  // namespace thor

@@ -1,0 +1,65 @@
+"""The C-ABI library builds, loads and exports every symbol include/thor.h declares;
+the product path never reaches the oracle.  CPU only (no compute calls)."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "thor.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(thor_\w+)\s*\(", src)))
+
+
+def test_header_declarations_match_binding():
+    from paper_2507_11603_gb300 import thor
+    assert _declared() == sorted(thor.SYMBOLS)
+
+
+def test_library_builds_and_exports_symbols():
+    import ctypes
+    from paper_2507_11603_gb300 import _build
+    lib = _build.build()
+    L = ctypes.CDLL(lib)
+    for name in _declared():
+        assert hasattr(L, name), name
+
+
+def test_library_is_sm103a_only():
+    from paper_2507_11603_gb300 import _build
+    assert _build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_init_without_gpu_fails_cleanly():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2507_11603_gb300 import thor
+    with pytest.raises(thor.ThorError) as e:
+        thor.Context(0)
+    assert e.value.code == thor.ERR_DEVICE
+
+
+def test_product_never_imports_oracle():
+    pkg = os.path.join(ROOT, "paper_2507_11603_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, f
+                assert "thor_oracle" not in txt and "liboracle" not in txt, f
+    # and the oracle never reaches the product
+    for f in os.listdir(os.path.join(ROOT, "oracle")):
+        if f.endswith((".py", ".cpp")):
+            txt = open(os.path.join(ROOT, "oracle", f)).read()
+            assert "paper_2507_11603_gb300" not in txt and "thor_device" not in txt, f
+
+
+def test_line_params_host_function():
+    from paper_2507_11603_gb300 import thor
+    p = thor.line_params(1e4)
+    assert abs(p["vth_kms"] - 12.845) < 1e-3
+    assert abs(p["a"] - 4.718e-4) < 1e-6
