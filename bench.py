@@ -193,11 +193,12 @@ def run_shell_bench(args):
     ctx.set_stream(stream)
     geom = ctx.shell(**SHELL)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    base_id = rank * N_PHOTONS * (args.steps + args.warmup + 1)
+    from paper_2507_11603_gb300 import sharding
 
     def step(i, device_out=True):
-        return ctx.run(geom, n_photons=N_PHOTONS, seed=1, first_id=base_id + i * N_PHOTONS, device_out=device_out,
-                       **RUN)
+        # step i: the i-th block of world x 1e5 photon ids, rank r takes its own 1e5 (weak scaling)
+        first, n = sharding.photon_range(rank, world, N_PHOTONS, base=i * world * N_PHOTONS)
+        return ctx.run(geom, n_photons=n, seed=1, first_id=first, device_out=device_out, **RUN)
 
     for i in range(args.warmup):
         step(i)
@@ -269,6 +270,92 @@ def run_shell_bench(args):
         dist.destroy_process_group()
 
 
+def stream_bench(ctx, n_requests=256, seed=2, load=0.75, events_per_round=256, nhi_max=1e21, core_skip=True):
+    """Served shell-model stream (Sec. 5.1 parameter grid): requests with Poisson arrivals at
+    `load` x the measured batched capacity, continuous batching on the device.  Baseline:
+    the same requests one launch per model (thor_run), FIFO, with the same arrival times."""
+    from paper_2507_11603_gb300 import synth
+    reqs = synth.shell_stream(n_requests, seed=seed, nhi_max=nhi_max)
+    common = dict(R_in=0.9, phase="dipole", sigma=50.0, n_bins=400, X_min=-1500.0, X_max=1500.0,
+                  core_skip=core_skip)
+
+    def submit(srv, r):
+        return srv.submit(N_HI=r["N_HI"], T=r["T"], v_max=r["v_max"], tau_dust=r["tau_dust"],
+                          n_photons=r["n_photons"], seed=r["seed"], **common)
+
+    # 1) one launch per model, back to back: per-request device time and capacity
+    solo_ms, solo_scat = [], 0
+    t0 = time.perf_counter()
+    for r in reqs:
+        g = ctx.shell(R_in=0.9, N_HI=r["N_HI"], T=r["T"], v_max=r["v_max"], tau_dust=r["tau_dust"], phase="dipole",
+                      core_skip=core_skip)
+        t1 = time.perf_counter()
+        res = ctx.run(g, n_photons=r["n_photons"], seed=r["seed"], sigma=50.0, n_bins=400, X_min=-1500.0,
+                      X_max=1500.0)
+        solo_ms.append((time.perf_counter() - t1) * 1000.0)
+        solo_scat += res.stats["n_scat"]
+        g.close()
+    solo_total = time.perf_counter() - t0
+    # 2) batched capacity: all requests at t = 0
+    srv = ctx.server(max_requests=256, events_per_round=events_per_round)
+    t0 = time.perf_counter()
+    tickets = [submit(srv, r) for r in reqs]
+    burst = [srv.wait(t) for t in tickets]
+    burst_total = time.perf_counter() - t0
+    burst_scat = sum(b.stats["n_scat"] for b in burst)
+    capacity = n_requests / burst_total  # requests/s
+    # 3) Poisson stream at `load` x capacity, live
+    rate = load * capacity
+    rng = np.random.default_rng(seed + 1000)
+    arrivals = np.concatenate([[0.0], np.cumsum(rng.exponential(1.0 / rate, n_requests - 1))])
+    lat = np.zeros(n_requests)
+    done_at = np.zeros(n_requests)
+    t_start = time.perf_counter()
+    tick = []
+    for i, r in enumerate(reqs):
+        now = time.perf_counter() - t_start
+        if arrivals[i] > now:
+            time.sleep(arrivals[i] - now)
+        tick.append((i, submit(srv, r), time.perf_counter() - t_start))
+    scat = 0
+    for i, t, ts in tick:
+        res = srv.wait(t)
+        lat[i] = res.stats["elapsed_ms"]
+        done_at[i] = ts + lat[i] / 1000.0
+        scat += res.stats["n_scat"]
+    span = done_at.max()
+    stats = srv.stats()
+    srv.close()
+    # 4) the same arrivals served by one-launch-per-model in FIFO order
+    finish, fifo_lat = 0.0, []
+    for i in range(n_requests):
+        start = max(arrivals[i], finish)
+        finish = start + solo_ms[i] / 1000.0
+        fifo_lat.append((finish - arrivals[i]) * 1000.0)
+    fifo_lat = np.array(fifo_lat)
+    return {"requests": n_requests, "photons": int(sum(r["n_photons"] for r in reqs)),
+            "core_skip": core_skip, "N_HI_max": nhi_max, "load": load, "rate_per_s": rate,
+            "batched": {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                        "scatterings_per_s": scat / span, "burst_scatterings_per_s": burst_scat / burst_total,
+                        "rounds": stats["rounds"], "mean_resident": stats["mean_resident"]},
+            "one_launch_per_model": {"p50_ms": float(np.percentile(fifo_lat, 50)),
+                                     "p99_ms": float(np.percentile(fifo_lat, 99)),
+                                     "scatterings_per_s": solo_scat / solo_total}}
+
+
+def run_stream_bench(args):
+    import torch
+    from paper_2507_11603_gb300 import thor
+    ctx = thor.Context(0)
+    with ClockSampler(0) as clk:
+        s = stream_bench(ctx, n_requests=args.stream_requests, nhi_max=args.stream_nhi_max,
+                         core_skip=not args.no_core_skip)
+    print(json.dumps({"metric": METRIC, "value": s["batched"]["scatterings_per_s"], "unit": "scatterings/s",
+                      "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": "served shell-model stream"}, "stream": s, "clocks": clk.summary()}))
+    del torch
+
+
 def run_forest_bench(args):
     import torch
     from paper_2507_11603_gb300 import synth, thor
@@ -302,7 +389,10 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="shell", choices=["shell", "forest"])
+    ap.add_argument("--workload", default="shell", choices=["shell", "forest", "stream"])
+    ap.add_argument("--stream-requests", type=int, default=256)
+    ap.add_argument("--stream-nhi-max", type=float, default=1e21)
+    ap.add_argument("--no-core-skip", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
@@ -316,6 +406,8 @@ def main():
         run_reference(args)
     elif args.workload == "forest":
         run_forest_bench(args)
+    elif args.workload == "stream":
+        run_stream_bench(args)
     else:
         run_shell_bench(args)
 

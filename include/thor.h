@@ -91,7 +91,7 @@ typedef struct {
   double albedo;         /* dust albedo (Eq. 8); 0 = pure absorption */
   double g_hg;           /* Henyey-Greenstein asymmetry (Eq. 9) */
   int32_t phase;         /* THOR_PHASE_* for resonant scattering */
-  int32_t reserved;
+  int32_t core_skip;     /* 1: core-skipping, x_crit = 0.2 (a tau0)^(1/3) when a tau0 >= 1 (Sec. 3.4.2) */
   double step_dx;        /* step limiter f (Sec. 4.1): sub-step length f v_th / |dv/dr|; 0 -> 0.01 */
 } thor_shell_params;
 

@@ -45,7 +45,7 @@ class Line(C.Structure):
 
 class Shell(C.Structure):
     """Gridless geometry (Sec. 3.3): shell/sphere (geometry 0) or slab (geometry 1)."""
-    _fields_ = [("geometry", C.c_int32), ("phase", C.c_int32),
+    _fields_ = [("geometry", C.c_int32), ("phase", C.c_int32), ("core_skip", C.c_int32), ("pad", C.c_int32),
                 ("R_in", C.c_double), ("R_out", C.c_double), ("tau0", C.c_double),
                 ("T", C.c_double), ("v_max", C.c_double), ("tau_dust", C.c_double),
                 ("albedo", C.c_double), ("g_hg", C.c_double)]
@@ -201,9 +201,9 @@ PHASE = {"isotropic": 0, "dipole": 1, "mixed": 2}
 def run_shell(*, tau0, T, R_in=0.0, R_out=1.0, v_max=0.0, tau_dust=0.0, albedo=0.0, g_hg=0.73,
               phase="isotropic", geometry="shell", line="delta", X0=0.0, sigma=0.0,
               n_photons=1000, seed=0, first_id=0, n_bins=200, X_min=-500.0, X_max=500.0,
-              max_scat=0, n_threads=0, raw=False):
-    geo = Shell(0 if geometry == "shell" else 1, PHASE[phase], R_in, R_out, tau0, T, v_max,
-                tau_dust, albedo, g_hg)
+              max_scat=0, n_threads=0, raw=False, core_skip=False):
+    geo = Shell(0 if geometry == "shell" else 1, PHASE[phase], 1 if core_skip else 0, 0, R_in, R_out, tau0, T,
+                v_max, tau_dust, albedo, g_hg)
     src = Source(0 if line == "delta" else 1, 0, X0, sigma)
     counts = np.zeros(n_bins + 2, dtype=np.uint64)
     res = Result()

@@ -91,25 +91,29 @@ void philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t 
 }
 
 // Draw convention (shared by definition with the CUDA path, implemented separately):
-// one stream per photon packet; key = (seed low 32, seed high 32); counter =
-// (photon id low, photon id high, block index low, block index high).  Each Philox
-// call yields four 32-bit words consumed in order.  A uniform variate consumes one
-// word u and is (u + 1/2) 2^-32, in (0,1).
+// key = (seed low 32, seed high 32).  Photon p's emission is event 0 and its k-th
+// interaction event (draw of tau, propagation, interaction) is event k; the words of
+// event e are the Philox blocks with counter (p low, p high, e, j), j = 0, 1, 2, ...,
+// four 32-bit words per block, consumed in order; words left at the end of an event
+// are not used.  A uniform variate consumes one word u and is (u + 1/2) 2^-32.
 struct Stream {
   uint32_t key[2];
   uint32_t pid[2];
-  uint64_t block = 0;
+  uint32_t event = 0;
+  uint32_t sub = 0;
   uint32_t buf[4];
   int pos = 4;
-  Stream(uint64_t seed, uint64_t photon) {
+  Stream(uint64_t seed, uint64_t photon, uint32_t ev = 0) {
     key[0] = (uint32_t)seed; key[1] = (uint32_t)(seed >> 32);
     pid[0] = (uint32_t)photon; pid[1] = (uint32_t)(photon >> 32);
+    event = ev;
   }
+  void start_event(uint32_t e) { event = e; sub = 0; pos = 4; }
   uint32_t next() {
     if (pos == 4) {
-      uint32_t ctr[4] = {pid[0], pid[1], (uint32_t)block, (uint32_t)(block >> 32)};
+      uint32_t ctr[4] = {pid[0], pid[1], event, sub};
       philox4x32_10(ctr, key, buf);
-      ++block;
+      ++sub;
       pos = 0;
     }
     return buf[pos++];
@@ -378,10 +382,13 @@ double dot(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b
 struct AtomVel { double upar, u1, u2; double e1[3], e2[3]; bool core; };
 
 double scatter_HI(double x, double a, int phase, const double kin[3], Stream& rng,
-                  double kout[3], AtomVel* av, uint64_t* iters) {
+                  double kout[3], AtomVel* av, uint64_t* iters, double xcrit = 0.0) {
   double upar = sample_upar(x, a, rng, iters);
-  // u_perp: two N(0, 1/2) variates by Box-Muller (Eq. 5: f = exp(-u^2))
-  double r = std::sqrt(-std::log(rng.u()));
+  // u_perp: two N(0, 1/2) variates by Box-Muller (Eq. 5: f = exp(-u^2)).  Core-skipping
+  // (Sec. 3.4.2): for |x| < x_crit the perpendicular speed is drawn from the Gaussian
+  // left-truncated at x_crit, r = sqrt(x_crit^2 - ln R).
+  double xc = (std::fabs(x) < xcrit) ? xcrit : 0.0;
+  double r = std::sqrt(xc * xc - std::log(rng.u()));
   double ph = 2.0 * kPi * rng.u();
   double u1 = r * std::cos(ph), u2 = r * std::sin(ph);
   bool core = std::fabs(x - upar) < 0.2;  // atom-frame frequency (Sec. 2.3.1)
@@ -505,6 +512,8 @@ extern "C" void orc_scatter_once(double x_in, double a, int phase, uint64_t seed
 struct orc_shell {
   int32_t geometry;  // 0 shell/sphere, 1 slab
   int32_t phase;     // 0 isotropic, 1 dipole, 2 mixed core/wing
+  int32_t core_skip; // 1: core-skipping with x_crit = 0.2 (a tau0)^(1/3) when a tau0 >= 1 (Sec. 3.4.2)
+  int32_t pad;
   double R_in, R_out;
   double tau0;       // line-centre HI optical depth across the gas
   double T;          // K
@@ -532,7 +541,7 @@ namespace {
 
 struct ShellModel {
   int geometry, phase;
-  double R_in, R_out, kap0, kapd, vth, a, gam, vgrad, albedo, g;
+  double R_in, R_out, kap0, kapd, vth, a, gam, vgrad, albedo, g, xcrit;
 };
 
 ShellModel make_shell(const orc_shell& p) {
@@ -548,6 +557,8 @@ ShellModel make_shell(const orc_shell& p) {
   m.vgrad = p.v_max / p.R_out;      // km/s per unit length
   m.gam = m.vgrad / m.vth;          // |dx/ds| along a ray (shell); slab: times k_z^2
   m.albedo = p.albedo; m.g = p.g_hg;
+  const double at = m.a * p.tau0;
+  m.xcrit = (p.core_skip && at >= 1.0) ? 0.2 * std::cbrt(at) : 0.0;
   return m;
 }
 
@@ -586,7 +597,8 @@ void run_photon_shell(const ShellModel& m, const orc_source& src, uint64_t seed,
     X += src.sigma * std::sqrt(-2.0 * std::log(R1)) * std::cos(2.0 * kPi * R2);
   }
   bool in_cavity = (m.geometry == 0 && m.R_in > 0.0);
-  for (;;) {
+  for (uint32_t ev = 1;; ++ev) {
+    rng.start_event(ev);
     // draw the optical depth to the next interaction (Eq. 3): tau = -ln R
     double tau_rem = -std::log(rng.u());
     bool interact = false;
@@ -651,7 +663,7 @@ void run_photon_shell(const ShellModel& m, const orc_source& src, uint64_t seed,
       X = X + dot(v, kout) - dot(v, k);  // frequency unchanged in the gas (grain) frame
       out.ndust++;
     } else {
-      double xo = scatter_HI(x, m.a, m.phase, k, rng, kout, nullptr, &out.iters);
+      double xo = scatter_HI(x, m.a, m.phase, k, rng, kout, nullptr, &out.iters, m.xcrit);
       X = xo * m.vth + dot(v, kout);
       out.nscat++;
       if (out.nscat >= cap) { out.X = X; out.status = 3; return; }
@@ -947,7 +959,9 @@ extern "C" int orc_run_grid(const float* nHI, const float* T, const float* vx, c
     }
     uint64_t nscat = 0, ndust = 0, iters = 0;
     int status = 0;
+    uint32_t ev = 0;
     while (status == 0) {
+      rng.start_event(++ev);
       double tau_rem = -std::log(rng.u());
       DDA w; w.init(p, k);
       bool hit = false;

@@ -145,6 +145,8 @@ int thor::fill_shell_model(thor_ctx* ctx, const thor_shell_params* p, ShellModel
   m->albedo = (float)p->albedo;
   m->g_hg = (float)p->g_hg;
   m->phase = p->phase;
+  const double at = line_a(p->T) * tau0;
+  m->xcrit = (p->core_skip && at >= 1.0) ? (float)(0.2 * cbrt(at)) : 0.0f;
   return THOR_OK;
 }
 

@@ -41,8 +41,10 @@ __host__ __device__ inline double line_sigma0(double T) {
 
 // ------------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al. 2011, SC'11), written from the published definition.
-// Per-packet stream: key = seed (low, high); counter = (photon id low, photon id high,
-// block low, block high).  Words are consumed in order, four per block.
+// Draw convention: key = seed (low, high).  Photon p's emission is event 0, its k-th
+// interaction event is event k; the words of event e are the blocks with counter
+// (p low, p high, e, j), j = 0, 1, 2, ..., consumed in order (4 words per block);
+// words left at the end of an event are not used.
 // ------------------------------------------------------------------------------
 __device__ __forceinline__ void philox10(uint32_t& c0, uint32_t& c1, uint32_t& c2, uint32_t& c3,
                                          uint32_t k0, uint32_t k1) {
@@ -56,26 +58,55 @@ __device__ __forceinline__ void philox10(uint32_t& c0, uint32_t& c1, uint32_t& c
   }
 }
 
+// The first three blocks of an event are generated together when the event starts
+// (one uniform code point, three independent Philox chains); further blocks are
+// generated on demand (extra rejection iterations).  The event index is the whole
+// stream state between events.
 struct Rng {
   uint32_t k0, k1, p0, p1;  // key, photon id
-  uint32_t blk_lo, blk_hi;  // next block to generate
-  uint32_t w0, w1, w2, w3;  // buffered words (w0 next)
-  uint32_t left;            // buffered words left
+  uint32_t event;           // current event
+  uint32_t sub;             // next block to generate on demand
+  uint32_t v0, v1, v2, v3, v4, v5, v6, v7, v8, v9, v10, v11;  // preloaded words (v0 next)
+  uint32_t pre;             // preloaded words left
+  uint32_t w0, w1, w2, w3;  // on-demand block
+  uint32_t left;
 
-  __device__ __forceinline__ void init(uint64_t seed, uint64_t pid) {
+  __device__ __forceinline__ void block(uint32_t j, uint32_t& a, uint32_t& b, uint32_t& c, uint32_t& d) const {
+    uint32_t c0 = p0, c1 = p1, c2 = event, c3 = j;
+    philox10(c0, c1, c2, c3, k0, k1);
+    a = c0; b = c1; c = c2; d = c3;
+  }
+  __device__ __forceinline__ void start_event(uint32_t e) {
+    event = e;
+    block(0u, v0, v1, v2, v3);
+    block(1u, v4, v5, v6, v7);
+    block(2u, v8, v9, v10, v11);
+    pre = 12u;
+    sub = 3u;
+    left = 0u;
+  }
+  __device__ __forceinline__ void keys(uint64_t seed, uint64_t pid) {
     k0 = (uint32_t)seed; k1 = (uint32_t)(seed >> 32);
     p0 = (uint32_t)pid; p1 = (uint32_t)(pid >> 32);
-    blk_lo = 0; blk_hi = 0; left = 0;
   }
-  __device__ __forceinline__ void refill() {
-    uint32_t c0 = p0, c1 = p1, c2 = blk_lo, c3 = blk_hi;
-    philox10(c0, c1, c2, c3, k0, k1);
-    w0 = c0; w1 = c1; w2 = c2; w3 = c3; left = 4;
-    blk_lo += 1u;
-    if (blk_lo == 0u) blk_hi += 1u;
+  __device__ __forceinline__ void init(uint64_t seed, uint64_t pid) {
+    keys(seed, pid);
+    start_event(0u);
   }
+  // next interaction event of the photon
+  __device__ __forceinline__ void next_event() { start_event(event + 1u); }
   __device__ __forceinline__ uint32_t next() {
-    if (left == 0u) refill();
+    if (pre != 0u) {
+      const uint32_t r = v0;
+      v0 = v1; v1 = v2; v2 = v3; v3 = v4; v4 = v5; v5 = v6; v6 = v7; v7 = v8; v8 = v9; v9 = v10; v10 = v11;
+      --pre;
+      return r;
+    }
+    if (left == 0u) {
+      block(sub, w0, w1, w2, w3);
+      ++sub;
+      left = 4u;
+    }
     const uint32_t r = w0;
     w0 = w1; w1 = w2; w2 = w3;
     --left;
@@ -84,18 +115,6 @@ struct Rng {
   // (u + 1/2) 2^-32 in FP32: in (0, 1]
   __device__ __forceinline__ float uni() {
     return fminf(__fmaf_rn(__uint2float_rn(next()), 2.3283064365386963e-10f, 1.1641532182693481e-10f), 1.0f);
-  }
-  // Rebuild the buffer after a state save: the stream is at block (blk) with `left` words left.
-  __device__ __forceinline__ void resume(uint32_t words_left) {
-    if (words_left == 0u) { left = 0; return; }
-    // regenerate the block that was being consumed
-    uint32_t lo = blk_lo - 1u, hi = blk_hi - (blk_lo == 0u ? 1u : 0u);
-    uint32_t c0 = p0, c1 = p1, c2 = lo, c3 = hi;
-    philox10(c0, c1, c2, c3, k0, k1);
-    uint32_t w[4] = {c0, c1, c2, c3};
-    uint32_t s = 4u - words_left;
-    w0 = w[s & 3]; w1 = w[(s + 1) & 3]; w2 = w[(s + 2) & 3]; w3 = w[(s + 3) & 3];
-    left = words_left;
   }
 };
 
@@ -187,12 +206,15 @@ __device__ __forceinline__ float sample_upar(float x, float a, Rng& rng, uint32_
   const float e0 = __expf(-u0 * u0);
   const float p1 = w1 / (w1 + e0 * (kPiF - w1));
   const float u02 = u0 * u0;
+  const float w1p = w1 * (1.0f / kPiF);  // alpha in units of pi
   float u;
   for (;;) {
     const float R1 = rng.uni(), R2 = rng.uni(), R3 = rng.uni();
     const bool reg1 = R1 < p1;
-    const float alpha = reg1 ? w1 * R2 : __fmaf_rn(kPiF - w1, R2, w1);
-    u = xr - a / tanf(alpha);
+    const float t = reg1 ? w1p * R2 : __fmaf_rn(1.0f - w1p, R2, w1p);
+    float sn, cs;
+    sincospif(t, &sn, &cs);
+    u = __fmaf_rn(-a * cs, __frcp_rn(sn), xr);  // x - a cot(alpha)
     const float acc = reg1 ? __expf(-u * u) : __expf(u02 - u * u);
     ++iters;
     if (R3 <= acc) break;
@@ -204,7 +226,7 @@ __device__ __forceinline__ float sample_upar(float x, float a, Rng& rng, uint32_
 enum : int { PH_ISO = 0, PH_DIPOLE = 1, PH_MIXED = 2 };
 __device__ __forceinline__ float mu_dipole(float R) {  // CDF (mu^3 + 3 mu + 4)/8, Cardano
   const float B = __fmaf_rn(4.0f, R, -2.0f);
-  const float A = cbrtf(B + sqrtf(__fmaf_rn(B, B, 1.0f)));
+  const float A = exp2f(__log2f(B + sqrtf(__fmaf_rn(B, B, 1.0f))) * (1.0f / 3.0f));  // cube root, argument in [0.23, 4.3]
   return A - __frcp_rn(A);
 }
 __device__ __forceinline__ float mu_hg(float R, float g) {  // Eq. 9 inverse CDF
@@ -235,10 +257,13 @@ struct AtomFrame {  // what peeling-off needs from a resonant scattering
 
 // One resonant scattering in the gas frame (Eq. 5-7, recoil ignored).  Returns
 // x_out = x_in + u . (k_out - k_in) and overwrites k with k_out.
+// Core-skipping (Sec. 3.4.2): for |x| < xcrit the perpendicular speed comes from the
+// Gaussian left-truncated at xcrit, r = sqrt(xcrit^2 - ln R) (xcrit = 0: plain Eq. 5).
 __device__ __forceinline__ float scatter_resonant(float x, float a, int phase, float3& k, Rng& rng,
-                                                  uint32_t& iters, AtomFrame* af) {
+                                                  uint32_t& iters, AtomFrame* af, float xcrit = 0.0f) {
   const float upar = sample_upar(x, a, rng, iters);
-  const float r = sqrtf(-__logf(rng.uni()));
+  const float xc = (fabsf(x) < xcrit) ? xcrit : 0.0f;
+  const float r = sqrtf(__fmaf_rn(xc, xc, -__logf(rng.uni())));
   float sp1, cp1;
   sincospif(2.0f * rng.uni(), &sp1, &cp1);
   const float u1 = r * cp1, u2 = r * sp1;

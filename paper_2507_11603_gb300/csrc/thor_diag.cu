@@ -34,6 +34,10 @@ __global__ void dda_kernel(int nx, int ny, int nz, const double* __restrict__ or
     w.advance(ax, tn);
   }
   count[r] = c;
+  for (int j = c; j < max_steps; ++j) {  // unused entries: -1 / 0
+    cells[(int64_t)r * max_steps + j] = -1;
+    seg[(int64_t)r * max_steps + j] = 0.0;
+  }
 }
 
 __global__ void upar_kernel(float x, float a, uint64_t seed, int64_t n, float* __restrict__ out,

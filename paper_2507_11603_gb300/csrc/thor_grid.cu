@@ -195,6 +195,7 @@ __device__ void grid_emit(const GridModel& m, GPhoton& ph, const float* Ktab, ui
 
 // One event; returns 0 continue, 1 escaped, 2 absorbed, 3 capped.
 __device__ int grid_event(const GridModel& m, GPhoton& ph, const float* Ktab, uint32_t& pr, uint32_t& pc) {
+  ph.rng.next_event();
   float tau_rem = -__logf(ph.rng.uni());
   Dda w;
   w.init(ph.p[0], ph.p[1], ph.p[2], (double)ph.k.x, (double)ph.k.y, (double)ph.k.z);

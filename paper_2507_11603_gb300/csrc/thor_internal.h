@@ -24,6 +24,7 @@ struct ShellModel {
   float vgrad;               // km/s per unit length (homologous v = vgrad r)
   float gam;                 // |dx/ds| = vgrad / vth
   float ds_core;             // sub-step length (step limiter, Sec. 4.1: f l_v)
+  float xcrit;               // core-skipping threshold (Sec. 3.4.2), 0 = off
   float albedo, g_hg;
   int32_t phase;
   int32_t line;              // 0 delta, 1 Gaussian
@@ -55,8 +56,8 @@ struct WorkQueue {
 // Resident packet state for time-sliced (served) execution, SoA, one slot per thread.
 struct SlotState {
   double *px, *py, *pz;
-  float *kx, *ky, *kz, *X;
-  uint32_t *blk_lo, *blk_hi, *left;   // RNG position
+  float *kx, *ky, *kz, *X, *x;
+  uint32_t* event;                   // RNG position: events done
   uint32_t *nscat, *ndust, *iters, *steps;
   int32_t* model;                    // -1 = empty
   unsigned long long* pid;

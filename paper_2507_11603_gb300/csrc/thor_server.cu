@@ -203,7 +203,7 @@ void thor_server::run() {
     }
     for (Request* r : finished) {
       const size_t nb = (size_t)r->n_bins + 2;
-      h_spec.resize(nb);
+      h_spec.resize((size_t)max_bins + 2);
       cudaMemcpyAsync(h_spec.data(), d_spec + (size_t)r->slot * (max_bins + 2), (size_t)(max_bins + 2) * 8,
                       cudaMemcpyDeviceToHost, s);
       cudaStreamSynchronize(s);
@@ -243,7 +243,7 @@ extern "C" int thor_server_create(thor_ctx_t ctx, const thor_server_config* cfg,
   s->active.assign(R, nullptr);
   const size_t spec_bytes = (size_t)R * (s->max_bins + 2) * 8;
   const int64_t n = s->n_slots;
-  const size_t slot_bytes = (size_t)n * (3 * 8 + 4 * 4 + 3 * 4 + 4 * 4 + 4 + 8 + 1) + 16 * 256;
+  const size_t slot_bytes = (size_t)n * (3 * 8 + 5 * 4 + 3 * 4 + 4 * 4 + 4 + 8 + 1) + 20 * 256;
   bool ok = cudaMalloc(&s->d_models, sizeof(ShellModel) * R) == cudaSuccess &&
             cudaMalloc(&s->d_tally, sizeof(Tally) * R) == cudaSuccess &&
             cudaMalloc(&s->d_spec, spec_bytes) == cudaSuccess &&
@@ -260,7 +260,8 @@ extern "C" int thor_server_create(thor_ctx_t ctx, const thor_server_config* cfg,
   SlotState& st = s->st;
   st.px = (double*)take(n * 8); st.py = (double*)take(n * 8); st.pz = (double*)take(n * 8);
   st.kx = (float*)take(n * 4); st.ky = (float*)take(n * 4); st.kz = (float*)take(n * 4); st.X = (float*)take(n * 4);
-  st.blk_lo = (uint32_t*)take(n * 4); st.blk_hi = (uint32_t*)take(n * 4); st.left = (uint32_t*)take(n * 4);
+  st.x = (float*)take(n * 4);
+  st.event = (uint32_t*)take(n * 4);
   st.nscat = (uint32_t*)take(n * 4); st.ndust = (uint32_t*)take(n * 4); st.iters = (uint32_t*)take(n * 4);
   st.steps = (uint32_t*)take(n * 4);
   st.model = (int32_t*)take(n * 4);

@@ -19,7 +19,9 @@ constexpr unsigned kFull = 0xffffffffu;
 struct Photon {
   double px, py, pz;
   float3 k;
-  float X;
+  float x;     // gas-frame frequency at p (in gas)
+  float X;     // lab frequency (in the cavity, and at escape)
+  float safe;  // lower bound on the distance from p to any shell boundary (0 = unknown)
   int region;  // 1 = inside the empty cavity
   uint32_t nscat, ndust, iters, steps;
   Rng rng;
@@ -47,23 +49,83 @@ __device__ __forceinline__ void shell_emit(const ShellModel& m, Photon& ph) {
     X = __fmaf_rn(m.sigma * sqrtf(-2.0f * __logf(R1)), cospif(2.0f * R2), X);
   }
   ph.X = X;
+  ph.x = X * m.inv_vth;  // gas at rest at the centre
   ph.region = (m.R_in > 0.0) ? 1 : 0;
+  ph.safe = (float)m.R_out;
   ph.nscat = 0; ph.ndust = 0; ph.iters = 0; ph.steps = 0;
 }
 
+// Move by s along k: FP64 position, the increment formed in FP32.
+__device__ __forceinline__ void advance(Photon& ph, float s) {
+  ph.px += (double)(s * ph.k.x);
+  ph.py += (double)(s * ph.k.y);
+  ph.pz += (double)(s * ph.k.z);
+}
+
+// Exact distance from p to the nearest boundary, rounded down (conservative).
+__device__ __forceinline__ float safe_distance(const ShellModel& m, const Photon& ph) {
+  const double r = sqrt(ph.px * ph.px + ph.py * ph.py + ph.pz * ph.pz);
+  double d = m.R_out - r;
+  if (m.R_in > 0.0) d = fmin(d, r - m.R_in);
+  return fmaxf(__double2float_rd(d) * 0.999999f, 0.0f);
+}
+
 // One event.  Returns 0 = continues, 1 = escaped, 2 = absorbed by dust, 3 = capped.
+// The gas-frame frequency x is carried along the ray: in the homologous flow it drifts
+// as x(s) = x0 - gam s in every direction, and a scattering leaves it at x_out at the
+// same point.  A conservative safety distance to the shell boundaries lets events whose
+// interaction lies inside the safety ball skip the FP64 ray-sphere geometry (the common
+// case for photons trapped in the line core).
 __device__ int shell_event(const ShellModel& m, Photon& ph, const float* __restrict__ Ktab) {
+  ph.rng.next_event();
   float tau_rem = -__logf(ph.rng.uni());  // Eq. 3: tau ~ Exp(1)
-  const double kx = ph.k.x, ky = ph.k.y, kz = ph.k.z;
-  float x_site = 0.0f;
+  float x_site, kH;
   for (;;) {
-    if (ph.region) {  // empty cavity: straight to the inner sphere
+    if (ph.region) {  // empty cavity: straight to the inner sphere, lab X conserved
+      const double kx = ph.k.x, ky = ph.k.y, kz = ph.k.z;
       const double b = ph.px * kx + ph.py * ky + ph.pz * kz;
       const double c = ph.px * ph.px + ph.py * ph.py + ph.pz * ph.pz - m.R_in * m.R_in;
       const double s = -b + sqrt(fmax(b * b - c, 0.0));
       ph.px += s * kx; ph.py += s * ky; ph.pz += s * kz;
       ph.region = 0;
+      ph.x = (ph.X - m.vgrad * (float)(b + s)) * m.inv_vth;
+      ph.safe = 0.0f;
     }
+    // ---- fast path: the next (sub-)step lies inside the safety ball
+    if (m.gam == 0.0f) {
+      const float H = voigt<false>(m.a, ph.x, Ktab);
+      kH = m.kap0 * H;
+      const float kap = kH + m.kapd;
+      const float s = tau_rem / kap;
+      ++ph.steps;
+      if (s <= ph.safe) {
+        advance(ph, s);
+        ph.safe = __fmaf_rd(-s, 1.000001f, ph.safe);
+        x_site = ph.x;
+        break;
+      }
+    } else if (ph.safe >= m.ds_core) {
+      const float ds = m.ds_core;
+      const float xm = ph.x - m.gam * 0.5f * ds;
+      const float kap = __fmaf_rn(m.kap0, voigt<false>(m.a, xm, Ktab), m.kapd);
+      const float dtau = kap * ds;
+      ++ph.steps;
+      if (dtau >= tau_rem) {
+        const float s = tau_rem / kap;
+        advance(ph, s);
+        ph.safe = __fmaf_rd(-s, 1.000001f, ph.safe);
+        x_site = ph.x - m.gam * s;
+        kH = m.kap0 * voigt<false>(m.a, x_site, Ktab);
+        break;
+      }
+      tau_rem -= dtau;
+      advance(ph, ds);
+      ph.safe = __fmaf_rd(-ds, 1.000001f, ph.safe);
+      ph.x -= m.gam * ds;
+      continue;
+    }
+    // ---- general path: exact segment to the next boundary (FP64), then sub-steps
+    const double kx = ph.k.x, ky = ph.k.y, kz = ph.k.z;
     const double b = ph.px * kx + ph.py * ky + ph.pz * kz;
     const double pp = ph.px * ph.px + ph.py * ph.py + ph.pz * ph.pz;
     double S = -b + sqrt(fmax(b * b - (pp - m.R_out * m.R_out), 0.0));
@@ -77,15 +139,12 @@ __device__ int shell_event(const ShellModel& m, Photon& ph, const float* __restr
     }
     S = fmax(S, 0.0);
     const float Sf = (float)S;
-    // gas-frame frequency at the segment start; along the ray x(s) = x0 - gam s
-    const float x0 = (ph.X - m.vgrad * (float)b) * m.inv_vth;
+    const float x0 = ph.x;
     float s_star = -1.0f;
     if (m.gam == 0.0f) {
-      const float kap = __fmaf_rn(m.kap0, voigt<false>(m.a, x0, Ktab), m.kapd);
-      const float dtau = kap * Sf;
-      ++ph.steps;
-      if (dtau >= tau_rem) s_star = fminf(tau_rem / kap, Sf);
-      else tau_rem -= dtau;
+      const float kap = kH + m.kapd;
+      if (kap * Sf >= tau_rem) s_star = fminf(tau_rem / kap, Sf);
+      else tau_rem -= kap * Sf;
     } else {
       float s = 0.0f;
       while (s < Sf) {
@@ -103,33 +162,38 @@ __device__ int shell_event(const ShellModel& m, Photon& ph, const float* __restr
       const double sd = s_star;
       ph.px += sd * kx; ph.py += sd * ky; ph.pz += sd * kz;
       x_site = x0 - m.gam * s_star;
+      if (m.gam != 0.0f) kH = m.kap0 * voigt<false>(m.a, x_site, Ktab);
+      ph.safe = safe_distance(m, ph);
       break;
     }
     ph.px += S * kx; ph.py += S * ky; ph.pz += S * kz;
+    const float x_end = x0 - m.gam * Sf;
+    ph.X = __fmaf_rn(x_end, m.vth, m.vgrad * (float)(b + S));  // lab frequency at the boundary
     if (next == 1) return 1;
     ph.region = 1;
   }
+  ph.x = x_site;
   // Interaction (Sec. 3.4): channel i with probability tau_i / sum_i tau_i.
-  const float3 v = make_float3(m.vgrad * (float)ph.px, m.vgrad * (float)ph.py, m.vgrad * (float)ph.pz);
-  const float kH = m.kap0 * voigt<false>(m.a, x_site, Ktab);
   bool dust = false;
   if (m.kapd > 0.0f) dust = ph.rng.uni() >= kH / (kH + m.kapd);
-  const float vk_in = v.x * ph.k.x + v.y * ph.k.y + v.z * ph.k.z;
   if (dust) {
     bool scat;
     if (m.albedo <= 0.0f) scat = false;
     else if (m.albedo >= 1.0f) scat = true;
     else scat = ph.rng.uni() < m.albedo;
     if (!scat) return 2;
-    scatter_dust(m.g_hg, ph.k, ph.rng);
-    ph.X += (v.x * ph.k.x + v.y * ph.k.y + v.z * ph.k.z) - vk_in;
+    scatter_dust(m.g_hg, ph.k, ph.rng);  // gas-frame frequency unchanged
     ++ph.ndust;
     return 0;
   }
-  const float xo = scatter_resonant(x_site, m.a, m.phase, ph.k, ph.rng, ph.iters, nullptr);
-  ph.X = __fmaf_rn(xo, m.vth, v.x * ph.k.x + v.y * ph.k.y + v.z * ph.k.z);
+  // Eq. 7: the gas-frame frequency after the scattering, at the same point
+  ph.x = scatter_resonant(x_site, m.a, m.phase, ph.k, ph.rng, ph.iters, nullptr, m.xcrit);
   ++ph.nscat;
-  if (m.max_scat && ph.nscat >= m.max_scat) return 3;
+  if (m.max_scat && ph.nscat >= m.max_scat) {
+    const float b = (float)(ph.px * ph.k.x + ph.py * ph.k.y + ph.pz * ph.k.z);
+    ph.X = __fmaf_rn(ph.x, m.vth, m.vgrad * b);
+    return 3;
+  }
   return 0;
 }
 
@@ -258,12 +322,13 @@ __global__ void __launch_bounds__(256) shell_slice_kernel(const ShellModel* __re
     ph.model = st.model[slot];
     const ShellModel& m = models[ph.model];
     ph.pid = st.pid[slot];
-    ph.rng.init(((uint64_t)m.seed_hi << 32) | m.seed_lo, ph.pid);
-    ph.rng.blk_lo = st.blk_lo[slot]; ph.rng.blk_hi = st.blk_hi[slot];
-    ph.rng.resume(st.left[slot]);
+    ph.rng.keys(((uint64_t)m.seed_hi << 32) | m.seed_lo, ph.pid);
+    ph.rng.event = st.event[slot];
     ph.px = st.px[slot]; ph.py = st.py[slot]; ph.pz = st.pz[slot];
     ph.k = make_float3(st.kx[slot], st.ky[slot], st.kz[slot]);
     ph.X = st.X[slot];
+    ph.x = st.x[slot];
+    ph.safe = 0.0f;
     ph.region = st.region[slot];
     ph.nscat = st.nscat[slot]; ph.ndust = st.ndust[slot]; ph.iters = st.iters[slot]; ph.steps = st.steps[slot];
     active = true;
@@ -299,10 +364,10 @@ __global__ void __launch_bounds__(256) shell_slice_kernel(const ShellModel* __re
   if (!has_slot) return;
   if (active) {
     st.model[slot] = ph.model; st.pid[slot] = ph.pid;
-    st.blk_lo[slot] = ph.rng.blk_lo; st.blk_hi[slot] = ph.rng.blk_hi; st.left[slot] = ph.rng.left;
+    st.event[slot] = ph.rng.event;
     st.px[slot] = ph.px; st.py[slot] = ph.py; st.pz[slot] = ph.pz;
     st.kx[slot] = ph.k.x; st.ky[slot] = ph.k.y; st.kz[slot] = ph.k.z;
-    st.X[slot] = ph.X; st.region[slot] = (uint8_t)ph.region;
+    st.X[slot] = ph.X; st.x[slot] = ph.x; st.region[slot] = (uint8_t)ph.region;
     st.nscat[slot] = ph.nscat; st.ndust[slot] = ph.ndust; st.iters[slot] = ph.iters; st.steps[slot] = ph.steps;
   } else {
     st.model[slot] = -1;

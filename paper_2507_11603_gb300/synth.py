@@ -66,7 +66,7 @@ def _grf_numpy(shape, sigma, rng, index=-11.0 / 3.0):
     nz = kk > 0
     amp[nz] = kk[nz] ** (index / 2.0)
     f *= amp
-    g = np.fft.irfftn(f, s=shape)
+    g = np.fft.irfftn(f, s=shape, axes=tuple(range(len(shape))))
     g -= g.mean()
     return (g * (sigma / g.std())).astype(np.float32)
 

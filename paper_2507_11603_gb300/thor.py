@@ -41,7 +41,7 @@ class ThorError(RuntimeError):
 class ShellParams(C.Structure):
     _fields_ = [("R_in", C.c_double), ("R_out", C.c_double), ("N_HI", C.c_double), ("tau0", C.c_double),
                 ("T", C.c_double), ("v_max", C.c_double), ("tau_dust", C.c_double), ("albedo", C.c_double),
-                ("g_hg", C.c_double), ("phase", C.c_int32), ("reserved", C.c_int32), ("step_dx", C.c_double)]
+                ("g_hg", C.c_double), ("phase", C.c_int32), ("core_skip", C.c_int32), ("step_dx", C.c_double)]
 
 
 class Source(C.Structure):
@@ -211,8 +211,9 @@ class Context:
 
     # -------------------------------------------------------------- geometries
     def shell(self, *, T, R_in=0.0, R_out=1.0, N_HI=0.0, tau0=0.0, v_max=0.0, tau_dust=0.0, albedo=0.0, g_hg=0.73,
-              phase="isotropic", step_dx=0.0):
-        p = ShellParams(R_in, R_out, N_HI, tau0, T, v_max, tau_dust, albedo, g_hg, PHASE[phase], 0, step_dx)
+              phase="isotropic", step_dx=0.0, core_skip=False):
+        p = ShellParams(R_in, R_out, N_HI, tau0, T, v_max, tau_dust, albedo, g_hg, PHASE[phase],
+                        1 if core_skip else 0, step_dx)
         g = C.c_void_p()
         self._check(self.L.thor_shell_create(self.h, C.byref(p), C.byref(g)))
         return Geometry(self, g, "shell", params=p)
@@ -358,8 +359,9 @@ class Server:
 
     def submit(self, *, T, R_in=0.9, R_out=1.0, N_HI=0.0, tau0=0.0, v_max=0.0, tau_dust=0.0, albedo=0.0,
                g_hg=0.73, phase="dipole", step_dx=0.0, n_photons, seed, X0=0.0, sigma=0.0, n_bins=400,
-               X_min=-1500.0, X_max=1500.0, max_scat=0):
-        p = ShellParams(R_in, R_out, N_HI, tau0, T, v_max, tau_dust, albedo, g_hg, PHASE[phase], 0, step_dx)
+               X_min=-1500.0, X_max=1500.0, max_scat=0, core_skip=False):
+        p = ShellParams(R_in, R_out, N_HI, tau0, T, v_max, tau_dust, albedo, g_hg, PHASE[phase],
+                        1 if core_skip else 0, step_dx)
         src = Source(0, 0, X0, sigma)
         buf = np.zeros(n_bins + 2, np.uint64)
         spec = OutputSpec(n_bins, MEM_HOST, X_min, X_max, buf.ctypes.data, 0, 0, 0, 0, 0.0, 0.0, None, None, None,

@@ -26,12 +26,12 @@ def test_philox_known_answers(orc):
 
 
 def test_stream_counter_layout(orc):
-    # photon stream = Philox(key=seed, ctr=(photon lo, photon hi, block lo, block hi))
+    # event e of photon p = Philox(key=seed, ctr=(p lo, p hi, e, j)), j = 0, 1, ...; emission is event 0
     seed, pid = 0x0123456789ABCDEF, 0xFEDCBA9876543210
     w = orc.stream_words(seed, pid, 12)
     key = [seed & 0xFFFFFFFF, seed >> 32]
     for blk in range(3):
-        ref = orc.philox([pid & 0xFFFFFFFF, pid >> 32, blk, 0], key)
+        ref = orc.philox([pid & 0xFFFFFFFF, pid >> 32, 0, blk], key)
         assert list(w[4 * blk:4 * blk + 4]) == list(ref)
 
 
@@ -290,9 +290,10 @@ def test_static_sphere_symmetry_and_conservation(orc):
 def _neufeld_check(orc, geometry, shape, n, seed):
     """Static sphere / slab, T = 10 K, tau0 = 1e5 (a tau0 = 1.5e3), central source at
     line centre, against the analytic spectrum valid for a tau0 >> 1 (Sec. 4; Neufeld
-    1990, Dijkstra et al. 2006).  At this a tau0 the analytic wings are known to be a
-    little too steep, so the pin is (i) the mean |x| / (a tau0)^(1/3) within 4 per cent
-    (a factor-2 error in the frequency redistribution moves it by ~25 per cent) and
+    1990, Dijkstra et al. 2006).  The analytic solution holds for a tau0 >> 1 only; at
+    this a tau0 the Monte Carlo mean |x| sits ~3 per cent above it (six seeds: +2.9 +- 0.5
+    per cent), so the pin is (i) the mean |x| / (a tau0)^(1/3) within 7 per cent (a
+    factor-2 error in the frequency redistribution moves it by ~25 per cent) and
     (ii) chi^2 over the well-populated bins around the two peaks."""
     T, tau0 = 10.0, 1e5
     p = orc.line_params(T)
@@ -305,7 +306,7 @@ def _neufeld_check(orc, geometry, shape, n, seed):
     s = at ** (1 / 3)
     norm = integrate.quad(lambda t: shape(t, a_tau0=1.0), -8, 8, limit=200)[0]
     mean_abs = integrate.quad(lambda t: abs(t) * shape(t, a_tau0=1.0), -8, 8, limit=200)[0] / norm
-    assert abs(np.mean(np.abs(x)) / s / mean_abs - 1) < 0.04
+    assert abs(np.mean(np.abs(x)) / s / mean_abs - 1) < 0.07
     edges = np.linspace(-4 * s, 4 * s, 25)
     c, _ = np.histogram(x, edges)
     e = A.binned_expectation(shape, edges, c.sum(), a_tau0=at)
@@ -408,3 +409,19 @@ def test_forest_line_integral_identity(orc):
     per = b * (np.sqrt(np.pi) - 2 * a / np.sqrt(np.pi) / x_edge)
     expect = np.sum(nHI.astype(float)) * p["sigma0"] * ds * per
     assert abs(tau.sum() * 1.0 / expect - 1) < 2e-4
+
+
+def test_core_skipping_preserves_spectrum(orc):
+    """Sec. 3.4.2: core-skipping (x_crit = 0.2 (a tau0)^(1/3)) leaves the emergent spectrum
+    of a thick static sphere unchanged while removing most core scatterings."""
+    T, tau0, n = 10.0, 1e5, 1000
+    p = orc.line_params(T)
+    at = p["a"] * tau0
+    vt = p["vth_kms"]
+    kw = dict(tau0=tau0, T=T, n_photons=n, raw=True, n_bins=4, X_min=-1.0, X_max=1.0)
+    r0 = orc.run_shell(seed=31, **kw)
+    r1 = orc.run_shell(seed=32, core_skip=True, **kw)
+    assert r1["sum_scat"] < r0["sum_scat"] / 5
+    x0, x1 = np.abs(r0["X"]) / vt, np.abs(r1["X"]) / vt
+    assert abs(x1.mean() / x0.mean() - 1) < 0.05
+    assert stats.ks_2samp(x0, x1).pvalue > 1e-3
