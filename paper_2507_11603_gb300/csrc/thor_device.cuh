@@ -363,8 +363,10 @@ struct Dda {
   }
   __device__ __forceinline__ void advance(int ax, double tn) {
     t = tn;
-    i[ax] += step[ax];
-    tm[ax] = face_t(ax);
+    // constant indices only, so the walk state stays in registers
+    if (ax == 0) { i[0] += step[0]; tm[0] = face_t(0); }
+    else if (ax == 1) { i[1] += step[1]; tm[1] = face_t(1); }
+    else { i[2] += step[2]; tm[2] = face_t(2); }
   }
   __device__ __forceinline__ bool inside(int nx, int ny, int nz) const {
     return i[0] >= 0 && i[1] >= 0 && i[2] >= 0 && i[0] < nx && i[1] < ny && i[2] < nz;

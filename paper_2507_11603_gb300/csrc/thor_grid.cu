@@ -119,24 +119,26 @@ __device__ __forceinline__ int64_t cell_index(const GridModel& m, int ix, int iy
 
 // Optical depth from p to the box face along +axis at lab frequency Xp (Sec. 3.4.1),
 // cell by cell, stopping once tau > tau_cut.
-__device__ float peel_tau(const GridModel& m, const double p[3], int axis, float Xp, const float* Ktab,
+__device__ __forceinline__ float peel_tau(const GridModel& m, const double p[3], int axis, float Xp, const float* Ktab,
                           uint32_t& ncell) {
-  int i[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) i[a] = (int)floor(p[a]);
+  // walk along +axis: the cell index advances by `stride` elements per step
+  const int ix = (int)floor(p[0]), iy = (int)floor(p[1]), iz = (int)floor(p[2]);
   const int n_ax = (axis == 0) ? m.nx : (axis == 1) ? m.ny : m.nz;
+  const int i0 = (axis == 0) ? ix : (axis == 1) ? iy : iz;
+  const double pa = (axis == 0) ? p[0] : (axis == 1) ? p[1] : p[2];
+  const int64_t stride = (axis == 0) ? 1 : (axis == 1) ? (int64_t)m.nx : (int64_t)m.nx * m.ny;
+  int64_t c = cell_index(m, ix, iy, iz);
   double t = 0.0;
   float tau = 0.0f;
-  while (i[axis] < n_ax) {
-    const double tn = __dadd_rn((double)(i[axis] + 1), -p[axis]);
-    const GridCell g = load_cell(m.cells, cell_index(m, i[0], i[1], i[2]));
+  for (int i = i0; i < n_ax; ++i, c += stride) {
+    const double tn = __dadd_rn((double)(i + 1), -pa);
+    const GridCell g = load_cell(m.cells, c);
     const float v = (axis == 0) ? g.vx : (axis == 1) ? g.vy : g.vz;
     const float x = (Xp - v) * g.inv_vth;
     tau = __fmaf_rn(__fmaf_rn(g.kap0, voigt<false>(g.a, x, Ktab), g.kd), (float)(tn - t), tau);
     ++ncell;
     if (tau > m.tau_cut) break;
     t = tn;
-    i[axis] += 1;
   }
   return tau;
 }
@@ -183,7 +185,7 @@ __device__ void grid_emit(const GridModel& m, GPhoton& ph, const float* Ktab, ui
   ph.nscat = 0; ph.ndust = 0; ph.iters = 0; ph.steps = 0;
   if (m.peel) {
     const float vv[3] = {g.vx, g.vy, g.vz};
-#pragma unroll 1
+#pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
       const float Xp = __fmaf_rn(xe, g.vth, vv[ax]);
       const float tau = peel_tau(m, ph.p, ax, Xp, Ktab, pc);
@@ -237,7 +239,7 @@ __device__ int grid_event(const GridModel& m, GPhoton& ph, const float* Ktab, ui
     if (!scat) return 2;
     if (m.peel) {
       const float kin[3] = {ph.k.x, ph.k.y, ph.k.z};
-#pragma unroll 1
+#pragma unroll
       for (int ax = 0; ax < 3; ++ax) {
         const float Xp = ph.X + vv[ax] - vk_in;
         const float tau = peel_tau(m, ph.p, ax, Xp, Ktab, pc);
@@ -255,7 +257,7 @@ __device__ int grid_event(const GridModel& m, GPhoton& ph, const float* Ktab, ui
   const float xo = scatter_resonant(x, g.a, m.phase, ph.k, ph.rng, ph.iters, &af);
   if (m.peel) {
     const float e1[3] = {af.e1.x, af.e1.y, af.e1.z}, e2[3] = {af.e2.x, af.e2.y, af.e2.z};
-#pragma unroll 1
+#pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
       const float mu = kin[ax];
       const float xp = x - af.upar + __fmaf_rn(af.upar, mu, __fmaf_rn(af.u1, e1[ax], af.u2 * e2[ax]));
