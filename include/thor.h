@@ -188,6 +188,31 @@ int thor_forest(thor_ctx_t ctx, const float* n_HI, const float* T, const float* 
 /* Device time of the last thor_forest call in milliseconds (CUDA events). */
 double thor_last_elapsed_ms(thor_ctx_t ctx);
 
+/* ---- shell run without device allocation --------------------------------------------- */
+
+/* The paper has no counterpart to this entry point; it serves callers that cannot
+ * allocate device memory when they need a run -- code running under an external memory
+ * pool with nothing to spare, a process whose GPU quota its own buffers already use up,
+ * or a host callback in which cudaMalloc is not allowed.  It runs the same shell photon
+ * loop as thor_run (identical results for identical arguments) on the current device and
+ * `stream` (a cudaStream_t, NULL = legacy default stream), with no context and no
+ * cudaMalloc / cudaFree: its scratch (model record, tallies, queue, and a staging copy of
+ * a host spectrum) lives in a fixed file-scope device array that every GPU loading the
+ * library keeps until the process exits.
+ *  - spectrum: n_bins + 2 uint64 counts (bins, underflow, overflow), host or device
+ *    memory per mem_kind.  Host spectra are staged in the fixed array, so then
+ *    n_bins <= THOR_NOALLOC_MAX_BINS (THOR_ERR_CAPACITY otherwise).
+ *  - The first call on a device looks up the array's device address and uploads a
+ *    coefficient table; make that first call before any stream capture.
+ *  - All calls share the array, and each call clears what must start at zero.  Calls
+ *    that overlap on the GPU race on it: serialise them.
+ *  - Errors: INVALID_ARG, CAPACITY, DEVICE; message in thor_noalloc_last_error(). */
+#define THOR_NOALLOC_MAX_BINS 4096
+int thor_run_shell_noalloc(const thor_shell_params* p, const thor_source* src, uint64_t first_id,
+                           uint64_t n_photons, uint64_t seed, int32_t n_bins, double X_min, double X_max,
+                           uint64_t* spectrum, int mem_kind, void* stream, thor_result* out);
+const char* thor_noalloc_last_error(void);
+
 /* ---- served stream of shell models (continuous batching) ---------------------------- */
 
 typedef struct {

@@ -29,6 +29,7 @@ SYMBOLS = [
     "thor_forest", "thor_last_elapsed_ms", "thor_server_create", "thor_server_submit", "thor_server_poll",
     "thor_server_wait", "thor_server_cancel", "thor_server_stats", "thor_server_destroy", "thor_voigt_eval",
     "thor_dda_trace", "thor_sample_upar", "thor_scatter_once", "thor_philox", "thor_line_params",
+    "thor_run_shell_noalloc", "thor_noalloc_last_error",
 ]
 
 
@@ -119,6 +120,9 @@ def load(build: bool = True) -> C.CDLL:
             "thor_scatter_once": ([vp, C.c_float, C.c_float, C.c_int, u64, i64, vp, vp, C.c_int], C.c_int),
             "thor_philox": ([vp, vp, vp, vp, i32, C.c_int], C.c_int),
             "thor_line_params": ([dbl, P(dbl), P(dbl), P(dbl)], None),
+            "thor_run_shell_noalloc": ([P(ShellParams), P(Source), u64, u64, u64, i32, dbl, dbl, vp, C.c_int, vp,
+                                        P(Result)], C.c_int),
+            "thor_noalloc_last_error": ([], C.c_char_p),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -133,6 +137,30 @@ def line_params(T: float) -> dict:
     v, a, s = C.c_double(), C.c_double(), C.c_double()
     L.thor_line_params(float(T), C.byref(v), C.byref(a), C.byref(s))
     return {"vth_kms": v.value, "a": a.value, "sigma0": s.value}
+
+
+def run_shell_noalloc(*, T, R_in=0.0, R_out=1.0, N_HI=0.0, tau0=0.0, v_max=0.0, tau_dust=0.0, albedo=0.0,
+                      g_hg=0.73, phase="isotropic", step_dx=0.0, core_skip=False, n_photons, seed, first_id=0,
+                      X0=0.0, sigma=0.0, n_bins=200, X_min=-1000.0, X_max=1000.0, spectrum=None, stream=None):
+    """thor_run_shell_noalloc: the shell photon loop on the current CUDA device without any
+    device allocation by the library (its scratch is a fixed static device array).  For
+    callers that cannot allocate device memory at the time of the run.  `spectrum`: a host
+    numpy uint64 array or a CUDA tensor of n_bins + 2 entries (allocated here as a host
+    array when omitted); calls that overlap on the GPU must be serialised."""
+    L = load()
+    p = ShellParams(R_in, R_out, N_HI, tau0, T, v_max, tau_dust, albedo, g_hg, PHASE[phase],
+                    1 if core_skip else 0, step_dx)
+    src = Source(0, 0, X0, sigma)
+    if spectrum is None:
+        spectrum = np.zeros(n_bins + 2, dtype=np.uint64)
+    ptr, kind, _ = _ptr(spectrum)
+    raw = getattr(stream, "cuda_stream", stream)
+    res = Result()
+    rc = L.thor_run_shell_noalloc(C.byref(p), C.byref(src), first_id, n_photons, seed, n_bins, X_min, X_max, ptr,
+                                  kind, C.c_void_p(raw or 0), C.byref(res))
+    if rc != OK:
+        raise ThorError(rc, L.thor_noalloc_last_error().decode())
+    return RunResult(spectrum[:n_bins], int(spectrum[n_bins]), int(spectrum[n_bins + 1]), res.as_dict())
 
 
 def _ptr(x):
