@@ -356,6 +356,55 @@ def run_stream_bench(args):
     del torch
 
 
+def run_probe(args):
+    """Small launch for profiling: a static sphere (tau0 = --probe-tau0, T = 1e4 K, dipole)
+    with --probe-photons photons, run twice (the second launch is the one to capture)."""
+    from paper_2507_11603_gb300 import thor
+    ctx = thor.Context(0)
+    g = ctx.shell(tau0=args.probe_tau0, T=1e4, phase="dipole")
+    for i in range(2):
+        r = ctx.run(g, n_photons=args.probe_photons, seed=i, n_bins=50, X_min=-500, X_max=500)
+    n = args.probe_photons
+    print(json.dumps({"probe": "static sphere", "tau0": args.probe_tau0, "photons": n, **r.stats,
+                      "us_per_event_chain": r.stats["elapsed_ms"] * 1e3 / (r.stats["n_scat"] / n)}))
+
+
+def run_grid_bench(args):
+    """Config 4: 256^3 grid, 100 pc cells, lognormal n_HI (mean 1e-3, sigma_ln 1.5), lognormal T
+    (median 1e4 K, sigma_ln 0.5), GRF velocities (k^-11/3, 50 km/s per axis), dust 0.01 n_HI,
+    emitters ~ n_HI^2, peeling-off to three axis observers (128x128 x 256 bins).  The photon
+    count is a stated subset of the 1e7 of the full configuration."""
+    import torch
+    from paper_2507_11603_gb300 import synth, thor
+    ctx = thor.Context(0)
+    f = synth.grid_fields(n=256, seed=3)
+    t0 = time.perf_counter()
+    g = ctx.grid(f["n_HI"], f["T"], f["v"], f["kd"], 100 * synth.PC_CM)
+    t_build = time.perf_counter() - t0
+    kw = dict(n_bins=256, X_min=-1000.0, X_max=1000.0, peel=True, img_n=128, peel_bins=256, peel_X_min=-1000.0,
+              peel_X_max=1000.0, device_out=True)
+    ctx.run(g, n_photons=max(256, args.grid_photons // 16), seed=4, first_id=10 ** 9, **kw)
+    ms, scat, steps, rays, cells = [], 0, 0, 0, 0
+    with ClockSampler(0) as clk:
+        for i in range(args.steps):
+            r = ctx.run(g, n_photons=args.grid_photons, seed=4, first_id=i * args.grid_photons, **kw)
+            ms.append(r.stats["elapsed_ms"])
+            scat += r.stats["n_scat"]
+            steps += r.stats["n_steps"]
+            rays += r.stats["n_peel_rays"]
+            cells += r.stats["n_peel_cells"]
+    t = sum(ms) / 1000.0
+    gathers = steps + cells
+    print(json.dumps({"metric": "Lyα scatterings/s (grid + peeling-off)", "value": scat / t, "unit": "scatterings/s",
+                      "n_gpus": 1, "steps": args.steps, "ms_per_step": 1000 * t / args.steps,
+                      "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": f"256^3 grid, {args.grid_photons} photons per step (subset of 1e7)",
+                                 "grid_build_s": t_build},
+                      "cell_steps_per_s": steps / t, "peel_rays_per_s": rays / t, "peel_cells_per_s": cells / t,
+                      "gather_bytes_per_s": 32.0 * gathers / t, "clocks": clk.summary()}))
+    del torch
+
+
 def run_forest_bench(args):
     import torch
     from paper_2507_11603_gb300 import synth, thor
@@ -386,14 +435,17 @@ def run_forest_bench(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="shell", choices=["shell", "forest", "stream"])
+    ap.add_argument("--workload", default="shell", choices=["shell", "forest", "stream", "grid", "probe"])
+    ap.add_argument("--probe-tau0", type=float, default=1e5)
+    ap.add_argument("--probe-photons", type=int, default=64)
+    ap.add_argument("--grid-photons", type=int, default=20000)
     ap.add_argument("--stream-requests", type=int, default=256)
     ap.add_argument("--stream-nhi-max", type=float, default=1e21)
     ap.add_argument("--no-core-skip", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--ops-per-scat", type=float, default=float(os.environ.get("THOR_OPS_PER_SCAT", "0") or 0))
@@ -408,6 +460,10 @@ def main():
         run_forest_bench(args)
     elif args.workload == "stream":
         run_stream_bench(args)
+    elif args.workload == "grid":
+        run_grid_bench(args)
+    elif args.workload == "probe":
+        run_probe(args)
     else:
         run_shell_bench(args)
 

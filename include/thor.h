@@ -21,9 +21,9 @@
  *  - Frequencies are lab-frame velocity offsets X = c (nu - nu0) / nu0 in km/s
  *    (positive = blue); velocities in km/s; the gas-frame dimensionless frequency
  *    is x = (X - v . k) / v_th (Sec. 2.3.1).
- *  - Results are deterministic for fixed (seed, photon ids): photon i uses the
- *    Philox4x32-10 stream keyed by the run seed with counter (i, draw block),
- *    and all spectrum tallies are integer counts.
+ *  - Results are deterministic for fixed (seed, photon ids): photon i draws from the
+ *    Philox4x32-10 blocks keyed by the run seed with counter (i, event, block), and
+ *    all spectrum tallies are integer counts.
  *  - Calls on one context are serialised by the caller; contexts are independent.
  */
 #ifndef THOR_H
@@ -75,6 +75,12 @@ int thor_ctx_set_stream(thor_ctx_t ctx, void* cuda_stream);
 /* Launch configuration of the persistent photon loops: threads per block (multiple
  * of 32, <= 256) and resident blocks per SM (0 = occupancy maximum). */
 int thor_ctx_set_launch(thor_ctx_t ctx, int block_size, int blocks_per_sm);
+
+/* Tail compaction of the gridless photon loop: once no new photons are left, a warp
+ * with fewer than spill_below (0..32; 0 = off, default 16) live lanes saves its packets
+ * and exits, and the next launch runs the survivors in full warps, for at most
+ * max_phases launches (default 24).  Results do not depend on these settings. */
+int thor_ctx_set_tail(thor_ctx_t ctx, int spill_below, int max_phases);
 
 /* ---- geometries (Sec. 3.3 datasets) ----------------------------------------------- */
 

@@ -48,7 +48,7 @@ void* thor_ctx::scratch(Buf& b, size_t bytes) {
 
 thor_ctx::~thor_ctx() {
   cudaSetDevice(device);
-  for (Buf* b : {&b_models, &b_tally, &b_queue, &b_spec, &b_cube, &b_raw, &b_diag, &b_stats})
+  for (Buf* b : {&b_models, &b_tally, &b_queue, &b_spec, &b_cube, &b_raw, &b_diag, &b_stats, &b_spill, &b_cmp})
     if (b->p) cudaFree(b->p);
   if (d_ktab) cudaFree(d_ktab);
   if (ev0) cudaEventDestroy(ev0);
@@ -95,6 +95,15 @@ extern "C" const char* thor_last_error(thor_ctx_t ctx) {
 extern "C" int thor_ctx_set_stream(thor_ctx_t ctx, void* s) {
   if (!ctx) return THOR_ERR_INVALID_ARG;
   ctx->stream = (cudaStream_t)s;
+  return THOR_OK;
+}
+
+extern "C" int thor_ctx_set_tail(thor_ctx_t ctx, int spill_below, int max_phases) {
+  if (!ctx) return THOR_ERR_INVALID_ARG;
+  if (spill_below < 0 || spill_below > 32 || max_phases < 1)
+    return ctx->fail(THOR_ERR_INVALID_ARG, "thor_ctx_set_tail: spill_below in [0, 32], max_phases >= 1");
+  ctx->spill_below = spill_below;
+  ctx->max_phases = max_phases;
   return THOR_OK;
 }
 
@@ -341,9 +350,51 @@ extern "C" int thor_run(thor_ctx_t ctx, thor_geom_t g, const thor_source* src, u
     if (!d_m) return ctx->fail(THOR_ERR_OOM, "model table");
     if ((rc = ctx->cuda(cudaMemcpyAsync(d_m, &m, sizeof m, cudaMemcpyHostToDevice, s), "model upload"))) return rc;
     const int gsz = shell_grid(ctx->block, ctx->blocks_per_sm, false);
-    cudaEventRecord(ctx->ev0, s);
-    rc = ctx->cuda(launch_shell_run(d_m, q, ctx->d_ktab, gsz, ctx->block, s), "shell photon loop");
-    cudaEventRecord(ctx->ev1, s);
+    if (ctx->spill_below <= 0) {
+      cudaEventRecord(ctx->ev0, s);
+      rc = ctx->cuda(launch_shell_run(d_m, q, ctx->d_ktab, gsz, ctx->block, s), "shell photon loop");
+      cudaEventRecord(ctx->ev1, s);
+    } else {
+      // Tail compaction: launch, then relaunch over the saved survivors in full warps
+      // until none are left (the last phase runs to completion).
+      const unsigned long long lanes = (unsigned long long)gsz * ctx->block;
+      const unsigned long long cap = n_photons < lanes ? n_photons : lanes;
+      PhotonRec* bufs = (PhotonRec*)ctx->scratch(ctx->b_spill, 2 * cap * sizeof(PhotonRec));
+      unsigned long long* ctr = (unsigned long long*)ctx->scratch(ctx->b_cmp, 4 * sizeof(unsigned long long));
+      if (!bufs || !ctr) return ctx->fail(THOR_ERR_OOM, "tail compaction buffers");
+      PhotonRec* in = bufs;
+      PhotonRec* outb = bufs + cap;
+      unsigned long long n_in = 0;
+      cudaEventRecord(ctx->ev0, s);
+      for (int phase = 0;; ++phase) {
+        const bool last = phase + 1 >= ctx->max_phases || (phase > 0 && n_in <= (unsigned long long)ctx->final_below);
+        if ((rc = ctx->cuda(cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned long long), s), "clear counters"))) break;
+        Compact c;
+        c.resume = in;
+        c.n_resume = n_in;
+        c.resume_next = ctr;
+        c.spill = outb;
+        c.n_spill = ctr + 1;
+        c.spill_below = last ? 0 : ctx->spill_below;
+        int g = gsz;
+        if (phase > 0) {
+          const unsigned long long want = (n_in + ctx->block - 1) / ctx->block;
+          g = (int)(want < (unsigned long long)gsz ? want : gsz);
+        }
+        if ((rc = ctx->cuda(launch_shell_run_compact(d_m, q, c, ctx->d_ktab, g, ctx->block, s), "shell photon loop")))
+          break;
+        if (last) break;
+        unsigned long long n_out = 0;
+        if ((rc = ctx->cuda(cudaMemcpyAsync(&n_out, ctr + 1, sizeof n_out, cudaMemcpyDeviceToHost, s), "spill count")))
+          break;
+        if ((rc = ctx->cuda(cudaStreamSynchronize(s), "tail phase"))) break;
+        if (n_out == 0) break;
+        n_in = n_out;
+        PhotonRec* t = in; in = outb; outb = t;
+        ++ctx->phases_last;
+      }
+      cudaEventRecord(ctx->ev1, s);
+    }
   } else {
     GridModel m;
     std::memset(&m, 0, sizeof m);

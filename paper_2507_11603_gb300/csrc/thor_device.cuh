@@ -76,13 +76,14 @@ struct Rng {
     philox10(c0, c1, c2, c3, k0, k1);
     a = c0; b = c1; c = c2; d = c3;
   }
-  __device__ __forceinline__ void start_event(uint32_t e) {
+  // nblk = 2 or 3 blocks preloaded (8 words cover a resonant event without dust)
+  __device__ __forceinline__ void start_event(uint32_t e, uint32_t nblk = 3u) {
     event = e;
     block(0u, v0, v1, v2, v3);
     block(1u, v4, v5, v6, v7);
-    block(2u, v8, v9, v10, v11);
-    pre = 12u;
-    sub = 3u;
+    if (nblk > 2u) block(2u, v8, v9, v10, v11);
+    pre = 4u * nblk;
+    sub = nblk;
     left = 0u;
   }
   __device__ __forceinline__ void keys(uint64_t seed, uint64_t pid) {
@@ -94,7 +95,7 @@ struct Rng {
     start_event(0u);
   }
   // next interaction event of the photon
-  __device__ __forceinline__ void next_event() { start_event(event + 1u); }
+  __device__ __forceinline__ void next_event(uint32_t nblk = 3u) { start_event(event + 1u, nblk); }
   __device__ __forceinline__ uint32_t next() {
     if (pre != 0u) {
       const uint32_t r = v0;
@@ -177,14 +178,23 @@ __device__ __forceinline__ float voigt(float a, float x, const float* __restrict
 // and (ii) three Newton steps on u0^2 = ln(2 pi u0 (x - u0)^2 / a) (only for x > 2).
 // Three draws per iteration: region, alpha, acceptance.
 // ------------------------------------------------------------------------------
+// atan2(a, d) for a, d >= 0: series when a/d <= 1/20 (relative error < 3e-9), else atan2f.
+__device__ __forceinline__ float atan2_pos(float a, float d) {
+  if (a <= 0.05f * d) {
+    const float t = __fdividef(a, d), t2 = t * t;
+    return t * __fmaf_rn(t2, __fmaf_rn(t2, 0.2f, -1.0f / 3.0f), 1.0f);
+  }
+  return atan2f(a, d);
+}
+
 __device__ __forceinline__ float envelope_D(float xr, float a, float u0) {
-  const float w1 = atan2f(a, xr - u0);
+  const float w1 = atan2_pos(a, xr - u0);
   return w1 + __expf(-u0 * u0) * (kPiF - w1);
 }
 
 __device__ __forceinline__ float u0_rule(float xr, float a) {
   if (xr <= 0.0f) return 0.0f;
-  const float d = sqrtf(a / (2.0f * kPiF * xr)) * __expf(fminf(0.5f * xr * xr, 80.0f));
+  const float d = sqrtf(a * (0.5f / kPiF)) * rsqrtf(xr) * __expf(fminf(0.5f * xr * xr, 80.0f));
   const float c1 = fmaxf(0.0f, xr - d);
   if (xr <= 2.0f) return c1;
   float u = fminf(xr - 0.3f, 2.0f + 0.6f * __logf(xr));
@@ -202,9 +212,9 @@ __device__ __forceinline__ float sample_upar(float x, float a, Rng& rng, uint32_
   const float sgn = (x < 0.0f) ? -1.0f : 1.0f;
   const float xr = fabsf(x);
   const float u0 = u0_rule(xr, a);
-  const float w1 = atan2f(a, xr - u0);
+  const float w1 = atan2_pos(a, xr - u0);
   const float e0 = __expf(-u0 * u0);
-  const float p1 = w1 / (w1 + e0 * (kPiF - w1));
+  const float p1 = __fdividef(w1, __fmaf_rn(e0, kPiF - w1, w1));
   const float u02 = u0 * u0;
   const float w1p = w1 * (1.0f / kPiF);  // alpha in units of pi
   float u;
@@ -243,7 +253,7 @@ __device__ __forceinline__ float P_hg(float mu, float g) {
 // Orthonormal basis perpendicular to unit k (Duff et al. 2017, JCGT 6(1)).
 __device__ __forceinline__ void basis(float kx, float ky, float kz, float3& e1, float3& e2) {
   const float s = copysignf(1.0f, kz);
-  const float a = -1.0f / (s + kz);
+  const float a = __fdividef(-1.0f, s + kz);
   const float b = kx * ky * a;
   e1 = make_float3(1.0f + s * kx * kx * a, s * b, -s * kx);
   e2 = make_float3(b, s + ky * ky * a, -ky);
@@ -265,7 +275,7 @@ __device__ __forceinline__ float scatter_resonant(float x, float a, int phase, f
   const float xc = (fabsf(x) < xcrit) ? xcrit : 0.0f;
   const float r = sqrtf(__fmaf_rn(xc, xc, -__logf(rng.uni())));
   float sp1, cp1;
-  sincospif(2.0f * rng.uni(), &sp1, &cp1);
+  __sincosf(2.0f * kPiF * rng.uni(), &sp1, &cp1);
   const float u1 = r * cp1, u2 = r * sp1;
   const bool core = fabsf(x - upar) < 0.2f;
   float mu;
@@ -279,7 +289,7 @@ __device__ __forceinline__ float scatter_resonant(float x, float a, int phase, f
     mu = (core && Rc < (1.0f / 3.0f)) ? __fmaf_rn(2.0f, Rm, -1.0f) : mu_dipole(Rm);
   }
   float sp, cp;
-  sincospif(2.0f * rng.uni(), &sp, &cp);
+  __sincosf(2.0f * kPiF * rng.uni(), &sp, &cp);
   float3 e1, e2;
   basis(k.x, k.y, k.z, e1, e2);
   const float st = sqrtf(fmaxf(0.0f, 1.0f - mu * mu));
@@ -297,7 +307,7 @@ __device__ __forceinline__ float scatter_resonant(float x, float a, int phase, f
 __device__ __forceinline__ void scatter_dust(float g, float3& k, Rng& rng) {
   const float mu = mu_hg(rng.uni(), g);
   float sp, cp;
-  sincospif(2.0f * rng.uni(), &sp, &cp);
+  __sincosf(2.0f * kPiF * rng.uni(), &sp, &cp);
   float3 e1, e2;
   basis(k.x, k.y, k.z, e1, e2);
   const float st = sqrtf(fmaxf(0.0f, 1.0f - mu * mu));
@@ -312,7 +322,7 @@ __device__ __forceinline__ void scatter_dust(float g, float3& k, Rng& rng) {
 __device__ __forceinline__ float3 iso_dir(Rng& rng) {
   const float mu = __fmaf_rn(2.0f, rng.uni(), -1.0f);
   float sp, cp;
-  sincospif(2.0f * rng.uni(), &sp, &cp);
+  __sincosf(2.0f * kPiF * rng.uni(), &sp, &cp);
   const float st = sqrtf(fmaxf(0.0f, 1.0f - mu * mu));
   return make_float3(st * cp, st * sp, mu);
 }

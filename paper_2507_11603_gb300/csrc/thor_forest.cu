@@ -19,30 +19,54 @@ constexpr int kForestThreads = 256;
 constexpr int kBinsPerThread = 8;   // n_bins <= 2048 per pass
 constexpr int kCellChunk = 1024;    // cells staged per pass
 
+// Wing series (|x| >= 6) without the a/sqrt(pi) factor: t sum_k ((2k+1)!!/2^k) t^k with
+// t = 1/(x^2 + a^2); 8 terms for |x| < 12, 5 terms beyond (truncation < 1e-7 relative).
+__device__ __forceinline__ float wing_tP(float a, float x2) {
+  const float t = __frcp_rn(__fmaf_rn(a, a, x2));
+  float s;
+  if (x2 >= 144.0f) {
+    s = __fmaf_rn(59.0625f, t, 13.125f);
+    s = __fmaf_rn(s, t, 3.75f);
+    s = __fmaf_rn(s, t, 1.5f);
+    s = __fmaf_rn(s, t, 1.0f);
+  } else {
+    s = __fmaf_rn(15836.1328125f, t, 2111.484375f);
+    s = __fmaf_rn(s, t, 324.84375f);
+    s = __fmaf_rn(s, t, 59.0625f);
+    s = __fmaf_rn(s, t, 13.125f);
+    s = __fmaf_rn(s, t, 3.75f);
+    s = __fmaf_rn(s, t, 1.5f);
+    s = __fmaf_rn(s, t, 1.0f);
+  }
+  return t * s;
+}
+
 __global__ void __launch_bounds__(kForestThreads) forest_kernel(
     const float* __restrict__ nHI, const float* __restrict__ T, const float* __restrict__ vlos, int nx, int ny,
     int nz, int64_t first, double ds_cm, double dv_cell, int n_bins, double dv_bin, float* __restrict__ tau,
     const float* __restrict__ gK) {
   __shared__ __align__(16) float sK[THOR_VOIGT_NINT * THOR_VOIGT_NCOEF];
   __shared__ float4 sCell[kCellChunk];  // (v_hi, v_lo, 1/v_th, a)
-  __shared__ float sAmp[kCellChunk];    // n sigma_0 ds
+  __shared__ float2 sAmp[kCellChunk];   // (n sigma_0 ds, n sigma_0 ds a / sqrt(pi))
   load_ktab(sK, gK);
   const int64_t sl = first + blockIdx.x;
   const int ix = (int)(sl % nx), iy = (int)(sl / nx);
   const double V = (double)nz * dv_cell;
-  const float Vf = (float)V, hV = 0.5f * Vf;
+  const float Vf = (float)V, invV = (float)(1.0 / V);
   const int64_t plane = (int64_t)nx * ny;
 
   for (int b0 = 0; b0 < n_bins; b0 += kForestThreads * kBinsPerThread) {
-    float vb_hi[kBinsPerThread], vb_lo[kBinsPerThread], acc[kBinsPerThread], part[kBinsPerThread];
+    // bin q of this thread sits q * blockDim bins after its first bin: exact offsets
+    const double vb0 = ((double)(b0 + threadIdx.x) + 0.5) * dv_bin;
+    const float vb0_hi = (float)vb0, vb0_lo = (float)(vb0 - (double)vb0_hi);
+    float off_hi[kBinsPerThread], off_lo[kBinsPerThread], acc[kBinsPerThread], part[kBinsPerThread];
 #pragma unroll
-    for (int j = 0; j < kBinsPerThread; ++j) {
-      const int b = b0 + threadIdx.x + j * kForestThreads;
-      const double vb = ((double)b + 0.5) * dv_bin;
-      vb_hi[j] = (float)vb;
-      vb_lo[j] = (float)(vb - (double)vb_hi[j]);
-      acc[j] = 0.0f;
-      part[j] = 0.0f;
+    for (int q = 0; q < kBinsPerThread; ++q) {
+      const double o = (double)q * kForestThreads * dv_bin;
+      off_hi[q] = (float)o;
+      off_lo[q] = (float)(o - (double)off_hi[q]);
+      acc[q] = 0.0f;
+      part[q] = 0.0f;
     }
     for (int k0 = 0; k0 < nz; k0 += kCellChunk) {
       const int nk = min(kCellChunk, nz - k0);
@@ -54,24 +78,25 @@ __global__ void __launch_bounds__(kForestThreads) forest_kernel(
         double vk = ((double)(k0 + j) + 0.5) * dv_cell + (double)__ldg(vlos + c);
         vk -= V * floor(vk / V);  // into [0, V)
         const float hi = (float)vk;
-        sCell[j] = make_float4(hi, (float)(vk - (double)hi), (float)(rT / THOR_VTH1), (float)(THOR_A1 * rT));
-        sAmp[j] = (float)((double)__ldg(nHI + c) * THOR_SIG1 * rT * ds_cm);
+        const double amp = (double)__ldg(nHI + c) * THOR_SIG1 * rT * ds_cm;
+        const double a = THOR_A1 * rT;
+        sCell[j] = make_float4(hi, (float)(vk - (double)hi), (float)(rT / THOR_VTH1), (float)a);
+        sAmp[j] = make_float2((float)amp, (float)(amp * a * 0.5641895835477563));
       }
       __syncthreads();
       for (int j = 0; j < nk; ++j) {
         const float4 cv = sCell[j];
-        const float amp = sAmp[j];
+        const float2 am = sAmp[j];
         const float a = cv.w;
+        const float dv0 = (vb0_hi - cv.x) + (vb0_lo - cv.y);
 #pragma unroll
         for (int q = 0; q < kBinsPerThread; ++q) {
-          float dv = (vb_hi[q] - cv.x) + (vb_lo[q] - cv.y);
-          dv = (dv >= hV) ? dv - Vf : ((dv < -hV) ? dv + Vf : dv);
+          float dv = (dv0 + off_hi[q]) + off_lo[q];
+          dv = __fmaf_rn(-Vf, rintf(dv * invV), dv);  // nearest periodic image
           const float x = dv * cv.z;
           const float x2 = x * x;
-          float H;
-          if (x2 >= 36.0f) H = voigt_wing(a, x2);
-          else H = voigt_core<true>(a, fabsf(x), x2, sK);
-          part[q] = __fmaf_rn(amp, H, part[q]);
+          if (x2 >= 36.0f) part[q] = __fmaf_rn(am.y, wing_tP(a, x2), part[q]);
+          else part[q] = __fmaf_rn(am.x, voigt_core<true>(a, fabsf(x), x2, sK), part[q]);
         }
         if ((j & 31) == 31) {
 #pragma unroll

@@ -230,7 +230,7 @@ __device__ int grid_event(const GridModel& m, GPhoton& ph, const float* Ktab, ui
   const float vv[3] = {g.vx, g.vy, g.vz};
   const float vk_in = g.vx * ph.k.x + g.vy * ph.k.y + g.vz * ph.k.z;
   bool dust = false;
-  if (g.kd > 0.0f) dust = ph.rng.uni() >= kH / (kH + g.kd);
+  if (g.kd > 0.0f) dust = ph.rng.uni() >= __fdividef(kH, kH + g.kd);
   if (dust) {
     bool scat;
     if (m.albedo <= 0.0f) scat = false;

@@ -40,6 +40,8 @@ struct ShellModel {
   uint8_t* raw_status;
   unsigned long long id_base;
   unsigned long long n_photons;
+  int32_t cancelled;         // served requests: drop in-flight packets (set by the host)
+  int32_t pad_;
 };
 
 // Photon work queue: photon g in [0, total) belongs to model m with
@@ -51,6 +53,27 @@ struct WorkQueue {
   const unsigned long long* first_id;
   const int32_t* model;              // model table index per queue entry
   int32_t n_entries;
+};
+
+// A packet saved between launches of the run-to-completion loop (tail compaction).
+struct PhotonRec {
+  double px, py, pz;
+  float kx, ky, kz, x, X, safe;
+  int32_t region;
+  uint32_t nscat, ndust, iters, steps, event;
+  unsigned long long pid;
+};
+
+// Tail compaction: a launch first resumes saved packets, then takes fresh photons; once
+// both sources are empty, a warp with fewer than `spill_below` live lanes saves them to
+// `spill` and exits, so the next launch runs the survivors in full warps.
+struct Compact {
+  const PhotonRec* resume;
+  unsigned long long n_resume;
+  unsigned long long* resume_next;
+  PhotonRec* spill;
+  unsigned long long* n_spill;
+  int32_t spill_below;  // 0: run to completion
 };
 
 // Resident packet state for time-sliced (served) execution, SoA, one slot per thread.
@@ -104,6 +127,8 @@ int shell_grid(int block, int blocks_per_sm, bool sliced);  // persistent grid s
 int grid_grid(int block, int blocks_per_sm);
 cudaError_t launch_shell_run(const ShellModel* d_models, WorkQueue q, const float* d_ktab, int grid,
                              int block, cudaStream_t s);
+cudaError_t launch_shell_run_compact(const ShellModel* d_models, WorkQueue q, Compact c, const float* d_ktab,
+                                     int grid, int block, cudaStream_t s);
 cudaError_t launch_shell_slice(const ShellModel* d_models, WorkQueue q, SlotState st, uint32_t event_budget,
                                const float* d_ktab, int grid, int block, cudaStream_t s);
 cudaError_t launch_grid_pack(const float* nHI, const float* T, const float* vx, const float* vy,

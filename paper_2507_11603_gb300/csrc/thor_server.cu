@@ -41,6 +41,7 @@ struct Request {
   int slot = -1;           // model-table index while admitted
   int state = 0;           // 0 pending, 1 active, 2 done, 3 cancelled
   bool cancel = false;
+  bool cancel_sent = false;
   Clock::time_point t_submit, t_done;
   thor_result result{};
 };
@@ -135,6 +136,18 @@ void thor_server::run() {
     }
     cudaStream_t s = stream;
     bool ok = true;
+    {
+      // tell the device which admitted requests were cancelled (their packets are dropped)
+      std::lock_guard<std::mutex> lk(mu);
+      for (int i = 0; i < R; ++i) {
+        Request* r = active[i];
+        if (r && r->cancel && !r->cancel_sent) {
+          static const int32_t one = 1;
+          ok &= cudaMemcpyAsync(&d_models[i].cancelled, &one, sizeof one, cudaMemcpyHostToDevice, s) == cudaSuccess;
+          r->cancel_sent = true;
+        }
+      }
+    }
     for (Request* r : fresh) {
       ShellModel m = r->model;
       m.spectrum = d_spec + (size_t)r->slot * (max_bins + 2);

@@ -77,7 +77,7 @@ __device__ __forceinline__ float safe_distance(const ShellModel& m, const Photon
 // interaction lies inside the safety ball skip the FP64 ray-sphere geometry (the common
 // case for photons trapped in the line core).
 __device__ int shell_event(const ShellModel& m, Photon& ph, const float* __restrict__ Ktab) {
-  ph.rng.next_event();
+  ph.rng.next_event(m.kapd > 0.0f ? 3u : 2u);
   float tau_rem = -__logf(ph.rng.uni());  // Eq. 3: tau ~ Exp(1)
   float x_site, kH;
   for (;;) {
@@ -96,7 +96,7 @@ __device__ int shell_event(const ShellModel& m, Photon& ph, const float* __restr
       const float H = voigt<false>(m.a, ph.x, Ktab);
       kH = m.kap0 * H;
       const float kap = kH + m.kapd;
-      const float s = tau_rem / kap;
+      const float s = __fdividef(tau_rem, kap);
       ++ph.steps;
       if (s <= ph.safe) {
         advance(ph, s);
@@ -111,7 +111,7 @@ __device__ int shell_event(const ShellModel& m, Photon& ph, const float* __restr
       const float dtau = kap * ds;
       ++ph.steps;
       if (dtau >= tau_rem) {
-        const float s = tau_rem / kap;
+        const float s = __fdividef(tau_rem, kap);
         advance(ph, s);
         ph.safe = __fmaf_rd(-s, 1.000001f, ph.safe);
         x_site = ph.x - m.gam * s;
@@ -175,7 +175,7 @@ __device__ int shell_event(const ShellModel& m, Photon& ph, const float* __restr
   ph.x = x_site;
   // Interaction (Sec. 3.4): channel i with probability tau_i / sum_i tau_i.
   bool dust = false;
-  if (m.kapd > 0.0f) dust = ph.rng.uni() >= kH / (kH + m.kapd);
+  if (m.kapd > 0.0f) dust = ph.rng.uni() >= __fdividef(kH, kH + m.kapd);
   if (dust) {
     bool scat;
     if (m.albedo <= 0.0f) scat = false;
@@ -246,9 +246,33 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Run-to-completion: all queue entries belong to one model (thor_run).
+__device__ __forceinline__ void save_rec(const Photon& ph, PhotonRec& r) {
+  r.px = ph.px; r.py = ph.py; r.pz = ph.pz;
+  r.kx = ph.k.x; r.ky = ph.k.y; r.kz = ph.k.z;
+  r.x = ph.x; r.X = ph.X; r.safe = ph.safe;
+  r.region = ph.region;
+  r.nscat = ph.nscat; r.ndust = ph.ndust; r.iters = ph.iters; r.steps = ph.steps;
+  r.event = ph.rng.event;
+  r.pid = ph.pid;
+}
+
+__device__ __forceinline__ void load_rec(const ShellModel& m, const PhotonRec& r, Photon& ph) {
+  ph.px = r.px; ph.py = r.py; ph.pz = r.pz;
+  ph.k = make_float3(r.kx, r.ky, r.kz);
+  ph.x = r.x; ph.X = r.X; ph.safe = r.safe;
+  ph.region = r.region;
+  ph.nscat = r.nscat; ph.ndust = r.ndust; ph.iters = r.iters; ph.steps = r.steps;
+  ph.pid = r.pid;
+  ph.rng.keys(((uint64_t)m.seed_hi << 32) | m.seed_lo, ph.pid);
+  ph.rng.event = r.event;
+}
+
+// Run-to-completion: all queue entries belong to one model (thor_run).  With kCompact,
+// lanes first resume saved packets, and a warp whose sources are empty and whose live
+// lanes drop below c.spill_below saves them and exits (tail compaction across launches).
+template <bool kCompact>
 __global__ void __launch_bounds__(256) shell_run_kernel(const ShellModel* __restrict__ models, WorkQueue q,
-                                                        const float* __restrict__ gK) {
+                                                        Compact c, const float* __restrict__ gK) {
   __shared__ __align__(16) float sK[THOR_VOIGT_NINT * THOR_VOIGT_NCOEF];
   __shared__ ShellModel sm;
   load_ktab(sK, gK);
@@ -260,7 +284,18 @@ __global__ void __launch_bounds__(256) shell_run_kernel(const ShellModel* __rest
   bool active = false, done = false;
   LaneTally lt;
   for (;;) {
-    const unsigned need = __ballot_sync(kFull, !active && !done);
+    unsigned need = __ballot_sync(kFull, !active && !done);
+    if (kCompact && need && c.n_resume) {  // saved packets first
+      const int leader = __ffs(need) - 1;
+      unsigned long long base = 0;
+      if ((int)lane == leader) base = atomicAdd(c.resume_next, (unsigned long long)__popc(need));
+      base = __shfl_sync(kFull, base, leader);
+      if (!active && !done) {
+        const unsigned long long g = base + __popc(need & ((1u << lane) - 1u));
+        if (g < c.n_resume) { load_rec(m, c.resume[g], ph); active = true; }
+      }
+      need = __ballot_sync(kFull, !active && !done);
+    }
     if (need) {
       const int leader = __ffs(need) - 1;
       unsigned long long base = 0;
@@ -278,6 +313,20 @@ __global__ void __launch_bounds__(256) shell_run_kernel(const ShellModel* __rest
         }
       }
     }
+    if (kCompact && c.spill_below > 0) {
+      const unsigned live = __ballot_sync(kFull, active);
+      if (__any_sync(kFull, done) && __popc(live) < c.spill_below) {
+        if (live) {
+          const int leader = __ffs(live) - 1;
+          unsigned long long base = 0;
+          if ((int)lane == leader) base = atomicAdd(c.n_spill, (unsigned long long)__popc(live));
+          base = __shfl_sync(kFull, base, leader);
+          if (active) save_rec(ph, c.spill[base + __popc(live & ((1u << lane) - 1u))]);
+        }
+        active = false;
+        break;
+      }
+    }
     if (__all_sync(kFull, !active)) break;
     if (active) {
       const int st = shell_event(m, ph, sK);
@@ -293,13 +342,13 @@ __global__ void __launch_bounds__(256) shell_run_kernel(const ShellModel* __rest
     }
   }
   // flush lane tallies: warp reduce, one atomic per warp and field
-  const unsigned long long e = warp_sum(lt.esc), a = warp_sum(lt.abs), c = warp_sum(lt.cap),
+  const unsigned long long e = warp_sum(lt.esc), a = warp_sum(lt.abs), cp = warp_sum(lt.cap),
                            s = warp_sum(lt.scat), d = warp_sum(lt.dust), it = warp_sum(lt.iters),
                            sp = warp_sum(lt.steps), dn = warp_sum(lt.done);
   const double s2 = warp_sum(lt.scat2);
   if (lane == 0 && dn) {
     Tally* T = m.tally;
-    atomicAdd(&T->n_escaped, e); atomicAdd(&T->n_absorbed, a); atomicAdd(&T->n_capped, c);
+    atomicAdd(&T->n_escaped, e); atomicAdd(&T->n_absorbed, a); atomicAdd(&T->n_capped, cp);
     atomicAdd(&T->n_scat, s); atomicAdd(&T->n_dust_scat, d); atomicAdd(&T->n_upar_iters, it);
     atomicAdd(&T->n_steps, sp); atomicAdd(&T->n_done, dn); atomicAdd(&T->sum_scat2, s2);
   }
@@ -357,6 +406,11 @@ __global__ void __launch_bounds__(256) shell_slice_kernel(const ShellModel* __re
     if (__all_sync(kFull, !active)) break;
     if (active) {
       const ShellModel& m = models[ph.model];
+      if (*(volatile const int32_t*)&m.cancelled) {  // request cancelled: drop the packet
+        atomicAdd(&m.tally->n_done, 1ull);
+        active = false;
+        continue;
+      }
       const int s = shell_event(m, ph, sK);
       if (s) { finish_global(m, ph, s); active = false; }
     }
@@ -381,7 +435,7 @@ int shell_grid(int block, int blocks_per_sm, bool sliced) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (sliced) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, shell_slice_kernel, block, 0);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, shell_run_kernel, block, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, shell_run_kernel<true>, block, 0);
   if (occ < 1) occ = 1;
   const int b = (blocks_per_sm > 0 && blocks_per_sm < occ) ? blocks_per_sm : occ;
   return sms * b;
@@ -389,7 +443,14 @@ int shell_grid(int block, int blocks_per_sm, bool sliced) {
 
 cudaError_t launch_shell_run(const ShellModel* d_models, WorkQueue q, const float* d_ktab, int grid, int block,
                              cudaStream_t s) {
-  shell_run_kernel<<<grid, block, 0, s>>>(d_models, q, d_ktab);
+  Compact none{};
+  shell_run_kernel<false><<<grid, block, 0, s>>>(d_models, q, none, d_ktab);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shell_run_compact(const ShellModel* d_models, WorkQueue q, Compact c, const float* d_ktab,
+                                     int grid, int block, cudaStream_t s) {
+  shell_run_kernel<true><<<grid, block, 0, s>>>(d_models, q, c, d_ktab);
   return cudaGetLastError();
 }
 

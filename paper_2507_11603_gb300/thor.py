@@ -24,7 +24,7 @@ PHASE = {"isotropic": 0, "dipole": 1, "mixed": 2}
 
 # Every entry point declared in include/thor.h.
 SYMBOLS = [
-    "thor_init", "thor_destroy", "thor_last_error", "thor_ctx_set_stream", "thor_ctx_set_launch",
+    "thor_init", "thor_destroy", "thor_last_error", "thor_ctx_set_stream", "thor_ctx_set_launch", "thor_ctx_set_tail",
     "thor_shell_create", "thor_grid_create", "thor_grid_set_scattering", "thor_geom_destroy", "thor_run",
     "thor_forest", "thor_last_elapsed_ms", "thor_server_create", "thor_server_submit", "thor_server_poll",
     "thor_server_wait", "thor_server_cancel", "thor_server_stats", "thor_server_destroy", "thor_voigt_eval",
@@ -100,6 +100,7 @@ def load(build: bool = True) -> C.CDLL:
             "thor_last_error": ([vp], C.c_char_p),
             "thor_ctx_set_stream": ([vp, vp], C.c_int),
             "thor_ctx_set_launch": ([vp, C.c_int, C.c_int], C.c_int),
+            "thor_ctx_set_tail": ([vp, C.c_int, C.c_int], C.c_int),
             "thor_shell_create": ([vp, P(ShellParams), P(vp)], C.c_int),
             "thor_grid_create": ([vp, vp, vp, vp, vp, P(i32), dbl, C.c_int, P(vp)], C.c_int),
             "thor_grid_set_scattering": ([vp, C.c_int, dbl, dbl], C.c_int),
@@ -236,6 +237,10 @@ class Context:
 
     def set_launch(self, block_size: int, blocks_per_sm: int = 0):
         self._check(self.L.thor_ctx_set_launch(self.h, block_size, blocks_per_sm))
+
+    def set_tail(self, spill_below: int = 16, max_phases: int = 24):
+        """Tail compaction of the shell photon loop (0 = off); results do not depend on it."""
+        self._check(self.L.thor_ctx_set_tail(self.h, spill_below, max_phases))
 
     # -------------------------------------------------------------- geometries
     def shell(self, *, T, R_in=0.0, R_out=1.0, N_HI=0.0, tau0=0.0, v_max=0.0, tau_dust=0.0, albedo=0.0, g_hg=0.73,
