@@ -30,6 +30,7 @@
 // DDA cell walk must be bit-reproducible, see dda_*).
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <cmath>
 #include <cstdint>
@@ -92,33 +93,44 @@ void philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t 
 
 // Draw convention (shared by definition with the CUDA path, implemented separately):
 // key = (seed low 32, seed high 32).  Photon p's emission is event 0 and its k-th
-// interaction event (draw of tau, propagation, interaction) is event k; the words of
-// event e are the Philox blocks with counter (p low, p high, e, j), j = 0, 1, 2, ...,
-// four 32-bit words per block, consumed in order; words left at the end of an event
-// are not used.  A uniform variate consumes one word u and is (u + 1/2) 2^-32.
+// interaction event (draw of tau, propagation, interaction) is event k.  Word j of
+// event e is component j % 4 of the Philox block with counter (p low, p high, e, j / 4).
+// Each random quantity has a fixed word (below); a uniform variate from word u is
+// (u + 1/2) 2^-32.  Words that an event does not need are never looked at.
+//   interaction event:
+//     0 tau; 1, 2, 3 u_par rejection iteration 0 (region, angle, acceptance);
+//     4, 5 perpendicular atom velocity (Box-Muller radius, angle); 6 mu; 7 azimuth;
+//     8 channel (HI or dust); 9 dust albedo test; 10 isotropic-or-dipole choice of the
+//     mixed phase function; u_par iteration i >= 1 takes words 0, 1, 2 of block i + 2.
+//     Dust scattering uses 6 (Henyey-Greenstein mu) and 7 (azimuth).
+//   emission (gridless): 0 mu, 1 azimuth, 2, 3 Gaussian line (Box-Muller);
+//   emission (grid): 0 cell, 1-3 position in the cell, 4 mu, 5 azimuth, 6, 7 line.
+enum Word : uint32_t {
+  W_TAU = 0, W_UPAR0 = 1, W_BM_R = 4, W_BM_PHI = 5, W_MU = 6, W_PHI = 7, W_CHANNEL = 8, W_ALBEDO = 9,
+  W_MIXED = 10
+};
+
 struct Stream {
   uint32_t key[2];
   uint32_t pid[2];
   uint32_t event = 0;
-  uint32_t sub = 0;
-  uint32_t buf[4];
-  int pos = 4;
+  std::vector<std::array<uint32_t, 4>> blocks;  // blocks of the current event generated so far
   Stream(uint64_t seed, uint64_t photon, uint32_t ev = 0) {
     key[0] = (uint32_t)seed; key[1] = (uint32_t)(seed >> 32);
     pid[0] = (uint32_t)photon; pid[1] = (uint32_t)(photon >> 32);
     event = ev;
   }
-  void start_event(uint32_t e) { event = e; sub = 0; pos = 4; }
-  uint32_t next() {
-    if (pos == 4) {
-      uint32_t ctr[4] = {pid[0], pid[1], event, sub};
-      philox4x32_10(ctr, key, buf);
-      ++sub;
-      pos = 0;
+  void start_event(uint32_t e) { event = e; blocks.clear(); }
+  uint32_t word(uint32_t j) {
+    while (blocks.size() <= j / 4) {
+      uint32_t ctr[4] = {pid[0], pid[1], event, (uint32_t)blocks.size()};
+      std::array<uint32_t, 4> b;
+      philox4x32_10(ctr, key, b.data());
+      blocks.push_back(b);
     }
-    return buf[pos++];
+    return blocks[j / 4][j % 4];
   }
-  double u() { return ((double)next() + 0.5) * 2.3283064365386963e-10; }
+  double u(uint32_t j) { return ((double)word(j) + 0.5) * 2.3283064365386963e-10; }
 };
 
 // ------------------------------------------------------------------------------
@@ -327,13 +339,15 @@ double u0_rule(double xr, double a) {
 // Region 2 (u >  u0): alpha in (w1, pi), accept with exp(u0^2 - u^2).
 // Negative x by symmetry.  Three draws per iteration: region, alpha, acceptance.
 double sample_upar(double x, double a, Stream& rng, uint64_t* iters) {
+  // iteration 0 uses words 1-3, iteration i >= 1 words 0-2 of block i + 2
   double sgn = (x < 0.0) ? -1.0 : 1.0, xr = std::fabs(x);
   double u0 = u0_rule(xr, a);
   double w1 = std::atan2(a, xr - u0);
   double e0 = std::exp(-u0 * u0);
   double p1 = w1 / (w1 + e0 * (kPi - w1));
   for (uint64_t it = 1;; ++it) {
-    double R1 = rng.u(), R2 = rng.u(), R3 = rng.u();
+    const uint32_t w = (it == 1) ? (uint32_t)W_UPAR0 : 4u * (uint32_t)(it + 1);
+    double R1 = rng.u(w), R2 = rng.u(w + 1), R3 = rng.u(w + 2);
     bool reg1 = R1 < p1;
     double alpha = reg1 ? w1 * R2 : w1 + (kPi - w1) * R2;
     double u = xr - a / std::tan(alpha);
@@ -388,21 +402,21 @@ double scatter_HI(double x, double a, int phase, const double kin[3], Stream& rn
   // (Sec. 3.4.2): for |x| < x_crit the perpendicular speed is drawn from the Gaussian
   // left-truncated at x_crit, r = sqrt(x_crit^2 - ln R).
   double xc = (std::fabs(x) < xcrit) ? xcrit : 0.0;
-  double r = std::sqrt(xc * xc - std::log(rng.u()));
-  double ph = 2.0 * kPi * rng.u();
+  double r = std::sqrt(xc * xc - std::log(rng.u(W_BM_R)));
+  double ph = 2.0 * kPi * rng.u(W_BM_PHI);
   double u1 = r * std::cos(ph), u2 = r * std::sin(ph);
   bool core = std::fabs(x - upar) < 0.2;  // atom-frame frequency (Sec. 2.3.1)
   double mu;
   if (phase == PH_ISO) {
-    mu = mu_isotropic(rng.u());
+    mu = mu_isotropic(rng.u(W_MU));
   } else if (phase == PH_DIPOLE) {
-    mu = mu_dipole(rng.u());
+    mu = mu_dipole(rng.u(W_MU));
   } else {
-    double Rc = rng.u();
-    double Rm = rng.u();
+    double Rc = rng.u(W_MIXED);
+    double Rm = rng.u(W_MU);
     mu = (core && Rc < 1.0 / 3.0) ? mu_isotropic(Rm) : mu_dipole(Rm);
   }
-  double phi = 2.0 * kPi * rng.u();
+  double phi = 2.0 * kPi * rng.u(W_PHI);
   double e1[3], e2[3];
   basis(kin, e1, e2);
   double st = std::sqrt(std::max(0.0, 1.0 - mu * mu));
@@ -421,8 +435,8 @@ double scatter_HI(double x, double a, int phase, const double kin[3], Stream& rn
 
 // Scattering angle sampled for a dust interaction (Eq. 9), new direction.
 void scatter_dust(double g, const double kin[3], Stream& rng, double kout[3]) {
-  double mu = mu_hg(rng.u(), g);
-  double phi = 2.0 * kPi * rng.u();
+  double mu = mu_hg(rng.u(W_MU), g);
+  double phi = 2.0 * kPi * rng.u(W_PHI);
   double e1[3], e2[3];
   basis(kin, e1, e2);
   double st = std::sqrt(std::max(0.0, 1.0 - mu * mu));
@@ -450,7 +464,7 @@ extern "C" void orc_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* o
 
 extern "C" void orc_stream_words(uint64_t seed, uint64_t photon, uint64_t n, uint32_t* out) {
   Stream s(seed, photon);
-  for (uint64_t i = 0; i < n; ++i) out[i] = s.next();
+  for (uint64_t i = 0; i < n; ++i) out[i] = s.word((uint32_t)i);
 }
 
 extern "C" double orc_dawson(double x) { return dawson(x); }
@@ -484,9 +498,9 @@ extern "C" void orc_sample_upar(double x, double a, uint64_t seed, int64_t n, do
 }
 
 extern "C" void orc_sample_mu(int kind, double g, uint64_t seed, int64_t n, double* out) {
-  Stream s(seed, 0);
   for (int64_t i = 0; i < n; ++i) {
-    double R = s.u();
+    Stream s(seed, (uint64_t)i);
+    double R = s.u(0);
     out[i] = (kind == 0) ? mu_isotropic(R) : (kind == 1) ? mu_dipole(R) : mu_hg(R, g);
   }
 }
@@ -586,21 +600,21 @@ void run_photon_shell(const ShellModel& m, const orc_source& src, uint64_t seed,
   // Emission: isotropic direction, line profile in the (static) source frame.
   double p[3] = {0.0, 0.0, 0.0}, k[3];
   {
-    double mu = mu_isotropic(rng.u());
-    double phi = 2.0 * kPi * rng.u();
+    double mu = mu_isotropic(rng.u(0));
+    double phi = 2.0 * kPi * rng.u(1);
     double st = std::sqrt(std::max(0.0, 1.0 - mu * mu));
     k[0] = st * std::cos(phi); k[1] = st * std::sin(phi); k[2] = mu;
   }
   double X = src.X0;
   if (src.line == 1) {
-    double R1 = rng.u(), R2 = rng.u();
+    double R1 = rng.u(2), R2 = rng.u(3);
     X += src.sigma * std::sqrt(-2.0 * std::log(R1)) * std::cos(2.0 * kPi * R2);
   }
   bool in_cavity = (m.geometry == 0 && m.R_in > 0.0);
   for (uint32_t ev = 1;; ++ev) {
     rng.start_event(ev);
     // draw the optical depth to the next interaction (Eq. 3): tau = -ln R
-    double tau_rem = -std::log(rng.u());
+    double tau_rem = -std::log(rng.u(W_TAU));
     bool interact = false;
     while (!interact) {
       if (in_cavity) {
@@ -651,13 +665,13 @@ void run_photon_shell(const ShellModel& m, const orc_source& src, uint64_t seed,
     double x = (X - dot(v, k)) / m.vth;
     double kHI = m.kap0 * voigt_H(m.a, x);
     bool dust = false;
-    if (m.kapd > 0.0) dust = rng.u() >= kHI / (kHI + m.kapd);
+    if (m.kapd > 0.0) dust = rng.u(W_CHANNEL) >= kHI / (kHI + m.kapd);
     double kout[3];
     if (dust) {
       bool scat;
       if (m.albedo <= 0.0) scat = false;
       else if (m.albedo >= 1.0) scat = true;
-      else scat = rng.u() < m.albedo;
+      else scat = rng.u(W_ALBEDO) < m.albedo;
       if (!scat) { out.X = X; out.status = 2; return; }
       scatter_dust(m.g, k, rng, kout);
       X = X + dot(v, kout) - dot(v, k);  // frequency unchanged in the gas (grain) frame
@@ -930,22 +944,22 @@ extern "C" int orc_run_grid(const float* nHI, const float* T, const float* vx, c
     std::vector<double>& cb = cubes[t];
     bool peel = run->peel && cube;
     // emission
-    double R = rng.u() * g.total;
+    double R = rng.u(0) * g.total;
     int64_t c = std::upper_bound(g.cdf.begin(), g.cdf.end(), R) - g.cdf.begin();
     if (c >= nc) c = nc - 1;
     int ci[3] = {(int)(c % g.n[0]), (int)((c / g.n[0]) % g.n[1]), (int)(c / ((int64_t)g.n[0] * g.n[1]))};
     double p[3];
-    for (int a = 0; a < 3; ++a) p[a] = (double)ci[a] + rng.u();
+    for (int a = 0; a < 3; ++a) p[a] = (double)ci[a] + rng.u(1 + a);
     double k[3];
     {
-      double mu = mu_isotropic(rng.u());
-      double phi = 2.0 * kPi * rng.u();
+      double mu = mu_isotropic(rng.u(4));
+      double phi = 2.0 * kPi * rng.u(5);
       double st = std::sqrt(std::max(0.0, 1.0 - mu * mu));
       k[0] = st * std::cos(phi); k[1] = st * std::sin(phi); k[2] = mu;
     }
     double xe;
     {
-      double R1 = rng.u(), R2 = rng.u();
+      double R1 = rng.u(6), R2 = rng.u(7);
       xe = std::sqrt(-std::log(R1)) * std::cos(2.0 * kPi * R2);  // N(0, 1/2)
     }
     double vc[3] = {g.vx[c], g.vy[c], g.vz[c]};
@@ -962,7 +976,7 @@ extern "C" int orc_run_grid(const float* nHI, const float* T, const float* vx, c
     uint32_t ev = 0;
     while (status == 0) {
       rng.start_event(++ev);
-      double tau_rem = -std::log(rng.u());
+      double tau_rem = -std::log(rng.u(W_TAU));
       DDA w; w.init(p, k);
       bool hit = false;
       int64_t cc = 0;
@@ -999,13 +1013,13 @@ extern "C" int orc_run_grid(const float* nHI, const float* T, const float* vx, c
       }
       double v[3] = {g.vx[cc], g.vy[cc], g.vz[cc]};
       bool dust = false;
-      if (kD > 0.0) dust = rng.u() >= kH / (kH + kD);
+      if (kD > 0.0) dust = rng.u(W_CHANNEL) >= kH / (kH + kD);
       double kout[3];
       if (dust) {
         bool scat;
         if (run->albedo <= 0.0) scat = false;
         else if (run->albedo >= 1.0) scat = true;
-        else scat = rng.u() < run->albedo;
+        else scat = rng.u(W_ALBEDO) < run->albedo;
         if (!scat) { status = 2; r.n_absorbed++; break; }
         if (peel) {
           for (int ax = 0; ax < 3; ++ax) {
