@@ -216,7 +216,7 @@ def run_shell_bench(args):
             ev[i][1].record(stream)
             kern_ms += r.stats["elapsed_ms"]
             n_scat += r.stats["n_scat"]
-            launches += 1
+            launches += int(r.stats["n_launches"])
         torch.cuda.synchronize()
     barrier(world)
     step_ms = sum(a.elapsed_time(b) for a, b in ev)
@@ -262,6 +262,11 @@ def run_shell_bench(args):
                      "peak_source": f"152 SMs x 128 lanes x {sm_max:.0f} MHz (max SM clock of measured peaks)"},
         "clocks": clk.summary(),
     }
+    if args.stream_in_line > 0:
+        # p50/p99 latency of the served shell-model stream (the metric's second half), on a
+        # stated subset of the 256-request stream
+        line["stream"] = stream_bench(ctx, n_requests=args.stream_in_line, nhi_max=args.stream_nhi_max,
+                                      core_skip=not args.no_core_skip)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(seconds=args.cpu_seconds)
     print(json.dumps(line))
@@ -357,16 +362,29 @@ def run_stream_bench(args):
 
 
 def run_probe(args):
-    """Small launch for profiling: a static sphere (tau0 = --probe-tau0, T = 1e4 K, dipole)
-    with --probe-photons photons, run twice (the second launch is the one to capture)."""
+    """Small launch for profiling, run twice (the second launch is the one to capture).
+    --probe-model sphere: a static sphere (tau0 = --probe-tau0, T = 1e4 K, dipole);
+    --probe-model shell: the bench's expanding shell.  Photons --probe-first-id ..
+    + --probe-photons - 1, each stopped after --probe-max-scat scatterings (0 = never).
+    With one photon this times the per-event latency of a lone lane, which bounds the
+    tail of the shell run."""
     from paper_2507_11603_gb300 import thor
     ctx = thor.Context(0)
-    g = ctx.shell(tau0=args.probe_tau0, T=1e4, phase="dipole")
-    for i in range(2):
-        r = ctx.run(g, n_photons=args.probe_photons, seed=i, n_bins=50, X_min=-500, X_max=500)
     n = args.probe_photons
-    print(json.dumps({"probe": "static sphere", "tau0": args.probe_tau0, "photons": n, **r.stats,
-                      "us_per_event_chain": r.stats["elapsed_ms"] * 1e3 / (r.stats["n_scat"] / n)}))
+    kw = dict(n_photons=n, first_id=args.probe_first_id, max_scat=args.probe_max_scat)
+    if args.probe_model == "shell":
+        g = ctx.shell(**SHELL)
+        for i in range(2):
+            r = ctx.run(g, seed=1, **RUN, **kw)
+        desc = {"probe": "expanding shell (bench workload)"}
+    else:
+        g = ctx.shell(tau0=args.probe_tau0, T=1e4, phase="dipole")
+        for i in range(2):
+            r = ctx.run(g, seed=i, n_bins=50, X_min=-500, X_max=500, **kw)
+        desc = {"probe": "static sphere", "tau0": args.probe_tau0}
+    events = r.stats["n_scat"] + r.stats["n_dust_scat"]
+    print(json.dumps({**desc, "photons": n, "first_id": args.probe_first_id, **r.stats,
+                      "us_per_event_chain": r.stats["elapsed_ms"] * 1e3 / max(events / n, 1e-30)}))
 
 
 def run_grid_bench(args):
@@ -441,8 +459,13 @@ def main():
     ap.add_argument("--workload", default="shell", choices=["shell", "forest", "stream", "grid", "probe"])
     ap.add_argument("--probe-tau0", type=float, default=1e5)
     ap.add_argument("--probe-photons", type=int, default=64)
+    ap.add_argument("--probe-model", choices=("sphere", "shell"), default="sphere")
+    ap.add_argument("--probe-first-id", type=int, default=0)
+    ap.add_argument("--probe-max-scat", type=int, default=0)
     ap.add_argument("--grid-photons", type=int, default=20000)
     ap.add_argument("--stream-requests", type=int, default=256)
+    ap.add_argument("--stream-in-line", type=int, default=64,
+                    help="requests of the served stream measured after the main bench (0 = skip)")
     ap.add_argument("--stream-nhi-max", type=float, default=1e21)
     ap.add_argument("--no-core-skip", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)

@@ -164,6 +164,9 @@ typedef struct {
   uint64_t n_peel_rays, n_peel_cells;
   double sum_scat2;       /* sum over photons of n_scat^2 */
   double elapsed_ms;      /* device time of the photon loop (CUDA events) */
+  uint64_t n_launches;    /* photon-loop kernel launches made by the call (thor_run, the
+                             allocation-free run); 0 from the server, whose launches are
+                             shared between requests */
 } thor_result;
 
 /* Run photons first_id .. first_id + n_photons - 1 of the stream `seed` through the

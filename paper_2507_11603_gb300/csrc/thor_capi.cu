@@ -56,6 +56,9 @@ thor_ctx::~thor_ctx() {
 }
 
 // ------------------------------------------------------------------------------ context
+// Target warps per SM sub-partition (scheduler) when a tail relaunch spreads survivors.
+constexpr int kWarpsPerSmsp = 4;
+
 extern "C" int thor_init(int device, thor_ctx_t* out) {
   if (!out) { g_init_error = "thor_init: out is NULL"; return THOR_ERR_INVALID_ARG; }
   *out = nullptr;
@@ -322,6 +325,7 @@ extern "C" int thor_run(thor_ctx_t ctx, thor_geom_t g, const thor_source* src, u
   if (int rc = ctx->cuda(cudaMemcpyAsync(qb, &qh, sizeof qh, cudaMemcpyHostToDevice, s), "queue upload")) return rc;
   if (int rc = ctx->cuda(cudaMemsetAsync(d_tally, 0, sizeof(Tally), s), "clear tally")) return rc;
   if (int rc = ctx->cuda(cudaMemsetAsync(d_stats, 0, 16, s), "clear stats")) return rc;
+  unsigned long long n_launch = 0;
   WorkQueue q;
   q.next = (unsigned long long*)(qb + offsetof(QHost, next));
   q.total = n_photons;
@@ -353,10 +357,14 @@ extern "C" int thor_run(thor_ctx_t ctx, thor_geom_t g, const thor_source* src, u
     if (ctx->spill_below <= 0) {
       cudaEventRecord(ctx->ev0, s);
       rc = ctx->cuda(launch_shell_run(d_m, q, ctx->d_ktab, gsz, ctx->block, s), "shell photon loop");
+      ++n_launch;
       cudaEventRecord(ctx->ev1, s);
     } else {
-      // Tail compaction: launch, then relaunch over the saved survivors in full warps
-      // until none are left (the last phase runs to completion).
+      // Tail compaction: launch, then relaunch over the saved survivors until none are
+      // left (the last phase runs to completion).  A relaunch packs per_warp survivors
+      // into each warp, per_warp chosen so that the survivors fill about kWarpsPerSmsp
+      // warps on every scheduler: once few packets are left each one runs alone in its
+      // warp, at the latency of a lone lane, instead of waiting on 31 divergent others.
       const unsigned long long lanes = (unsigned long long)gsz * ctx->block;
       const unsigned long long cap = n_photons < lanes ? n_photons : lanes;
       PhotonRec* bufs = (PhotonRec*)ctx->scratch(ctx->b_spill, 2 * cap * sizeof(PhotonRec));
@@ -376,14 +384,26 @@ extern "C" int thor_run(thor_ctx_t ctx, thor_geom_t g, const thor_source* src, u
         c.spill = outb;
         c.n_spill = ctr + 1;
         c.spill_below = last ? 0 : ctx->spill_below;
+        c.per_warp = 32;
         int g = gsz;
         if (phase > 0) {
-          const unsigned long long want = (n_in + ctx->block - 1) / ctx->block;
+          const unsigned long long warps_target = (unsigned long long)ctx->sm_count * 4 * kWarpsPerSmsp;
+          unsigned long long pw = (n_in + warps_target - 1) / warps_target;
+          pw = pw < 1 ? 1 : (pw > 32 ? 32 : pw);
+          c.per_warp = (int)pw;
+          // a warp spills once fewer than half its resumed packets are live; one or two
+          // per warp run to completion
+          if (pw <= 2) c.spill_below = 0;
+          else if (c.spill_below > (int)pw / 2) c.spill_below = (int)pw / 2;
+          const unsigned long long warps = (n_in + pw - 1) / pw;
+          const unsigned long long want = (warps * 32 + ctx->block - 1) / ctx->block;
           g = (int)(want < (unsigned long long)gsz ? want : gsz);
         }
+        const bool final_phase = last || c.spill_below == 0;
         if ((rc = ctx->cuda(launch_shell_run_compact(d_m, q, c, ctx->d_ktab, g, ctx->block, s), "shell photon loop")))
           break;
-        if (last) break;
+        ++n_launch;
+        if (final_phase) break;
         unsigned long long n_out = 0;
         if ((rc = ctx->cuda(cudaMemcpyAsync(&n_out, ctr + 1, sizeof n_out, cudaMemcpyDeviceToHost, s), "spill count")))
           break;
@@ -418,6 +438,7 @@ extern "C" int thor_run(thor_ctx_t ctx, thor_geom_t g, const thor_source* src, u
     const int gsz = grid_grid(ctx->block, ctx->blocks_per_sm);
     cudaEventRecord(ctx->ev0, s);
     rc = ctx->cuda(launch_grid_run(m, q, ctx->d_ktab, gsz, ctx->block, s), "grid photon loop");
+    ++n_launch;
     cudaEventRecord(ctx->ev1, s);
   }
   if (rc) return rc;
@@ -431,6 +452,7 @@ extern "C" int thor_run(thor_ctx_t ctx, thor_geom_t g, const thor_source* src, u
   tally_to_result(t, n_photons, out);
   out->n_peel_rays = st[0];
   out->n_peel_cells = st[1];
+  out->n_launches = n_launch;
   float ms = 0.0f;
   cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
   out->elapsed_ms = ms;

@@ -42,9 +42,15 @@ __host__ __device__ inline double line_sigma0(double T) {
 // ------------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al. 2011, SC'11), written from the published definition.
 // Draw convention: key = seed (low, high).  Photon p's emission is event 0, its k-th
-// interaction event is event k; the words of event e are the blocks with counter
-// (p low, p high, e, j), j = 0, 1, 2, ..., consumed in order (4 words per block);
-// words left at the end of an event are not used.
+// interaction event is event k.  Word j of event e is component j % 4 of the block with
+// counter (p low, p high, e, j / 4).  Every random quantity has a fixed word:
+//   interaction event: 0 tau; 1, 2, 3 u_par rejection iteration 0 (region, angle,
+//     acceptance); 4, 5 perpendicular atom velocity (Box-Muller radius, angle); 6 mu;
+//     7 azimuth; 8 channel (HI or dust); 9 dust albedo test; 10 isotropic-or-dipole
+//     choice of the mixed phase function; rejection iteration i >= 1 takes words 0, 1, 2
+//     of block i + 2.  Dust scattering uses 6 (mu) and 7 (azimuth).
+//   emission (gridless): 0 mu, 1 azimuth, 2, 3 Gaussian line;
+//   emission (grid): 0 cell, 1-3 position in the cell, 4 mu, 5 azimuth, 6, 7 line.
 // ------------------------------------------------------------------------------
 __device__ __forceinline__ void philox10(uint32_t& c0, uint32_t& c1, uint32_t& c2, uint32_t& c3,
                                          uint32_t k0, uint32_t k1) {
@@ -58,65 +64,66 @@ __device__ __forceinline__ void philox10(uint32_t& c0, uint32_t& c1, uint32_t& c
   }
 }
 
-// The first three blocks of an event are generated together when the event starts
-// (one uniform code point, three independent Philox chains); further blocks are
-// generated on demand (extra rejection iterations).  The event index is the whole
-// stream state between events.
+enum : int { W_TAU = 0, W_UPAR0 = 1, W_BM_R = 4, W_BM_PHI = 5, W_MU = 6, W_PHI = 7, W_CHANNEL = 8, W_ALBEDO = 9,
+             W_MIXED = 10 };
+
+// PTX approximate square root, reciprocal and base-2 exponential (one MUFU instruction
+// each, relative error of order 2^-22, no special-case branch; ftz).  Used in the
+// samplers, whose parity with the oracle is statistical.
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// (w + 1/2) 2^-32 in FP32: in (0, 1]
+__device__ __forceinline__ float uni32(uint32_t w) {
+  return fminf(__fmaf_rn(__uint2float_rn(w), 2.3283064365386963e-10f, 1.1641532182693481e-10f), 1.0f);
+}
+
+// The first blocks of an event (one to three) are generated together when the event
+// starts, at one uniform code point; they are read by constant index only, so they stay
+// in registers.  Later blocks (extra rejection iterations) are generated on demand.
+// The event index is the whole stream state between events.
 struct Rng {
   uint32_t k0, k1, p0, p1;  // key, photon id
   uint32_t event;           // current event
-  uint32_t sub;             // next block to generate on demand
-  uint32_t v0, v1, v2, v3, v4, v5, v6, v7, v8, v9, v10, v11;  // preloaded words (v0 next)
-  uint32_t pre;             // preloaded words left
-  uint32_t w0, w1, w2, w3;  // on-demand block
-  uint32_t left;
+  uint32_t v[12];           // words 0..11 of the current event (the preloaded blocks)
 
   __device__ __forceinline__ void block(uint32_t j, uint32_t& a, uint32_t& b, uint32_t& c, uint32_t& d) const {
     uint32_t c0 = p0, c1 = p1, c2 = event, c3 = j;
     philox10(c0, c1, c2, c3, k0, k1);
     a = c0; b = c1; c = c2; d = c3;
   }
-  // nblk = 2 or 3 blocks preloaded (8 words cover a resonant event without dust)
-  __device__ __forceinline__ void start_event(uint32_t e, uint32_t nblk = 3u) {
+  // nblk = 1, 2 or 3 blocks preloaded: 2 cover a resonant or dust event without the
+  // channel, albedo and mixed-phase words
+  __device__ __forceinline__ void start_event(uint32_t e, uint32_t nblk) {
     event = e;
-    block(0u, v0, v1, v2, v3);
-    block(1u, v4, v5, v6, v7);
-    if (nblk > 2u) block(2u, v8, v9, v10, v11);
-    pre = 4u * nblk;
-    sub = nblk;
-    left = 0u;
+    block(0u, v[0], v[1], v[2], v[3]);
+    if (nblk > 1u) block(1u, v[4], v[5], v[6], v[7]);
+    if (nblk > 2u) block(2u, v[8], v[9], v[10], v[11]);
   }
   __device__ __forceinline__ void keys(uint64_t seed, uint64_t pid) {
     k0 = (uint32_t)seed; k1 = (uint32_t)(seed >> 32);
     p0 = (uint32_t)pid; p1 = (uint32_t)(pid >> 32);
   }
-  __device__ __forceinline__ void init(uint64_t seed, uint64_t pid) {
+  __device__ __forceinline__ void init(uint64_t seed, uint64_t pid, uint32_t nblk) {
     keys(seed, pid);
-    start_event(0u);
+    start_event(0u, nblk);
   }
   // next interaction event of the photon
-  __device__ __forceinline__ void next_event(uint32_t nblk = 3u) { start_event(event + 1u, nblk); }
-  __device__ __forceinline__ uint32_t next() {
-    if (pre != 0u) {
-      const uint32_t r = v0;
-      v0 = v1; v1 = v2; v2 = v3; v3 = v4; v4 = v5; v5 = v6; v6 = v7; v7 = v8; v8 = v9; v9 = v10; v10 = v11;
-      --pre;
-      return r;
-    }
-    if (left == 0u) {
-      block(sub, w0, w1, w2, w3);
-      ++sub;
-      left = 4u;
-    }
-    const uint32_t r = w0;
-    w0 = w1; w1 = w2; w2 = w3;
-    --left;
-    return r;
-  }
-  // (u + 1/2) 2^-32 in FP32: in (0, 1]
-  __device__ __forceinline__ float uni() {
-    return fminf(__fmaf_rn(__uint2float_rn(next()), 2.3283064365386963e-10f, 1.1641532182693481e-10f), 1.0f);
-  }
+  __device__ __forceinline__ void next_event(uint32_t nblk) { start_event(event + 1u, nblk); }
+  __device__ __forceinline__ float u(int j) const { return uni32(v[j]); }
 };
 
 // ------------------------------------------------------------------------------
@@ -129,8 +136,9 @@ struct Rng {
 // Relative error against the FP64 truth below 1e-6 for a <= 1e-2 (tested).
 // Ktab points to the 6x12 coefficient table (shared memory in the kernels).
 // ------------------------------------------------------------------------------
+template <bool kAccurate = true>
 __device__ __forceinline__ float voigt_wing(float a, float x2) {
-  const float t = __frcp_rn(__fmaf_rn(a, a, x2));
+  const float t = kAccurate ? __frcp_rn(__fmaf_rn(a, a, x2)) : rcp_approx(__fmaf_rn(a, a, x2));
   float s = 15836.1328125f;
   s = __fmaf_rn(s, t, 2111.484375f);
   s = __fmaf_rn(s, t, 324.84375f);
@@ -164,7 +172,7 @@ template <bool kAccurateExp = true>
 __device__ __forceinline__ float voigt(float a, float x, const float* __restrict__ Ktab) {
   const float ax = fabsf(x);
   const float x2 = ax * ax;
-  if (ax >= 6.0f) return voigt_wing(a, x2);
+  if (ax >= 6.0f) return voigt_wing<kAccurateExp>(a, x2);
   return voigt_core<kAccurateExp>(a, ax, x2, Ktab);
 }
 
@@ -194,21 +202,42 @@ __device__ __forceinline__ float envelope_D(float xr, float a, float u0) {
 
 __device__ __forceinline__ float u0_rule(float xr, float a) {
   if (xr <= 0.0f) return 0.0f;
-  const float d = sqrtf(a * (0.5f / kPiF)) * rsqrtf(xr) * __expf(fminf(0.5f * xr * xr, 80.0f));
+  const float d = sqrt_approx(a * (0.5f / kPiF)) * rsqrtf(xr) * __expf(fminf(0.5f * xr * xr, 80.0f));
   const float c1 = fmaxf(0.0f, xr - d);
   if (xr <= 2.0f) return c1;
   float u = fminf(xr - 0.3f, 2.0f + 0.6f * __logf(xr));
+  const float c2 = 2.0f * kPiF * rcp_approx(a);
 #pragma unroll
   for (int it = 0; it < 3; ++it) {
     const float dx = xr - u;
-    const float g = u * u - __logf(2.0f * kPiF * u * dx * dx / a);
-    const float gp = 2.0f * u - __frcp_rn(u) + 2.0f * __frcp_rn(dx);
-    u = fminf(fmaxf(u - g / gp, 0.5f), xr - 1e-3f);
+    const float g = u * u - __logf(c2 * u * dx * dx);
+    const float gp = 2.0f * u - rcp_approx(u) + 2.0f * rcp_approx(dx);
+    u = fminf(fmaxf(u - __fdividef(g, gp), 0.5f), xr - 1e-3f);
   }
   return (envelope_D(xr, a, c1) <= envelope_D(xr, a, u)) ? c1 : u;
 }
 
-__device__ __forceinline__ float sample_upar(float x, float a, Rng& rng, uint32_t& iters) {
+// cot(pi t) for t in (0, 1]: with s = t (t <= 1/2) or t - 1 (exact), z = pi s in
+// [-pi/2, pi/2]; near the pole (|z| <= 1/4) the Laurent series
+// 1/z - z (1/3 + z^2/45 + 2 z^4/945 + z^6/4725) (truncation < 1e-10 relative), elsewhere
+// MUFU cosine / sine (|sin z| > 0.24, so their 2^-21 absolute error stays ~1e-6 relative).
+__device__ __forceinline__ float cot_pi(float t) {
+  const float s = (t > 0.5f) ? t - 1.0f : t;
+  const float z = kPiF * s;
+  if (fabsf(z) <= 0.25f) {
+    const float z2 = z * z;
+    float g = __fmaf_rn(z2, 1.0f / 4725.0f, 2.0f / 945.0f);
+    g = __fmaf_rn(g, z2, 1.0f / 45.0f);
+    g = __fmaf_rn(g, z2, 1.0f / 3.0f);
+    return __fmaf_rn(-z, g, rcp_approx(z));
+  }
+  float sn, cs;
+  __sincosf(z, &sn, &cs);
+  return cs * rcp_approx(sn);
+}
+
+// Iteration 0 takes words 1-3 of the event, iteration i >= 1 words 0-2 of block i + 2.
+__device__ __forceinline__ float sample_upar(float x, float a, const Rng& rng, uint32_t& iters) {
   const float sgn = (x < 0.0f) ? -1.0f : 1.0f;
   const float xr = fabsf(x);
   const float u0 = u0_rule(xr, a);
@@ -217,17 +246,17 @@ __device__ __forceinline__ float sample_upar(float x, float a, Rng& rng, uint32_
   const float p1 = __fdividef(w1, __fmaf_rn(e0, kPiF - w1, w1));
   const float u02 = u0 * u0;
   const float w1p = w1 * (1.0f / kPiF);  // alpha in units of pi
+  uint32_t r1 = rng.v[W_UPAR0], r2 = rng.v[W_UPAR0 + 1], r3 = rng.v[W_UPAR0 + 2], spare, blk = 3u;
   float u;
   for (;;) {
-    const float R1 = rng.uni(), R2 = rng.uni(), R3 = rng.uni();
+    const float R1 = uni32(r1), R2 = uni32(r2), R3 = uni32(r3);
     const bool reg1 = R1 < p1;
     const float t = reg1 ? w1p * R2 : __fmaf_rn(1.0f - w1p, R2, w1p);
-    float sn, cs;
-    sincospif(t, &sn, &cs);
-    u = __fmaf_rn(-a * cs, __frcp_rn(sn), xr);  // x - a cot(alpha)
+    u = __fmaf_rn(-a, cot_pi(t), xr);  // x - a cot(alpha)
     const float acc = reg1 ? __expf(-u * u) : __expf(u02 - u * u);
     ++iters;
     if (R3 <= acc) break;
+    rng.block(blk++, r1, r2, r3, spare);
   }
   return sgn * u;
 }
@@ -236,8 +265,8 @@ __device__ __forceinline__ float sample_upar(float x, float a, Rng& rng, uint32_
 enum : int { PH_ISO = 0, PH_DIPOLE = 1, PH_MIXED = 2 };
 __device__ __forceinline__ float mu_dipole(float R) {  // CDF (mu^3 + 3 mu + 4)/8, Cardano
   const float B = __fmaf_rn(4.0f, R, -2.0f);
-  const float A = exp2f(__log2f(B + sqrtf(__fmaf_rn(B, B, 1.0f))) * (1.0f / 3.0f));  // cube root, argument in [0.23, 4.3]
-  return A - __frcp_rn(A);
+  const float A = ex2_approx(__log2f(B + sqrt_approx(__fmaf_rn(B, B, 1.0f))) * (1.0f / 3.0f));  // cube root, argument in [0.23, 4.3]
+  return A - rcp_approx(A);
 }
 __device__ __forceinline__ float mu_hg(float R, float g) {  // Eq. 9 inverse CDF
   if (fabsf(g) < 1e-6f) return __fmaf_rn(2.0f, R, -1.0f);
@@ -269,30 +298,30 @@ struct AtomFrame {  // what peeling-off needs from a resonant scattering
 // x_out = x_in + u . (k_out - k_in) and overwrites k with k_out.
 // Core-skipping (Sec. 3.4.2): for |x| < xcrit the perpendicular speed comes from the
 // Gaussian left-truncated at xcrit, r = sqrt(xcrit^2 - ln R) (xcrit = 0: plain Eq. 5).
-__device__ __forceinline__ float scatter_resonant(float x, float a, int phase, float3& k, Rng& rng,
+__device__ __forceinline__ float scatter_resonant(float x, float a, int phase, float3& k, const Rng& rng,
                                                   uint32_t& iters, AtomFrame* af, float xcrit = 0.0f) {
   const float upar = sample_upar(x, a, rng, iters);
   const float xc = (fabsf(x) < xcrit) ? xcrit : 0.0f;
-  const float r = sqrtf(__fmaf_rn(xc, xc, -__logf(rng.uni())));
+  const float r = sqrt_approx(__fmaf_rn(xc, xc, -__logf(rng.u(W_BM_R))));
   float sp1, cp1;
-  __sincosf(2.0f * kPiF * rng.uni(), &sp1, &cp1);
+  __sincosf(2.0f * kPiF * rng.u(W_BM_PHI), &sp1, &cp1);
   const float u1 = r * cp1, u2 = r * sp1;
   const bool core = fabsf(x - upar) < 0.2f;
   float mu;
   if (phase == PH_ISO) {
-    mu = __fmaf_rn(2.0f, rng.uni(), -1.0f);
+    mu = __fmaf_rn(2.0f, rng.u(W_MU), -1.0f);
   } else if (phase == PH_DIPOLE) {
-    mu = mu_dipole(rng.uni());
+    mu = mu_dipole(rng.u(W_MU));
   } else {
-    const float Rc = rng.uni();
-    const float Rm = rng.uni();
+    const float Rc = rng.u(W_MIXED);
+    const float Rm = rng.u(W_MU);
     mu = (core && Rc < (1.0f / 3.0f)) ? __fmaf_rn(2.0f, Rm, -1.0f) : mu_dipole(Rm);
   }
   float sp, cp;
-  __sincosf(2.0f * kPiF * rng.uni(), &sp, &cp);
+  __sincosf(2.0f * kPiF * rng.u(W_PHI), &sp, &cp);
   float3 e1, e2;
   basis(k.x, k.y, k.z, e1, e2);
-  const float st = sqrtf(fmaxf(0.0f, 1.0f - mu * mu));
+  const float st = sqrt_approx(fmaxf(0.0f, 1.0f - mu * mu));
   float3 ko;
   ko.x = mu * k.x + st * (cp * e1.x + sp * e2.x);
   ko.y = mu * k.y + st * (cp * e1.y + sp * e2.y);
@@ -304,10 +333,10 @@ __device__ __forceinline__ float scatter_resonant(float x, float a, int phase, f
   return x - upar + __fmaf_rn(upar, mu, st * __fmaf_rn(u1, cp, u2 * sp));
 }
 
-__device__ __forceinline__ void scatter_dust(float g, float3& k, Rng& rng) {
-  const float mu = mu_hg(rng.uni(), g);
+__device__ __forceinline__ void scatter_dust(float g, float3& k, const Rng& rng) {
+  const float mu = mu_hg(rng.u(W_MU), g);
   float sp, cp;
-  __sincosf(2.0f * kPiF * rng.uni(), &sp, &cp);
+  __sincosf(2.0f * kPiF * rng.u(W_PHI), &sp, &cp);
   float3 e1, e2;
   basis(k.x, k.y, k.z, e1, e2);
   const float st = sqrtf(fmaxf(0.0f, 1.0f - mu * mu));
@@ -319,10 +348,10 @@ __device__ __forceinline__ void scatter_dust(float g, float3& k, Rng& rng) {
   k = make_float3(ko.x * inv, ko.y * inv, ko.z * inv);
 }
 
-__device__ __forceinline__ float3 iso_dir(Rng& rng) {
-  const float mu = __fmaf_rn(2.0f, rng.uni(), -1.0f);
+__device__ __forceinline__ float3 iso_dir(float Rmu, float Rphi) {
+  const float mu = __fmaf_rn(2.0f, Rmu, -1.0f);
   float sp, cp;
-  __sincosf(2.0f * kPiF * rng.uni(), &sp, &cp);
+  __sincosf(2.0f * kPiF * Rphi, &sp, &cp);
   const float st = sqrtf(fmaxf(0.0f, 1.0f - mu * mu));
   return make_float3(st * cp, st * sp, mu);
 }

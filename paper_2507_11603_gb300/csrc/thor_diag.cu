@@ -46,7 +46,7 @@ __global__ void upar_kernel(float x, float a, uint64_t seed, int64_t n, float* _
   uint32_t it = 0;
   if (i < n) {
     Rng rng;
-    rng.init(seed, (uint64_t)i);
+    rng.init(seed, (uint64_t)i, 1u);
     out[i] = sample_upar(x, a, rng, it);
   }
   unsigned long long s = it;
@@ -59,7 +59,7 @@ __global__ void scatter_once_kernel(float x, float a, int phase, uint64_t seed, 
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   Rng rng;
-  rng.init(seed, (uint64_t)i);
+  rng.init(seed, (uint64_t)i, 3u);
   float3 k = make_float3(0.0f, 0.0f, 1.0f);
   uint32_t it = 0;
   xo[i] = scatter_resonant(x, a, phase, k, rng, it, nullptr);

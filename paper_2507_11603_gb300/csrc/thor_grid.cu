@@ -158,10 +158,10 @@ __device__ __forceinline__ void deposit(const GridModel& m, const double p[3], i
 // Emission (Sec. 2.1, 3.4): cell with probability n_HI^2 / sum, uniform position in it,
 // isotropic direction, thermal x ~ N(0, 1/2) in the cell frame; peel at emission.
 __device__ void grid_emit(const GridModel& m, GPhoton& ph, const float* Ktab, uint32_t& pr, uint32_t& pc) {
-  ph.rng.init(((uint64_t)m.seed_hi << 32) | m.seed_lo, ph.pid);
+  ph.rng.init(((uint64_t)m.seed_hi << 32) | m.seed_lo, ph.pid, 2u);
   const int64_t n = (int64_t)m.nx * m.ny * m.nz;
   const double total = m.cdf[n - 1];
-  const double R = (double)ph.rng.uni() * total;
+  const double R = (double)ph.rng.u(0) * total;
   int64_t lo = 0, hi = n - 1;  // smallest c with cdf[c] > R
   while (lo < hi) {
     const int64_t mid = (lo + hi) >> 1;
@@ -169,16 +169,16 @@ __device__ void grid_emit(const GridModel& m, GPhoton& ph, const float* Ktab, ui
   }
   const int64_t c = lo;
   const int ix = (int)(c % m.nx), iy = (int)((c / m.nx) % m.ny), iz = (int)(c / ((int64_t)m.nx * m.ny));
-  ph.p[0] = ix + (double)ph.rng.uni();
-  ph.p[1] = iy + (double)ph.rng.uni();
-  ph.p[2] = iz + (double)ph.rng.uni();
+  ph.p[0] = ix + (double)ph.rng.u(1);
+  ph.p[1] = iy + (double)ph.rng.u(2);
+  ph.p[2] = iz + (double)ph.rng.u(3);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {  // a uniform of exactly 1.0 would land on the next cell's face
     const double lim = (a == 0 ? ix : a == 1 ? iy : iz) + 1.0;
     if (ph.p[a] >= lim) ph.p[a] = nextafter(lim, 0.0);
   }
-  ph.k = iso_dir(ph.rng);
-  const float R1 = ph.rng.uni(), R2 = ph.rng.uni();
+  ph.k = iso_dir(ph.rng.u(4), ph.rng.u(5));
+  const float R1 = ph.rng.u(6), R2 = ph.rng.u(7);
   const float xe = sqrtf(-__logf(R1)) * cospif(2.0f * R2);
   const GridCell g = load_cell(m.cells, c);
   ph.X = __fmaf_rn(xe, g.vth, g.vx * ph.k.x + g.vy * ph.k.y + g.vz * ph.k.z);
@@ -197,8 +197,8 @@ __device__ void grid_emit(const GridModel& m, GPhoton& ph, const float* Ktab, ui
 
 // One event; returns 0 continue, 1 escaped, 2 absorbed, 3 capped.
 __device__ int grid_event(const GridModel& m, GPhoton& ph, const float* Ktab, uint32_t& pr, uint32_t& pc) {
-  ph.rng.next_event();
-  float tau_rem = -__logf(ph.rng.uni());
+  ph.rng.next_event(3u);
+  float tau_rem = -__logf(ph.rng.u(W_TAU));
   Dda w;
   w.init(ph.p[0], ph.p[1], ph.p[2], (double)ph.k.x, (double)ph.k.y, (double)ph.k.z);
   GridCell g;
@@ -230,12 +230,12 @@ __device__ int grid_event(const GridModel& m, GPhoton& ph, const float* Ktab, ui
   const float vv[3] = {g.vx, g.vy, g.vz};
   const float vk_in = g.vx * ph.k.x + g.vy * ph.k.y + g.vz * ph.k.z;
   bool dust = false;
-  if (g.kd > 0.0f) dust = ph.rng.uni() >= __fdividef(kH, kH + g.kd);
+  if (g.kd > 0.0f) dust = ph.rng.u(W_CHANNEL) >= __fdividef(kH, kH + g.kd);
   if (dust) {
     bool scat;
     if (m.albedo <= 0.0f) scat = false;
     else if (m.albedo >= 1.0f) scat = true;
-    else scat = ph.rng.uni() < m.albedo;
+    else scat = ph.rng.u(W_ALBEDO) < m.albedo;
     if (!scat) return 2;
     if (m.peel) {
       const float kin[3] = {ph.k.x, ph.k.y, ph.k.z};

@@ -57,7 +57,8 @@ struct WorkQueue {
 
 // A packet saved between launches of the run-to-completion loop (tail compaction).
 struct PhotonRec {
-  double px, py, pz;
+  double px, py, pz;  // FP64 anchor
+  float ox, oy, oz;   // FP32 offset from the anchor (saved as is: resuming is bit-exact)
   float kx, ky, kz, x, X, safe;
   int32_t region;
   uint32_t nscat, ndust, iters, steps, event;
@@ -74,11 +75,13 @@ struct Compact {
   PhotonRec* spill;
   unsigned long long* n_spill;
   int32_t spill_below;  // 0: run to completion
+  int32_t per_warp;     // saved packets resumed per warp (1..32): spreads a small tail over the SMs
 };
 
 // Resident packet state for time-sliced (served) execution, SoA, one slot per thread.
 struct SlotState {
-  double *px, *py, *pz;
+  double *px, *py, *pz;              // FP64 anchor
+  float *ox, *oy, *oz, *safe;        // FP32 offset, safety distance (saved as is)
   float *kx, *ky, *kz, *X, *x;
   uint32_t* event;                   // RNG position: events done
   uint32_t *nscat, *ndust, *iters, *steps;

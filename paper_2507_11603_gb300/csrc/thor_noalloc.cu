@@ -165,6 +165,7 @@ extern "C" int thor_run_shell_noalloc(const thor_shell_params* p, const thor_sou
   if (e != cudaSuccess) return fail(THOR_ERR_DEVICE, cudaGetErrorString(e));
   std::memset(out, 0, sizeof *out);
   tally_to_result(t, n_photons, out);
+  out->n_launches = 1;
   if (t.n_done != n_photons) return fail(THOR_ERR_DEVICE, "thor_run_shell_noalloc: photon loop did not finish");
   return THOR_OK;
 }

@@ -256,7 +256,7 @@ extern "C" int thor_server_create(thor_ctx_t ctx, const thor_server_config* cfg,
   s->active.assign(R, nullptr);
   const size_t spec_bytes = (size_t)R * (s->max_bins + 2) * 8;
   const int64_t n = s->n_slots;
-  const size_t slot_bytes = (size_t)n * (3 * 8 + 5 * 4 + 3 * 4 + 4 * 4 + 4 + 8 + 1) + 20 * 256;
+  const size_t slot_bytes = (size_t)n * (3 * 8 + 4 * 4 + 5 * 4 + 4 + 4 * 4 + 4 + 8 + 1) + 24 * 256;
   bool ok = cudaMalloc(&s->d_models, sizeof(ShellModel) * R) == cudaSuccess &&
             cudaMalloc(&s->d_tally, sizeof(Tally) * R) == cudaSuccess &&
             cudaMalloc(&s->d_spec, spec_bytes) == cudaSuccess &&
@@ -272,6 +272,8 @@ extern "C" int thor_server_create(thor_ctx_t ctx, const thor_server_config* cfg,
   auto take = [&](size_t bytes) { char* q = p; p += (bytes + 255) & ~(size_t)255; return (void*)q; };
   SlotState& st = s->st;
   st.px = (double*)take(n * 8); st.py = (double*)take(n * 8); st.pz = (double*)take(n * 8);
+  st.ox = (float*)take(n * 4); st.oy = (float*)take(n * 4); st.oz = (float*)take(n * 4);
+  st.safe = (float*)take(n * 4);
   st.kx = (float*)take(n * 4); st.ky = (float*)take(n * 4); st.kz = (float*)take(n * 4); st.X = (float*)take(n * 4);
   st.x = (float*)take(n * 4);
   st.event = (uint32_t*)take(n * 4);

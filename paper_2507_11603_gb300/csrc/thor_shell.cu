@@ -17,7 +17,8 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 
 struct Photon {
-  double px, py, pz;
+  double px, py, pz;  // FP64 anchor; the position is anchor + offset
+  float ox, oy, oz;   // FP32 offset moved since the anchor (inside the safety ball)
   float3 k;
   float x;     // gas-frame frequency at p (in gas)
   float X;     // lab frequency (in the cavity, and at escape)
@@ -40,12 +41,13 @@ __device__ __forceinline__ int find_entry(const WorkQueue& q, unsigned long long
 
 // Emission (Sec. 3.4): central point source, isotropic, line profile in the source frame.
 __device__ __forceinline__ void shell_emit(const ShellModel& m, Photon& ph) {
-  ph.rng.init(((uint64_t)m.seed_hi << 32) | m.seed_lo, ph.pid);
+  ph.rng.init(((uint64_t)m.seed_hi << 32) | m.seed_lo, ph.pid, 1u);
   ph.px = 0.0; ph.py = 0.0; ph.pz = 0.0;
-  ph.k = iso_dir(ph.rng);
+  ph.ox = 0.0f; ph.oy = 0.0f; ph.oz = 0.0f;
+  ph.k = iso_dir(ph.rng.u(0), ph.rng.u(1));
   float X = m.X0;
   if (m.line == 1) {
-    const float R1 = ph.rng.uni(), R2 = ph.rng.uni();
+    const float R1 = ph.rng.u(2), R2 = ph.rng.u(3);
     X = __fmaf_rn(m.sigma * sqrtf(-2.0f * __logf(R1)), cospif(2.0f * R2), X);
   }
   ph.X = X;
@@ -55,11 +57,18 @@ __device__ __forceinline__ void shell_emit(const ShellModel& m, Photon& ph) {
   ph.nscat = 0; ph.ndust = 0; ph.iters = 0; ph.steps = 0;
 }
 
-// Move by s along k: FP64 position, the increment formed in FP32.
+// Move by s along k inside the safety ball: FP32 offset only.  The moves since the last
+// anchor sum to at most the safety distance (< R_out - R_in), and the offset of a packet
+// trapped in the core stays tiny, so FP32 keeps it far below the step size.
 __device__ __forceinline__ void advance(Photon& ph, float s) {
-  ph.px += (double)(s * ph.k.x);
-  ph.py += (double)(s * ph.k.y);
-  ph.pz += (double)(s * ph.k.z);
+  ph.ox = __fmaf_rn(s, ph.k.x, ph.ox);
+  ph.oy = __fmaf_rn(s, ph.k.y, ph.oy);
+  ph.oz = __fmaf_rn(s, ph.k.z, ph.oz);
+}
+// Fold the offset into the FP64 anchor (before any use of the absolute position).
+__device__ __forceinline__ void anchor(Photon& ph) {
+  ph.px += (double)ph.ox; ph.py += (double)ph.oy; ph.pz += (double)ph.oz;
+  ph.ox = 0.0f; ph.oy = 0.0f; ph.oz = 0.0f;
 }
 
 // Exact distance from p to the nearest boundary, rounded down (conservative).
@@ -77,11 +86,12 @@ __device__ __forceinline__ float safe_distance(const ShellModel& m, const Photon
 // interaction lies inside the safety ball skip the FP64 ray-sphere geometry (the common
 // case for photons trapped in the line core).
 __device__ int shell_event(const ShellModel& m, Photon& ph, const float* __restrict__ Ktab) {
-  ph.rng.next_event(m.kapd > 0.0f ? 3u : 2u);
-  float tau_rem = -__logf(ph.rng.uni());  // Eq. 3: tau ~ Exp(1)
+  ph.rng.next_event((m.kapd > 0.0f || m.phase == PH_MIXED) ? 3u : 2u);
+  float tau_rem = -__logf(ph.rng.u(W_TAU));  // Eq. 3: tau ~ Exp(1)
   float x_site, kH;
   for (;;) {
     if (ph.region) {  // empty cavity: straight to the inner sphere, lab X conserved
+      anchor(ph);
       const double kx = ph.k.x, ky = ph.k.y, kz = ph.k.z;
       const double b = ph.px * kx + ph.py * ky + ph.pz * kz;
       const double c = ph.px * ph.px + ph.py * ph.py + ph.pz * ph.pz - m.R_in * m.R_in;
@@ -105,6 +115,19 @@ __device__ int shell_event(const ShellModel& m, Photon& ph, const float* __restr
         break;
       }
     } else if (ph.safe >= m.ds_core) {
+      // Rate at the start of the step: a crossing within ds_core / 16 of the start is a
+      // sub-step of its own, integrated with that rate (the common case in the core).
+      const float H0 = voigt<false>(m.a, ph.x, Ktab);
+      const float kap_s = __fmaf_rn(m.kap0, H0, m.kapd);
+      const float s0 = __fdividef(tau_rem, kap_s);
+      if (s0 <= 0.0625f * m.ds_core) {
+        ++ph.steps;
+        advance(ph, s0);
+        ph.safe = __fmaf_rd(-s0, 1.000001f, ph.safe);
+        x_site = ph.x - m.gam * s0;
+        kH = m.kap0 * H0;
+        break;
+      }
       const float ds = m.ds_core;
       const float xm = ph.x - m.gam * 0.5f * ds;
       const float kap = __fmaf_rn(m.kap0, voigt<false>(m.a, xm, Ktab), m.kapd);
@@ -125,6 +148,7 @@ __device__ int shell_event(const ShellModel& m, Photon& ph, const float* __restr
       continue;
     }
     // ---- general path: exact segment to the next boundary (FP64), then sub-steps
+    anchor(ph);
     const double kx = ph.k.x, ky = ph.k.y, kz = ph.k.z;
     const double b = ph.px * kx + ph.py * ky + ph.pz * kz;
     const double pp = ph.px * ph.px + ph.py * ph.py + ph.pz * ph.pz;
@@ -175,12 +199,12 @@ __device__ int shell_event(const ShellModel& m, Photon& ph, const float* __restr
   ph.x = x_site;
   // Interaction (Sec. 3.4): channel i with probability tau_i / sum_i tau_i.
   bool dust = false;
-  if (m.kapd > 0.0f) dust = ph.rng.uni() >= __fdividef(kH, kH + m.kapd);
+  if (m.kapd > 0.0f) dust = ph.rng.u(W_CHANNEL) >= __fdividef(kH, kH + m.kapd);
   if (dust) {
     bool scat;
     if (m.albedo <= 0.0f) scat = false;
     else if (m.albedo >= 1.0f) scat = true;
-    else scat = ph.rng.uni() < m.albedo;
+    else scat = ph.rng.u(W_ALBEDO) < m.albedo;
     if (!scat) return 2;
     scatter_dust(m.g_hg, ph.k, ph.rng);  // gas-frame frequency unchanged
     ++ph.ndust;
@@ -190,6 +214,7 @@ __device__ int shell_event(const ShellModel& m, Photon& ph, const float* __restr
   ph.x = scatter_resonant(x_site, m.a, m.phase, ph.k, ph.rng, ph.iters, nullptr, m.xcrit);
   ++ph.nscat;
   if (m.max_scat && ph.nscat >= m.max_scat) {
+    anchor(ph);
     const float b = (float)(ph.px * ph.k.x + ph.py * ph.k.y + ph.pz * ph.k.z);
     ph.X = __fmaf_rn(ph.x, m.vth, m.vgrad * b);
     return 3;
@@ -248,6 +273,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 __device__ __forceinline__ void save_rec(const Photon& ph, PhotonRec& r) {
   r.px = ph.px; r.py = ph.py; r.pz = ph.pz;
+  r.ox = ph.ox; r.oy = ph.oy; r.oz = ph.oz;
   r.kx = ph.k.x; r.ky = ph.k.y; r.kz = ph.k.z;
   r.x = ph.x; r.X = ph.X; r.safe = ph.safe;
   r.region = ph.region;
@@ -258,6 +284,7 @@ __device__ __forceinline__ void save_rec(const Photon& ph, PhotonRec& r) {
 
 __device__ __forceinline__ void load_rec(const ShellModel& m, const PhotonRec& r, Photon& ph) {
   ph.px = r.px; ph.py = r.py; ph.pz = r.pz;
+  ph.ox = r.ox; ph.oy = r.oy; ph.oz = r.oz;
   ph.k = make_float3(r.kx, r.ky, r.kz);
   ph.x = r.x; ph.X = r.X; ph.safe = r.safe;
   ph.region = r.region;
@@ -271,7 +298,7 @@ __device__ __forceinline__ void load_rec(const ShellModel& m, const PhotonRec& r
 // lanes first resume saved packets, and a warp whose sources are empty and whose live
 // lanes drop below c.spill_below saves them and exits (tail compaction across launches).
 template <bool kCompact>
-__global__ void __launch_bounds__(256) shell_run_kernel(const ShellModel* __restrict__ models, WorkQueue q,
+__global__ void __launch_bounds__(256, 1) shell_run_kernel(const ShellModel* __restrict__ models, WorkQueue q,
                                                         Compact c, const float* __restrict__ gK) {
   __shared__ __align__(16) float sK[THOR_VOIGT_NINT * THOR_VOIGT_NCOEF];
   __shared__ ShellModel sm;
@@ -285,13 +312,14 @@ __global__ void __launch_bounds__(256) shell_run_kernel(const ShellModel* __rest
   LaneTally lt;
   for (;;) {
     unsigned need = __ballot_sync(kFull, !active && !done);
-    if (kCompact && need && c.n_resume) {  // saved packets first
-      const int leader = __ffs(need) - 1;
+    const unsigned takers = (kCompact && c.per_warp < 32) ? need & ((1u << c.per_warp) - 1u) : need;
+    if (kCompact && takers && c.n_resume) {  // saved packets first (lanes below per_warp)
+      const int leader = __ffs(takers) - 1;
       unsigned long long base = 0;
-      if ((int)lane == leader) base = atomicAdd(c.resume_next, (unsigned long long)__popc(need));
+      if ((int)lane == leader) base = atomicAdd(c.resume_next, (unsigned long long)__popc(takers));
       base = __shfl_sync(kFull, base, leader);
-      if (!active && !done) {
-        const unsigned long long g = base + __popc(need & ((1u << lane) - 1u));
+      if ((takers >> lane) & 1u) {
+        const unsigned long long g = base + __popc(takers & ((1u << lane) - 1u));
         if (g < c.n_resume) { load_rec(m, c.resume[g], ph); active = true; }
       }
       need = __ballot_sync(kFull, !active && !done);
@@ -357,7 +385,7 @@ __global__ void __launch_bounds__(256) shell_run_kernel(const ShellModel* __rest
 // Time-sliced execution over resident slots (one per thread): resume the packet in the
 // slot, run at most `budget` events per lane, refill finished lanes from the queue of
 // admitted requests, and save what is still in flight.
-__global__ void __launch_bounds__(256) shell_slice_kernel(const ShellModel* __restrict__ models, WorkQueue q,
+__global__ void __launch_bounds__(256, 2) shell_slice_kernel(const ShellModel* __restrict__ models, WorkQueue q,
                                                           SlotState st, uint32_t budget,
                                                           const float* __restrict__ gK) {
   __shared__ __align__(16) float sK[THOR_VOIGT_NINT * THOR_VOIGT_NCOEF];
@@ -374,10 +402,11 @@ __global__ void __launch_bounds__(256) shell_slice_kernel(const ShellModel* __re
     ph.rng.keys(((uint64_t)m.seed_hi << 32) | m.seed_lo, ph.pid);
     ph.rng.event = st.event[slot];
     ph.px = st.px[slot]; ph.py = st.py[slot]; ph.pz = st.pz[slot];
+    ph.ox = st.ox[slot]; ph.oy = st.oy[slot]; ph.oz = st.oz[slot];
     ph.k = make_float3(st.kx[slot], st.ky[slot], st.kz[slot]);
     ph.X = st.X[slot];
     ph.x = st.x[slot];
-    ph.safe = 0.0f;
+    ph.safe = st.safe[slot];
     ph.region = st.region[slot];
     ph.nscat = st.nscat[slot]; ph.ndust = st.ndust[slot]; ph.iters = st.iters[slot]; ph.steps = st.steps[slot];
     active = true;
@@ -420,6 +449,7 @@ __global__ void __launch_bounds__(256) shell_slice_kernel(const ShellModel* __re
     st.model[slot] = ph.model; st.pid[slot] = ph.pid;
     st.event[slot] = ph.rng.event;
     st.px[slot] = ph.px; st.py[slot] = ph.py; st.pz[slot] = ph.pz;
+    st.ox[slot] = ph.ox; st.oy[slot] = ph.oy; st.oz[slot] = ph.oz; st.safe[slot] = ph.safe;
     st.kx[slot] = ph.k.x; st.ky[slot] = ph.k.y; st.kz[slot] = ph.k.z;
     st.X[slot] = ph.X; st.x[slot] = ph.x; st.region[slot] = (uint8_t)ph.region;
     st.nscat[slot] = ph.nscat; st.ndust[slot] = ph.ndust; st.iters[slot] = ph.iters; st.steps[slot] = ph.steps;

@@ -61,7 +61,8 @@ class Result(C.Structure):
     _fields_ = [("n_photons", C.c_uint64), ("n_escaped", C.c_uint64), ("n_absorbed", C.c_uint64),
                 ("n_capped", C.c_uint64), ("n_scat", C.c_uint64), ("n_dust_scat", C.c_uint64),
                 ("n_upar_iters", C.c_uint64), ("n_steps", C.c_uint64), ("n_peel_rays", C.c_uint64),
-                ("n_peel_cells", C.c_uint64), ("sum_scat2", C.c_double), ("elapsed_ms", C.c_double)]
+                ("n_peel_cells", C.c_uint64), ("sum_scat2", C.c_double), ("elapsed_ms", C.c_double),
+                ("n_launches", C.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
