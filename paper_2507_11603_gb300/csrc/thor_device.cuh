@@ -156,11 +156,21 @@ __device__ __forceinline__ float voigt_core(float a, float ax, float x2, const f
   const float u = ax - ((float)i + 0.5f);
   const float4* c4 = reinterpret_cast<const float4*>(Ktab + i * THOR_VOIGT_NCOEF);
   const float4 q0 = c4[0], q1 = c4[1], q2 = c4[2];
-  float k = q2.w;
-  k = __fmaf_rn(k, u, q2.z); k = __fmaf_rn(k, u, q2.y); k = __fmaf_rn(k, u, q2.x);
-  k = __fmaf_rn(k, u, q1.w); k = __fmaf_rn(k, u, q1.z); k = __fmaf_rn(k, u, q1.y);
-  k = __fmaf_rn(k, u, q1.x); k = __fmaf_rn(k, u, q0.w); k = __fmaf_rn(k, u, q0.z);
-  k = __fmaf_rn(k, u, q0.y); k = __fmaf_rn(k, u, q0.x);
+  float k;
+  if (kAccurateExp) {  // throughput-bound callers: Horner (fewest instructions)
+    k = q2.w;
+    k = __fmaf_rn(k, u, q2.z); k = __fmaf_rn(k, u, q2.y); k = __fmaf_rn(k, u, q2.x);
+    k = __fmaf_rn(k, u, q1.w); k = __fmaf_rn(k, u, q1.z); k = __fmaf_rn(k, u, q1.y);
+    k = __fmaf_rn(k, u, q1.x); k = __fmaf_rn(k, u, q0.w); k = __fmaf_rn(k, u, q0.z);
+    k = __fmaf_rn(k, u, q0.y); k = __fmaf_rn(k, u, q0.x);
+  } else {  // latency-bound callers (photon loops): Estrin, dependency depth 4 instead of 11
+    const float u2 = u * u, u4 = u2 * u2, u8 = u4 * u4;
+    const float p01 = __fmaf_rn(q0.y, u, q0.x), p23 = __fmaf_rn(q0.w, u, q0.z);
+    const float p45 = __fmaf_rn(q1.y, u, q1.x), p67 = __fmaf_rn(q1.w, u, q1.z);
+    const float p89 = __fmaf_rn(q2.y, u, q2.x), pab = __fmaf_rn(q2.w, u, q2.z);
+    const float p03 = __fmaf_rn(p23, u2, p01), p47 = __fmaf_rn(p67, u2, p45), p8b = __fmaf_rn(pab, u2, p89);
+    k = __fmaf_rn(__fmaf_rn(p8b, u4, p47), u4, p03);
+  }
   const float g = kAccurateExp ? expf(-x2) : __expf(-x2);
   const float a2 = a * a;
   const float gauss = g * __fmaf_rn(a2, __fmaf_rn(-2.0f, x2, 1.0f), 1.0f);

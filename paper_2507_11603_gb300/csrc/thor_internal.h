@@ -53,6 +53,9 @@ struct WorkQueue {
   const unsigned long long* first_id;
   const int32_t* model;              // model table index per queue entry
   int32_t n_entries;
+  // optional: {total, n_entries} read from device memory at kernel start instead of the
+  // two fields above, so one captured launch (CUDA graph) serves every round
+  const unsigned long long* hdr = nullptr;
 };
 
 // A packet saved between launches of the run-to-completion loop (tail compaction).

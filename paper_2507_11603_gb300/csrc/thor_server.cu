@@ -10,7 +10,10 @@
 // finished (their spectrum and tallies are copied to the caller's buffers).
 // Packet state and tallies stay on the device across rounds; the per-round host
 // traffic is the queue table (a few hundred bytes) and the tallies of the active
-// requests.  Each photon's stream depends only on (request seed, photon id), and
+// requests.  A round (queue upload, photon-loop launch, counter and tally download) is
+// one CUDA graph captured when the server is created and replayed every round: the
+// kernel reads the queue size from the uploaded table, and the host side of both copies
+// is a fixed pinned buffer.  Each photon's stream depends only on (request seed, photon id), and
 // tallies are integers, so a request's result does not depend on what else ran.
 #include <algorithm>
 #include <chrono>
@@ -58,10 +61,16 @@ struct thor_server {
   ShellModel* d_models = nullptr;
   Tally* d_tally = nullptr;
   unsigned long long* d_spec = nullptr;  // max_requests x (max_bins + 2)
-  char* d_queue = nullptr;               // counter + prefix + first_id + model
+  char* d_queue = nullptr;               // counter, total, n_entries, prefix, first_id, model
   void* d_slots = nullptr;
   SlotState st{};
   cudaStream_t stream = nullptr;
+  // one round as a graph: h_queue (pinned, layout of d_queue) -> d_queue, slice kernel,
+  // d_queue counter and the tallies -> h_out (pinned)
+  char* h_queue = nullptr;
+  char* h_out = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
   // host state
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -82,15 +91,27 @@ struct thor_server {
 
 namespace {
 
-size_t queue_bytes(int max_req) { return 8 + (size_t)(max_req + 1) * 8 + (size_t)max_req * 8 + (size_t)max_req * 4 + 64; }
+// d_queue / h_queue layout: next counter, total, n_entries (u64 each), prefix[R + 1],
+// first_id[R] (u64), model[R] (i32)
+struct QLayout {
+  size_t next = 0, total = 8, n_entries = 16, prefix = 24, first, model, bytes;
+  explicit QLayout(int R) {
+    first = prefix + (size_t)(R + 1) * 8;
+    model = first + (size_t)R * 8;
+    bytes = model + (size_t)R * 4;
+  }
+};
+size_t queue_bytes(int max_req) { return QLayout(max_req).bytes; }
 
 }  // namespace
 
 void thor_server::run() {
   cudaSetDevice(ctx->device);
   const int R = cfg.max_requests;
-  std::vector<unsigned long long> h_prefix(R + 1), h_first(R);
-  std::vector<int32_t> h_model(R);
+  const QLayout L(R);
+  unsigned long long* h_prefix = (unsigned long long*)(h_queue + L.prefix);
+  unsigned long long* h_first = (unsigned long long*)(h_queue + L.first);
+  int32_t* h_model = (int32_t*)(h_queue + L.model);
   std::vector<int> h_entry_req(R);
   std::vector<Tally> h_tally(R);
   std::vector<uint64_t> h_spec;
@@ -156,30 +177,14 @@ void thor_server::run() {
       ok &= cudaMemsetAsync(m.spectrum, 0, (size_t)(max_bins + 2) * 8, s) == cudaSuccess;
       ok &= cudaMemsetAsync(m.tally, 0, sizeof(Tally), s) == cudaSuccess;
     }
-    // queue tables
-    const int ne = std::max(n_entries, 1);
-    unsigned long long zero = 0;
-    char* q = d_queue;
-    unsigned long long* d_next = (unsigned long long*)q;
-    unsigned long long* d_prefix = (unsigned long long*)(q + 8);
-    unsigned long long* d_first = (unsigned long long*)(q + 8 + (size_t)(R + 1) * 8);
-    int32_t* d_model = (int32_t*)(q + 8 + (size_t)(R + 1) * 8 + (size_t)R * 8);
-    ok &= cudaMemcpyAsync(d_next, &zero, 8, cudaMemcpyHostToDevice, s) == cudaSuccess;
-    ok &= cudaMemcpyAsync(d_prefix, h_prefix.data(), (size_t)(ne + 1) * 8, cudaMemcpyHostToDevice, s) == cudaSuccess;
-    ok &= cudaMemcpyAsync(d_first, h_first.data(), (size_t)ne * 8, cudaMemcpyHostToDevice, s) == cudaSuccess;
-    ok &= cudaMemcpyAsync(d_model, h_model.data(), (size_t)ne * 4, cudaMemcpyHostToDevice, s) == cudaSuccess;
-    WorkQueue wq;
-    wq.next = d_next;
-    wq.total = total;
-    wq.prefix = d_prefix;
-    wq.first_id = d_first;
-    wq.model = d_model;
-    wq.n_entries = n_entries;
-    ok &= launch_shell_slice(d_models, wq, st, (uint32_t)cfg.events_per_round, ctx->d_ktab, grid, block, s) == cudaSuccess;
-    unsigned long long h_next = 0;
-    ok &= cudaMemcpyAsync(&h_next, d_next, 8, cudaMemcpyDeviceToHost, s) == cudaSuccess;
-    ok &= cudaMemcpyAsync(h_tally.data(), d_tally, sizeof(Tally) * R, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+    // queue header (the tables were filled in place above), then the captured round
+    ((unsigned long long*)(h_queue + L.next))[0] = 0;
+    ((unsigned long long*)(h_queue + L.total))[0] = total;
+    ((unsigned long long*)(h_queue + L.n_entries))[0] = (unsigned long long)n_entries;
+    ok &= cudaGraphLaunch(gexec, s) == cudaSuccess;
     ok &= cudaStreamSynchronize(s) == cudaSuccess;
+    const unsigned long long h_next = ((const unsigned long long*)h_out)[0];
+    std::memcpy(h_tally.data(), h_out + 8, sizeof(Tally) * R);
     if (!ok) {
       std::lock_guard<std::mutex> lk(mu);
       device_error = true;
@@ -257,7 +262,9 @@ extern "C" int thor_server_create(thor_ctx_t ctx, const thor_server_config* cfg,
   const size_t spec_bytes = (size_t)R * (s->max_bins + 2) * 8;
   const int64_t n = s->n_slots;
   const size_t slot_bytes = (size_t)n * (3 * 8 + 4 * 4 + 5 * 4 + 4 + 4 * 4 + 4 + 8 + 1) + 24 * 256;
-  bool ok = cudaMalloc(&s->d_models, sizeof(ShellModel) * R) == cudaSuccess &&
+  bool ok = cudaMallocHost(&s->h_queue, queue_bytes(R)) == cudaSuccess &&
+            cudaMallocHost(&s->h_out, 8 + sizeof(Tally) * R) == cudaSuccess &&
+            cudaMalloc(&s->d_models, sizeof(ShellModel) * R) == cudaSuccess &&
             cudaMalloc(&s->d_tally, sizeof(Tally) * R) == cudaSuccess &&
             cudaMalloc(&s->d_spec, spec_bytes) == cudaSuccess &&
             cudaMalloc(&s->d_queue, queue_bytes(R)) == cudaSuccess &&
@@ -285,6 +292,33 @@ extern "C" int thor_server_create(thor_ctx_t ctx, const thor_server_config* cfg,
   st.n_slots = n;
   cudaMemsetAsync(st.model, 0xff, n * 4, s->stream);  // all slots empty (-1)
   cudaStreamSynchronize(s->stream);
+  // capture one round (thread-local capture mode: other host threads are unaffected)
+  {
+    const QLayout L(R);
+    WorkQueue wq;
+    wq.next = (unsigned long long*)(s->d_queue + L.next);
+    wq.total = 0;
+    wq.prefix = (const unsigned long long*)(s->d_queue + L.prefix);
+    wq.first_id = (const unsigned long long*)(s->d_queue + L.first);
+    wq.model = (const int32_t*)(s->d_queue + L.model);
+    wq.n_entries = 0;
+    wq.hdr = (const unsigned long long*)(s->d_queue + L.total);
+    cudaStream_t cs = s->stream;
+    bool cap = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (cap) {
+      cudaMemcpyAsync(s->d_queue, s->h_queue, L.bytes, cudaMemcpyHostToDevice, cs);
+      launch_shell_slice(s->d_models, wq, st, (uint32_t)s->cfg.events_per_round, ctx->d_ktab, s->grid, s->block, cs);
+      cudaMemcpyAsync(s->h_out, s->d_queue + L.next, 8, cudaMemcpyDeviceToHost, cs);
+      cudaMemcpyAsync(s->h_out + 8, s->d_tally, sizeof(Tally) * R, cudaMemcpyDeviceToHost, cs);
+      cap = cudaStreamEndCapture(cs, &s->graph) == cudaSuccess &&
+            cudaGraphInstantiate(&s->gexec, s->graph, 0) == cudaSuccess;
+    }
+    if (!cap) {
+      cudaGetLastError();
+      thor_server_destroy(s);
+      return ctx->fail(THOR_ERR_DEVICE, "thor_server_create: capturing the round graph failed");
+    }
+  }
   s->worker = std::thread([s]() { s->run(); });
   *out = s;
   return THOR_OK;
@@ -388,8 +422,12 @@ extern "C" void thor_server_destroy(thor_server_t s) {
   if (s->worker.joinable()) s->worker.join();
   cudaSetDevice(s->ctx->device);
   if (s->stream) cudaStreamSynchronize(s->stream);
+  if (s->gexec) cudaGraphExecDestroy(s->gexec);
+  if (s->graph) cudaGraphDestroy(s->graph);
   for (void* p : {(void*)s->d_models, (void*)s->d_tally, (void*)s->d_spec, (void*)s->d_queue, s->d_slots})
     if (p) cudaFree(p);
+  if (s->h_queue) cudaFreeHost(s->h_queue);
+  if (s->h_out) cudaFreeHost(s->h_out);
   if (s->stream) cudaStreamDestroy(s->stream);
   for (auto& kv : s->all) delete kv.second;
   delete s;

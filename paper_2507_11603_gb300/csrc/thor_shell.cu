@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(256, 1) shell_run_kernel(const ShellModel* __r
   load_ktab(sK, gK);
   if (threadIdx.x == 0) sm = models[q.model[0]];
   __syncthreads();
-  const ShellModel& m = sm;
+  const ShellModel m = sm;  // by value: the fields the event loop reads stay in registers
   const unsigned lane = threadIdx.x & 31u;
   Photon ph;
   bool active = false, done = false;
@@ -356,18 +356,25 @@ __global__ void __launch_bounds__(256, 1) shell_run_kernel(const ShellModel* __r
       }
     }
     if (__all_sync(kFull, !active)) break;
-    if (active) {
-      const int st = shell_event(m, ph, sK);
-      if (st) {
-        if (st == 1) { ++lt.esc; tally_spectrum(m, ph.X); }
-        else if (st == 2) ++lt.abs;
-        else ++lt.cap;
-        lt.scat += ph.nscat; lt.dust += ph.ndust; lt.iters += ph.iters; lt.steps += ph.steps; ++lt.done;
-        lt.scat2 += (double)ph.nscat * (double)ph.nscat;
-        write_raw(m, ph, st);
-        active = false;
+    // events until some lane of the warp finishes its packet: one vote per event, the
+    // refill and spill checks above run only when the set of live lanes changed
+    bool fin;
+    do {
+      fin = false;
+      if (active) {
+        const int st = shell_event(m, ph, sK);
+        if (st) {
+          if (st == 1) { ++lt.esc; tally_spectrum(m, ph.X); }
+          else if (st == 2) ++lt.abs;
+          else ++lt.cap;
+          lt.scat += ph.nscat; lt.dust += ph.ndust; lt.iters += ph.iters; lt.steps += ph.steps; ++lt.done;
+          lt.scat2 += (double)ph.nscat * (double)ph.nscat;
+          write_raw(m, ph, st);
+          active = false;
+          fin = true;
+        }
       }
-    }
+    } while (!__any_sync(kFull, fin));
   }
   // flush lane tallies: warp reduce, one atomic per warp and field
   const unsigned long long e = warp_sum(lt.esc), a = warp_sum(lt.abs), cp = warp_sum(lt.cap),
@@ -390,6 +397,7 @@ __global__ void __launch_bounds__(256, 2) shell_slice_kernel(const ShellModel* _
                                                           const float* __restrict__ gK) {
   __shared__ __align__(16) float sK[THOR_VOIGT_NINT * THOR_VOIGT_NCOEF];
   load_ktab(sK, gK);
+  if (q.hdr) { q.total = q.hdr[0]; q.n_entries = (int32_t)q.hdr[1]; }
   const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool has_slot = slot < st.n_slots;
   const unsigned lane = threadIdx.x & 31u;
