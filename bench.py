@@ -168,7 +168,7 @@ def run_reference(args):
     cb = oracle_sample(seconds=2.0)
     cb["value"] = v
     cb["sample"] = f"{args.steps} steps of ~{args.ref_seconds:.0f} s oracle work each on this workload; " + cb["sample"]
-    print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": "scatterings/s", "n_gpus": 0,
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": "scatterings/s", "n_gpus": world,
                       "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
                       "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                       "data": "synthetic", "config": {"workload": WORKLOAD},
@@ -242,10 +242,13 @@ def run_shell_bench(args):
         return
     pk = peaks()
     sm_max = pk.get("sm_max_mhz", 2070.0)
-    # ALU roofline: lane-instruction issue peak = SMs x 128 lanes x max SM clock
-    peak_lane_ops = 152 * 128 * sm_max * 1e6
-    ops_per_scat = args.ops_per_scat
-    achieved = (n_scat / args.steps) * ops_per_scat / (kern_avg_ms / 1000.0)
+    # Issue roofline of the photon loop (no DRAM traffic to speak of, no dense contraction):
+    # peak = SMs x 4 schedulers x 1 warp instruction per clock x max SM clock; per-unit
+    # figure = warp instructions the kernel executes per resonant scattering on this
+    # workload (ncu smsp__inst_executed.sum / n_scat, profiles/shell_run_kernel_expanding_shell.md)
+    peak_issue = 152 * 4 * sm_max * 1e6
+    inst_per_scat = args.inst_per_scat
+    achieved = (n_scat / args.steps) * inst_per_scat / (kern_avg_ms / 1000.0)
     line = {
         "metric": METRIC, "value": value, "unit": "scatterings/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -256,10 +259,10 @@ def run_shell_bench(args):
         "e2e": {"value": e2e_value, "unit": "scatterings/s", "h2d_bytes_per_step": 256 + 48,
                 "d2h_bytes_per_step": (RUN["n_bins"] + 2) * 8 + 96},
         "gpu_launches": launches,
-        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_lane_ops / 1e12,
-                     "unit": "Tlane-ops/s", "frac": achieved / peak_lane_ops, "traffic": None,
-                     "per_unit": f"{ops_per_scat} thread instructions per scattering (ncu, DESIGN.md)",
-                     "peak_source": f"152 SMs x 128 lanes x {sm_max:.0f} MHz (max SM clock of measured peaks)"},
+        "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_issue / 1e9,
+                     "unit": "Gwarp-inst/s", "frac": achieved / peak_issue, "traffic": None,
+                     "per_unit": f"{inst_per_scat:g} warp instructions per scattering (ncu)",
+                     "peak_source": f"152 SMs x 4 schedulers x {sm_max:.0f} MHz (max SM clock of measured peaks)"},
         "clocks": clk.summary(),
     }
     if args.stream_in_line > 0:
@@ -471,7 +474,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
-    ap.add_argument("--ops-per-scat", type=float, default=float(os.environ.get("THOR_OPS_PER_SCAT", "0") or 0))
+    ap.add_argument("--inst-per-scat", type=float, default=352.0,
+                    help="warp instructions per scattering of the shell photon loop (ncu, bench workload)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

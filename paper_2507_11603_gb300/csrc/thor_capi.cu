@@ -436,6 +436,10 @@ extern "C" int thor_run(thor_ctx_t ctx, thor_geom_t g, const thor_source* src, u
     m.n_photons = n_photons; m.id_base = first_id;
     m.peel_rays = d_stats; m.peel_cells = d_stats + 1;
     const int gsz = grid_grid(ctx->block, ctx->blocks_per_sm);
+    // few photons: spread them so that each runs in a warp of its own where possible
+    const unsigned long long warps = (unsigned long long)gsz * (ctx->block / 32);
+    const unsigned long long pw = (n_photons + warps - 1) / warps;
+    m.per_warp = (int)(pw < 1 ? 1 : (pw > 32 ? 32 : pw));
     cudaEventRecord(ctx->ev0, s);
     rc = ctx->cuda(launch_grid_run(m, q, ctx->d_ktab, gsz, ctx->block, s), "grid photon loop");
     ++n_launch;

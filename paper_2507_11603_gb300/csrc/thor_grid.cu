@@ -96,13 +96,36 @@ __global__ void add_offsets(double* data, int64_t n, const double* tile_pre) {
 
 // ---- photon loop ------------------------------------------------------------------
 struct GPhoton {
-  double p[3];  // position in cell units
+  double p[3];   // FP64 anchor, cell units; the position is anchor + offset
+  float o[3];    // FP32 offset moved since the anchor (inside the current cell)
+  float fhi[3];  // distance from the anchor to the + face of the current cell, per axis
+  float safe;    // lower bound on the distance from the position to any face of the cell (0 = unknown)
+  GridCell gc;   // record of the current cell (valid while safe > 0)
   float3 k;
   float X;
   uint32_t nscat, ndust, iters, steps;
   Rng rng;
   unsigned long long pid;
 };
+
+// Fold the offset into the anchor (before the position is used in FP64).
+__device__ __forceinline__ void g_anchor(GPhoton& ph) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) { ph.p[a] += (double)ph.o[a]; ph.o[a] = 0.0f; }
+}
+
+// Cell-local distances from the anchor (which lies in cell i): + faces per axis and the
+// nearest face overall, rounded down.
+__device__ __forceinline__ void g_cell_frame(GPhoton& ph, const int i[3]) {
+  float s = 1.0f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const double lo = ph.p[a] - (double)i[a], hi = (double)(i[a] + 1) - ph.p[a];
+    ph.fhi[a] = __double2float_rd(hi);
+    s = fminf(s, fminf(__double2float_rd(lo), ph.fhi[a]));
+  }
+  ph.safe = fmaxf(s * 0.999999f, 0.0f);
+}
 
 __device__ __forceinline__ GridCell load_cell(const GridCell* __restrict__ cells, int64_t c) {
   const float4* q = reinterpret_cast<const float4*>(cells + c);
@@ -119,17 +142,18 @@ __device__ __forceinline__ int64_t cell_index(const GridModel& m, int ix, int iy
 
 // Optical depth from p to the box face along +axis at lab frequency Xp (Sec. 3.4.1),
 // cell by cell, stopping once tau > tau_cut.
-__device__ __forceinline__ float peel_tau(const GridModel& m, const double p[3], int axis, float Xp, const float* Ktab,
-                          uint32_t& ncell) {
-  // walk along +axis: the cell index advances by `stride` elements per step
+__device__ __forceinline__ float peel_tau_from(const GridModel& m, const double p[3], int axis, float Xp,
+                                               const float* Ktab, uint32_t& ncell, int skip, float tau0) {
+  // walk along +axis: the cell index advances by `stride` elements per step; the first
+  // `skip` cells (0 or 1) are already in tau0
   const int ix = (int)floor(p[0]), iy = (int)floor(p[1]), iz = (int)floor(p[2]);
   const int n_ax = (axis == 0) ? m.nx : (axis == 1) ? m.ny : m.nz;
-  const int i0 = (axis == 0) ? ix : (axis == 1) ? iy : iz;
+  const int i0 = ((axis == 0) ? ix : (axis == 1) ? iy : iz) + skip;
   const double pa = (axis == 0) ? p[0] : (axis == 1) ? p[1] : p[2];
   const int64_t stride = (axis == 0) ? 1 : (axis == 1) ? (int64_t)m.nx : (int64_t)m.nx * m.ny;
-  int64_t c = cell_index(m, ix, iy, iz);
-  double t = 0.0;
-  float tau = 0.0f;
+  int64_t c = cell_index(m, ix, iy, iz) + (int64_t)skip * stride;
+  double t = skip ? __dadd_rn((double)i0, -pa) : 0.0;
+  float tau = tau0;
   for (int i = i0; i < n_ax; ++i, c += stride) {
     const double tn = __dadd_rn((double)(i + 1), -pa);
     const GridCell g = load_cell(m.cells, c);
@@ -141,6 +165,10 @@ __device__ __forceinline__ float peel_tau(const GridModel& m, const double p[3],
     t = tn;
   }
   return tau;
+}
+__device__ __forceinline__ float peel_tau(const GridModel& m, const double p[3], int axis, float Xp, const float* Ktab,
+                                          uint32_t& ncell) {
+  return peel_tau_from(m, p, axis, Xp, Ktab, ncell, 0, 0.0f);
 }
 
 __device__ __forceinline__ void deposit(const GridModel& m, const double p[3], int axis, float Xp, float wgt) {
@@ -177,6 +205,8 @@ __device__ void grid_emit(const GridModel& m, GPhoton& ph, const float* Ktab, ui
     const double lim = (a == 0 ? ix : a == 1 ? iy : iz) + 1.0;
     if (ph.p[a] >= lim) ph.p[a] = nextafter(lim, 0.0);
   }
+  ph.o[0] = 0.0f; ph.o[1] = 0.0f; ph.o[2] = 0.0f;
+  ph.safe = 0.0f;
   ph.k = iso_dir(ph.rng.u(4), ph.rng.u(5));
   const float R1 = ph.rng.u(6), R2 = ph.rng.u(7);
   const float xe = sqrtf(-__logf(R1)) * cospif(2.0f * R2);
@@ -195,38 +225,82 @@ __device__ void grid_emit(const GridModel& m, GPhoton& ph, const float* Ktab, ui
   }
 }
 
+// Peel-off from the current position towards +axis (Sec. 3.4.1): the first segment runs
+// through the current cell, whose record is known (no load); only a ray that leaves it
+// with tau <= tau_cut walks on.  Weights below e^-tau_cut are not deposited.
+__device__ __forceinline__ void peel_from_cell(const GridModel& m, const GPhoton& ph, int ax, float Xp, float w0,
+                                               const float* Ktab, uint32_t& pr, uint32_t& pc) {
+  const GridCell& g = ph.gc;
+  const float v = (ax == 0) ? g.vx : (ax == 1) ? g.vy : g.vz;
+  const float x = (Xp - v) * g.inv_vth;
+  const float d = (ax == 0) ? ph.fhi[0] - ph.o[0] : (ax == 1) ? ph.fhi[1] - ph.o[1] : ph.fhi[2] - ph.o[2];
+  float tau = __fmaf_rn(g.kap0, voigt<false>(g.a, x, Ktab), g.kd) * fmaxf(d, 0.0f);
+  ++pr;
+  ++pc;
+  double p[3] = {ph.p[0] + (double)ph.o[0], ph.p[1] + (double)ph.o[1], ph.p[2] + (double)ph.o[2]};
+  if (tau <= m.tau_cut) tau = peel_tau_from(m, p, ax, Xp, Ktab, pc, 1, tau);
+  if (tau <= m.tau_cut) deposit(m, p, ax, Xp, w0 * __expf(-tau));
+}
+
 // One event; returns 0 continue, 1 escaped, 2 absorbed, 3 capped.
+// Fast path: while the photon is known to be inside a cell (safe > 0) and the sampled
+// interaction lies within the safety distance, the event needs neither the cell walk nor
+// any FP64 arithmetic (the common case for photons trapped in optically thick cells).
+// Otherwise the cell walk runs from the current position (FP64, the bit-reproducible
+// contract of Dda) and re-establishes the cell frame at the interaction point.
 __device__ int grid_event(const GridModel& m, GPhoton& ph, const float* Ktab, uint32_t& pr, uint32_t& pc) {
   ph.rng.next_event(3u);
   float tau_rem = -__logf(ph.rng.u(W_TAU));
-  Dda w;
-  w.init(ph.p[0], ph.p[1], ph.p[2], (double)ph.k.x, (double)ph.k.y, (double)ph.k.z);
-  GridCell g;
   float x = 0.0f, kH = 0.0f;
-  for (;;) {
-    if (!w.inside(m.nx, m.ny, m.nz)) return 1;
-    double tn;
-    const int ax = w.next_axis(tn);
-    g = load_cell(m.cells, cell_index(m, w.i[0], w.i[1], w.i[2]));
+  bool fast = false;
+  if (ph.safe > 0.0f) {
+    const GridCell& g = ph.gc;
     x = (ph.X - (g.vx * ph.k.x + g.vy * ph.k.y + g.vz * ph.k.z)) * g.inv_vth;
     kH = g.kap0 * voigt<false>(g.a, x, Ktab);
     const float kt = kH + g.kd;
-    const float dt = (float)(tn - w.t);
-    const float dtau = kt * dt;
-    ++ph.steps;
-    if (dtau >= tau_rem && kt > 0.0f) {
-      const double ts = w.t + (double)(tau_rem / kt);
-      const double kk[3] = {(double)ph.k.x, (double)ph.k.y, (double)ph.k.z};
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const double lo = (double)w.i[a], hi = nextafter((double)(w.i[a] + 1), lo);
-        ph.p[a] = fmin(fmax(ph.p[a] + ts * kk[a], lo), hi);
-      }
-      break;
+    const float sdist = __fdividef(tau_rem, kt);
+    if (kt > 0.0f && sdist <= ph.safe) {
+      ++ph.steps;
+      ph.o[0] = __fmaf_rn(sdist, ph.k.x, ph.o[0]);
+      ph.o[1] = __fmaf_rn(sdist, ph.k.y, ph.o[1]);
+      ph.o[2] = __fmaf_rn(sdist, ph.k.z, ph.o[2]);
+      ph.safe = __fmaf_rd(-sdist, 1.000001f, ph.safe);
+      fast = true;
     }
-    tau_rem -= dtau;
-    w.advance(ax, tn);
   }
+  if (!fast) {
+    g_anchor(ph);
+    Dda w;
+    w.init(ph.p[0], ph.p[1], ph.p[2], (double)ph.k.x, (double)ph.k.y, (double)ph.k.z);
+    GridCell g;
+    for (;;) {
+      if (!w.inside(m.nx, m.ny, m.nz)) return 1;
+      double tn;
+      const int ax = w.next_axis(tn);
+      g = load_cell(m.cells, cell_index(m, w.i[0], w.i[1], w.i[2]));
+      x = (ph.X - (g.vx * ph.k.x + g.vy * ph.k.y + g.vz * ph.k.z)) * g.inv_vth;
+      kH = g.kap0 * voigt<false>(g.a, x, Ktab);
+      const float kt = kH + g.kd;
+      const float dt = (float)(tn - w.t);
+      const float dtau = kt * dt;
+      ++ph.steps;
+      if (dtau >= tau_rem && kt > 0.0f) {
+        const double ts = w.t + (double)(tau_rem / kt);
+        const double kk[3] = {(double)ph.k.x, (double)ph.k.y, (double)ph.k.z};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const double lo = (double)w.i[a], hi = nextafter((double)(w.i[a] + 1), lo);
+          ph.p[a] = fmin(fmax(ph.p[a] + ts * kk[a], lo), hi);
+        }
+        break;
+      }
+      tau_rem -= dtau;
+      w.advance(ax, tn);
+    }
+    ph.gc = g;
+    g_cell_frame(ph, w.i);
+  }
+  const GridCell& g = ph.gc;
   const float vv[3] = {g.vx, g.vy, g.vz};
   const float vk_in = g.vx * ph.k.x + g.vy * ph.k.y + g.vz * ph.k.z;
   bool dust = false;
@@ -242,9 +316,7 @@ __device__ int grid_event(const GridModel& m, GPhoton& ph, const float* Ktab, ui
 #pragma unroll
       for (int ax = 0; ax < 3; ++ax) {
         const float Xp = ph.X + vv[ax] - vk_in;
-        const float tau = peel_tau(m, ph.p, ax, Xp, Ktab, pc);
-        ++pr;
-        deposit(m, ph.p, ax, Xp, P_hg(kin[ax], m.g_hg) * (0.5f / kPiF) * __expf(-tau));
+        peel_from_cell(m, ph, ax, Xp, P_hg(kin[ax], m.g_hg) * (0.5f / kPiF), Ktab, pr, pc);
       }
     }
     scatter_dust(m.g_hg, ph.k, ph.rng);
@@ -266,9 +338,7 @@ __device__ int grid_event(const GridModel& m, GPhoton& ph, const float* Ktab, ui
       if (m.phase == PH_ISO) P = 0.5f;
       else if (m.phase == PH_DIPOLE) P = P_dipole(mu);
       else P = af.core ? (0.5f / 3.0f + 2.0f * P_dipole(mu) / 3.0f) : P_dipole(mu);
-      const float tau = peel_tau(m, ph.p, ax, Xp, Ktab, pc);
-      ++pr;
-      deposit(m, ph.p, ax, Xp, P * (0.5f / kPiF) * __expf(-tau));
+      peel_from_cell(m, ph, ax, Xp, P * (0.5f / kPiF), Ktab, pr, pc);
     }
   }
   ph.X = __fmaf_rn(xo, g.vth, g.vx * ph.k.x + g.vy * ph.k.y + g.vz * ph.k.z);
@@ -293,7 +363,7 @@ __global__ void __launch_bounds__(256) grid_run_kernel(GridModel m, WorkQueue q,
   load_ktab(sK, gK);
   const unsigned lane = threadIdx.x & 31u;
   GPhoton ph;
-  bool active = false, done = false;
+  bool active = false, done = (int)lane >= m.per_warp;
   unsigned long long esc = 0, ab = 0, cap = 0, sc = 0, du = 0, it = 0, stp = 0, dn = 0;
   double sc2 = 0.0;
   uint32_t pr = 0, pc = 0;
@@ -316,21 +386,27 @@ __global__ void __launch_bounds__(256) grid_run_kernel(GridModel m, WorkQueue q,
       }
     }
     if (__all_sync(kFull, !active)) break;
-    if (active) {
-      const int st = grid_event(m, ph, sK, pr, pc);
-      if (st) {
-        if (st == 1) {
-          ++esc;
-          const float f = (ph.X - m.X_min) * m.inv_dX;
-          int bin = !(f >= 0.0f) ? m.n_bins : (f >= (float)m.n_bins ? m.n_bins + 1 : (int)f);
-          atomicAdd(&m.spectrum[bin], 1ull);
-        } else if (st == 2) ++ab;
-        else ++cap;
-        sc += ph.nscat; du += ph.ndust; it += ph.iters; stp += ph.steps; ++dn;
-        sc2 += (double)ph.nscat * (double)ph.nscat;
-        active = false;
+    // events until some lane of the warp finishes its packet (one vote per event)
+    bool fin;
+    do {
+      fin = false;
+      if (active) {
+        const int st = grid_event(m, ph, sK, pr, pc);
+        if (st) {
+          if (st == 1) {
+            ++esc;
+            const float f = (ph.X - m.X_min) * m.inv_dX;
+            int bin = !(f >= 0.0f) ? m.n_bins : (f >= (float)m.n_bins ? m.n_bins + 1 : (int)f);
+            atomicAdd(&m.spectrum[bin], 1ull);
+          } else if (st == 2) ++ab;
+          else ++cap;
+          sc += ph.nscat; du += ph.ndust; it += ph.iters; stp += ph.steps; ++dn;
+          sc2 += (double)ph.nscat * (double)ph.nscat;
+          active = false;
+          fin = true;
+        }
       }
-    }
+    } while (!__any_sync(kFull, fin));
   }
   esc = wsum(esc); ab = wsum(ab); cap = wsum(cap); sc = wsum(sc); du = wsum(du); it = wsum(it);
   stp = wsum(stp); dn = wsum(dn); sc2 = wsum(sc2);

@@ -53,8 +53,9 @@ struct WorkQueue {
   const unsigned long long* first_id;
   const int32_t* model;              // model table index per queue entry
   int32_t n_entries;
-  // optional: {total, n_entries} read from device memory at kernel start instead of the
-  // two fields above, so one captured launch (CUDA graph) serves every round
+  // optional: {total, n_entries, event budget} read from device memory at kernel start
+  // instead of the fields above (and the launch's budget), so one captured launch (CUDA
+  // graph) serves every round
   const unsigned long long* hdr = nullptr;
 };
 
@@ -126,6 +127,7 @@ struct GridModel {
   unsigned long long id_base;
   unsigned long long* peel_rays;   // statistics: peel rays traced, cells visited
   unsigned long long* peel_cells;
+  int32_t per_warp;       // lanes per warp that take photons (1..32): few photons spread over all schedulers
 };
 
 // ---- launchers (implemented in the .cu files) ------------------------------------

@@ -91,10 +91,10 @@ struct thor_server {
 
 namespace {
 
-// d_queue / h_queue layout: next counter, total, n_entries (u64 each), prefix[R + 1],
-// first_id[R] (u64), model[R] (i32)
+// d_queue / h_queue layout: next counter, total, n_entries, event budget (u64 each),
+// prefix[R + 1], first_id[R] (u64), model[R] (i32)
 struct QLayout {
-  size_t next = 0, total = 8, n_entries = 16, prefix = 24, first, model, bytes;
+  size_t next = 0, total = 8, n_entries = 16, budget = 24, prefix = 32, first, model, bytes;
   explicit QLayout(int R) {
     first = prefix + (size_t)(R + 1) * 8;
     model = first + (size_t)R * 8;
@@ -102,6 +102,8 @@ struct QLayout {
   }
 };
 size_t queue_bytes(int max_req) { return QLayout(max_req).bytes; }
+
+constexpr uint64_t kIdleRounds = 4;
 
 }  // namespace
 
@@ -118,6 +120,7 @@ void thor_server::run() {
   for (;;) {
     std::vector<Request*> fresh;
     int n_entries = 0;
+    uint64_t budget = 0;
     unsigned long long total = 0;
     {
       std::unique_lock<std::mutex> lk(mu);
@@ -154,6 +157,9 @@ void thor_server::run() {
         ++n_entries;
       }
       h_prefix[n_entries] = total;
+      // rounds run kIdleRounds x longer while nobody waits for admission: fewer launches
+      // and host round trips for the tails of admitted requests
+      budget = pending.empty() ? (uint64_t)cfg.events_per_round * kIdleRounds : (uint64_t)cfg.events_per_round;
     }
     cudaStream_t s = stream;
     bool ok = true;
@@ -181,6 +187,7 @@ void thor_server::run() {
     ((unsigned long long*)(h_queue + L.next))[0] = 0;
     ((unsigned long long*)(h_queue + L.total))[0] = total;
     ((unsigned long long*)(h_queue + L.n_entries))[0] = (unsigned long long)n_entries;
+    ((unsigned long long*)(h_queue + L.budget))[0] = (unsigned long long)budget;
     ok &= cudaGraphLaunch(gexec, s) == cudaSuccess;
     ok &= cudaStreamSynchronize(s) == cudaSuccess;
     const unsigned long long h_next = ((const unsigned long long*)h_out)[0];

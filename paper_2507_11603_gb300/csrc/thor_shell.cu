@@ -392,12 +392,12 @@ __global__ void __launch_bounds__(256, 1) shell_run_kernel(const ShellModel* __r
 // Time-sliced execution over resident slots (one per thread): resume the packet in the
 // slot, run at most `budget` events per lane, refill finished lanes from the queue of
 // admitted requests, and save what is still in flight.
-__global__ void __launch_bounds__(256, 2) shell_slice_kernel(const ShellModel* __restrict__ models, WorkQueue q,
+__global__ void __launch_bounds__(256, 1) shell_slice_kernel(const ShellModel* __restrict__ models, WorkQueue q,
                                                           SlotState st, uint32_t budget,
                                                           const float* __restrict__ gK) {
   __shared__ __align__(16) float sK[THOR_VOIGT_NINT * THOR_VOIGT_NCOEF];
   load_ktab(sK, gK);
-  if (q.hdr) { q.total = q.hdr[0]; q.n_entries = (int32_t)q.hdr[1]; }
+  if (q.hdr) { q.total = q.hdr[0]; q.n_entries = (int32_t)q.hdr[1]; budget = (uint32_t)q.hdr[2]; }
   const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool has_slot = slot < st.n_slots;
   const unsigned lane = threadIdx.x & 31u;
@@ -420,7 +420,8 @@ __global__ void __launch_bounds__(256, 2) shell_slice_kernel(const ShellModel* _
     active = true;
   }
   if (!has_slot) done = true;
-  for (uint32_t ev = 0; ev < budget; ++ev) {
+  uint32_t ev = 0;  // event iterations of this launch (warp-uniform)
+  while (ev < budget) {
     const unsigned need = __ballot_sync(kFull, !active && !done);
     if (need) {
       const int leader = __ffs(need) - 1;
@@ -441,16 +442,27 @@ __global__ void __launch_bounds__(256, 2) shell_slice_kernel(const ShellModel* _
       }
     }
     if (__all_sync(kFull, !active)) break;
-    if (active) {
-      const ShellModel& m = models[ph.model];
-      if (*(volatile const int32_t*)&m.cancelled) {  // request cancelled: drop the packet
-        atomicAdd(&m.tally->n_done, 1ull);
-        active = false;
-        continue;
-      }
-      const int s = shell_event(m, ph, sK);
-      if (s) { finish_global(m, ph, s); active = false; }
+    // The lane's model record, and the cancel flag, once per run of events: a request
+    // cancelled on the host drops its packets here (the flag is set between launches).
+    const ShellModel* mp = models + (active ? ph.model : 0);
+    bool dropped = false;
+    if (active && *(volatile const int32_t*)&mp->cancelled) {
+      atomicAdd(&mp->tally->n_done, 1ull);
+      active = false;
+      dropped = true;
     }
+    if (__any_sync(kFull, dropped)) { ++ev; continue; }  // refill the dropped lanes first
+    const ShellModel mr = *mp;  // by value: the fields the event loop reads stay in registers
+    // events until some lane finishes its packet or the budget is used: one vote per event
+    bool fin;
+    do {
+      fin = false;
+      if (active) {
+        const int r = shell_event(mr, ph, sK);
+        if (r) { finish_global(mr, ph, r); active = false; fin = true; }
+      }
+      ++ev;
+    } while (ev < budget && !__any_sync(kFull, fin));
   }
   if (!has_slot) return;
   if (active) {
