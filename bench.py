@@ -403,7 +403,7 @@ def run_grid_bench(args):
     g = ctx.grid(f["n_HI"], f["T"], f["v"], f["kd"], 100 * synth.PC_CM)
     t_build = time.perf_counter() - t0
     kw = dict(n_bins=256, X_min=-1000.0, X_max=1000.0, peel=True, img_n=128, peel_bins=256, peel_X_min=-1000.0,
-              peel_X_max=1000.0, device_out=True)
+              peel_X_max=1000.0, device_out=True, max_scat=args.grid_max_scat)
     ctx.run(g, n_photons=max(256, args.grid_photons // 16), seed=4, first_id=10 ** 9, **kw)
     ms, scat, steps, rays, cells = [], 0, 0, 0, 0
     with ClockSampler(0) as clk:
@@ -420,9 +420,11 @@ def run_grid_bench(args):
                       "n_gpus": 1, "steps": args.steps, "ms_per_step": 1000 * t / args.steps,
                       "higher_is_better": True, "dtype": "f32", "data": "synthetic",
                       "config": {"workload": f"256^3 grid, {args.grid_photons} photons per step (subset of 1e7)",
-                                 "grid_build_s": t_build},
+                                 "max_scat": args.grid_max_scat, "grid_build_s": t_build},
                       "cell_steps_per_s": steps / t, "peel_rays_per_s": rays / t, "peel_cells_per_s": cells / t,
-                      "gather_bytes_per_s": 32.0 * gathers / t, "clocks": clk.summary()}))
+                      # 32 B per cell step and per peel cell, whether the record comes from memory or,
+                      # for the photon's current cell, from registers
+                      "algorithmic_gather_bytes_per_s": 32.0 * gathers / t, "clocks": clk.summary()}))
     del torch
 
 
@@ -466,6 +468,8 @@ def main():
     ap.add_argument("--probe-first-id", type=int, default=0)
     ap.add_argument("--probe-max-scat", type=int, default=0)
     ap.add_argument("--grid-photons", type=int, default=20000)
+    ap.add_argument("--grid-max-scat", type=int, default=0,
+                    help="stop grid photons after this many scatterings (0 = never; for short profiling runs)")
     ap.add_argument("--stream-requests", type=int, default=256)
     ap.add_argument("--stream-in-line", type=int, default=64,
                     help="requests of the served stream measured after the main bench (0 = skip)")

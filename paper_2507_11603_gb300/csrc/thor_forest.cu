@@ -21,27 +21,12 @@ constexpr int kForestThreads = 256;
 constexpr int kMaxBinsPerThread = 8;  // n_bins <= 2048 per pass
 constexpr int kCellChunk = 1024;    // cells staged per pass
 
-// Wing series (|x| >= 6) without the a/sqrt(pi) factor: t sum_k ((2k+1)!!/2^k) t^k with
-// t = 1/(x^2 + a^2); 8 terms for |x| < 12, 5 terms beyond (truncation < 1e-7 relative).
-// MUFU reciprocal (relative error ~1 ulp, well inside the 1e-5 budget).
+// Wing (|x| >= 6) without the a/sqrt(pi) factor: t g(t), t = 1/(x^2 + a^2), g the
+// degree-4 fit of thor_device.cuh (one polynomial for the whole wing, no branch).  MUFU
+// reciprocal (relative error ~1 ulp, well inside the 1e-5 budget).
 __device__ __forceinline__ float wing_tP(float a2, float x2) {
   const float t = rcp_approx(x2 + a2);
-  float s;
-  if (x2 >= 144.0f) {
-    s = __fmaf_rn(59.0625f, t, 13.125f);
-    s = __fmaf_rn(s, t, 3.75f);
-    s = __fmaf_rn(s, t, 1.5f);
-    s = __fmaf_rn(s, t, 1.0f);
-  } else {
-    s = __fmaf_rn(15836.1328125f, t, 2111.484375f);
-    s = __fmaf_rn(s, t, 324.84375f);
-    s = __fmaf_rn(s, t, 59.0625f);
-    s = __fmaf_rn(s, t, 13.125f);
-    s = __fmaf_rn(s, t, 3.75f);
-    s = __fmaf_rn(s, t, 1.5f);
-    s = __fmaf_rn(s, t, 1.0f);
-  }
-  return t * s;
+  return t * wing_g(t);
 }
 
 // kBinsPerThread bins per thread per pass (1, 2, 4 or 8, the smallest that covers n_bins

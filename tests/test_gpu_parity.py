@@ -267,6 +267,30 @@ def test_grid_photon_loop_and_peeling(ctx, orc):
     assert np.median(rel) < 0.08
 
 
+def test_grid_thick_cells_fast_path(ctx, orc):
+    """Optically thick cells (tau ~ 2e3 per cell at the mean density): nearly every event
+    takes the in-cell fast path (no cell walk) and peel rays start from the known cell;
+    spectrum, scattering counts and the peeled total still match the oracle."""
+    from paper_2507_11603_gb300 import synth
+    mean = 1e-4
+    f = synth.grid_fields(n=16, seed=7, mean_nHI=mean, sigma_ln=1.0, sigma_v=50.0, dust_ratio=1.0,
+                          sigma_dust=4e-22)
+    f["kd"] = (f["kd"] * 2e4 * 2e-7 / mean).astype(np.float32)
+    cell = 100 * 3.0856775814913673e18
+    g = ctx.grid(f["n_HI"], f["T"], f["v"], f["kd"], cell, phase="dipole", albedo=0.32, g_hg=0.73)
+    n = 8000
+    r = ctx.run(g, n_photons=n, seed=4, n_bins=64, X_min=-600, X_max=600, peel=True, img_n=8, peel_bins=64,
+                peel_X_min=-600, peel_X_max=600)
+    of = {"n_HI": f["n_HI"], "T": f["T"], "vx": f["v"][0], "vy": f["v"][1], "vz": f["v"][2], "kd": f["kd"]}
+    ro = orc.run_grid(of, cell_cm=cell, n_photons=n, seed=1004, n_bins=64, img_nx=8, X_min=-600, X_max=600,
+                      phase="dipole", albedo=0.32, g_hg=0.73)
+    c, dof = chi2_dof(r.spectrum, ro["counts"])
+    assert c <= 1.2, (c, dof)
+    assert mean_nscat_z(r.stats, n, ro, n) < 3.0
+    tot_g, tot_o = float(r.cube.astype(np.float64).sum()), float(ro["cube"].sum())
+    assert abs(tot_g / tot_o - 1) < 0.05, (tot_g, tot_o)
+
+
 def test_grid_config4_full_size_builds(ctx):
     """Config 4 fields at 256^3 (packed on the device, emission CDF); a short run checks
     conservation on the full-size grid."""
