@@ -61,6 +61,17 @@ class Result(C.Structure):
                 ("sum_upar_iters", C.c_uint64), ("unused", C.c_double)]
 
 
+class PLShell(C.Structure):
+    """Power-law shell of the shell-model sweep (Sec. 5.1)."""
+    _fields_ = [("dv_ratio", C.c_double), ("N_HI", C.c_double), ("T", C.c_double), ("v_avg", C.c_double),
+                ("alpha_rho", C.c_double), ("alpha_v", C.c_double), ("tau_dust", C.c_double),
+                ("phase", C.c_int32), ("pad", C.c_int32)]
+
+
+class PLSource(C.Structure):
+    _fields_ = [("sigma", C.c_double), ("ew", C.c_double), ("C", C.c_double)]
+
+
 class GridRun(C.Structure):
     _fields_ = [("dims", C.c_int32 * 3), ("phase", C.c_int32), ("cell_cm", C.c_double),
                 ("albedo", C.c_double), ("g_hg", C.c_double), ("n_bins", C.c_int32),
@@ -97,6 +108,14 @@ def lib():
                                         C.c_int32, C.c_double, C.c_double, C.c_uint64, C.c_int32,
                                         P(C.c_uint64), P(Result), P(C.c_double), P(C.c_uint64),
                                         P(C.c_uint8)]
+            L.orc_plshell_profile.argtypes = [P(PLShell), C.c_double, P(C.c_double), P(C.c_double)]
+            L.orc_run_plshell.restype = C.c_int
+            L.orc_run_plshell.argtypes = [P(PLShell), P(PLSource), C.c_uint64, C.c_uint64, C.c_uint64,
+                                          C.c_int32, C.c_double, C.c_double, C.c_uint64, C.c_int32,
+                                          P(C.c_uint64), P(Result), P(C.c_double), P(C.c_double),
+                                          P(C.c_double), P(C.c_uint64), P(C.c_uint8)]
+            L.orc_reweight.argtypes = [C.c_int64, P(C.c_double), P(C.c_double), P(C.c_double), P(C.c_uint8)] + \
+                [C.c_double] * 7 + [C.c_int32, C.c_double, C.c_double, P(C.c_double)]
             L.orc_dda_trace.restype = C.c_int
             L.orc_dda_trace.argtypes = [P(C.c_int32), P(C.c_double), P(C.c_float), C.c_int32,
                                         C.c_int32, P(C.c_int64), P(C.c_double), P(C.c_int32)]
@@ -225,6 +244,49 @@ def run_shell(*, tau0, T, R_in=0.0, R_out=1.0, v_max=0.0, tau_dust=0.0, albedo=0
            "sum_upar_iters": res.sum_upar_iters}
     if raw:
         out.update(X=rx, nscat=rn, status=rs)
+    return out
+
+
+def plshell_profile(*, dv_ratio, N_HI, T, v_avg, alpha_rho, alpha_v, r):
+    """HI opacity per unit length (outer radius = 1) and outflow speed at radius r."""
+    geo = PLShell(dv_ratio, N_HI, T, v_avg, alpha_rho, alpha_v, 0.0, 1, 0)
+    k, v = C.c_double(), C.c_double()
+    lib().orc_plshell_profile(C.byref(geo), r, C.byref(k), C.byref(v))
+    return k.value, v.value
+
+
+def run_plshell(*, dv_ratio, N_HI, T, v_avg, alpha_rho=0.0, alpha_v=1.0, tau_dust=0.0, phase="dipole",
+                sigma=800.0, ew=0.0, C_cont=0.0, n_photons=1000, seed=0, first_id=0, n_bins=200,
+                X_min=-2500.0, X_max=2500.0, max_scat=0, n_threads=0):
+    """Power-law shell run (Sec. 5.1) with per-photon records X0, X, col (units of N_HI)."""
+    geo = PLShell(dv_ratio, N_HI, T, v_avg, alpha_rho, alpha_v, tau_dust, PHASE[phase], 0)
+    src = PLSource(sigma, ew, C_cont)
+    counts = np.zeros(n_bins + 2, dtype=np.uint64)
+    res = Result()
+    x0, x, col = np.zeros(n_photons), np.zeros(n_photons), np.zeros(n_photons)
+    rn = np.zeros(n_photons, dtype=np.uint64)
+    rs = np.zeros(n_photons, dtype=np.uint8)
+    rc = lib().orc_run_plshell(C.byref(geo), C.byref(src), first_id, n_photons, seed, n_bins, X_min, X_max,
+                               max_scat, n_threads, _p(counts, C.c_uint64), C.byref(res), _p(x0, C.c_double),
+                               _p(x, C.c_double), _p(col, C.c_double), _p(rn, C.c_uint64), _p(rs, C.c_uint8))
+    if rc != 0:
+        raise ValueError("orc_run_plshell rejected its arguments")
+    return {"counts": counts[:n_bins], "underflow": int(counts[n_bins]), "overflow": int(counts[n_bins + 1]),
+            "n_escaped": res.n_escaped, "n_absorbed": res.n_absorbed, "n_capped": res.n_capped,
+            "sum_scat": res.sum_scat, "sum_scat2": res.sum_scat2, "sum_upar_iters": res.sum_upar_iters,
+            "X0": x0, "X": x, "col": col, "nscat": rn, "status": rs}
+
+
+def reweight(X0, X, col, status, *, sample, target, tau_d, n_bins, X_min, X_max):
+    """Emergent spectrum reweighted from the sampled intrinsic spectrum sample = (sigma, ew, C)
+    to target = (sigma, ew, C) and dust depth tau_d: sum of weights per bin / n."""
+    X0 = np.ascontiguousarray(X0, dtype=np.float64)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    col = np.ascontiguousarray(col, dtype=np.float64)
+    st = np.ascontiguousarray(status, dtype=np.uint8)
+    out = np.zeros(n_bins + 2)
+    lib().orc_reweight(len(X0), _p(X0, C.c_double), _p(X, C.c_double), _p(col, C.c_double), _p(st, C.c_uint8),
+                       *sample, *target, tau_d, n_bins, X_min, X_max, _p(out, C.c_double))
     return out
 
 

@@ -764,6 +764,304 @@ extern "C" int orc_run_shell(const orc_shell* geo, const orc_source* src, uint64
 }
 
 // ------------------------------------------------------------------------------
+// Power-law shells for the shell-model parameter sweep (Sec. 5.1).
+// Outer radius 1, inner radius 1/dv_ratio (the ratio of the shell radii, >= 1); number
+// density n(r) ~ r^alpha_rho normalised so that the radial column between the radii is
+// N_HI; radial outflow v(r) ~ r^alpha_v normalised so that its distance average over
+// [r_i, 1] is v_avg; uniform T; optional dust with the same radial profile as the gas
+// (tau_dust = its radial optical depth).  Lengths in units of the outer radius, so the
+// HI opacity per unit length is kappa(r) = tau0 f(r) / F with f = r^alpha_rho,
+// F = int_{r_i}^1 f dr and tau0 = N_HI sigma_0 (line-centre column optical depth).
+// Transport integrates tau exactly along each straight path (adaptive Gauss-Legendre
+// pieces, Newton for the crossing), with x(s) = (X - v(r) (p + s k).k / r) / v_th.
+// Each photon records its emitted and escaping lab frequencies and the HI column it
+// traversed (in units of N_HI), from which the emergent spectrum is reweighted to other
+// intrinsic widths, equivalent widths and dust depths (the post-processing of Sec. 5.1).
+// ------------------------------------------------------------------------------
+struct orc_plshell {
+  double dv_ratio;          // r_o / r_i (> 1)
+  double N_HI;              // cm^-2, radial column between the radii
+  double T;                 // K
+  double v_avg;             // km/s, distance-averaged outflow speed
+  double alpha_rho, alpha_v;
+  double tau_dust;          // radial dust optical depth (dust follows the gas), 0 = none
+  int32_t phase;            // 0 isotropic, 1 dipole, 2 mixed
+  int32_t pad;
+};
+
+// Intrinsic spectrum sampled at emission: a Gaussian line of width sigma (km/s) with
+// equivalent width ew (km/s) on a flat continuum over [-C, C] (C = 0: line only).
+struct orc_plsource {
+  double sigma, ew, C;
+};
+
+namespace {
+
+// int_{lo}^{hi} r^alpha dr
+double pow_integral(double alpha, double lo, double hi) {
+  if (std::fabs(alpha + 1.0) < 1e-12) return std::log(hi / lo);
+  return (std::pow(hi, alpha + 1.0) - std::pow(lo, alpha + 1.0)) / (alpha + 1.0);
+}
+
+struct PLShell {
+  double ri, F, kap_n, kap_d, vth, a, v1, ar, av, G;  // v(r) = v1 r^av; G bounds |d(v mu_r)/ds|
+  int phase;
+  double n_rel(double r) const { return std::pow(r, ar); }
+  double vel(double r) const { return v1 * std::pow(r, av); }
+};
+
+PLShell make_plshell(const orc_plshell& p) {
+  PLShell m;
+  m.ri = 1.0 / p.dv_ratio;
+  const double F = pow_integral(p.alpha_rho, m.ri, 1.0);
+  const double tau0 = p.N_HI * sigma0_cm2(p.T);
+  m.F = F;
+  m.kap_n = tau0 / F;
+  m.kap_d = p.tau_dust / F;
+  m.vth = vth_kms(p.T);
+  m.a = voigt_a(p.T);
+  m.ar = p.alpha_rho; m.av = p.alpha_v;
+  m.v1 = p.v_avg * (1.0 - m.ri) / pow_integral(p.alpha_v, m.ri, 1.0);
+  // |d(v(r) mu_r)/ds| = |v'(r) mu_r^2 + v(r) (1 - mu_r^2) / r| <= max(|v'|, v / r)
+  double G = 0.0;
+  for (int i = 0; i <= 2000; ++i) {
+    double r = m.ri + (1.0 - m.ri) * i / 2000.0;
+    G = std::max(G, std::max(std::fabs(p.alpha_v) * m.vel(r) / r, m.vel(r) / r));
+  }
+  m.G = 1.05 * G;
+  m.phase = p.phase;
+  return m;
+}
+
+// Opacity along the ray p + s k inside the gas: HI line plus dust, and the HI column
+// density rate (in units of N_HI per unit length).
+struct PLRay {
+  const PLShell* m;
+  double p[3], k[3], X;
+  void at(double s, double& kap, double& col_rate, double& x) const {
+    double q[3] = {p[0] + s * k[0], p[1] + s * k[1], p[2] + s * k[2]};
+    double r = std::sqrt(dot(q, q));
+    double mur = dot(q, k) / r;
+    double nr = m->n_rel(r);
+    x = (X - m->vel(r) * mur) / m->vth;
+    kap = nr * (m->kap_n * voigt_H(m->a, x) + m->kap_d);
+    col_rate = nr / m->F;  // HI column per unit length in units of N_HI
+  }
+  double kappa(double s) const { double k0, c, x; at(s, k0, c, x); return k0; }
+  // tau and column over [s0, s1] on one Gauss-Legendre piece
+  void piece(double s0, double s1, double& tau, double& col) const {
+    const GaussLegendre& g = gl();
+    double hm = 0.5 * (s1 - s0), c = 0.5 * (s1 + s0), st = 0.0, sc = 0.0;
+    for (int i = 0; i < GaussLegendre::N; ++i) {
+      double k0, cr, x;
+      at(c + hm * g.x[i], k0, cr, x);
+      st += g.w[i] * k0; sc += g.w[i] * cr;
+    }
+    tau = st * hm; col = sc * hm;
+  }
+  // piece length: x moves by at most 0.1 (0.01 |x| in the wings), the density by ~1%
+  double piece_len(double s) const {
+    double k0, cr, x;
+    at(s, k0, cr, x);
+    double dx = (std::fabs(x) < 10.0) ? 0.1 : 0.01 * std::fabs(x);
+    double ls = dx * m->vth / m->G;
+    double q[3] = {p[0] + s * k[0], p[1] + s * k[1], p[2] + s * k[2]};
+    double r = std::sqrt(dot(q, q));
+    if (m->ar != 0.0) ls = std::min(ls, 0.01 * r / std::fabs(m->ar));
+    return ls;
+  }
+};
+
+// Walk [0, S]: true and s_star when tau reaches tau_rem, else false and the total tau;
+// col accumulates the HI column (units of N_HI) up to the stop.
+bool plray_walk(const PLRay& ry, double S, double tau_rem, double* s_star, double* tau_tot, double* col) {
+  double s = 0.0, acc = 0.0;
+  while (s < S) {
+    double s1 = std::min(S, s + ry.piece_len(s));
+    double tp, cp;
+    ry.piece(s, s1, tp, cp);
+    if (acc + tp >= tau_rem && tp > 0.0) {
+      double need = tau_rem - acc, lo = s, hi = s1;
+      double t = s + (s1 - s) * (need / tp);
+      for (int it = 0; it < 100; ++it) {
+        double ft, fc;
+        ry.piece(s, t, ft, fc);
+        double f = ft - need;
+        if (f > 0) hi = t; else lo = t;
+        double k = ry.kappa(t);
+        double tn = (k > 0) ? t - f / k : 0.5 * (lo + hi);
+        if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
+        if (std::fabs(tn - t) <= 1e-14 * std::max(1.0, std::fabs(t)) || hi - lo < 1e-15) { t = tn; break; }
+        t = tn;
+      }
+      double ft, fc;
+      ry.piece(s, t, ft, fc);
+      *col += fc;
+      *s_star = t;
+      return true;
+    }
+    acc += tp;
+    *col += cp;
+    s = s1;
+  }
+  *tau_tot = acc;
+  return false;
+}
+
+struct PLOut { double X0, X, col; uint64_t nscat, iters; uint32_t ndust; uint8_t status; };
+
+// One photon: central point source, isotropic, intrinsic spectrum of orc_plsource
+// (emission words: 0 mu, 1 azimuth, 2-3 Gaussian, 4 line or continuum, 5 continuum
+// position); then the event loop of the shell (Sec. 3.4) on the power-law profiles.
+void run_photon_plshell(const PLShell& m, const orc_plsource& src, uint64_t seed, uint64_t pid, uint64_t cap,
+                        PLOut& out) {
+  Stream rng(seed, pid);
+  out.nscat = 0; out.ndust = 0; out.iters = 0; out.status = 0; out.col = 0.0;
+  double p[3] = {0.0, 0.0, 0.0}, k[3];
+  {
+    double mu = mu_isotropic(rng.u(0));
+    double phi = 2.0 * kPi * rng.u(1);
+    double st = std::sqrt(std::max(0.0, 1.0 - mu * mu));
+    k[0] = st * std::cos(phi); k[1] = st * std::sin(phi); k[2] = mu;
+  }
+  const double p_line = (src.C > 0.0) ? src.ew / (src.ew + 2.0 * src.C) : 1.0;
+  double X;
+  if (rng.u(4) <= p_line) {
+    double R1 = rng.u(2), R2 = rng.u(3);
+    X = src.sigma * std::sqrt(-2.0 * std::log(R1)) * std::cos(2.0 * kPi * R2);
+  } else {
+    X = src.C * (2.0 * rng.u(5) - 1.0);
+  }
+  out.X0 = X;
+  bool in_cavity = true;
+  for (uint32_t ev = 1;; ++ev) {
+    rng.start_event(ev);
+    double tau_rem = -std::log(rng.u(W_TAU));
+    bool interact = false;
+    while (!interact) {
+      if (in_cavity) {  // empty: straight to the inner sphere
+        double s = exit_sphere(p, k, m.ri);
+        for (int i = 0; i < 3; ++i) p[i] += s * k[i];
+        in_cavity = false;
+        continue;
+      }
+      double S = exit_sphere(p, k, 1.0); int next = 0;
+      {
+        double b = dot(p, k), c = dot(p, p) - m.ri * m.ri, disc = b * b - c;
+        if (b < 0.0 && disc > 0.0) {
+          double s_in = -b - std::sqrt(disc);
+          if (s_in < S) { S = std::max(0.0, s_in); next = 1; }
+        }
+      }
+      PLRay ry{&m, {p[0], p[1], p[2]}, {k[0], k[1], k[2]}, X};
+      double s_star = 0.0, tseg = 0.0;
+      if (plray_walk(ry, S, tau_rem, &s_star, &tseg, &out.col)) {
+        for (int i = 0; i < 3; ++i) p[i] += s_star * k[i];
+        interact = true;
+      } else {
+        tau_rem -= tseg;
+        for (int i = 0; i < 3; ++i) p[i] += S * k[i];
+        if (next == 0) { out.X = X; out.status = 1; return; }
+        in_cavity = true;
+      }
+    }
+    // interaction at p: gas velocity v(r) r_hat
+    double r = std::sqrt(dot(p, p));
+    double vr = m.vel(r);
+    double v[3] = {vr * p[0] / r, vr * p[1] / r, vr * p[2] / r};
+    double x = (X - dot(v, k)) / m.vth;
+    double kHI = m.kap_n * m.n_rel(r) * voigt_H(m.a, x);
+    double kd = m.kap_d * m.n_rel(r);
+    bool dust = false;
+    if (kd > 0.0) dust = rng.u(W_CHANNEL) >= kHI / (kHI + kd);
+    if (dust) { out.X = X; out.status = 2; return; }  // dust absorbs (albedo 0 in the sweep)
+    double kout[3];
+    double xo = scatter_HI(x, m.a, m.phase, k, rng, kout, nullptr, &out.iters);
+    X = xo * m.vth + dot(v, kout);
+    out.nscat++;
+    if (out.nscat >= cap) { out.X = X; out.status = 3; return; }
+    for (int i = 0; i < 3; ++i) k[i] = kout[i];
+  }
+}
+
+// Intrinsic spectrum density (per km/s) of the line-plus-continuum model.
+double intrinsic_pdf(double X, double sigma, double ew, double C) {
+  const double pl = (C > 0.0) ? ew / (ew + 2.0 * C) : 1.0;
+  double g = std::exp(-0.5 * X * X / (sigma * sigma)) / (std::sqrt(2.0 * kPi) * sigma);
+  double c = (C > 0.0 && std::fabs(X) <= C) ? 1.0 / (2.0 * C) : 0.0;
+  return pl * g + (1.0 - pl) * c;
+}
+
+}  // namespace
+
+extern "C" void orc_plshell_profile(const orc_plshell* geo, double r, double* n_rel_kappa, double* v) {
+  PLShell m = make_plshell(*geo);
+  *n_rel_kappa = m.kap_n * m.n_rel(r);
+  *v = m.vel(r);
+}
+
+extern "C" int orc_run_plshell(const orc_plshell* geo, const orc_plsource* src, uint64_t first_id, uint64_t n,
+                               uint64_t seed, int32_t n_bins, double X_min, double X_max, uint64_t max_scat,
+                               int32_t n_threads, uint64_t* counts, orc_result* res, double* raw_X0,
+                               double* raw_X, double* raw_col, uint64_t* raw_nscat, uint8_t* raw_status) {
+  if (!geo || !src || !res || !(geo->dv_ratio > 1.0) || !(geo->T > 0.0)) return -1;
+  PLShell m = make_plshell(*geo);
+  int nt = (n_threads <= 0) ? (int)std::max(1u, std::thread::hardware_concurrency()) : n_threads;
+  std::vector<SpecAcc> spec(nt);
+  std::vector<orc_result> acc(nt);
+  for (int t = 0; t < nt; ++t) { spec[t].init(n_bins, X_min, X_max); std::memset(&acc[t], 0, sizeof(orc_result)); }
+  uint64_t cap = max_scat ? max_scat : ~0ull;
+  parallel_photons(n, nt, [&](int t, uint64_t i) {
+    PLOut po;
+    run_photon_plshell(m, *src, seed, first_id + i, cap, po);
+    orc_result& r = acc[t];
+    if (po.status == 1) { r.n_escaped++; spec[t].add(po.X); }
+    else if (po.status == 2) r.n_absorbed++;
+    else r.n_capped++;
+    r.sum_scat += po.nscat;
+    r.sum_scat2 += (double)po.nscat * (double)po.nscat;
+    r.sum_upar_iters += po.iters;
+    if (raw_X0) raw_X0[i] = po.X0;
+    if (raw_X) raw_X[i] = po.X;
+    if (raw_col) raw_col[i] = po.col;
+    if (raw_nscat) raw_nscat[i] = po.nscat;
+    if (raw_status) raw_status[i] = po.status;
+  });
+  std::memset(res, 0, sizeof(orc_result));
+  if (counts) std::memset(counts, 0, sizeof(uint64_t) * (size_t)(n_bins + 2));
+  for (int t = 0; t < nt; ++t) {
+    res->n_escaped += acc[t].n_escaped; res->n_absorbed += acc[t].n_absorbed;
+    res->n_capped += acc[t].n_capped; res->sum_scat += acc[t].sum_scat;
+    res->sum_scat2 += acc[t].sum_scat2; res->sum_upar_iters += acc[t].sum_upar_iters;
+    if (counts) for (int b = 0; b < n_bins + 2; ++b) counts[b] += spec[t].counts[b];
+  }
+  return 0;
+}
+
+// Post-processing of a run's escaped photons (Sec. 5.1): weight
+//   w = p_target(X0) / p_sampled(X0) * exp(-tau_d * col)
+// for a target intrinsic spectrum (sigma, ew, C) and dust depth tau_d (dust following
+// the gas, so its optical depth along a path is tau_d times the HI column in units of
+// N_HI); out[b] = sum of weights per bin / n (n_bins + underflow, overflow).
+extern "C" void orc_reweight(int64_t n, const double* X0, const double* X, const double* col,
+                             const uint8_t* status, double s_sigma, double s_ew, double s_C, double t_sigma,
+                             double t_ew, double t_C, double tau_d, int32_t n_bins, double X_min, double X_max,
+                             double* out) {
+  for (int b = 0; b < n_bins + 2; ++b) out[b] = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (status[i] != 1) continue;
+    const double ps = intrinsic_pdf(X0[i], s_sigma, s_ew, s_C);
+    const double w = (ps > 0.0) ? intrinsic_pdf(X0[i], t_sigma, t_ew, t_C) / ps * std::exp(-tau_d * col[i]) : 0.0;
+    int b;
+    if (X[i] < X_min) b = n_bins;
+    else if (X[i] >= X_max) b = n_bins + 1;
+    else { b = (int)std::floor((X[i] - X_min) / (X_max - X_min) * n_bins); if (b >= n_bins) b = n_bins - 1; }
+    out[b] += w;
+  }
+  for (int b = 0; b < n_bins + 2; ++b) out[b] /= (double)n;
+}
+
+// ------------------------------------------------------------------------------
 // Uniform Cartesian grid (Sec. 3.3), positions in cell units, domain [0,n)^3.
 // Cell walk: Amanatides & Woo (1987) with the following bit-reproducible contract,
 // shared by definition with the CUDA path: FP64 round-to-nearest, no fused
