@@ -428,6 +428,48 @@ def run_grid_bench(args):
     del torch
 
 
+def run_sweep_bench(args):
+    """Shell-model sweep (Sec. 5.1): one radiative-transfer run of the paper's mock model
+    (log N_HI = 18.4, v_avg = 120 km/s, log T = 4, alpha_v = 1, alpha_rho = -0.5, ratio of
+    the radii 10, dipole phase function, intrinsic line sigma = 800 km/s and EW = 3 A on a
+    continuum over +-2500 km/s, 2e5 photons, no dust in the transport), then the
+    post-processing that reweights its escaped photons to --sweep-targets (sigma, EW, tau_d)
+    combinations (400 bins over +-2500 km/s)."""
+    import torch
+    from paper_2507_11603_gb300 import thor
+    ctx = thor.Context(0)
+    stream = torch.cuda.Stream()
+    ctx.set_stream(stream)
+    g = ctx.shell(profile="power_law", R_in=0.1, R_out=1.0, N_HI=10 ** 18.4, T=1e4, v_max=120.0, alpha_rho=-0.5,
+                  alpha_v=1.0, phase="dipole")
+    ew3 = 3.0 / 1215.67 * 299792.458
+    kw = dict(n_photons=200_000, sigma=800.0, ew=ew3, C_cont=2500.0, n_bins=400, X_min=-2500.0, X_max=2500.0,
+              raw=True, raw_sweep=True, device_out=True)
+    ctx.run(g, seed=9, first_id=10 ** 9, **kw)
+    rng = np.random.default_rng(12)
+    K = args.sweep_targets
+    targets = np.stack([rng.uniform(100.0, 800.0, K), rng.uniform(10.0, 200.0, K) / 1215.67 * 299792.458,
+                        np.full(K, 2500.0), rng.uniform(0.0, 2.0, K)], axis=1)
+    ms_rt, ms_rw, scat = [], [], 0
+    with ClockSampler(0) as clk:
+        for i in range(args.steps):
+            r = ctx.run(g, seed=9, first_id=i * 200_000, **kw)
+            ms_rt.append(r.stats["elapsed_ms"])
+            scat += r.stats["n_scat"]
+            ctx.reweight(r.raw_X0, r.raw_X, r.raw_col, r.raw_status, sample=(800.0, ew3, 2500.0), targets=targets,
+                         n_bins=400, X_min=-2500.0, X_max=2500.0)
+            ms_rw.append(ctx.last_elapsed_ms())
+    t_rt, t_rw = sum(ms_rt) / 1000.0, sum(ms_rw) / 1000.0
+    print(json.dumps({"metric": "Lya scatterings/s (power-law shell sweep model, Sec. 5.1)", "value": scat / t_rt,
+                      "unit": "scatterings/s", "n_gpus": 1, "steps": args.steps, "ms_per_step": 1000 * t_rt / args.steps,
+                      "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": "power-law shell, log N_HI 18.4, v_avg 120, log T 4, alpha_v 1, "
+                                             "alpha_rho -0.5, radius ratio 10, 2e5 photons", "targets": K},
+                      "reweight": {"ms_per_call": 1000 * t_rw / args.steps,
+                                   "photon_targets_per_s": 200_000 * K * args.steps / t_rw},
+                      "clocks": clk.summary()}))
+
+
 def run_forest_bench(args):
     import torch
     from paper_2507_11603_gb300 import synth, thor
@@ -461,7 +503,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="shell", choices=["shell", "forest", "stream", "grid", "probe"])
+    ap.add_argument("--workload", default="shell", choices=["shell", "forest", "stream", "grid", "probe", "sweep"])
+    ap.add_argument("--sweep-targets", type=int, default=256)
     ap.add_argument("--probe-tau0", type=float, default=1e5)
     ap.add_argument("--probe-photons", type=int, default=64)
     ap.add_argument("--probe-model", choices=("sphere", "shell"), default="sphere")
@@ -495,6 +538,8 @@ def main():
         run_grid_bench(args)
     elif args.workload == "probe":
         run_probe(args)
+    elif args.workload == "sweep":
+        run_sweep_bench(args)
     else:
         run_shell_bench(args)
 

@@ -85,8 +85,16 @@ int thor_ctx_set_tail(thor_ctx_t ctx, int spill_below, int max_phases);
 /* ---- geometries (Sec. 3.3 datasets) ----------------------------------------------- */
 
 /* Gridless spherical shell (Sec. 3.3; a sphere when R_in = 0), lengths in units of
- * R_out, homologous radial outflow v(r) = v_max r / R_out, a central point source in
- * the empty cavity (Sec. 4 validation setups, shell models of Sec. 5.1). */
+ * R_out, a central point source in the empty cavity.
+ *   profile THOR_PROFILE_HOMOLOGOUS: uniform density, homologous radial outflow
+ *     v(r) = v_max r / R_out (Sec. 4 validation setups);
+ *   profile THOR_PROFILE_POWER_LAW: the shell-model sweep geometry of Sec. 5.1, density
+ *     n ~ r^alpha_rho normalised to the radial column (N_HI or tau0), radial outflow
+ *     v ~ r^alpha_v with distance average v_max over [R_in, R_out] (R_in > 0), dust
+ *     following the gas with radial optical depth tau_dust and albedo 0, and the step
+ *     limiter f min(v_th / max|d(v r_hat.k)/ds|, R_in / |alpha_rho|) (Sec. 5.1). */
+#define THOR_PROFILE_HOMOLOGOUS 0
+#define THOR_PROFILE_POWER_LAW 1
 typedef struct {
   double R_in, R_out;    /* radii, 0 <= R_in < R_out */
   double N_HI;           /* HI column R_in -> R_out [cm^-2]; used when tau0 <= 0 */
@@ -99,6 +107,10 @@ typedef struct {
   int32_t phase;         /* THOR_PHASE_* for resonant scattering */
   int32_t core_skip;     /* 1: core-skipping, x_crit = 0.2 (a tau0)^(1/3) when a tau0 >= 1 (Sec. 3.4.2) */
   double step_dx;        /* step limiter f (Sec. 4.1): sub-step length f v_th / |dv/dr|; 0 -> 0.01 */
+  int32_t profile;       /* THOR_PROFILE_* (0 = homologous) */
+  int32_t reserved3;
+  double alpha_rho;      /* power law: density index */
+  double alpha_v;        /* power law: velocity index */
 } thor_shell_params;
 
 int thor_shell_create(thor_ctx_t ctx, const thor_shell_params* p, thor_geom_t* out);
@@ -129,6 +141,9 @@ typedef struct {
   int32_t kind;
   int32_t reserved;
   double X0, sigma;      /* km/s */
+  /* kind 0 on a power-law shell only: the line has equivalent width ew [km/s] on a flat
+   * continuum over [X0 - C, X0 + C] (Sec. 5.1); C = 0: line only */
+  double ew, C;
 } thor_source;
 
 typedef struct {
@@ -153,6 +168,8 @@ typedef struct {
   uint8_t* raw_status;   /* 1 escaped, 2 absorbed, 3 stopped at max_scat */
   uint32_t max_scat;     /* stop a photon after this many scatterings (0 = never) */
   uint32_t reserved2;
+  float* raw_X0;         /* emitted lab X [km/s] (shells) */
+  float* raw_col;        /* HI column traversed, in units of the radial column (power-law shells) */
 } thor_output_spec;
 
 typedef struct {
@@ -194,8 +211,24 @@ typedef struct {
 int thor_forest(thor_ctx_t ctx, const float* n_HI, const float* T, const float* v_los, const int32_t dims[3],
                 int mem_kind, const thor_forest_spec* spec, float* tau_out);
 
-/* Device time of the last thor_forest call in milliseconds (CUDA events). */
+/* Device time of the last thor_forest or thor_reweight call in milliseconds (CUDA events). */
 double thor_last_elapsed_ms(thor_ctx_t ctx);
+
+/* ---- Post-processing of a shell run (Sec. 5.1) -------------------------------------- */
+
+/* Reweight the escaped photons of a run to other intrinsic spectra and dust depths:
+ * photon i (status 1) gets, for target t = {sigma, ew, C, tau_d},
+ *   w_ti = p_t(X0_i) / p_s(X0_i) * exp(-tau_d col_i),
+ * p(X) = pl N(X; 0, sigma^2) + (1 - pl) U(X; -C, C), pl = ew / (ew + 2C) (1 when C = 0),
+ * p_s the spectrum the run sampled (sample = {sigma, ew, C}), and col_i its HI column in
+ * units of the radial column (dust following the gas).  out[t * (n_bins + 2) + b] = sum of
+ * the weights of the photons whose X_i falls in bin b of [X_min, X_max) (then underflow,
+ * overflow), divided by n.  X0, X, col, status: n entries of kind mem_kind (the raw
+ * records of thor_run); targets: host, n_targets x 4 doubles; out: host, n_targets x
+ * (n_bins + 2) doubles, caller-owned.  n_bins <= 4096.  Errors: THOR_ERR_INVALID_ARG. */
+int thor_reweight(thor_ctx_t ctx, int64_t n, const float* X0, const float* X, const float* col,
+                  const uint8_t* status, int mem_kind, const double sample[3], int32_t n_targets,
+                  const double* targets, int32_t n_bins, double X_min, double X_max, double* out);
 
 /* ---- shell run without device allocation --------------------------------------------- */
 

@@ -48,7 +48,7 @@ void* thor_ctx::scratch(Buf& b, size_t bytes) {
 
 thor_ctx::~thor_ctx() {
   cudaSetDevice(device);
-  for (Buf* b : {&b_models, &b_tally, &b_queue, &b_spec, &b_cube, &b_raw, &b_diag, &b_stats, &b_spill, &b_cmp})
+  for (Buf* b : {&b_models, &b_tally, &b_queue, &b_spec, &b_cube, &b_raw, &b_raw2, &b_diag, &b_stats, &b_spill, &b_cmp})
     if (b->p) cudaFree(b->p);
   if (d_ktab) cudaFree(d_ktab);
   if (ev0) cudaEventDestroy(ev0);
@@ -126,6 +126,77 @@ extern "C" void thor_line_params(double T, double* vth, double* a, double* sigma
 }
 
 // ------------------------------------------------------------------------------ geometry
+// int_lo^hi r^alpha dr
+static double pow_int(double alpha, double lo, double hi) {
+  if (fabs(alpha + 1.0) < 1e-12) return log(hi / lo);
+  return (pow(hi, alpha + 1.0) - pow(lo, alpha + 1.0)) / (alpha + 1.0);
+}
+
+// Power-law shell (Sec. 5.1): lengths in units of R_out, n ~ r^alpha_rho with radial
+// column tau0 / sigma_0, v ~ r^alpha_v with distance average v_max, dust following the
+// gas, global step limiter f min(v_th / G, r_i / |alpha_rho|) with G a bound on
+// |d(v r_hat . k)/ds| = |v' mu_r^2 + v (1 - mu_r^2) / r| <= max(|v'|, v / r).
+static int fill_power_law(thor_ctx* ctx, const thor_shell_params* p, ShellModel* m) {
+  using namespace thor;
+  if (!(p->R_in > 0.0)) return ctx->fail(THOR_ERR_INVALID_ARG, "power-law shells need R_in > 0");
+  if (!(fabs(p->alpha_rho) <= 8.0) || !(fabs(p->alpha_v) <= 8.0))
+    return ctx->fail(THOR_ERR_INVALID_ARG, "power-law indices out of range");
+  if (p->albedo != 0.0) return ctx->fail(THOR_ERR_INVALID_ARG, "power-law shells take albedo 0 (dust absorbs)");
+  double tau0 = p->tau0;
+  if (!(tau0 > 0.0)) {
+    if (!(p->N_HI >= 0.0)) return ctx->fail(THOR_ERR_INVALID_ARG, "N_HI must be >= 0");
+    tau0 = p->N_HI * line_sigma0(p->T);
+  }
+  const double ri = p->R_in / p->R_out;
+  const double F = pow_int(p->alpha_rho, ri, 1.0);
+  const double vth = line_vth_kms(p->T);
+  const double v1 = p->v_max * (1.0 - ri) / pow_int(p->alpha_v, ri, 1.0);
+  double G = 0.0;
+  for (int i = 0; i <= 2000; ++i) {
+    const double r = ri + (1.0 - ri) * i / 2000.0;
+    const double v = v1 * pow(r, p->alpha_v);
+    G = fmax(G, fmax(fabs(p->alpha_v) * v / r, v / r));
+  }
+  const double f = (p->step_dx > 0.0) ? p->step_dx : 0.01;
+  double ds = (G > 0.0) ? f * vth / (1.05 * G) : 1e30;
+  if (p->alpha_rho != 0.0) ds = fmin(ds, f * ri / fabs(p->alpha_rho));
+  std::memset(m, 0, sizeof(*m));
+  m->profile = THOR_PROFILE_POWER_LAW;
+  m->R_in = ri;
+  m->R_out = 1.0;
+  m->kapn = (float)(tau0 / F);
+  m->kapdn = (float)(p->tau_dust / F);
+  m->invF = (float)(1.0 / F);
+  m->ar = (float)p->alpha_rho;
+  m->av = (float)p->alpha_v;
+  m->v1 = (float)v1;
+  m->vth = (float)vth;
+  m->inv_vth = (float)(1.0 / vth);
+  m->a = (float)line_a(p->T);
+  m->ds_core = (float)ds;
+  m->albedo = 0.0f;
+  m->g_hg = (float)p->g_hg;
+  m->phase = p->phase;
+  const double at = line_a(p->T) * tau0;
+  m->xcrit = (p->core_skip && at >= 1.0) ? (float)(0.2 * cbrt(at)) : 0.0f;
+  return THOR_OK;
+}
+
+int thor::fill_shell_source(thor_ctx* ctx, const thor_source* src, ShellModel* m) {
+  if (src->kind != 0) return ctx->fail(THOR_ERR_INVALID_ARG, "shells take source kind 0 (central point source)");
+  if (!(src->sigma >= 0.0)) return ctx->fail(THOR_ERR_INVALID_ARG, "source sigma must be >= 0");
+  if (!(src->C >= 0.0) || !(src->ew >= 0.0)) return ctx->fail(THOR_ERR_INVALID_ARG, "source ew and C must be >= 0");
+  if (src->C > 0.0 && m->profile != THOR_PROFILE_POWER_LAW)
+    return ctx->fail(THOR_ERR_INVALID_ARG, "a continuum source needs a power-law shell");
+  if (src->C > 0.0 && !(src->sigma > 0.0)) return ctx->fail(THOR_ERR_INVALID_ARG, "a continuum source needs sigma > 0");
+  m->line = (src->sigma > 0.0) ? 1 : 0;
+  m->X0 = (float)src->X0;
+  m->sigma = (float)src->sigma;
+  m->cont_C = (float)src->C;
+  m->p_line = (src->C > 0.0) ? (float)(src->ew / (src->ew + 2.0 * src->C)) : 1.0f;
+  return THOR_OK;
+}
+
 int thor::fill_shell_model(thor_ctx* ctx, const thor_shell_params* p, ShellModel* m) {
   if (!p) return ctx->fail(THOR_ERR_INVALID_ARG, "shell parameters are NULL");
   if (!(p->R_out > 0.0) || !(p->R_in >= 0.0) || !(p->R_in < p->R_out))
@@ -135,6 +206,9 @@ int thor::fill_shell_model(thor_ctx* ctx, const thor_shell_params* p, ShellModel
     return ctx->fail(THOR_ERR_INVALID_ARG, "dust parameters out of range");
   if (p->phase < 0 || p->phase > 2) return ctx->fail(THOR_ERR_INVALID_ARG, "unknown phase function");
   if (!(p->v_max >= 0.0)) return ctx->fail(THOR_ERR_INVALID_ARG, "v_max must be >= 0");
+  if (p->profile != THOR_PROFILE_HOMOLOGOUS && p->profile != THOR_PROFILE_POWER_LAW)
+    return ctx->fail(THOR_ERR_INVALID_ARG, "unknown density/velocity profile");
+  if (p->profile == THOR_PROFILE_POWER_LAW) return fill_power_law(ctx, p, m);
   const double L = (p->R_out - p->R_in) / p->R_out;  // in units of R_out
   double tau0 = p->tau0;
   if (!(tau0 > 0.0)) {
@@ -258,7 +332,18 @@ int thor::prepare_outputs(thor_ctx* ctx, const thor_output_spec* spec, uint64_t 
     if (!o->cube) return ctx->fail(THOR_ERR_OOM, "cube buffer");
     if (int rc = ctx->cuda(cudaMemsetAsync(o->cube, 0, cb, ctx->stream), "clear cube")) return rc;
   }
-  o->raw_X = nullptr; o->raw_n = nullptr; o->raw_s = nullptr;
+  o->raw_X = nullptr; o->raw_n = nullptr; o->raw_s = nullptr; o->raw_X0 = nullptr; o->raw_col = nullptr;
+  if (spec->raw_X0 || spec->raw_col) {
+    if (grid) return ctx->fail(THOR_ERR_INVALID_ARG, "raw_X0 / raw_col are shell records");
+    if (dev) {
+      o->raw_X0 = spec->raw_X0; o->raw_col = spec->raw_col;
+    } else {
+      char* p = (char*)ctx->scratch(ctx->b_raw2, (size_t)n_photons * 8 + 64);
+      if (!p) return ctx->fail(THOR_ERR_OOM, "raw buffers");
+      if (spec->raw_X0) o->raw_X0 = (float*)p;
+      if (spec->raw_col) o->raw_col = (float*)(p + 4 * n_photons);
+    }
+  }
   if (spec->raw_X || spec->raw_nscat || spec->raw_status) {
     if (!spec->raw_X || !spec->raw_nscat || !spec->raw_status)
       return ctx->fail(THOR_ERR_INVALID_ARG, "raw_X, raw_nscat and raw_status go together");
@@ -289,6 +374,10 @@ int thor::finish_outputs(thor_ctx* ctx, const thor_output_spec* spec, uint64_t n
     if (rc == THOR_OK) rc = ctx->cuda(cudaMemcpyAsync(spec->raw_nscat, o.raw_n, n_photons * 4, cudaMemcpyDeviceToHost, s), "copy raw");
     if (rc == THOR_OK) rc = ctx->cuda(cudaMemcpyAsync(spec->raw_status, o.raw_s, n_photons, cudaMemcpyDeviceToHost, s), "copy raw");
   }
+  if (rc == THOR_OK && o.raw_X0)
+    rc = ctx->cuda(cudaMemcpyAsync(spec->raw_X0, o.raw_X0, n_photons * 4, cudaMemcpyDeviceToHost, s), "copy raw");
+  if (rc == THOR_OK && o.raw_col)
+    rc = ctx->cuda(cudaMemcpyAsync(spec->raw_col, o.raw_col, n_photons * 4, cudaMemcpyDeviceToHost, s), "copy raw");
   return rc;
 }
 
@@ -337,9 +426,10 @@ extern "C" int thor_run(thor_ctx_t ctx, thor_geom_t g, const thor_source* src, u
   int rc = THOR_OK;
   if (!grid) {
     ShellModel m = g->shell;
-    m.line = (src->sigma > 0.0) ? 1 : 0;
-    m.X0 = (float)src->X0;
-    m.sigma = (float)src->sigma;
+    if ((rc = fill_shell_source(ctx, src, &m))) return rc;
+    if (o.raw_col && m.profile != THOR_PROFILE_POWER_LAW)
+      return ctx->fail(THOR_ERR_INVALID_ARG, "raw_col is recorded on power-law shells");
+    m.raw_X0 = o.raw_X0; m.raw_col = o.raw_col;
     m.X_min = (float)spec->X_min;
     m.inv_dX = 1.0f / dX;
     m.n_bins = spec->n_bins;
@@ -356,7 +446,7 @@ extern "C" int thor_run(thor_ctx_t ctx, thor_geom_t g, const thor_source* src, u
     const int gsz = shell_grid(ctx->block, ctx->blocks_per_sm, false);
     if (ctx->spill_below <= 0) {
       cudaEventRecord(ctx->ev0, s);
-      rc = ctx->cuda(launch_shell_run(d_m, q, ctx->d_ktab, gsz, ctx->block, s), "shell photon loop");
+      rc = ctx->cuda(launch_shell_run(d_m, q, ctx->d_ktab, gsz, ctx->block, m.profile, s), "shell photon loop");
       ++n_launch;
       cudaEventRecord(ctx->ev1, s);
     } else {
@@ -400,7 +490,8 @@ extern "C" int thor_run(thor_ctx_t ctx, thor_geom_t g, const thor_source* src, u
           g = (int)(want < (unsigned long long)gsz ? want : gsz);
         }
         const bool final_phase = last || c.spill_below == 0;
-        if ((rc = ctx->cuda(launch_shell_run_compact(d_m, q, c, ctx->d_ktab, g, ctx->block, s), "shell photon loop")))
+        if ((rc = ctx->cuda(launch_shell_run_compact(d_m, q, c, ctx->d_ktab, g, ctx->block, m.profile, s),
+                            "shell photon loop")))
           break;
         ++n_launch;
         if (final_phase) break;
@@ -524,6 +615,74 @@ extern "C" int thor_forest(thor_ctx_t ctx, const float* n_HI, const float* T, co
 }
 
 extern "C" double thor_last_elapsed_ms(thor_ctx_t ctx) { return ctx ? ctx->last_ms : -1.0; }
+
+// ------------------------------------------------------------------------------ reweighting
+// Spectrum parameters for the kernel: {pl / (sqrt(2 pi) sigma), 1 / (2 sigma^2), (1 - pl) / (2C), C, tau_d}.
+static bool spectrum_params(const double* p, double tau_d, float* q) {
+  const double sigma = p[0], ew = p[1], C = p[2];
+  if (!(sigma > 0.0) || !(ew >= 0.0) || !(C >= 0.0) || !(tau_d >= 0.0)) return false;
+  const double pl = (C > 0.0) ? ew / (ew + 2.0 * C) : 1.0;
+  q[0] = (float)(pl / (2.5066282746310002 * sigma));
+  q[1] = (float)(0.5 / (sigma * sigma));
+  q[2] = (C > 0.0) ? (float)((1.0 - pl) / (2.0 * C)) : 0.0f;
+  q[3] = (float)C;
+  q[4] = (float)tau_d;
+  return true;
+}
+
+extern "C" int thor_reweight(thor_ctx_t ctx, int64_t n, const float* X0, const float* X, const float* col,
+                             const uint8_t* status, int mem_kind, const double sample[3], int32_t n_targets,
+                             const double* targets, int32_t n_bins, double X_min, double X_max, double* out) {
+  if (!ctx) return THOR_ERR_INVALID_ARG;
+  if (n <= 0 || !X0 || !X || !col || !status || !sample || !targets || !out)
+    return ctx->fail(THOR_ERR_INVALID_ARG, "thor_reweight: NULL or empty input");
+  if (mem_kind != THOR_MEM_HOST && mem_kind != THOR_MEM_DEVICE) return ctx->fail(THOR_ERR_INVALID_ARG, "bad mem_kind");
+  if (n_targets <= 0 || n_targets > 65535) return ctx->fail(THOR_ERR_INVALID_ARG, "n_targets in [1, 65535]");
+  if (n_bins <= 0 || n_bins > 4096 || !(X_max > X_min)) return ctx->fail(THOR_ERR_INVALID_ARG, "bad binning");
+  std::vector<float> prm((size_t)5 * (n_targets + 1));
+  if (!spectrum_params(sample, 0.0, prm.data())) return ctx->fail(THOR_ERR_INVALID_ARG, "bad sampled spectrum");
+  for (int t = 0; t < n_targets; ++t)
+    if (!spectrum_params(targets + 4 * t, targets[4 * t + 3], prm.data() + 5 * (t + 1)))
+      return ctx->fail(THOR_ERR_INVALID_ARG, "bad target %d", t);
+  if (int rc = ctx->select()) return rc;
+  cudaStream_t s = ctx->stream;
+  const size_t ob = (size_t)n_targets * (n_bins + 2) * sizeof(double);
+  const size_t pb = prm.size() * sizeof(float);
+  const size_t ib = (mem_kind == THOR_MEM_HOST) ? (size_t)n * 13 + 64 : 0;
+  char* d = (char*)ctx->scratch(ctx->b_diag, ob + pb + ib + 512);
+  if (!d) return ctx->fail(THOR_ERR_OOM, "thor_reweight scratch");
+  double* d_out = (double*)d;
+  float* d_prm = (float*)(d + ((ob + 255) & ~(size_t)255));
+  char* in = (char*)d_prm + ((pb + 255) & ~(size_t)255);
+  const float *x0 = X0, *x = X, *c = col;
+  const uint8_t* st = status;
+  int rc = ctx->cuda(cudaMemsetAsync(d_out, 0, ob, s), "clear reweight output");
+  if (!rc) rc = ctx->cuda(cudaMemcpyAsync(d_prm, prm.data(), pb, cudaMemcpyHostToDevice, s), "reweight params");
+  if (!rc && mem_kind == THOR_MEM_HOST) {
+    float* fx0 = (float*)in;
+    float* fx = fx0 + n;
+    float* fc = fx + n;
+    uint8_t* fs = (uint8_t*)(fc + n);
+    rc = ctx->cuda(cudaMemcpyAsync(fx0, X0, n * 4, cudaMemcpyHostToDevice, s), "reweight inputs");
+    if (!rc) rc = ctx->cuda(cudaMemcpyAsync(fx, X, n * 4, cudaMemcpyHostToDevice, s), "reweight inputs");
+    if (!rc) rc = ctx->cuda(cudaMemcpyAsync(fc, col, n * 4, cudaMemcpyHostToDevice, s), "reweight inputs");
+    if (!rc) rc = ctx->cuda(cudaMemcpyAsync(fs, status, n, cudaMemcpyHostToDevice, s), "reweight inputs");
+    x0 = fx0; x = fx; c = fc; st = fs;
+  }
+  if (rc) return rc;
+  cudaEventRecord(ctx->ev0, s);
+  rc = ctx->cuda(launch_reweight(n, x0, x, c, st, d_prm, n_targets, n_bins, X_min, X_max, d_out, ctx->sm_count, s),
+                 "reweight kernel");
+  cudaEventRecord(ctx->ev1, s);
+  if (!rc) rc = ctx->cuda(cudaMemcpyAsync(out, d_out, ob, cudaMemcpyDeviceToHost, s), "reweight output");
+  if (!rc) rc = ctx->cuda(cudaStreamSynchronize(s), "thor_reweight");
+  if (rc) return rc;
+  cudaEventElapsedTime(&ctx->last_ms, ctx->ev0, ctx->ev1);
+  const double inv = 1.0 / (double)n;
+  for (size_t i = 0; i < (size_t)n_targets * (n_bins + 2); ++i) out[i] *= inv;
+  ctx->last_error.clear();
+  return THOR_OK;
+}
 
 // ------------------------------------------------------------------------------ diagnostics
 namespace {

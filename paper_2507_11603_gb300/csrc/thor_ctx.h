@@ -23,7 +23,7 @@ struct thor_ctx {
   float last_ms = 0.0f;
   std::string last_error;
   // grow-only scratch buffers reused across calls
-  Buf b_models, b_tally, b_queue, b_spec, b_cube, b_raw, b_diag, b_stats, b_spill, b_cmp;
+  Buf b_models, b_tally, b_queue, b_spec, b_cube, b_raw, b_raw2, b_diag, b_stats, b_spill, b_cmp;
   // tail compaction of the shell photon loop
   int spill_below = 16;     // warps with fewer live lanes hand them to the next launch (0 = off)
   int max_phases = 24;      // launches at most
@@ -62,7 +62,11 @@ struct OutBufs {
   float* raw_X = nullptr;
   uint32_t* raw_n = nullptr;
   uint8_t* raw_s = nullptr;
+  float* raw_X0 = nullptr;
+  float* raw_col = nullptr;
 };
+// Source fields of a shell model (line, continuum); validated against the profile.
+int fill_shell_source(thor_ctx* ctx, const thor_source* src, ShellModel* m);
 int fill_shell_model(thor_ctx* ctx, const thor_shell_params* p, ShellModel* m);
 int prepare_outputs(thor_ctx* ctx, const thor_output_spec* spec, uint64_t n_photons, bool grid, OutBufs* o);
 int finish_outputs(thor_ctx* ctx, const thor_output_spec* spec, uint64_t n_photons, bool grid, const OutBufs& o);

@@ -41,7 +41,13 @@ struct ShellModel {
   unsigned long long id_base;
   unsigned long long n_photons;
   int32_t cancelled;         // served requests: drop in-flight packets (set by the host)
-  int32_t pad_;
+  int32_t profile;           // 0 homologous uniform shell, 1 power-law shell (Sec. 5.1)
+  // power law: n(r) / n(1) = r^ar, v(r) = v1 r^av (radial), opacities per unit length at r = 1
+  float ar, av, v1, kapn, kapdn;
+  float invF;                // HI column per unit length at r = 1, in units of the radial column
+  float p_line, cont_C;      // source: probability of the line, continuum half-width (km/s; 0 = none)
+  float* raw_X0;             // optional per-photon emitted X and column
+  float* raw_col;
 };
 
 // Photon work queue: photon g in [0, total) belongs to model m with
@@ -63,6 +69,7 @@ struct WorkQueue {
 struct PhotonRec {
   double px, py, pz;  // FP64 anchor
   float ox, oy, oz;   // FP32 offset from the anchor (saved as is: resuming is bit-exact)
+  float X0, col_hi, col_lo;  // emitted X, HI column traversed (two-level sum)
   float kx, ky, kz, x, X, safe;
   int32_t region;
   uint32_t nscat, ndust, iters, steps, event;
@@ -134,9 +141,12 @@ struct GridModel {
 int shell_grid(int block, int blocks_per_sm, bool sliced);  // persistent grid size
 int grid_grid(int block, int blocks_per_sm);
 cudaError_t launch_shell_run(const ShellModel* d_models, WorkQueue q, const float* d_ktab, int grid,
-                             int block, cudaStream_t s);
+                             int block, int profile, cudaStream_t s);
 cudaError_t launch_shell_run_compact(const ShellModel* d_models, WorkQueue q, Compact c, const float* d_ktab,
-                                     int grid, int block, cudaStream_t s);
+                                     int grid, int block, int profile, cudaStream_t s);
+cudaError_t launch_reweight(int64_t n, const float* X0, const float* X, const float* col, const uint8_t* status,
+                            const float* d_params, int n_targets, int n_bins, double X_min, double X_max,
+                            double* d_out, int n_sm, cudaStream_t s);
 cudaError_t launch_shell_slice(const ShellModel* d_models, WorkQueue q, SlotState st, uint32_t event_budget,
                                const float* d_ktab, int grid, int block, cudaStream_t s);
 cudaError_t launch_grid_pack(const float* nHI, const float* T, const float* vx, const float* vy,

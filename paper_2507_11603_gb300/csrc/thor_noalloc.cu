@@ -72,6 +72,8 @@ int model_from_params(const thor_shell_params* p, ShellModel* m) {
     return fail(THOR_ERR_INVALID_ARG, "thor_run_shell_noalloc: dust parameters out of range");
   if (p->phase < 0 || p->phase > 2) return fail(THOR_ERR_INVALID_ARG, "thor_run_shell_noalloc: unknown phase");
   if (!(p->v_max >= 0.0)) return fail(THOR_ERR_INVALID_ARG, "thor_run_shell_noalloc: v_max must be >= 0");
+  if (p->profile != THOR_PROFILE_HOMOLOGOUS)
+    return fail(THOR_ERR_INVALID_ARG, "thor_run_shell_noalloc: homologous shells only");
   double tau0 = p->tau0;
   if (!(tau0 > 0.0)) {
     if (!(p->N_HI >= 0.0)) return fail(THOR_ERR_INVALID_ARG, "thor_run_shell_noalloc: N_HI must be >= 0");
@@ -110,8 +112,8 @@ extern "C" int thor_run_shell_noalloc(const thor_shell_params* p, const thor_sou
   if (!p || !src || !spectrum || !out) return fail(THOR_ERR_INVALID_ARG, "thor_run_shell_noalloc: NULL argument");
   if (n_photons == 0 || first_id + n_photons < first_id)
     return fail(THOR_ERR_INVALID_ARG, "thor_run_shell_noalloc: bad photon range");
-  if (src->kind != 0 || !(src->sigma >= 0.0))
-    return fail(THOR_ERR_INVALID_ARG, "thor_run_shell_noalloc: shells take a central point source (kind 0)");
+  if (src->kind != 0 || !(src->sigma >= 0.0) || src->C > 0.0)
+    return fail(THOR_ERR_INVALID_ARG, "thor_run_shell_noalloc: shells take a central point source (kind 0, no continuum)");
   if (n_bins <= 0 || !(X_max > X_min)) return fail(THOR_ERR_INVALID_ARG, "thor_run_shell_noalloc: bad binning");
   if (mem_kind != THOR_MEM_HOST && mem_kind != THOR_MEM_DEVICE)
     return fail(THOR_ERR_INVALID_ARG, "thor_run_shell_noalloc: bad mem_kind");
@@ -133,6 +135,11 @@ extern "C" int thor_run_shell_noalloc(const thor_shell_params* p, const thor_sou
   m.line = (src->sigma > 0.0) ? 1 : 0;
   m.X0 = (float)src->X0;
   m.sigma = (float)src->sigma;
+  m.p_line = 1.0f;
+  m.cont_C = 0.0f;
+  m.profile = THOR_PROFILE_HOMOLOGOUS;
+  m.raw_X0 = nullptr;
+  m.raw_col = nullptr;
   m.X_min = (float)X_min;
   m.inv_dX = (float)(n_bins / (X_max - X_min));
   m.n_bins = n_bins;
@@ -156,7 +163,8 @@ extern "C" int thor_run_shell_noalloc(const thor_shell_params* p, const thor_sou
   q.model = (const int32_t*)(qb + offsetof(QHost, model));
   q.n_entries = 1;
   if (e == cudaSuccess)
-    e = launch_shell_run((const ShellModel*)(scratch + kOffModel), q, ktab, shell_grid(128, 0, false), 128, s);
+    e = launch_shell_run((const ShellModel*)(scratch + kOffModel), q, ktab, shell_grid(128, 0, false), 128,
+                         THOR_PROFILE_HOMOLOGOUS, s);
   Tally t;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&t, tally, sizeof t, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess && mem_kind == THOR_MEM_HOST)

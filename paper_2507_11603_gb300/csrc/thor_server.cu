@@ -336,16 +336,14 @@ extern "C" int thor_server_submit(thor_server_t s, const thor_shell_params* p, c
   if (!s || !p || !src || !spec || !ticket) return s ? s->ctx->fail(THOR_ERR_INVALID_ARG, "thor_server_submit: NULL") : THOR_ERR_INVALID_ARG;
   thor_ctx* ctx = s->ctx;
   if (n_photons == 0 || n_photons > (1ull << 40)) return ctx->fail(THOR_ERR_INVALID_ARG, "n_photons out of range");
-  if (src->kind != 0 || !(src->sigma >= 0.0)) return ctx->fail(THOR_ERR_INVALID_ARG, "served requests take a point source");
+  if (src->kind != 0) return ctx->fail(THOR_ERR_INVALID_ARG, "served requests take a point source");
   if (!spec->spectrum || spec->mem_kind != THOR_MEM_HOST || spec->n_bins <= 0 || !(spec->X_max > spec->X_min))
     return ctx->fail(THOR_ERR_INVALID_ARG, "served requests need a host spectrum buffer and a valid binning");
   if (spec->n_bins > s->max_bins) return ctx->fail(THOR_ERR_CAPACITY, "n_bins exceeds %d", s->max_bins);
   Request* r = new Request();
   if (int rc = fill_shell_model(ctx, p, &r->model)) { delete r; return rc; }
   ShellModel& m = r->model;
-  m.line = (src->sigma > 0.0) ? 1 : 0;
-  m.X0 = (float)src->X0;
-  m.sigma = (float)src->sigma;
+  if (int rc = fill_shell_source(ctx, src, &m)) { delete r; return rc; }
   m.X_min = (float)spec->X_min;
   m.inv_dX = (float)(spec->n_bins / (spec->X_max - spec->X_min));
   m.n_bins = spec->n_bins;

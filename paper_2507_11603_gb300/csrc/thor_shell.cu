@@ -25,6 +25,8 @@ struct Photon {
   float safe;  // lower bound on the distance from p to any shell boundary (0 = unknown)
   int region;  // 1 = inside the empty cavity
   uint32_t nscat, ndust, iters, steps;
+  float X0;              // emitted lab frequency
+  float col_hi, col_lo;  // HI column traversed (power-law shells), two-level FP32 sum
   Rng rng;
   int model;
   unsigned long long pid;
@@ -39,18 +41,24 @@ __device__ __forceinline__ int find_entry(const WorkQueue& q, unsigned long long
   return lo;
 }
 
-// Emission (Sec. 3.4): central point source, isotropic, line profile in the source frame.
+// Emission (Sec. 3.4): central point source, isotropic, line profile in the source frame;
+// with a continuum (Sec. 5.1) word 4 picks the line (probability p_line) or the flat
+// continuum, whose position is word 5.
 __device__ __forceinline__ void shell_emit(const ShellModel& m, Photon& ph) {
-  ph.rng.init(((uint64_t)m.seed_hi << 32) | m.seed_lo, ph.pid, 1u);
+  ph.rng.init(((uint64_t)m.seed_hi << 32) | m.seed_lo, ph.pid, m.cont_C > 0.0f ? 2u : 1u);
   ph.px = 0.0; ph.py = 0.0; ph.pz = 0.0;
   ph.ox = 0.0f; ph.oy = 0.0f; ph.oz = 0.0f;
   ph.k = iso_dir(ph.rng.u(0), ph.rng.u(1));
   float X = m.X0;
-  if (m.line == 1) {
+  if (m.cont_C > 0.0f && ph.rng.u(4) > m.p_line) {
+    X = __fmaf_rn(m.cont_C, __fmaf_rn(2.0f, ph.rng.u(5), -1.0f), X);
+  } else if (m.line == 1) {
     const float R1 = ph.rng.u(2), R2 = ph.rng.u(3);
     X = __fmaf_rn(m.sigma * sqrtf(-2.0f * __logf(R1)), cospif(2.0f * R2), X);
   }
   ph.X = X;
+  ph.X0 = X;
+  ph.col_hi = 0.0f; ph.col_lo = 0.0f;
   ph.x = X * m.inv_vth;  // gas at rest at the centre
   ph.region = (m.R_in > 0.0) ? 1 : 0;
   ph.safe = (float)m.R_out;
@@ -222,6 +230,128 @@ __device__ int shell_event(const ShellModel& m, Photon& ph, const float* __restr
   return 0;
 }
 
+// ---- power-law shells (Sec. 5.1) ---------------------------------------------------
+// Gas state at a point q (FP32, |q| <= 1) for direction k: radius, r_hat . k, density
+// relative to r = 1 and outflow speed.
+struct PLState { float r, mur, nr, v; };
+__device__ __forceinline__ PLState pl_state(const ShellModel& m, float qx, float qy, float qz, float3 k) {
+  const float r2 = __fmaf_rn(qx, qx, __fmaf_rn(qy, qy, qz * qz));
+  const float ir = rsqrtf(r2);
+  PLState st;
+  st.r = r2 * ir;
+  st.mur = __fmaf_rn(qx, k.x, __fmaf_rn(qy, k.y, qz * k.z)) * ir;
+  const float lr = __log2f(st.r);
+  st.nr = ex2_approx(m.ar * lr);
+  st.v = m.v1 * ex2_approx(m.av * lr);
+  return st;
+}
+__device__ __forceinline__ void col_add(Photon& ph, float d) {
+  ph.col_lo += d;
+  if (ph.col_lo >= 0.00390625f) { ph.col_hi += ph.col_lo; ph.col_lo = 0.0f; }
+}
+
+// One event on a power-law shell; returns as shell_event.  The lab frequency X is the
+// photon's frequency variable (the flow is not homologous, so x is evaluated from the
+// local state).  A crossing predicted from the rate at the current point within
+// min(safety distance, ds / 16) is taken with that rate (one Voigt evaluation, no FP64);
+// otherwise sub-steps of at most ds (the global step limiter) use the midpoint state.
+// Dust follows the gas and absorbs.
+__device__ int shell_event_pl(const ShellModel& m, Photon& ph, const float* __restrict__ Ktab) {
+  ph.rng.next_event((m.kapdn > 0.0f || m.phase == PH_MIXED) ? 3u : 2u);
+  float tau_rem = -__logf(ph.rng.u(W_TAU));  // Eq. 3
+  float kH, kD;
+  PLState site;
+  for (;;) {
+    if (ph.region) {  // empty cavity: straight to the inner sphere, lab X conserved
+      anchor(ph);
+      const double kx = ph.k.x, ky = ph.k.y, kz = ph.k.z;
+      const double b = ph.px * kx + ph.py * ky + ph.pz * kz;
+      const double c = ph.px * ph.px + ph.py * ph.py + ph.pz * ph.pz - m.R_in * m.R_in;
+      const double s = -b + sqrt(fmax(b * b - c, 0.0));
+      ph.px += s * kx; ph.py += s * ky; ph.pz += s * kz;
+      ph.region = 0;
+      ph.safe = 0.0f;
+    }
+    {  // short step with the rate at the current point
+      const PLState st = pl_state(m, (float)ph.px + ph.ox, (float)ph.py + ph.oy, (float)ph.pz + ph.oz, ph.k);
+      const float x = (ph.X - st.v * st.mur) * m.inv_vth;
+      const float H = voigt<false>(m.a, x, Ktab);
+      const float kap = st.nr * __fmaf_rn(m.kapn, H, m.kapdn);
+      const float s0 = __fdividef(tau_rem, kap);
+      ++ph.steps;
+      if (s0 <= ph.safe && s0 <= 0.0625f * m.ds_core) {
+        advance(ph, s0);
+        ph.safe = __fmaf_rd(-s0, 1.000001f, ph.safe);
+        col_add(ph, st.nr * m.invF * s0);
+        kH = m.kapn * st.nr * H;
+        kD = m.kapdn * st.nr;
+        site = pl_state(m, (float)ph.px + ph.ox, (float)ph.py + ph.oy, (float)ph.pz + ph.oz, ph.k);
+        break;
+      }
+    }
+    // general path: exact segment to the next boundary (FP64), sub-steps of <= ds
+    anchor(ph);
+    const double kx = ph.k.x, ky = ph.k.y, kz = ph.k.z;
+    const double b = ph.px * kx + ph.py * ky + ph.pz * kz;
+    const double pp = ph.px * ph.px + ph.py * ph.py + ph.pz * ph.pz;
+    double S = -b + sqrt(fmax(b * b - (pp - m.R_out * m.R_out), 0.0));
+    int next = 1;  // 1 escape, 2 cavity
+    if (b < 0.0) {
+      const double disc = b * b - (pp - m.R_in * m.R_in);
+      if (disc > 0.0) {
+        const double s_in = -b - sqrt(disc);
+        if (s_in < S) { S = s_in; next = 2; }
+      }
+    }
+    S = fmax(S, 0.0);
+    const float Sf = (float)S;
+    const float p0x = (float)ph.px, p0y = (float)ph.py, p0z = (float)ph.pz;
+    float s = 0.0f, s_star = -1.0f;
+    while (s < Sf) {
+      const float s1 = fminf(Sf, s + m.ds_core);
+      const float sm = 0.5f * (s + s1);
+      const PLState st = pl_state(m, __fmaf_rn(sm, ph.k.x, p0x), __fmaf_rn(sm, ph.k.y, p0y),
+                                  __fmaf_rn(sm, ph.k.z, p0z), ph.k);
+      const float x = (ph.X - st.v * st.mur) * m.inv_vth;
+      const float H = voigt<false>(m.a, x, Ktab);
+      const float kap = st.nr * __fmaf_rn(m.kapn, H, m.kapdn);
+      const float dtau = kap * (s1 - s);
+      ++ph.steps;
+      if (dtau >= tau_rem) {
+        s_star = fminf(s + __fdividef(tau_rem, kap), Sf);
+        col_add(ph, st.nr * m.invF * (s_star - s));
+        kH = m.kapn * st.nr * H;
+        kD = m.kapdn * st.nr;
+        break;
+      }
+      col_add(ph, st.nr * m.invF * (s1 - s));
+      tau_rem -= dtau;
+      s = s1;
+    }
+    if (s_star >= 0.0f) {
+      const double sd = s_star;
+      ph.px += sd * kx; ph.py += sd * ky; ph.pz += sd * kz;
+      ph.safe = safe_distance(m, ph);
+      site = pl_state(m, (float)ph.px, (float)ph.py, (float)ph.pz, ph.k);
+      break;
+    }
+    ph.px += S * kx; ph.py += S * ky; ph.pz += S * kz;
+    if (next == 1) return 1;  // escapes with its lab X
+    ph.region = 1;
+  }
+  // Interaction (Sec. 3.4): HI or dust in proportion to their opacities; dust absorbs.
+  if (kD > 0.0f && ph.rng.u(W_CHANNEL) >= __fdividef(kH, kH + kD)) return 2;
+  const float x_site = (ph.X - site.v * site.mur) * m.inv_vth;
+  const float xo = scatter_resonant(x_site, m.a, m.phase, ph.k, ph.rng, ph.iters, nullptr, m.xcrit);
+  // back to the lab frame with the new direction: X = x v_th + v(r) r_hat . k_out
+  const float qx = (float)ph.px + ph.ox, qy = (float)ph.py + ph.oy, qz = (float)ph.pz + ph.oz;
+  const float mur = __fmaf_rn(qx, ph.k.x, __fmaf_rn(qy, ph.k.y, qz * ph.k.z)) / site.r;
+  ph.X = __fmaf_rn(xo, m.vth, site.v * mur);
+  ++ph.nscat;
+  if (m.max_scat && ph.nscat >= m.max_scat) return 3;
+  return 0;
+}
+
 __device__ __forceinline__ void tally_spectrum(const ShellModel& m, float X) {
   int bin;
   const float f = (X - m.X_min) * m.inv_dX;
@@ -232,12 +362,14 @@ __device__ __forceinline__ void tally_spectrum(const ShellModel& m, float X) {
 }
 
 __device__ __forceinline__ void write_raw(const ShellModel& m, const Photon& ph, int status) {
+  const unsigned long long j = ph.pid - m.id_base;
   if (m.raw_X) {
-    const unsigned long long j = ph.pid - m.id_base;
     m.raw_X[j] = ph.X;
     m.raw_nscat[j] = ph.nscat;
     m.raw_status[j] = (uint8_t)status;
   }
+  if (m.raw_X0) m.raw_X0[j] = ph.X0;
+  if (m.raw_col) m.raw_col[j] = ph.col_hi + ph.col_lo;
 }
 
 // Per-photon tally with global atomics (used where lanes may belong to different models).
@@ -274,6 +406,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 __device__ __forceinline__ void save_rec(const Photon& ph, PhotonRec& r) {
   r.px = ph.px; r.py = ph.py; r.pz = ph.pz;
   r.ox = ph.ox; r.oy = ph.oy; r.oz = ph.oz;
+  r.X0 = ph.X0; r.col_hi = ph.col_hi; r.col_lo = ph.col_lo;
   r.kx = ph.k.x; r.ky = ph.k.y; r.kz = ph.k.z;
   r.x = ph.x; r.X = ph.X; r.safe = ph.safe;
   r.region = ph.region;
@@ -285,6 +418,7 @@ __device__ __forceinline__ void save_rec(const Photon& ph, PhotonRec& r) {
 __device__ __forceinline__ void load_rec(const ShellModel& m, const PhotonRec& r, Photon& ph) {
   ph.px = r.px; ph.py = r.py; ph.pz = r.pz;
   ph.ox = r.ox; ph.oy = r.oy; ph.oz = r.oz;
+  ph.X0 = r.X0; ph.col_hi = r.col_hi; ph.col_lo = r.col_lo;
   ph.k = make_float3(r.kx, r.ky, r.kz);
   ph.x = r.x; ph.X = r.X; ph.safe = r.safe;
   ph.region = r.region;
@@ -297,7 +431,7 @@ __device__ __forceinline__ void load_rec(const ShellModel& m, const PhotonRec& r
 // Run-to-completion: all queue entries belong to one model (thor_run).  With kCompact,
 // lanes first resume saved packets, and a warp whose sources are empty and whose live
 // lanes drop below c.spill_below saves them and exits (tail compaction across launches).
-template <bool kCompact>
+template <bool kCompact, int kProfile>
 __global__ void __launch_bounds__(256, 1) shell_run_kernel(const ShellModel* __restrict__ models, WorkQueue q,
                                                         Compact c, const float* __restrict__ gK) {
   __shared__ __align__(16) float sK[THOR_VOIGT_NINT * THOR_VOIGT_NCOEF];
@@ -362,7 +496,7 @@ __global__ void __launch_bounds__(256, 1) shell_run_kernel(const ShellModel* __r
     do {
       fin = false;
       if (active) {
-        const int st = shell_event(m, ph, sK);
+        const int st = kProfile ? shell_event_pl(m, ph, sK) : shell_event(m, ph, sK);
         if (st) {
           if (st == 1) { ++lt.esc; tally_spectrum(m, ph.X); }
           else if (st == 2) ++lt.abs;
@@ -415,6 +549,7 @@ __global__ void __launch_bounds__(256, 1) shell_slice_kernel(const ShellModel* _
     ph.X = st.X[slot];
     ph.x = st.x[slot];
     ph.safe = st.safe[slot];
+    ph.X0 = 0.0f; ph.col_hi = 0.0f; ph.col_lo = 0.0f;  // raw records are not served
     ph.region = st.region[slot];
     ph.nscat = st.nscat[slot]; ph.ndust = st.ndust[slot]; ph.iters = st.iters[slot]; ph.steps = st.steps[slot];
     active = true;
@@ -458,7 +593,7 @@ __global__ void __launch_bounds__(256, 1) shell_slice_kernel(const ShellModel* _
     do {
       fin = false;
       if (active) {
-        const int r = shell_event(mr, ph, sK);
+        const int r = mr.profile ? shell_event_pl(mr, ph, sK) : shell_event(mr, ph, sK);
         if (r) { finish_global(mr, ph, r); active = false; fin = true; }
       }
       ++ev;
@@ -485,22 +620,24 @@ int shell_grid(int block, int blocks_per_sm, bool sliced) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (sliced) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, shell_slice_kernel, block, 0);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, shell_run_kernel<true>, block, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, shell_run_kernel<true, 0>, block, 0);
   if (occ < 1) occ = 1;
   const int b = (blocks_per_sm > 0 && blocks_per_sm < occ) ? blocks_per_sm : occ;
   return sms * b;
 }
 
 cudaError_t launch_shell_run(const ShellModel* d_models, WorkQueue q, const float* d_ktab, int grid, int block,
-                             cudaStream_t s) {
+                             int profile, cudaStream_t s) {
   Compact none{};
-  shell_run_kernel<false><<<grid, block, 0, s>>>(d_models, q, none, d_ktab);
+  if (profile) shell_run_kernel<false, 1><<<grid, block, 0, s>>>(d_models, q, none, d_ktab);
+  else shell_run_kernel<false, 0><<<grid, block, 0, s>>>(d_models, q, none, d_ktab);
   return cudaGetLastError();
 }
 
 cudaError_t launch_shell_run_compact(const ShellModel* d_models, WorkQueue q, Compact c, const float* d_ktab,
-                                     int grid, int block, cudaStream_t s) {
-  shell_run_kernel<true><<<grid, block, 0, s>>>(d_models, q, c, d_ktab);
+                                     int grid, int block, int profile, cudaStream_t s) {
+  if (profile) shell_run_kernel<true, 1><<<grid, block, 0, s>>>(d_models, q, c, d_ktab);
+  else shell_run_kernel<true, 0><<<grid, block, 0, s>>>(d_models, q, c, d_ktab);
   return cudaGetLastError();
 }
 

@@ -29,8 +29,9 @@ SYMBOLS = [
     "thor_forest", "thor_last_elapsed_ms", "thor_server_create", "thor_server_submit", "thor_server_poll",
     "thor_server_wait", "thor_server_cancel", "thor_server_stats", "thor_server_destroy", "thor_voigt_eval",
     "thor_dda_trace", "thor_sample_upar", "thor_scatter_once", "thor_philox", "thor_line_params",
-    "thor_run_shell_noalloc", "thor_noalloc_last_error",
+    "thor_run_shell_noalloc", "thor_noalloc_last_error", "thor_reweight",
 ]
+PROFILE = {"homologous": 0, "power_law": 1}
 
 
 class ThorError(RuntimeError):
@@ -42,11 +43,13 @@ class ThorError(RuntimeError):
 class ShellParams(C.Structure):
     _fields_ = [("R_in", C.c_double), ("R_out", C.c_double), ("N_HI", C.c_double), ("tau0", C.c_double),
                 ("T", C.c_double), ("v_max", C.c_double), ("tau_dust", C.c_double), ("albedo", C.c_double),
-                ("g_hg", C.c_double), ("phase", C.c_int32), ("core_skip", C.c_int32), ("step_dx", C.c_double)]
+                ("g_hg", C.c_double), ("phase", C.c_int32), ("core_skip", C.c_int32), ("step_dx", C.c_double),
+                ("profile", C.c_int32), ("reserved3", C.c_int32), ("alpha_rho", C.c_double), ("alpha_v", C.c_double)]
 
 
 class Source(C.Structure):
-    _fields_ = [("kind", C.c_int32), ("reserved", C.c_int32), ("X0", C.c_double), ("sigma", C.c_double)]
+    _fields_ = [("kind", C.c_int32), ("reserved", C.c_int32), ("X0", C.c_double), ("sigma", C.c_double),
+                ("ew", C.c_double), ("C", C.c_double)]
 
 
 class OutputSpec(C.Structure):
@@ -54,7 +57,7 @@ class OutputSpec(C.Structure):
                 ("spectrum", C.c_void_p), ("peel", C.c_int32), ("img_n", C.c_int32), ("peel_bins", C.c_int32),
                 ("reserved", C.c_int32), ("peel_X_min", C.c_double), ("peel_X_max", C.c_double),
                 ("cube", C.c_void_p), ("raw_X", C.c_void_p), ("raw_nscat", C.c_void_p), ("raw_status", C.c_void_p),
-                ("max_scat", C.c_uint32), ("reserved2", C.c_uint32)]
+                ("max_scat", C.c_uint32), ("reserved2", C.c_uint32), ("raw_X0", C.c_void_p), ("raw_col", C.c_void_p)]
 
 
 class Result(C.Structure):
@@ -125,6 +128,8 @@ def load(build: bool = True) -> C.CDLL:
             "thor_run_shell_noalloc": ([P(ShellParams), P(Source), u64, u64, u64, i32, dbl, dbl, vp, C.c_int, vp,
                                         P(Result)], C.c_int),
             "thor_noalloc_last_error": ([], C.c_char_p),
+            "thor_reweight": ([vp, i64, vp, vp, vp, vp, C.c_int, P(dbl), i32, P(dbl), i32, dbl, dbl, P(dbl)],
+                              C.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -201,6 +206,8 @@ class RunResult:
     raw_X: object = None
     raw_nscat: object = None
     raw_status: object = None
+    raw_X0: object = None
+    raw_col: object = None
 
 
 class Context:
@@ -245,9 +252,10 @@ class Context:
 
     # -------------------------------------------------------------- geometries
     def shell(self, *, T, R_in=0.0, R_out=1.0, N_HI=0.0, tau0=0.0, v_max=0.0, tau_dust=0.0, albedo=0.0, g_hg=0.73,
-              phase="isotropic", step_dx=0.0, core_skip=False):
+              phase="isotropic", step_dx=0.0, core_skip=False, profile="homologous", alpha_rho=0.0, alpha_v=1.0):
+        """thor_shell_create.  profile "power_law": the Sec. 5.1 geometry, v_max = distance-averaged speed."""
         p = ShellParams(R_in, R_out, N_HI, tau0, T, v_max, tau_dust, albedo, g_hg, PHASE[phase],
-                        1 if core_skip else 0, step_dx)
+                        1 if core_skip else 0, step_dx, PROFILE[profile], 0, alpha_rho, alpha_v)
         g = C.c_void_p()
         self._check(self.L.thor_shell_create(self.h, C.byref(p), C.byref(g)))
         return Geometry(self, g, "shell", params=p)
@@ -265,11 +273,12 @@ class Context:
         return geo
 
     # -------------------------------------------------------------- runs
-    def run(self, geom, *, n_photons, seed, first_id=0, X0=0.0, sigma=0.0, n_bins=200, X_min=-1000.0,
-            X_max=1000.0, peel=False, img_n=128, peel_bins=256, peel_X_min=-1000.0, peel_X_max=1000.0,
-            raw=False, max_scat=0, device_out=False):
-        """thor_run: photons first_id .. first_id + n_photons - 1 of stream `seed`."""
-        src = Source(1 if geom.kind == "grid" else 0, 0, X0, sigma)
+    def run(self, geom, *, n_photons, seed, first_id=0, X0=0.0, sigma=0.0, ew=0.0, C_cont=0.0, n_bins=200,
+            X_min=-1000.0, X_max=1000.0, peel=False, img_n=128, peel_bins=256, peel_X_min=-1000.0,
+            peel_X_max=1000.0, raw=False, raw_sweep=False, max_scat=0, device_out=False):
+        """thor_run: photons first_id .. first_id + n_photons - 1 of stream `seed`.  raw_sweep
+        (power-law shells) also returns the emitted X0 and the HI column of every photon."""
+        src = Source(1 if geom.kind == "grid" else 0, 0, X0, sigma, ew, C_cont)
         torch = None
         if device_out:
             import torch
@@ -289,15 +298,37 @@ class Context:
                 rs = torch.zeros(n_photons, dtype=torch.uint8, device="cuda")
             else:
                 rX, rn, rs = np.zeros(n_photons, np.float32), np.zeros(n_photons, np.uint32), np.zeros(n_photons, np.uint8)
+        r0 = rc = None
+        if raw_sweep:
+            if device_out:
+                r0 = torch.zeros(n_photons, dtype=torch.float32, device="cuda")
+                rc = torch.zeros(n_photons, dtype=torch.float32, device="cuda")
+            else:
+                r0, rc = np.zeros(n_photons, np.float32), np.zeros(n_photons, np.float32)
         spec = OutputSpec(n_bins, mk, X_min, X_max, _ptr(spec_arr)[0], 1 if peel else 0, img_n, peel_bins, 0,
                           peel_X_min, peel_X_max, _ptr(cube)[0] if peel else None,
                           _ptr(rX)[0] if raw else None, _ptr(rn)[0] if raw else None, _ptr(rs)[0] if raw else None,
-                          max_scat, 0)
+                          max_scat, 0, _ptr(r0)[0] if raw_sweep else None, _ptr(rc)[0] if raw_sweep else None)
         res = Result()
         self._check(self.L.thor_run(self.h, geom.h, C.byref(src), first_id, n_photons, seed, C.byref(spec),
                                     C.byref(res)))
         counts = spec_arr if not device_out else spec_arr
-        return RunResult(counts[:n_bins], int(counts[n_bins]), int(counts[n_bins + 1]), res.as_dict(), cube, rX, rn, rs)
+        return RunResult(counts[:n_bins], int(counts[n_bins]), int(counts[n_bins + 1]), res.as_dict(), cube, rX, rn, rs,
+                         r0, rc)
+
+    def reweight(self, X0, X, col, status, *, sample, targets, n_bins, X_min, X_max):
+        """thor_reweight: spectra of the escaped photons for each target (sigma, ew, C, tau_d),
+        reweighted from the sampled intrinsic spectrum sample = (sigma, ew, C); shape
+        (n_targets, n_bins + 2), sum of weights per bin / n."""
+        kind = _same_kind(X0, X, col, status)
+        n = int(X0.shape[0])
+        smp = (C.c_double * 3)(*[float(v) for v in sample])
+        tg = np.ascontiguousarray(np.asarray(targets, dtype=np.float64).reshape(-1, 4))
+        out = np.zeros((tg.shape[0], n_bins + 2))
+        self._check(self.L.thor_reweight(self.h, n, _ptr(X0)[0], _ptr(X)[0], _ptr(col)[0], _ptr(status)[0], kind, smp,
+                                         tg.shape[0], tg.ctypes.data_as(C.POINTER(C.c_double)), n_bins, float(X_min),
+                                         float(X_max), out.ctypes.data_as(C.POINTER(C.c_double))))
+        return out
 
     def forest(self, n_HI, T, v_los, *, ds_cm, dv_cell, n_bins, dv_bin, first=0, count=None, out=None):
         kind = _same_kind(n_HI, T, v_los)
@@ -392,14 +423,15 @@ class Server:
         self._bufs = {}
 
     def submit(self, *, T, R_in=0.9, R_out=1.0, N_HI=0.0, tau0=0.0, v_max=0.0, tau_dust=0.0, albedo=0.0,
-               g_hg=0.73, phase="dipole", step_dx=0.0, n_photons, seed, X0=0.0, sigma=0.0, n_bins=400,
-               X_min=-1500.0, X_max=1500.0, max_scat=0, core_skip=False):
+               g_hg=0.73, phase="dipole", step_dx=0.0, n_photons, seed, X0=0.0, sigma=0.0, ew=0.0, C_cont=0.0,
+               n_bins=400, X_min=-1500.0, X_max=1500.0, max_scat=0, core_skip=False, profile="homologous",
+               alpha_rho=0.0, alpha_v=1.0):
         p = ShellParams(R_in, R_out, N_HI, tau0, T, v_max, tau_dust, albedo, g_hg, PHASE[phase],
-                        1 if core_skip else 0, step_dx)
-        src = Source(0, 0, X0, sigma)
+                        1 if core_skip else 0, step_dx, PROFILE[profile], 0, alpha_rho, alpha_v)
+        src = Source(0, 0, X0, sigma, ew, C_cont)
         buf = np.zeros(n_bins + 2, np.uint64)
         spec = OutputSpec(n_bins, MEM_HOST, X_min, X_max, buf.ctypes.data, 0, 0, 0, 0, 0.0, 0.0, None, None, None,
-                          None, max_scat, 0)
+                          None, max_scat, 0, None, None)
         t = C.c_int64()
         self.ctx._check(self.ctx.L.thor_server_submit(self.h, C.byref(p), C.byref(src), n_photons, seed, C.byref(spec),
                                                       C.byref(t)))

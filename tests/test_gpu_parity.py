@@ -395,3 +395,86 @@ def test_invalid_arguments_are_rejected(ctx):
     # the context is still usable afterwards
     r = ctx.run(g, n_photons=100, seed=1, n_bins=10, X_min=-100, X_max=100)
     assert r.stats["n_escaped"] == 100
+
+
+# --------------------------------------------------------- shell-model sweep (Sec. 5.1)
+_SWEEP = dict(R_in=0.2, R_out=1.0, N_HI=10 ** 17.6, T=1e4, v_max=120.0, alpha_rho=-1.0, alpha_v=0.5)
+_SAMPLE = (800.0, 740.0, 2500.0)
+
+
+def test_power_law_shell_parity(ctx, orc):
+    """Power-law shell (non-homologous flow, falling density, dust in the transport) against
+    the oracle's exact-tau transport: spectra, scattering counts, emitted X0, columns."""
+    g = ctx.shell(profile="power_law", tau_dust=0.3, phase="dipole", **_SWEEP)
+    n = 20000
+    kw = dict(n_bins=100, X_min=-2500.0, X_max=2500.0)
+    r = ctx.run(g, n_photons=n, seed=21, sigma=_SAMPLE[0], ew=_SAMPLE[1], C_cont=_SAMPLE[2], raw=True,
+                raw_sweep=True, **kw)
+    ro = orc.run_plshell(dv_ratio=5.0, N_HI=_SWEEP["N_HI"], T=1e4, v_avg=120.0, alpha_rho=-1.0, alpha_v=0.5,
+                         tau_dust=0.3, phase="dipole", sigma=_SAMPLE[0], ew=_SAMPLE[1], C_cont=_SAMPLE[2],
+                         n_photons=n, seed=21, **kw)
+    # emission uses the same words on both sides: X0 photon by photon
+    assert np.abs(r.raw_X0.astype(np.float64) - ro["X0"]).max() < 0.05
+    c, dof = chi2_dof(r.spectrum, ro["counts"])
+    assert c <= 1.2, (c, dof)
+    assert mean_nscat_z(r.stats, n, ro, n) < 3.0
+    esc_g, esc_o = r.raw_status == 1, ro["status"] == 1
+    cg, co = r.raw_col[esc_g].astype(np.float64), ro["col"][esc_o]
+    z = abs(cg.mean() - co.mean()) / np.sqrt(cg.var() / cg.size + co.var() / co.size)
+    assert z < 3.0, z
+
+
+def test_power_law_homologous_case_matches_uniform_shell(ctx):
+    """alpha_rho = 0, alpha_v = 1 through the power-law event equals the uniform homologous
+    shell photon by photon (two device paths, one of them pinned against the oracle)."""
+    base = dict(R_in=0.9, N_HI=1e17, T=1e4, tau_dust=0.3, phase="dipole")
+    a = ctx.shell(v_max=200.0, **base)
+    b = ctx.shell(profile="power_law", v_max=0.95 * 200.0, alpha_rho=0.0, alpha_v=1.0, **base)
+    kw = dict(n_photons=4000, seed=5, sigma=50.0, n_bins=60, X_min=-1500.0, X_max=1500.0, raw=True)
+    ra, rb = ctx.run(a, **kw), ctx.run(b, **kw)
+    same = (ra.raw_status == rb.raw_status) & (np.abs(ra.raw_X - rb.raw_X) < 0.5)
+    assert same.mean() > 0.9, same.mean()
+    c, _ = chi2_dof(ra.spectrum, rb.spectrum)
+    assert c < 0.5
+
+
+def test_reweight_kernel_against_oracle(ctx, orc):
+    """thor_reweight on seeded synthetic photon records (never the CUDA path's output) against
+    the oracle's reweighting, element by element."""
+    rng = np.random.default_rng(31)
+    n = 200_000
+    pl = _SAMPLE[1] / (_SAMPLE[1] + 2 * _SAMPLE[2])
+    line = rng.random(n) < pl
+    X0 = np.where(line, rng.normal(0.0, _SAMPLE[0], n), rng.uniform(-_SAMPLE[2], _SAMPLE[2], n)).astype(np.float32)
+    X = (X0 + rng.normal(0.0, 300.0, n)).astype(np.float32)
+    col = rng.lognormal(0.0, 0.7, n).astype(np.float32)
+    st = np.where(rng.random(n) < 0.8, 1, 2).astype(np.uint8)
+    targets = [(800.0, 740.0, 2500.0, 0.0), (300.0, 100 * 246.6, 2500.0, 0.2), (150.0, 20 * 246.6, 2500.0, 1.5)]
+    got = ctx.reweight(X0, X, col, st, sample=_SAMPLE, targets=targets, n_bins=80, X_min=-3000.0, X_max=3000.0)
+    for t, tg in enumerate(targets):
+        ref = orc.reweight(X0.astype(np.float64), X.astype(np.float64), col.astype(np.float64), st,
+                           sample=_SAMPLE, target=tg[:3], tau_d=tg[3], n_bins=80, X_min=-3000.0, X_max=3000.0)
+        m = ref > 1e-6 * ref.max()
+        rel = np.abs(got[t][m] - ref[m]) / ref[m]
+        assert rel.max() < 1e-5, (t, rel.max())
+    # the identity target reproduces the plain histogram of escaped photons
+    h = np.histogram(X[st == 1], bins=80, range=(-3000.0, 3000.0))[0] / n
+    assert np.allclose(got[0][:80], h, rtol=1e-5, atol=1e-12)
+
+
+def test_reweighted_dust_matches_dust_in_transport(ctx):
+    """A dust-free power-law run reweighted by exp(-tau_d col) equals a run with the dust in
+    the transport (dust following the gas): escape fraction and spectrum."""
+    kw = dict(n_photons=20000, sigma=_SAMPLE[0], ew=_SAMPLE[1], C_cont=_SAMPLE[2], n_bins=50, X_min=-2500.0,
+              X_max=2500.0)
+    clean = ctx.run(ctx.shell(profile="power_law", phase="dipole", **_SWEEP), seed=41, raw=True, raw_sweep=True, **kw)
+    dusty = ctx.run(ctx.shell(profile="power_law", phase="dipole", tau_dust=0.8, **_SWEEP), seed=42, **kw)
+    rw = ctx.reweight(clean.raw_X0, clean.raw_X, clean.raw_col, clean.raw_status, sample=_SAMPLE,
+                      targets=[(*_SAMPLE, 0.8)], n_bins=50, X_min=-2500.0, X_max=2500.0)[0]
+    n = kw["n_photons"]
+    f_rt, f_rw = dusty.stats["n_escaped"] / n, rw.sum()
+    assert abs(f_rt - f_rw) < 4 * np.sqrt(f_rt * (1 - f_rt) / n), (f_rt, f_rw)
+    c = dusty.spectrum / n
+    var = c / n + rw[:50] / n
+    m = (c + rw[:50]) > 5.0 / n
+    assert np.sum((c[m] - rw[:50][m]) ** 2 / var[m]) / m.sum() < 2.0
