@@ -65,11 +65,14 @@ class PLShell(C.Structure):
     """Power-law shell of the shell-model sweep (Sec. 5.1)."""
     _fields_ = [("dv_ratio", C.c_double), ("N_HI", C.c_double), ("T", C.c_double), ("v_avg", C.c_double),
                 ("alpha_rho", C.c_double), ("alpha_v", C.c_double), ("tau_dust", C.c_double),
-                ("phase", C.c_int32), ("pad", C.c_int32)]
+                ("phase", C.c_int32), ("species", C.c_int32)]
+
+
+SPECIES = {"HI": 0, "MgII": 1}
 
 
 class PLSource(C.Structure):
-    _fields_ = [("sigma", C.c_double), ("ew", C.c_double), ("C", C.c_double)]
+    _fields_ = [("sigma", C.c_double), ("ew", C.c_double), ("C", C.c_double), ("X0", C.c_double)]
 
 
 class GridRun(C.Structure):
@@ -109,6 +112,7 @@ def lib():
                                         P(C.c_uint64), P(Result), P(C.c_double), P(C.c_uint64),
                                         P(C.c_uint8)]
             L.orc_plshell_profile.argtypes = [P(PLShell), C.c_double, P(C.c_double), P(C.c_double)]
+            L.orc_mgii_params.argtypes = [C.c_double, P(C.c_double)]
             L.orc_run_plshell.restype = C.c_int
             L.orc_run_plshell.argtypes = [P(PLShell), P(PLSource), C.c_uint64, C.c_uint64, C.c_uint64,
                                           C.c_int32, C.c_double, C.c_double, C.c_uint64, C.c_int32,
@@ -249,18 +253,27 @@ def run_shell(*, tau0, T, R_in=0.0, R_out=1.0, v_max=0.0, tau_dust=0.0, albedo=0
 
 def plshell_profile(*, dv_ratio, N_HI, T, v_avg, alpha_rho, alpha_v, r):
     """HI opacity per unit length (outer radius = 1) and outflow speed at radius r."""
-    geo = PLShell(dv_ratio, N_HI, T, v_avg, alpha_rho, alpha_v, 0.0, 1, 0)
+    geo = PLShell(dv_ratio, N_HI, T, v_avg, alpha_rho, alpha_v, 0.0, 1, SPECIES["HI"])
     k, v = C.c_double(), C.c_double()
     lib().orc_plshell_profile(C.byref(geo), r, C.byref(k), C.byref(v))
     return k.value, v.value
 
 
+def mgii_params(T):
+    """Mg II doublet line data at T: v_th, a and sigma_0 of K and H, H centre on the K scale."""
+    out = np.zeros(6)
+    lib().orc_mgii_params(T, _p(out, C.c_double))
+    return {"vth_kms": out[0], "a_K": out[1], "sigma0_K": out[2], "a_H": out[3], "sigma0_H": out[4],
+            "X_H": out[5]}
+
+
 def run_plshell(*, dv_ratio, N_HI, T, v_avg, alpha_rho=0.0, alpha_v=1.0, tau_dust=0.0, phase="dipole",
                 sigma=800.0, ew=0.0, C_cont=0.0, n_photons=1000, seed=0, first_id=0, n_bins=200,
-                X_min=-2500.0, X_max=2500.0, max_scat=0, n_threads=0):
-    """Power-law shell run (Sec. 5.1) with per-photon records X0, X, col (units of N_HI)."""
-    geo = PLShell(dv_ratio, N_HI, T, v_avg, alpha_rho, alpha_v, tau_dust, PHASE[phase], 0)
-    src = PLSource(sigma, ew, C_cont)
+                X_min=-2500.0, X_max=2500.0, max_scat=0, n_threads=0, species="HI", X0=0.0):
+    """Power-law shell run (Sec. 5.1) with per-photon records X0, X, col (units of N_HI);
+    species "MgII": the doublet, N_HI is then the Mg II column."""
+    geo = PLShell(dv_ratio, N_HI, T, v_avg, alpha_rho, alpha_v, tau_dust, PHASE[phase], SPECIES[species])
+    src = PLSource(sigma, ew, C_cont, X0)
     counts = np.zeros(n_bins + 2, dtype=np.uint64)
     res = Result()
     x0, x, col = np.zeros(n_photons), np.zeros(n_photons), np.zeros(n_photons)

@@ -786,13 +786,14 @@ struct orc_plshell {
   double alpha_rho, alpha_v;
   double tau_dust;          // radial dust optical depth (dust follows the gas), 0 = none
   int32_t phase;            // 0 isotropic, 1 dipole, 2 mixed
-  int32_t pad;
+  int32_t species;          // 0: HI Lyman alpha; 1: Mg II doublet (N_HI is then the Mg II column)
 };
 
 // Intrinsic spectrum sampled at emission: a Gaussian line of width sigma (km/s) with
 // equivalent width ew (km/s) on a flat continuum over [-C, C] (C = 0: line only).
 struct orc_plsource {
   double sigma, ew, C;
+  double X0;                // centre of the line and of the continuum (km/s)
 };
 
 namespace {
@@ -803,9 +804,31 @@ double pow_integral(double alpha, double lo, double hi) {
   return (std::pow(hi, alpha + 1.0) - std::pow(lo, alpha + 1.0)) / (alpha + 1.0);
 }
 
+// Mg II doublet (Sec. 2.4): K = 2S1/2-2P3/2 at 2796.352 A (f 0.608, A 2.60e8 /s) and
+// H = 2S1/2-2P1/2 at 2803.531 A (f 0.303, A 2.57e8 /s), vacuum wavelengths and atomic
+// data of the NIST Atomic Spectra Database; ion mass 24.305 u.  Both transitions are
+// resonant (the upper levels decay only to the ground state), so a scattering re-emits
+// in the transition that absorbed.  The frequency variable is X = c (nu - nu_K) / nu_K;
+// for transition l with r_l = lambda_l / lambda_K its own offset is
+// X_l = c (nu - nu_l) / nu_l = X + (r_l - 1)(c + X).  The K line scatters with the
+// configured phase function, H (J = 1/2 upper level) isotropically.
+const double kC_kms = 2.99792458e5;
+const double kLamMgK = 2796.352e-8, kLamMgH = 2803.531e-8;
+const double kFMgK = 0.608, kFMgH = 0.303, kAMgK = 2.60e8, kAMgH = 2.57e8;
+const double kMassMg = 24.305 * 1.66053906660e-24;
+double vth_mg(double T) { return std::sqrt(2.0 * kBoltz * T / kMassMg) * 1e-5; }
+double a_line(double A, double lam, double vth) { return A * lam / (4.0 * kPi * vth * 1e5); }
+double sigma0_line(double f, double lam, double vth) {
+  return f * kSqrtPi * kEsu * kEsu / (kMe * kC * (vth * 1e5 / lam));
+}
+
 struct PLShell {
   double ri, F, kap_n, kap_d, vth, a, v1, ar, av, G;  // v(r) = v1 r^av; G bounds |d(v mu_r)/ds|
   int phase;
+  int n_lines = 1;                 // 2: Mg II doublet, line 2 = H
+  double kap_n2 = 0.0, a2 = 0.0, eps2 = 0.0;  // line 2: opacity at r = 1, Voigt a, r_2 - 1
+  double X2(double X) const { return X + eps2 * (kC_kms + X); }
+  double X_from2(double X2v) const { return X2v - eps2 / (1.0 + eps2) * (kC_kms + X2v); }
   double n_rel(double r) const { return std::pow(r, ar); }
   double vel(double r) const { return v1 * std::pow(r, av); }
 };
@@ -814,12 +837,21 @@ PLShell make_plshell(const orc_plshell& p) {
   PLShell m;
   m.ri = 1.0 / p.dv_ratio;
   const double F = pow_integral(p.alpha_rho, m.ri, 1.0);
-  const double tau0 = p.N_HI * sigma0_cm2(p.T);
   m.F = F;
-  m.kap_n = tau0 / F;
   m.kap_d = p.tau_dust / F;
-  m.vth = vth_kms(p.T);
-  m.a = voigt_a(p.T);
+  if (p.species == 1) {
+    m.vth = vth_mg(p.T);
+    m.a = a_line(kAMgK, kLamMgK, m.vth);
+    m.kap_n = p.N_HI * sigma0_line(kFMgK, kLamMgK, m.vth) / F;
+    m.n_lines = 2;
+    m.a2 = a_line(kAMgH, kLamMgH, m.vth);
+    m.kap_n2 = p.N_HI * sigma0_line(kFMgH, kLamMgH, m.vth) / F;
+    m.eps2 = kLamMgH / kLamMgK - 1.0;
+  } else {
+    m.vth = vth_kms(p.T);
+    m.a = voigt_a(p.T);
+    m.kap_n = p.N_HI * sigma0_cm2(p.T) / F;
+  }
   m.ar = p.alpha_rho; m.av = p.alpha_v;
   m.v1 = p.v_avg * (1.0 - m.ri) / pow_integral(p.alpha_v, m.ri, 1.0);
   // |d(v(r) mu_r)/ds| = |v'(r) mu_r^2 + v(r) (1 - mu_r^2) / r| <= max(|v'|, v / r)
@@ -845,7 +877,12 @@ struct PLRay {
     double nr = m->n_rel(r);
     x = (X - m->vel(r) * mur) / m->vth;
     kap = nr * (m->kap_n * voigt_H(m->a, x) + m->kap_d);
-    col_rate = nr / m->F;  // HI column per unit length in units of N_HI
+    if (m->n_lines == 2) {
+      const double x2 = (m->X2(X) - m->vel(r) * mur) / m->vth;
+      kap += nr * m->kap_n2 * voigt_H(m->a2, x2);
+      if (std::fabs(x2) < std::fabs(x)) x = x2;  // the nearer line sets the quadrature pieces
+    }
+    col_rate = nr / m->F;  // column per unit length in units of the radial column
   }
   double kappa(double s) const { double k0, c, x; at(s, k0, c, x); return k0; }
   // tau and column over [s0, s1] on one Gauss-Legendre piece
@@ -928,9 +965,9 @@ void run_photon_plshell(const PLShell& m, const orc_plsource& src, uint64_t seed
   double X;
   if (rng.u(4) <= p_line) {
     double R1 = rng.u(2), R2 = rng.u(3);
-    X = src.sigma * std::sqrt(-2.0 * std::log(R1)) * std::cos(2.0 * kPi * R2);
+    X = src.X0 + src.sigma * std::sqrt(-2.0 * std::log(R1)) * std::cos(2.0 * kPi * R2);
   } else {
-    X = src.C * (2.0 * rng.u(5) - 1.0);
+    X = src.X0 + src.C * (2.0 * rng.u(5) - 1.0);
   }
   out.X0 = X;
   bool in_cavity = true;
@@ -970,14 +1007,28 @@ void run_photon_plshell(const PLShell& m, const orc_plsource& src, uint64_t seed
     double vr = m.vel(r);
     double v[3] = {vr * p[0] / r, vr * p[1] / r, vr * p[2] / r};
     double x = (X - dot(v, k)) / m.vth;
-    double kHI = m.kap_n * m.n_rel(r) * voigt_H(m.a, x);
+    double k1 = m.kap_n * m.n_rel(r) * voigt_H(m.a, x);
     double kd = m.kap_d * m.n_rel(r);
-    bool dust = false;
-    if (kd > 0.0) dust = rng.u(W_CHANNEL) >= kHI / (kHI + kd);
-    if (dust) { out.X = X; out.status = 2; return; }  // dust absorbs (albedo 0 in the sweep)
+    double x2 = 0.0, k2 = 0.0;
+    if (m.n_lines == 2) {
+      x2 = (m.X2(X) - dot(v, k)) / m.vth;
+      k2 = m.kap_n2 * m.n_rel(r) * voigt_H(m.a2, x2);
+    }
+    // channel in proportion to the opacities: line 1, line 2, dust (one uniform)
+    int ch = 0;
+    if (kd > 0.0 || m.n_lines == 2) {
+      const double u = rng.u(W_CHANNEL), kt = k1 + k2 + kd;
+      ch = (u < k1 / kt) ? 0 : ((u < (k1 + k2) / kt) ? 1 : 2);
+    }
+    if (ch == 2) { out.X = X; out.status = 2; return; }  // dust absorbs (albedo 0 in the sweep)
     double kout[3];
-    double xo = scatter_HI(x, m.a, m.phase, k, rng, kout, nullptr, &out.iters);
-    X = xo * m.vth + dot(v, kout);
+    if (ch == 0) {
+      double xo = scatter_HI(x, m.a, m.phase, k, rng, kout, nullptr, &out.iters);
+      X = xo * m.vth + dot(v, kout);
+    } else {
+      double xo = scatter_HI(x2, m.a2, PH_ISO, k, rng, kout, nullptr, &out.iters);
+      X = m.X_from2(xo * m.vth + dot(v, kout));
+    }
     out.nscat++;
     if (out.nscat >= cap) { out.X = X; out.status = 3; return; }
     for (int i = 0; i < 3; ++i) k[i] = kout[i];
@@ -993,6 +1044,18 @@ double intrinsic_pdf(double X, double sigma, double ew, double C) {
 }
 
 }  // namespace
+
+// Mg II line data at temperature T: v_th [km/s], a_K, sigma0_K [cm^2], a_H, sigma0_H, and the
+// H line centre on the K-relative scale X [km/s].
+extern "C" void orc_mgii_params(double T, double* out) {
+  const double vth = vth_mg(T);
+  out[0] = vth;
+  out[1] = a_line(kAMgK, kLamMgK, vth);
+  out[2] = sigma0_line(kFMgK, kLamMgK, vth);
+  out[3] = a_line(kAMgH, kLamMgH, vth);
+  out[4] = sigma0_line(kFMgH, kLamMgH, vth);
+  out[5] = kC_kms * (kLamMgK / kLamMgH - 1.0);
+}
 
 extern "C" void orc_plshell_profile(const orc_plshell* geo, double r, double* n_rel_kappa, double* v) {
   PLShell m = make_plshell(*geo);

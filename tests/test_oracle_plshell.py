@@ -80,3 +80,36 @@ def test_reweight_identity_and_dust(orc):
     m = (c + rw[:40]) > 5.0 / 6000
     chi2 = np.sum((c[m] - rw[:40][m]) ** 2 / var[m]) / m.sum()
     assert chi2 < 2.0, chi2
+
+
+def test_mgii_line_data(orc):
+    """Mg II doublet data: thermal speed scales as sqrt(m_H / m_Mg) from the HI value, the
+    line-centre cross-sections are in the ratio f_K lambda_K : f_H lambda_H, and the H line
+    sits c (lambda_K / lambda_H - 1) = -767.68 km/s from K."""
+    m = orc.mgii_params(1e4)
+    h = orc.line_params(1e4)
+    assert abs(m["vth_kms"] / h["vth_kms"] - np.sqrt(1.6735575e-24 / (24.305 * 1.66053906660e-24))) < 1e-12
+    assert abs(m["sigma0_K"] / m["sigma0_H"] - (0.608 * 2796.352) / (0.303 * 2803.531)) < 1e-12
+    assert abs(m["X_H"] - 299792.458 * (2796.352 / 2803.531 - 1.0)) < 1e-9
+    assert 2.1e-3 < m["a_K"] < 2.3e-3 and 2.1e-3 < m["a_H"] < 2.3e-3
+
+
+@pytest.mark.parametrize("where", ["K", "H", "between"])
+def test_mgii_first_flight_escape(orc, where):
+    """Static uniform sphere around a monochromatic source: the fraction of photons that
+    escape without scattering is exp(-tau(X)), tau summed over both transitions, each with
+    its own Voigt profile (scipy's Faddeeva function) at its own offset."""
+    from scipy.special import wofz
+    m = orc.mgii_params(1e4)
+    X0 = {"K": 0.0, "H": m["X_H"], "between": 0.5 * m["X_H"]}[where]
+    N = 1.5e12
+    n = 20000
+    r = orc.run_plshell(dv_ratio=1000.0, N_HI=N, T=1e4, v_avg=0.0, alpha_rho=0.0, alpha_v=1.0, phase="dipole",
+                        sigma=1e-4, ew=1.0, C_cont=0.0, X0=X0, n_photons=n, seed=11, species="MgII")
+    xK = X0 / m["vth_kms"]
+    xH = (X0 + (2803.531 / 2796.352 - 1.0) * (299792.458 + X0)) / m["vth_kms"]
+    tau = N * (m["sigma0_K"] * wofz(xK + 1j * m["a_K"]).real
+                            + m["sigma0_H"] * wofz(xH + 1j * m["a_H"]).real)
+    p = np.exp(-tau)
+    f = float(np.mean(r["nscat"] == 0))
+    assert abs(f - p) < 4 * np.sqrt(max(p * (1 - p), 1e-9) / n) + 1e-9, (where, f, p, tau)
