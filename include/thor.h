@@ -95,6 +95,12 @@ int thor_ctx_set_tail(thor_ctx_t ctx, int spill_below, int max_phases);
  *     limiter f min(v_th / max|d(v r_hat.k)/ds|, R_in / |alpha_rho|) (Sec. 5.1). */
 #define THOR_PROFILE_HOMOLOGOUS 0
 #define THOR_PROFILE_POWER_LAW 1
+/* Scattering species (power-law shells): HI Lyman alpha, or the Mg II doublet (Sec. 2.4:
+ * K 2796.352 A and H 2803.531 A, total cross-section the sum of both, re-emission in the
+ * absorbing transition; N_HI / tau0 then give the Mg II column / the K line-centre depth;
+ * frequencies X are relative to the K line). */
+#define THOR_SPECIES_HI 0
+#define THOR_SPECIES_MGII 1
 typedef struct {
   double R_in, R_out;    /* radii, 0 <= R_in < R_out */
   double N_HI;           /* HI column R_in -> R_out [cm^-2]; used when tau0 <= 0 */
@@ -106,9 +112,9 @@ typedef struct {
   double g_hg;           /* Henyey-Greenstein asymmetry (Eq. 9) */
   int32_t phase;         /* THOR_PHASE_* for resonant scattering */
   int32_t core_skip;     /* 1: core-skipping, x_crit = 0.2 (a tau0)^(1/3) when a tau0 >= 1 (Sec. 3.4.2) */
-  double step_dx;        /* step limiter f (Sec. 4.1): sub-step length f v_th / |dv/dr|; 0 -> 0.01 */
+  double step_dx;        /* step limiter f (Sec. 5.1): sub-step length f v_th / |dv/dr|; 0 -> 0.01 */
   int32_t profile;       /* THOR_PROFILE_* (0 = homologous) */
-  int32_t reserved3;
+  int32_t species;       /* THOR_SPECIES_* (power-law shells; 0 = HI) */
   double alpha_rho;      /* power law: density index */
   double alpha_v;        /* power law: velocity index */
 } thor_shell_params;

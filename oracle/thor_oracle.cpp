@@ -21,7 +21,7 @@
 //   * Sec. 3.4.1             peeling-off towards observers
 //   * Sec. 3.5.2, Eq. 11     synthetic Lyman-alpha forest optical depth
 //   * App. A.3               Voigt profile H(a,x) = Re w(x + i a) (Faddeeva truth)
-//   * Sec. 4.1               step limiter / velocity gradients: here the oracle does
+//   * Sec. 5.1               step limiter / velocity gradients: here the oracle does
 //                            not sub-step; it integrates tau exactly along the path
 //                            (Gauss-Legendre quadrature on analytic H) and root-finds
 //                            the interaction point.

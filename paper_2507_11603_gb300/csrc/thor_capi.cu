@@ -136,20 +136,31 @@ static double pow_int(double alpha, double lo, double hi) {
 // column tau0 / sigma_0, v ~ r^alpha_v with distance average v_max, dust following the
 // gas, global step limiter f min(v_th / G, r_i / |alpha_rho|) with G a bound on
 // |d(v r_hat . k)/ds| = |v' mu_r^2 + v (1 - mu_r^2) / r| <= max(|v'|, v / r).
+// Mg II doublet (Sec. 2.4), NIST Atomic Spectra Database: vacuum wavelengths [cm],
+// oscillator strengths, Einstein A [1/s]; ion mass 24.305 u.
+static const double kMgLamK = 2796.352e-8, kMgLamH = 2803.531e-8, kMgFK = 0.608, kMgFH = 0.303;
+static const double kMgAK = 2.60e8, kMgAH = 2.57e8, kMgMass = 24.305 * 1.66053906660e-24;
+
 static int fill_power_law(thor_ctx* ctx, const thor_shell_params* p, ShellModel* m) {
   using namespace thor;
   if (!(p->R_in > 0.0)) return ctx->fail(THOR_ERR_INVALID_ARG, "power-law shells need R_in > 0");
+  if (p->species != THOR_SPECIES_HI && p->species != THOR_SPECIES_MGII)
+    return ctx->fail(THOR_ERR_INVALID_ARG, "unknown species");
   if (!(fabs(p->alpha_rho) <= 8.0) || !(fabs(p->alpha_v) <= 8.0))
     return ctx->fail(THOR_ERR_INVALID_ARG, "power-law indices out of range");
   if (p->albedo != 0.0) return ctx->fail(THOR_ERR_INVALID_ARG, "power-law shells take albedo 0 (dust absorbs)");
+  const bool mg = p->species == THOR_SPECIES_MGII;
+  // thermal speed, Voigt a and line-centre cross-section of the (first) transition
+  const double vth = mg ? sqrt(2.0 * 1.380649e-16 * p->T / kMgMass) * 1e-5 : line_vth_kms(p->T);
+  const double esu2_mec = 1.7724538509055159 * 4.80320471e-10 * 4.80320471e-10 / (9.1093837015e-28 * 2.99792458e10);
+  const double sig_K = mg ? kMgFK * esu2_mec * kMgLamK / (vth * 1e5) : line_sigma0(p->T);
   double tau0 = p->tau0;
   if (!(tau0 > 0.0)) {
     if (!(p->N_HI >= 0.0)) return ctx->fail(THOR_ERR_INVALID_ARG, "N_HI must be >= 0");
-    tau0 = p->N_HI * line_sigma0(p->T);
+    tau0 = p->N_HI * sig_K;
   }
   const double ri = p->R_in / p->R_out;
   const double F = pow_int(p->alpha_rho, ri, 1.0);
-  const double vth = line_vth_kms(p->T);
   const double v1 = p->v_max * (1.0 - ri) / pow_int(p->alpha_v, ri, 1.0);
   double G = 0.0;
   for (int i = 0; i <= 2000; ++i) {
@@ -172,12 +183,20 @@ static int fill_power_law(thor_ctx* ctx, const thor_shell_params* p, ShellModel*
   m->v1 = (float)v1;
   m->vth = (float)vth;
   m->inv_vth = (float)(1.0 / vth);
-  m->a = (float)line_a(p->T);
+  m->a = mg ? (float)(kMgAK * kMgLamK / (4.0 * M_PI * vth * 1e5)) : (float)line_a(p->T);
+  m->n_lines = 1;
+  if (mg) {
+    const double sig_H = kMgFH * esu2_mec * kMgLamH / (vth * 1e5);
+    m->n_lines = 2;
+    m->kapn2 = (float)(tau0 * (sig_H / sig_K) / F);
+    m->a2 = (float)(kMgAH * kMgLamH / (4.0 * M_PI * vth * 1e5));
+    m->eps2 = (float)(kMgLamH / kMgLamK - 1.0);
+  }
   m->ds_core = (float)ds;
   m->albedo = 0.0f;
   m->g_hg = (float)p->g_hg;
   m->phase = p->phase;
-  const double at = line_a(p->T) * tau0;
+  const double at = (double)m->a * tau0;
   m->xcrit = (p->core_skip && at >= 1.0) ? (float)(0.2 * cbrt(at)) : 0.0f;
   return THOR_OK;
 }
@@ -208,6 +227,8 @@ int thor::fill_shell_model(thor_ctx* ctx, const thor_shell_params* p, ShellModel
   if (!(p->v_max >= 0.0)) return ctx->fail(THOR_ERR_INVALID_ARG, "v_max must be >= 0");
   if (p->profile != THOR_PROFILE_HOMOLOGOUS && p->profile != THOR_PROFILE_POWER_LAW)
     return ctx->fail(THOR_ERR_INVALID_ARG, "unknown density/velocity profile");
+  if (p->profile == THOR_PROFILE_HOMOLOGOUS && p->species != THOR_SPECIES_HI)
+    return ctx->fail(THOR_ERR_INVALID_ARG, "the Mg II doublet runs on power-law shells");
   if (p->profile == THOR_PROFILE_POWER_LAW) return fill_power_law(ctx, p, m);
   const double L = (p->R_out - p->R_in) / p->R_out;  // in units of R_out
   double tau0 = p->tau0;

@@ -23,7 +23,7 @@ struct ShellModel {
   float vth, inv_vth, a;     // km/s, s/km, Voigt parameter
   float vgrad;               // km/s per unit length (homologous v = vgrad r)
   float gam;                 // |dx/ds| = vgrad / vth
-  float ds_core;             // sub-step length (step limiter, Sec. 4.1: f l_v)
+  float ds_core;             // sub-step length (step limiter, Sec. 5.1: f l_v)
   float xcrit;               // core-skipping threshold (Sec. 3.4.2), 0 = off
   float albedo, g_hg;
   int32_t phase;
@@ -46,6 +46,8 @@ struct ShellModel {
   float ar, av, v1, kapn, kapdn;
   float invF;                // HI column per unit length at r = 1, in units of the radial column
   float p_line, cont_C;      // source: probability of the line, continuum half-width (km/s; 0 = none)
+  int32_t n_lines;           // power law: 2 = Mg II doublet (line 2 = H, isotropic re-emission)
+  float kapn2, a2, eps2;     // line 2: opacity at r = 1, Voigt a, lambda_2 / lambda_1 - 1
   float* raw_X0;             // optional per-photon emitted X and column
   float* raw_col;
 };

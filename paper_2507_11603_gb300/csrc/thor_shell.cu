@@ -1,6 +1,6 @@
 // thor_shell.cu -- photon-packet loop through gridless spherical shells (THOR
 // Sec. 3.3-3.4): emission, propagation with the velocity-gradient step limiter
-// (Sec. 4.1), interaction channel choice, resonant / dust scattering, escape tally.
+// (Sec. 5.1), interaction channel choice, resonant / dust scattering, escape tally.
 //
 // Execution model: persistent warps.  Every loop iteration is one event (draw tau,
 // propagate to the interaction or the boundary, interact) for every live lane;
@@ -256,10 +256,18 @@ __device__ __forceinline__ void col_add(Photon& ph, float d) {
 // min(safety distance, ds / 16) is taken with that rate (one Voigt evaluation, no FP64);
 // otherwise sub-steps of at most ds (the global step limiter) use the midpoint state.
 // Dust follows the gas and absorbs.
+// Second transition of a doublet (Mg II H): its own offset X_2 = X + eps2 (c + X) on the
+// scale of the first, and back.
+constexpr float kCkms = 299792.458f;
+__device__ __forceinline__ float to_line2(const ShellModel& m, float X) { return __fmaf_rn(m.eps2, kCkms + X, X); }
+__device__ __forceinline__ float from_line2(const ShellModel& m, float X2) {
+  return __fmaf_rn(-__fdividef(m.eps2, 1.0f + m.eps2), kCkms + X2, X2);
+}
+
 __device__ int shell_event_pl(const ShellModel& m, Photon& ph, const float* __restrict__ Ktab) {
-  ph.rng.next_event((m.kapdn > 0.0f || m.phase == PH_MIXED) ? 3u : 2u);
+  ph.rng.next_event((m.kapdn > 0.0f || m.phase == PH_MIXED || m.n_lines == 2) ? 3u : 2u);
   float tau_rem = -__logf(ph.rng.u(W_TAU));  // Eq. 3
-  float kH, kD;
+  float kH, kH2 = 0.0f, kD;
   PLState site;
   for (;;) {
     if (ph.region) {  // empty cavity: straight to the inner sphere, lab X conserved
@@ -276,7 +284,9 @@ __device__ int shell_event_pl(const ShellModel& m, Photon& ph, const float* __re
       const PLState st = pl_state(m, (float)ph.px + ph.ox, (float)ph.py + ph.oy, (float)ph.pz + ph.oz, ph.k);
       const float x = (ph.X - st.v * st.mur) * m.inv_vth;
       const float H = voigt<false>(m.a, x, Ktab);
-      const float kap = st.nr * __fmaf_rn(m.kapn, H, m.kapdn);
+      const float H2 = (m.n_lines == 2) ? voigt<false>(m.a2, (to_line2(m, ph.X) - st.v * st.mur) * m.inv_vth, Ktab)
+                                         : 0.0f;
+      const float kap = st.nr * __fmaf_rn(m.kapn, H, __fmaf_rn(m.kapn2, H2, m.kapdn));
       const float s0 = __fdividef(tau_rem, kap);
       ++ph.steps;
       if (s0 <= ph.safe && s0 <= 0.0625f * m.ds_core) {
@@ -284,6 +294,7 @@ __device__ int shell_event_pl(const ShellModel& m, Photon& ph, const float* __re
         ph.safe = __fmaf_rd(-s0, 1.000001f, ph.safe);
         col_add(ph, st.nr * m.invF * s0);
         kH = m.kapn * st.nr * H;
+        kH2 = m.kapn2 * st.nr * H2;
         kD = m.kapdn * st.nr;
         site = pl_state(m, (float)ph.px + ph.ox, (float)ph.py + ph.oy, (float)ph.pz + ph.oz, ph.k);
         break;
@@ -314,13 +325,16 @@ __device__ int shell_event_pl(const ShellModel& m, Photon& ph, const float* __re
                                   __fmaf_rn(sm, ph.k.z, p0z), ph.k);
       const float x = (ph.X - st.v * st.mur) * m.inv_vth;
       const float H = voigt<false>(m.a, x, Ktab);
-      const float kap = st.nr * __fmaf_rn(m.kapn, H, m.kapdn);
+      const float H2 = (m.n_lines == 2) ? voigt<false>(m.a2, (to_line2(m, ph.X) - st.v * st.mur) * m.inv_vth, Ktab)
+                                         : 0.0f;
+      const float kap = st.nr * __fmaf_rn(m.kapn, H, __fmaf_rn(m.kapn2, H2, m.kapdn));
       const float dtau = kap * (s1 - s);
       ++ph.steps;
       if (dtau >= tau_rem) {
         s_star = fminf(s + __fdividef(tau_rem, kap), Sf);
         col_add(ph, st.nr * m.invF * (s_star - s));
         kH = m.kapn * st.nr * H;
+        kH2 = m.kapn2 * st.nr * H2;
         kD = m.kapdn * st.nr;
         break;
       }
@@ -339,14 +353,27 @@ __device__ int shell_event_pl(const ShellModel& m, Photon& ph, const float* __re
     if (next == 1) return 1;  // escapes with its lab X
     ph.region = 1;
   }
-  // Interaction (Sec. 3.4): HI or dust in proportion to their opacities; dust absorbs.
-  if (kD > 0.0f && ph.rng.u(W_CHANNEL) >= __fdividef(kH, kH + kD)) return 2;
-  const float x_site = (ph.X - site.v * site.mur) * m.inv_vth;
-  const float xo = scatter_resonant(x_site, m.a, m.phase, ph.k, ph.rng, ph.iters, nullptr, m.xcrit);
-  // back to the lab frame with the new direction: X = x v_th + v(r) r_hat . k_out
+  // Interaction (Sec. 3.4): transition 1, transition 2 or dust in proportion to their
+  // opacities (one uniform); dust absorbs.
+  int ch = 0;
+  if (kD > 0.0f || m.n_lines == 2) {
+    const float u = ph.rng.u(W_CHANNEL), kt = kH + kH2 + kD;
+    ch = (u < __fdividef(kH, kt)) ? 0 : ((u < __fdividef(kH + kH2, kt)) ? 1 : 2);
+  }
+  if (ch == 2) return 2;
   const float qx = (float)ph.px + ph.ox, qy = (float)ph.py + ph.oy, qz = (float)ph.pz + ph.oz;
+  float xo;
+  if (ch == 0) {
+    xo = scatter_resonant((ph.X - site.v * site.mur) * m.inv_vth, m.a, m.phase, ph.k, ph.rng, ph.iters, nullptr,
+                          m.xcrit);
+  } else {  // second transition: J = 1/2 upper level, isotropic
+    xo = scatter_resonant((to_line2(m, ph.X) - site.v * site.mur) * m.inv_vth, m.a2, PH_ISO, ph.k, ph.rng,
+                          ph.iters, nullptr, 0.0f);
+  }
+  // back to the lab frame with the new direction: X = x v_th + v(r) r_hat . k_out
   const float mur = __fmaf_rn(qx, ph.k.x, __fmaf_rn(qy, ph.k.y, qz * ph.k.z)) / site.r;
-  ph.X = __fmaf_rn(xo, m.vth, site.v * mur);
+  const float Xl = __fmaf_rn(xo, m.vth, site.v * mur);
+  ph.X = (ch == 0) ? Xl : from_line2(m, Xl);
   ++ph.nscat;
   if (m.max_scat && ph.nscat >= m.max_scat) return 3;
   return 0;

@@ -32,6 +32,7 @@ SYMBOLS = [
     "thor_run_shell_noalloc", "thor_noalloc_last_error", "thor_reweight",
 ]
 PROFILE = {"homologous": 0, "power_law": 1}
+SPECIES = {"HI": 0, "MgII": 1}
 
 
 class ThorError(RuntimeError):
@@ -44,7 +45,7 @@ class ShellParams(C.Structure):
     _fields_ = [("R_in", C.c_double), ("R_out", C.c_double), ("N_HI", C.c_double), ("tau0", C.c_double),
                 ("T", C.c_double), ("v_max", C.c_double), ("tau_dust", C.c_double), ("albedo", C.c_double),
                 ("g_hg", C.c_double), ("phase", C.c_int32), ("core_skip", C.c_int32), ("step_dx", C.c_double),
-                ("profile", C.c_int32), ("reserved3", C.c_int32), ("alpha_rho", C.c_double), ("alpha_v", C.c_double)]
+                ("profile", C.c_int32), ("species", C.c_int32), ("alpha_rho", C.c_double), ("alpha_v", C.c_double)]
 
 
 class Source(C.Structure):
@@ -252,10 +253,12 @@ class Context:
 
     # -------------------------------------------------------------- geometries
     def shell(self, *, T, R_in=0.0, R_out=1.0, N_HI=0.0, tau0=0.0, v_max=0.0, tau_dust=0.0, albedo=0.0, g_hg=0.73,
-              phase="isotropic", step_dx=0.0, core_skip=False, profile="homologous", alpha_rho=0.0, alpha_v=1.0):
-        """thor_shell_create.  profile "power_law": the Sec. 5.1 geometry, v_max = distance-averaged speed."""
+              phase="isotropic", step_dx=0.0, core_skip=False, profile="homologous", alpha_rho=0.0, alpha_v=1.0,
+              species="HI"):
+        """thor_shell_create.  profile "power_law": the Sec. 5.1 geometry, v_max = distance-averaged
+        speed; species "MgII" (power law): the doublet, N_HI = the Mg II column."""
         p = ShellParams(R_in, R_out, N_HI, tau0, T, v_max, tau_dust, albedo, g_hg, PHASE[phase],
-                        1 if core_skip else 0, step_dx, PROFILE[profile], 0, alpha_rho, alpha_v)
+                        1 if core_skip else 0, step_dx, PROFILE[profile], SPECIES[species], alpha_rho, alpha_v)
         g = C.c_void_p()
         self._check(self.L.thor_shell_create(self.h, C.byref(p), C.byref(g)))
         return Geometry(self, g, "shell", params=p)

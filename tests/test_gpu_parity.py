@@ -478,3 +478,37 @@ def test_reweighted_dust_matches_dust_in_transport(ctx):
     var = c / n + rw[:50] / n
     m = (c + rw[:50]) > 5.0 / n
     assert np.sum((c[m] - rw[:50][m]) ** 2 / var[m]) / m.sum() < 2.0
+
+
+# ---------------------------------------------------------------- Mg II doublet (Sec. 2.4)
+def test_mgii_first_flight_escape_on_device(ctx, orc):
+    """Static uniform sphere, monochromatic source at the H line centre: the fraction of
+    photons escaping unscattered is exp(-tau), tau from both transitions (scipy Faddeeva)."""
+    from scipy.special import wofz
+    m = orc.mgii_params(1e4)
+    N, n = 1.5e12, 40000
+    g = ctx.shell(profile="power_law", species="MgII", R_in=1e-3, R_out=1.0, N_HI=N, T=1e4, v_max=0.0,
+                  alpha_rho=0.0, alpha_v=1.0, phase="dipole")
+    r = ctx.run(g, n_photons=n, seed=13, X0=m["X_H"], sigma=0.0, n_bins=20, X_min=-1000.0, X_max=200.0, raw=True)
+    xK = m["X_H"] / m["vth_kms"]
+    xH = (m["X_H"] + (2803.531 / 2796.352 - 1.0) * (299792.458 + m["X_H"])) / m["vth_kms"]
+    tau = N * (m["sigma0_K"] * wofz(xK + 1j * m["a_K"]).real + m["sigma0_H"] * wofz(xH + 1j * m["a_H"]).real)
+    p = np.exp(-tau)
+    f = float(np.mean(r.raw_nscat == 0))
+    assert abs(f - p) < 4 * np.sqrt(p * (1 - p) / n), (f, p, tau)
+
+
+def test_mgii_outflow_parity(ctx, orc):
+    """The paper's Mg II test geometry (uniform sphere, homologous outflow, N_MgII = 10^14.5,
+    T = 1e4 K) lit by a flat continuum: P Cygni profiles of both transitions, device vs oracle."""
+    n = 20000
+    kw = dict(n_bins=80, X_min=-2000.0, X_max=1000.0)
+    g = ctx.shell(profile="power_law", species="MgII", R_in=1e-3, R_out=1.0, N_HI=10 ** 14.5, T=1e4, v_max=100.0,
+                  alpha_rho=0.0, alpha_v=1.0, phase="dipole")
+    r = ctx.run(g, n_photons=n, seed=17, X0=-400.0, sigma=100.0, ew=0.0, C_cont=1400.0, **kw)
+    ro = orc.run_plshell(dv_ratio=1000.0, N_HI=10 ** 14.5, T=1e4, v_avg=100.0, alpha_rho=0.0, alpha_v=1.0,
+                         phase="dipole", sigma=100.0, ew=0.0, C_cont=1400.0, X0=-400.0, n_photons=n, seed=17,
+                         species="MgII", **kw)
+    c, dof = chi2_dof(r.spectrum, ro["counts"])
+    assert c <= 1.2, (c, dof)
+    assert mean_nscat_z(r.stats, n, ro, n) < 3.0
