@@ -470,6 +470,35 @@ def run_sweep_bench(args):
                       "clocks": clk.summary()}))
 
 
+def run_mgii_bench(args):
+    """Mg II doublet (Sec. 2.4) in the paper's test geometry: uniform sphere, homologous outflow
+    (--mgii-v km/s distance-averaged), N_MgII = 10^14.5 cm^-2, T = 1e4 K, dipole K / isotropic
+    H, lit by a flat continuum over -1800..+1000 km/s (K scale); 1e5 photons per step."""
+    import torch
+    from paper_2507_11603_gb300 import thor
+    ctx = thor.Context(0)
+    stream = torch.cuda.Stream()
+    ctx.set_stream(stream)
+    g = ctx.shell(profile="power_law", species="MgII", R_in=1e-3, R_out=1.0, N_HI=10 ** 14.5, T=1e4,
+                  v_max=args.mgii_v, alpha_rho=0.0, alpha_v=1.0, phase="dipole")
+    kw = dict(n_photons=100_000, X0=-400.0, sigma=100.0, ew=0.0, C_cont=1400.0, n_bins=300, X_min=-2000.0,
+              X_max=1000.0, device_out=True)
+    for i in range(args.warmup):
+        ctx.run(g, seed=19, first_id=10 ** 9 + i * 100_000, **kw)
+    ms, scat = [], 0
+    with ClockSampler(0) as clk:
+        for i in range(args.steps):
+            r = ctx.run(g, seed=19, first_id=i * 100_000, **kw)
+            ms.append(r.stats["elapsed_ms"])
+            scat += r.stats["n_scat"]
+    t = sum(ms) / 1000.0
+    print(json.dumps({"metric": "Mg II scatterings/s (doublet, uniform outflowing sphere)", "value": scat / t,
+                      "unit": "scatterings/s", "n_gpus": 1, "steps": args.steps, "ms_per_step": 1000 * t / args.steps,
+                      "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": f"Mg II sphere N=10^14.5 T=1e4 v_avg={args.mgii_v} km/s, 1e5 photons"},
+                      "clocks": clk.summary()}))
+
+
 def run_forest_bench(args):
     import torch
     from paper_2507_11603_gb300 import synth, thor
@@ -503,7 +532,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="shell", choices=["shell", "forest", "stream", "grid", "probe", "sweep"])
+    ap.add_argument("--workload", default="shell", choices=["shell", "forest", "stream", "grid", "probe", "sweep", "mgii"])
+    ap.add_argument("--mgii-v", type=float, default=100.0)
     ap.add_argument("--sweep-targets", type=int, default=256)
     ap.add_argument("--probe-tau0", type=float, default=1e5)
     ap.add_argument("--probe-photons", type=int, default=64)
@@ -540,6 +570,8 @@ def main():
         run_probe(args)
     elif args.workload == "sweep":
         run_sweep_bench(args)
+    elif args.workload == "mgii":
+        run_mgii_bench(args)
     else:
         run_shell_bench(args)
 

@@ -77,9 +77,13 @@ int thor_ctx_set_stream(thor_ctx_t ctx, void* cuda_stream);
 int thor_ctx_set_launch(thor_ctx_t ctx, int block_size, int blocks_per_sm);
 
 /* Tail compaction of the gridless photon loop: once no new photons are left, a warp
- * with fewer than spill_below (0..32; 0 = off, default 16) live lanes saves its packets
- * and exits, and the next launch runs the survivors in full warps, for at most
- * max_phases launches (default 24).  Results do not depend on these settings. */
+ * with fewer than spill_below (0..32; 0 = off, the default) live lanes saves its packets
+ * and exits, and the next launch repacks the survivors (a few per warp, spread over all
+ * schedulers), for at most max_phases launches (default 24).  Off by default: a run that
+ * is bound by the latency of its longest photons finishes soonest when each of them
+ * stays alone in its warp, which the single launch already gives.  Runs with fewer
+ * photons than lanes spread them over all warps either way.  Results do not depend on
+ * these settings. */
 int thor_ctx_set_tail(thor_ctx_t ctx, int spill_below, int max_phases);
 
 /* ---- geometries (Sec. 3.3 datasets) ----------------------------------------------- */

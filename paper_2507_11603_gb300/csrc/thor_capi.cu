@@ -465,9 +465,14 @@ extern "C" int thor_run(thor_ctx_t ctx, thor_geom_t g, const thor_source* src, u
     if (!d_m) return ctx->fail(THOR_ERR_OOM, "model table");
     if ((rc = ctx->cuda(cudaMemcpyAsync(d_m, &m, sizeof m, cudaMemcpyHostToDevice, s), "model upload"))) return rc;
     const int gsz = shell_grid(ctx->block, ctx->blocks_per_sm, false);
+    // fewer photons than lanes: spread them over all warps (each runs closer to alone)
+    const unsigned long long warps0 = (unsigned long long)gsz * (ctx->block / 32);
+    const unsigned long long pw0 = (n_photons + warps0 - 1) / warps0;
+    const int per_warp0 = (int)(pw0 < 1 ? 1 : (pw0 > 32 ? 32 : pw0));
     if (ctx->spill_below <= 0) {
       cudaEventRecord(ctx->ev0, s);
-      rc = ctx->cuda(launch_shell_run(d_m, q, ctx->d_ktab, gsz, ctx->block, m.profile, s), "shell photon loop");
+      rc = ctx->cuda(launch_shell_run(d_m, q, ctx->d_ktab, gsz, ctx->block, m.profile, per_warp0, s),
+                     "shell photon loop");
       ++n_launch;
       cudaEventRecord(ctx->ev1, s);
     } else {
@@ -495,7 +500,9 @@ extern "C" int thor_run(thor_ctx_t ctx, thor_geom_t g, const thor_source* src, u
         c.spill = outb;
         c.n_spill = ctr + 1;
         c.spill_below = last ? 0 : ctx->spill_below;
-        c.per_warp = 32;
+        c.per_warp = per_warp0;
+        if (per_warp0 <= 2) c.spill_below = 0;
+        else if (c.spill_below > per_warp0 / 2) c.spill_below = per_warp0 / 2;
         int g = gsz;
         if (phase > 0) {
           const unsigned long long warps_target = (unsigned long long)ctx->sm_count * 4 * kWarpsPerSmsp;

@@ -25,7 +25,7 @@ struct thor_ctx {
   // grow-only scratch buffers reused across calls
   Buf b_models, b_tally, b_queue, b_spec, b_cube, b_raw, b_raw2, b_diag, b_stats, b_spill, b_cmp;
   // tail compaction of the shell photon loop
-  int spill_below = 16;     // warps with fewer live lanes hand them to the next launch (0 = off)
+  int spill_below = 0;      // warps with fewer live lanes hand them to the next launch (0 = off)
   int max_phases = 24;      // launches at most
   int final_below = 256;    // run to completion once this few packets are left
   int phases_last = 0;

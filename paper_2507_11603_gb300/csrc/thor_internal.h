@@ -88,7 +88,7 @@ struct Compact {
   PhotonRec* spill;
   unsigned long long* n_spill;
   int32_t spill_below;  // 0: run to completion
-  int32_t per_warp;     // saved packets resumed per warp (1..32): spreads a small tail over the SMs
+  int32_t per_warp;     // lanes per warp that take packets (1..32): few packets spread over all schedulers
 };
 
 // Resident packet state for time-sliced (served) execution, SoA, one slot per thread.
@@ -143,7 +143,7 @@ struct GridModel {
 int shell_grid(int block, int blocks_per_sm, bool sliced);  // persistent grid size
 int grid_grid(int block, int blocks_per_sm);
 cudaError_t launch_shell_run(const ShellModel* d_models, WorkQueue q, const float* d_ktab, int grid,
-                             int block, int profile, cudaStream_t s);
+                             int block, int profile, int per_warp, cudaStream_t s);
 cudaError_t launch_shell_run_compact(const ShellModel* d_models, WorkQueue q, Compact c, const float* d_ktab,
                                      int grid, int block, int profile, cudaStream_t s);
 cudaError_t launch_reweight(int64_t n, const float* X0, const float* X, const float* col, const uint8_t* status,

@@ -164,7 +164,7 @@ extern "C" int thor_run_shell_noalloc(const thor_shell_params* p, const thor_sou
   q.n_entries = 1;
   if (e == cudaSuccess)
     e = launch_shell_run((const ShellModel*)(scratch + kOffModel), q, ktab, shell_grid(128, 0, false), 128,
-                         THOR_PROFILE_HOMOLOGOUS, s);
+                         THOR_PROFILE_HOMOLOGOUS, 32, s);
   Tally t;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&t, tally, sizeof t, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess && mem_kind == THOR_MEM_HOST)

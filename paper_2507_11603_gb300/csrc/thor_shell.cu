@@ -469,18 +469,18 @@ __global__ void __launch_bounds__(256, 1) shell_run_kernel(const ShellModel* __r
   const ShellModel m = sm;  // by value: the fields the event loop reads stay in registers
   const unsigned lane = threadIdx.x & 31u;
   Photon ph;
-  bool active = false, done = false;
+  bool active = false, done = (int)lane >= c.per_warp;  // lanes above per_warp stay idle
+  bool drained = false;  // warp-uniform: a refill found the photon queue exhausted
   LaneTally lt;
   for (;;) {
     unsigned need = __ballot_sync(kFull, !active && !done);
-    const unsigned takers = (kCompact && c.per_warp < 32) ? need & ((1u << c.per_warp) - 1u) : need;
-    if (kCompact && takers && c.n_resume) {  // saved packets first (lanes below per_warp)
-      const int leader = __ffs(takers) - 1;
+    if (kCompact && need && c.n_resume) {  // saved packets first
+      const int leader = __ffs(need) - 1;
       unsigned long long base = 0;
-      if ((int)lane == leader) base = atomicAdd(c.resume_next, (unsigned long long)__popc(takers));
+      if ((int)lane == leader) base = atomicAdd(c.resume_next, (unsigned long long)__popc(need));
       base = __shfl_sync(kFull, base, leader);
-      if ((takers >> lane) & 1u) {
-        const unsigned long long g = base + __popc(takers & ((1u << lane) - 1u));
+      if (!active && !done) {
+        const unsigned long long g = base + __popc(need & ((1u << lane) - 1u));
         if (g < c.n_resume) { load_rec(m, c.resume[g], ph); active = true; }
       }
       need = __ballot_sync(kFull, !active && !done);
@@ -490,6 +490,7 @@ __global__ void __launch_bounds__(256, 1) shell_run_kernel(const ShellModel* __r
       unsigned long long base = 0;
       if ((int)lane == leader) base = atomicAdd(q.next, (unsigned long long)__popc(need));
       base = __shfl_sync(kFull, base, leader);
+      if (base + __popc(need) > q.total) drained = true;
       if (!active && !done) {
         const unsigned long long g = base + __popc(need & ((1u << lane) - 1u));
         if (g < q.total) {
@@ -504,7 +505,7 @@ __global__ void __launch_bounds__(256, 1) shell_run_kernel(const ShellModel* __r
     }
     if (kCompact && c.spill_below > 0) {
       const unsigned live = __ballot_sync(kFull, active);
-      if (__any_sync(kFull, done) && __popc(live) < c.spill_below) {
+      if (drained && __popc(live) < c.spill_below) {
         if (live) {
           const int leader = __ffs(live) - 1;
           unsigned long long base = 0;
@@ -654,8 +655,9 @@ int shell_grid(int block, int blocks_per_sm, bool sliced) {
 }
 
 cudaError_t launch_shell_run(const ShellModel* d_models, WorkQueue q, const float* d_ktab, int grid, int block,
-                             int profile, cudaStream_t s) {
+                             int profile, int per_warp, cudaStream_t s) {
   Compact none{};
+  none.per_warp = per_warp;
   if (profile) shell_run_kernel<false, 1><<<grid, block, 0, s>>>(d_models, q, none, d_ktab);
   else shell_run_kernel<false, 0><<<grid, block, 0, s>>>(d_models, q, none, d_ktab);
   return cudaGetLastError();
