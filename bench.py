@@ -341,7 +341,11 @@ def stream_bench(ctx, n_requests=256, seed=2, load=0.75, events_per_round=256, n
         finish = start + solo_ms[i] / 1000.0
         fifo_lat.append((finish - arrivals[i]) * 1000.0)
     fifo_lat = np.array(fifo_lat)
-    return {"requests": n_requests, "photons": int(sum(r["n_photons"] for r in reqs)),
+    j = int(np.argmax(lat))  # the request that sets the batched tail
+    slowest = {"request": j, "N_HI": reqs[j]["N_HI"], "T": reqs[j]["T"], "v_max": reqs[j]["v_max"],
+               "photons": reqs[j]["n_photons"], "batched_ms": float(lat[j]), "one_launch_run_ms": solo_ms[j],
+               "one_launch_fifo_ms": float(fifo_lat[j])}
+    return {"requests": n_requests, "slowest": slowest, "photons": int(sum(r["n_photons"] for r in reqs)),
             "core_skip": core_skip, "N_HI_max": nhi_max, "load": load, "rate_per_s": rate,
             "batched": {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                         "scatterings_per_s": scat / span, "burst_scatterings_per_s": burst_scat / burst_total,
@@ -551,7 +555,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
-    ap.add_argument("--inst-per-scat", type=float, default=352.0,
+    ap.add_argument("--inst-per-scat", type=float, default=356.0,
                     help="warp instructions per scattering of the shell photon loop (ncu, bench workload)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=10.0)

@@ -237,8 +237,9 @@ __device__ __forceinline__ void peel_from_cell(const GridModel& m, const GPhoton
   float tau = __fmaf_rn(g.kap0, voigt<false>(g.a, x, Ktab), g.kd) * fmaxf(d, 0.0f);
   ++pr;
   ++pc;
-  double p[3] = {ph.p[0] + (double)ph.o[0], ph.p[1] + (double)ph.o[1], ph.p[2] + (double)ph.o[2]};
-  if (tau <= m.tau_cut) tau = peel_tau_from(m, p, ax, Xp, Ktab, pc, 1, tau);
+  if (tau > m.tau_cut) return;  // blocked inside the current cell: no FP64, no gather
+  const double p[3] = {ph.p[0] + (double)ph.o[0], ph.p[1] + (double)ph.o[1], ph.p[2] + (double)ph.o[2]};
+  tau = peel_tau_from(m, p, ax, Xp, Ktab, pc, 1, tau);
   if (tau <= m.tau_cut) deposit(m, p, ax, Xp, w0 * __expf(-tau));
 }
 

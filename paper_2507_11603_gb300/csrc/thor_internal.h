@@ -98,10 +98,11 @@ struct SlotState {
   float *kx, *ky, *kz, *X, *x;
   uint32_t* event;                   // RNG position: events done
   uint32_t *nscat, *ndust, *iters, *steps;
-  int32_t* model;                    // -1 = empty
+  int32_t* model;
   unsigned long long* pid;
   uint8_t* region;
-  int64_t n_slots;
+  int64_t n_slots;                   // capacity (packets)
+  unsigned long long* live;          // [0] packets stored in this buffer, [1] append counter of the next
 };
 
 // Grid model (Sec. 3.3 uniform Cartesian grid), packed 32 B per cell.
@@ -149,8 +150,9 @@ cudaError_t launch_shell_run_compact(const ShellModel* d_models, WorkQueue q, Co
 cudaError_t launch_reweight(int64_t n, const float* X0, const float* X, const float* col, const uint8_t* status,
                             const float* d_params, int n_targets, int n_bins, double X_min, double X_max,
                             double* d_out, int n_sm, cudaStream_t s);
-cudaError_t launch_shell_slice(const ShellModel* d_models, WorkQueue q, SlotState st, uint32_t event_budget,
-                               const float* d_ktab, int grid, int block, cudaStream_t s);
+cudaError_t launch_shell_slice(const ShellModel* d_models, WorkQueue q, SlotState in, SlotState out,
+                               uint32_t event_budget,
+                               const float* d_ktab, int grid, int block, bool mixed, cudaStream_t s);
 cudaError_t launch_grid_pack(const float* nHI, const float* T, const float* vx, const float* vy,
                              const float* vz, const float* dust, int64_t n, double cell_cm, GridCell* out,
                              double* w, cudaStream_t s);

@@ -62,15 +62,17 @@ struct thor_server {
   Tally* d_tally = nullptr;
   unsigned long long* d_spec = nullptr;  // max_requests x (max_bins + 2)
   char* d_queue = nullptr;               // counter, total, n_entries, prefix, first_id, model
-  void* d_slots = nullptr;
-  SlotState st{};
+  void* d_slots = nullptr;               // two packet lists (in, out) of n_slots entries + counters
+  size_t slot_bytes = 0;
+  SlotState st_in{}, st_out{};
   cudaStream_t stream = nullptr;
   // one round as a graph: h_queue (pinned, layout of d_queue) -> d_queue, slice kernel,
   // d_queue counter and the tallies -> h_out (pinned)
   char* h_queue = nullptr;
   char* h_out = nullptr;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t gexec = nullptr;
+  // [0]: homologous shells only; [1]: power-law models among them (event chosen per lane)
+  cudaGraph_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
   // host state
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -83,6 +85,7 @@ struct thor_server {
   bool device_error = false;
   std::string error;
   uint64_t rounds = 0, admitted = 0;
+  uint64_t last_resident = 0;  // packets in flight after the last round
   double resident_sum = 0.0;
   std::thread worker;
 
@@ -91,10 +94,10 @@ struct thor_server {
 
 namespace {
 
-// d_queue / h_queue layout: next counter, total, n_entries, event budget (u64 each),
-// prefix[R + 1], first_id[R] (u64), model[R] (i32)
+// d_queue / h_queue layout: next counter, total, n_entries, event budget, lanes per warp
+// that take new packets (u64 each), prefix[R + 1], first_id[R] (u64), model[R] (i32)
 struct QLayout {
-  size_t next = 0, total = 8, n_entries = 16, budget = 24, prefix = 32, first, model, bytes;
+  size_t next = 0, total = 8, n_entries = 16, budget = 24, per_warp = 32, prefix = 40, first, model, bytes;
   explicit QLayout(int R) {
     first = prefix + (size_t)(R + 1) * 8;
     model = first + (size_t)R * 8;
@@ -120,7 +123,7 @@ void thor_server::run() {
   for (;;) {
     std::vector<Request*> fresh;
     int n_entries = 0;
-    uint64_t budget = 0;
+    uint64_t budget = 0, per_warp = 32;
     unsigned long long total = 0;
     {
       std::unique_lock<std::mutex> lk(mu);
@@ -146,9 +149,15 @@ void thor_server::run() {
         if (any) break;
         cv_work.wait(lk);
       }
-      for (int i = 0; i < R; ++i) {
+      // queue entries oldest request first: free lanes go to the photons that waited longest
+      std::vector<std::pair<int64_t, int>> order;
+      for (int i = 0; i < R; ++i)
+        if (active[i] && !active[i]->cancel && active[i]->issued < active[i]->n_photons)
+          order.emplace_back(active[i]->ticket, i);
+      std::sort(order.begin(), order.end());
+      for (const auto& oi : order) {
+        const int i = oi.second;
         Request* r = active[i];
-        if (!r || r->cancel || r->issued >= r->n_photons) continue;
         h_prefix[n_entries] = total;
         h_first[n_entries] = r->issued;
         h_model[n_entries] = i;
@@ -160,6 +169,12 @@ void thor_server::run() {
       // rounds run kIdleRounds x longer while nobody waits for admission: fewer launches
       // and host round trips for the tails of admitted requests
       budget = pending.empty() ? (uint64_t)cfg.events_per_round * kIdleRounds : (uint64_t)cfg.events_per_round;
+      // few packets in flight: new ones spread over the warps (each runs closer to alone,
+      // not behind the divergent packets of other requests); many: full warps
+      const uint64_t n_warps = (uint64_t)(n_slots / 32);
+      const uint64_t load = last_resident + total;
+      uint64_t pw = n_warps ? (load + n_warps - 1) / n_warps : 32;
+      per_warp = pw < 1 ? 1 : (pw > 32 ? 32 : pw);
     }
     cudaStream_t s = stream;
     bool ok = true;
@@ -188,7 +203,13 @@ void thor_server::run() {
     ((unsigned long long*)(h_queue + L.total))[0] = total;
     ((unsigned long long*)(h_queue + L.n_entries))[0] = (unsigned long long)n_entries;
     ((unsigned long long*)(h_queue + L.budget))[0] = (unsigned long long)budget;
-    ok &= cudaGraphLaunch(gexec, s) == cudaSuccess;
+    ((unsigned long long*)(h_queue + L.per_warp))[0] = (unsigned long long)per_warp;
+    bool mixed = false;
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      for (int i = 0; i < R; ++i) if (active[i] && active[i]->model.profile != 0) mixed = true;
+    }
+    ok &= cudaGraphLaunch(gexec[mixed ? 1 : 0], s) == cudaSuccess;
     ok &= cudaStreamSynchronize(s) == cudaSuccess;
     const unsigned long long h_next = ((const unsigned long long*)h_out)[0];
     std::memcpy(h_tally.data(), h_out + 8, sizeof(Tally) * R);
@@ -225,6 +246,7 @@ void thor_server::run() {
         if (all_done || cancelled_drained) finished.push_back(r);
       }
       resident_sum += (double)resident;
+      last_resident = resident;
     }
     for (Request* r : finished) {
       const size_t nb = (size_t)r->n_bins + 2;
@@ -269,35 +291,43 @@ extern "C" int thor_server_create(thor_ctx_t ctx, const thor_server_config* cfg,
   const size_t spec_bytes = (size_t)R * (s->max_bins + 2) * 8;
   const int64_t n = s->n_slots;
   const size_t slot_bytes = (size_t)n * (3 * 8 + 4 * 4 + 5 * 4 + 4 + 4 * 4 + 4 + 8 + 1) + 24 * 256;
+  s->slot_bytes = slot_bytes;
   bool ok = cudaMallocHost(&s->h_queue, queue_bytes(R)) == cudaSuccess &&
             cudaMallocHost(&s->h_out, 8 + sizeof(Tally) * R) == cudaSuccess &&
             cudaMalloc(&s->d_models, sizeof(ShellModel) * R) == cudaSuccess &&
             cudaMalloc(&s->d_tally, sizeof(Tally) * R) == cudaSuccess &&
             cudaMalloc(&s->d_spec, spec_bytes) == cudaSuccess &&
             cudaMalloc(&s->d_queue, queue_bytes(R)) == cudaSuccess &&
-            cudaMalloc(&s->d_slots, slot_bytes) == cudaSuccess &&
+            cudaMalloc(&s->d_slots, 2 * slot_bytes + 256) == cudaSuccess &&
             cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) == cudaSuccess;
   if (!ok) {
     thor_server_destroy(s);
     return ctx->fail(THOR_ERR_OOM, "thor_server_create: device allocation failed");
   }
-  // carve the slot SoA (256-byte aligned arrays)
-  char* p = (char*)s->d_slots;
-  auto take = [&](size_t bytes) { char* q = p; p += (bytes + 255) & ~(size_t)255; return (void*)q; };
-  SlotState& st = s->st;
-  st.px = (double*)take(n * 8); st.py = (double*)take(n * 8); st.pz = (double*)take(n * 8);
-  st.ox = (float*)take(n * 4); st.oy = (float*)take(n * 4); st.oz = (float*)take(n * 4);
-  st.safe = (float*)take(n * 4);
-  st.kx = (float*)take(n * 4); st.ky = (float*)take(n * 4); st.kz = (float*)take(n * 4); st.X = (float*)take(n * 4);
-  st.x = (float*)take(n * 4);
-  st.event = (uint32_t*)take(n * 4);
-  st.nscat = (uint32_t*)take(n * 4); st.ndust = (uint32_t*)take(n * 4); st.iters = (uint32_t*)take(n * 4);
-  st.steps = (uint32_t*)take(n * 4);
-  st.model = (int32_t*)take(n * 4);
-  st.pid = (unsigned long long*)take(n * 8);
-  st.region = (uint8_t*)take(n);
-  st.n_slots = n;
-  cudaMemsetAsync(st.model, 0xff, n * 4, s->stream);  // all slots empty (-1)
+  // carve the two packet lists (256-byte aligned SoA arrays, identical layouts) and the
+  // counters {packets in the in list, append counter of the out list}
+  auto carve = [&](char* p, SlotState& st) {
+    auto take = [&](size_t bytes) { char* q = p; p += (bytes + 255) & ~(size_t)255; return (void*)q; };
+    st.px = (double*)take(n * 8); st.py = (double*)take(n * 8); st.pz = (double*)take(n * 8);
+    st.ox = (float*)take(n * 4); st.oy = (float*)take(n * 4); st.oz = (float*)take(n * 4);
+    st.safe = (float*)take(n * 4);
+    st.kx = (float*)take(n * 4); st.ky = (float*)take(n * 4); st.kz = (float*)take(n * 4); st.X = (float*)take(n * 4);
+    st.x = (float*)take(n * 4);
+    st.event = (uint32_t*)take(n * 4);
+    st.nscat = (uint32_t*)take(n * 4); st.ndust = (uint32_t*)take(n * 4); st.iters = (uint32_t*)take(n * 4);
+    st.steps = (uint32_t*)take(n * 4);
+    st.model = (int32_t*)take(n * 4);
+    st.pid = (unsigned long long*)take(n * 8);
+    st.region = (uint8_t*)take(n);
+    st.n_slots = n;
+  };
+  char* base = (char*)s->d_slots;
+  carve(base, s->st_in);
+  carve(base + slot_bytes, s->st_out);
+  unsigned long long* live = (unsigned long long*)(base + 2 * slot_bytes);
+  s->st_in.live = live;
+  s->st_out.live = live;
+  cudaMemsetAsync(live, 0, 16, s->stream);  // no packets in flight
   cudaStreamSynchronize(s->stream);
   // capture one round (thread-local capture mode: other host threads are unaffected)
   {
@@ -311,14 +341,21 @@ extern "C" int thor_server_create(thor_ctx_t ctx, const thor_server_config* cfg,
     wq.n_entries = 0;
     wq.hdr = (const unsigned long long*)(s->d_queue + L.total);
     cudaStream_t cs = s->stream;
-    bool cap = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-    if (cap) {
+    bool cap = true;
+    for (int v = 0; v < 2 && cap; ++v) {
+      cap = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      if (!cap) break;
       cudaMemcpyAsync(s->d_queue, s->h_queue, L.bytes, cudaMemcpyHostToDevice, cs);
-      launch_shell_slice(s->d_models, wq, st, (uint32_t)s->cfg.events_per_round, ctx->d_ktab, s->grid, s->block, cs);
+      launch_shell_slice(s->d_models, wq, s->st_in, s->st_out, (uint32_t)s->cfg.events_per_round, ctx->d_ktab,
+                         s->grid, s->block, v == 1, cs);
+      // the survivors become the next round's list
+      cudaMemcpyAsync(s->d_slots, (char*)s->d_slots + s->slot_bytes, s->slot_bytes, cudaMemcpyDeviceToDevice, cs);
+      cudaMemcpyAsync(&s->st_in.live[0], &s->st_in.live[1], 8, cudaMemcpyDeviceToDevice, cs);
+      cudaMemsetAsync(&s->st_in.live[1], 0, 8, cs);
       cudaMemcpyAsync(s->h_out, s->d_queue + L.next, 8, cudaMemcpyDeviceToHost, cs);
       cudaMemcpyAsync(s->h_out + 8, s->d_tally, sizeof(Tally) * R, cudaMemcpyDeviceToHost, cs);
-      cap = cudaStreamEndCapture(cs, &s->graph) == cudaSuccess &&
-            cudaGraphInstantiate(&s->gexec, s->graph, 0) == cudaSuccess;
+      cap = cudaStreamEndCapture(cs, &s->graph[v]) == cudaSuccess &&
+            cudaGraphInstantiate(&s->gexec[v], s->graph[v], 0) == cudaSuccess;
     }
     if (!cap) {
       cudaGetLastError();
@@ -427,8 +464,10 @@ extern "C" void thor_server_destroy(thor_server_t s) {
   if (s->worker.joinable()) s->worker.join();
   cudaSetDevice(s->ctx->device);
   if (s->stream) cudaStreamSynchronize(s->stream);
-  if (s->gexec) cudaGraphExecDestroy(s->gexec);
-  if (s->graph) cudaGraphDestroy(s->graph);
+  for (int v = 0; v < 2; ++v) {
+    if (s->gexec[v]) cudaGraphExecDestroy(s->gexec[v]);
+    if (s->graph[v]) cudaGraphDestroy(s->graph[v]);
+  }
   for (void* p : {(void*)s->d_models, (void*)s->d_tally, (void*)s->d_spec, (void*)s->d_queue, s->d_slots})
     if (p) cudaFree(p);
   if (s->h_queue) cudaFreeHost(s->h_queue);

@@ -551,21 +551,34 @@ __global__ void __launch_bounds__(256, 1) shell_run_kernel(const ShellModel* __r
   }
 }
 
-// Time-sliced execution over resident slots (one per thread): resume the packet in the
-// slot, run at most `budget` events per lane, refill finished lanes from the queue of
-// admitted requests, and save what is still in flight.
+// Time-sliced execution (serving): packets in flight live in a list (`in`, in.live[0]
+// entries); lane l of warp w resumes entry w + l * n_warps, so the packets spread over all
+// warps every launch.  Each lane runs at most `budget` events, finished lanes take new
+// photons from the queue of admitted requests while the warp has fewer than per_warp live
+// packets, and what is still in flight is appended to `out` (out.live[1]).
+// kMixed: the round holds power-law models too (the event function is chosen per lane);
+// otherwise only homologous shells, compiled without the power-law event.
+template <bool kMixed>
 __global__ void __launch_bounds__(256, 1) shell_slice_kernel(const ShellModel* __restrict__ models, WorkQueue q,
-                                                          SlotState st, uint32_t budget,
+                                                          SlotState in, SlotState out, uint32_t budget,
                                                           const float* __restrict__ gK) {
   __shared__ __align__(16) float sK[THOR_VOIGT_NINT * THOR_VOIGT_NCOEF];
   load_ktab(sK, gK);
-  if (q.hdr) { q.total = q.hdr[0]; q.n_entries = (int32_t)q.hdr[1]; budget = (uint32_t)q.hdr[2]; }
-  const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool has_slot = slot < st.n_slots;
+  int per_warp = 32;  // at most this many live packets per warp after a refill
+  if (q.hdr) {
+    q.total = q.hdr[0]; q.n_entries = (int32_t)q.hdr[1]; budget = (uint32_t)q.hdr[2];
+    per_warp = (int)q.hdr[3];
+  }
   const unsigned lane = threadIdx.x & 31u;
+  const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned long long n_in = in.live[0];
+  const int pw_in = (int)((n_in + n_warps - 1) / n_warps);  // every stored packet is resumed
+  const int64_t slot = warp + (int64_t)lane * n_warps;
   Photon ph;
   bool active = false, done = false;
-  if (has_slot && st.model[slot] >= 0) {
+  const SlotState& st = in;
+  if ((int)lane < pw_in && (unsigned long long)slot < n_in) {
     ph.model = st.model[slot];
     const ShellModel& m = models[ph.model];
     ph.pid = st.pid[slot];
@@ -582,16 +595,18 @@ __global__ void __launch_bounds__(256, 1) shell_slice_kernel(const ShellModel* _
     ph.nscat = st.nscat[slot]; ph.ndust = st.ndust[slot]; ph.iters = st.iters[slot]; ph.steps = st.steps[slot];
     active = true;
   }
-  if (!has_slot) done = true;
   uint32_t ev = 0;  // event iterations of this launch (warp-uniform)
   while (ev < budget) {
-    const unsigned need = __ballot_sync(kFull, !active && !done);
+    const unsigned idle = __ballot_sync(kFull, !active && !done);
+    const int room = per_warp - __popc(__ballot_sync(kFull, active));
+    const bool take = ((idle >> lane) & 1u) && (int)__popc(idle & ((1u << lane) - 1u)) < room;
+    const unsigned need = __ballot_sync(kFull, take);
     if (need) {
       const int leader = __ffs(need) - 1;
       unsigned long long base = 0;
       if ((int)lane == leader) base = atomicAdd(q.next, (unsigned long long)__popc(need));
       base = __shfl_sync(kFull, base, leader);
-      if (!active && !done) {
+      if (take) {
         const unsigned long long g = base + __popc(need & ((1u << lane) - 1u));
         if (g < q.total) {
           const int e = find_entry(q, g);
@@ -621,23 +636,30 @@ __global__ void __launch_bounds__(256, 1) shell_slice_kernel(const ShellModel* _
     do {
       fin = false;
       if (active) {
-        const int r = mr.profile ? shell_event_pl(mr, ph, sK) : shell_event(mr, ph, sK);
+        const int r = (kMixed && mr.profile) ? shell_event_pl(mr, ph, sK) : shell_event(mr, ph, sK);
         if (r) { finish_global(mr, ph, r); active = false; fin = true; }
       }
       ++ev;
     } while (ev < budget && !__any_sync(kFull, fin));
   }
-  if (!has_slot) return;
-  if (active) {
-    st.model[slot] = ph.model; st.pid[slot] = ph.pid;
-    st.event[slot] = ph.rng.event;
-    st.px[slot] = ph.px; st.py[slot] = ph.py; st.pz[slot] = ph.pz;
-    st.ox[slot] = ph.ox; st.oy[slot] = ph.oy; st.oz[slot] = ph.oz; st.safe[slot] = ph.safe;
-    st.kx[slot] = ph.k.x; st.ky[slot] = ph.k.y; st.kz[slot] = ph.k.z;
-    st.X[slot] = ph.X; st.x[slot] = ph.x; st.region[slot] = (uint8_t)ph.region;
-    st.nscat[slot] = ph.nscat; st.ndust[slot] = ph.ndust; st.iters[slot] = ph.iters; st.steps[slot] = ph.steps;
-  } else {
-    st.model[slot] = -1;
+  // append the packets still in flight to the next list (one atomic per warp)
+  const unsigned live = __ballot_sync(kFull, active);
+  if (live) {
+    const int leader = __ffs(live) - 1;
+    unsigned long long base = 0;
+    if ((int)lane == leader) base = atomicAdd(&out.live[1], (unsigned long long)__popc(live));
+    base = __shfl_sync(kFull, base, leader);
+    if (active) {
+      const unsigned long long j = base + __popc(live & ((1u << lane) - 1u));
+      SlotState& o = out;
+      o.model[j] = ph.model; o.pid[j] = ph.pid;
+      o.event[j] = ph.rng.event;
+      o.px[j] = ph.px; o.py[j] = ph.py; o.pz[j] = ph.pz;
+      o.ox[j] = ph.ox; o.oy[j] = ph.oy; o.oz[j] = ph.oz; o.safe[j] = ph.safe;
+      o.kx[j] = ph.k.x; o.ky[j] = ph.k.y; o.kz[j] = ph.k.z;
+      o.X[j] = ph.X; o.x[j] = ph.x; o.region[j] = (uint8_t)ph.region;
+      o.nscat[j] = ph.nscat; o.ndust[j] = ph.ndust; o.iters[j] = ph.iters; o.steps[j] = ph.steps;
+    }
   }
 }
 
@@ -647,7 +669,7 @@ int shell_grid(int block, int blocks_per_sm, bool sliced) {
   int dev = 0, sms = 0, occ = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (sliced) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, shell_slice_kernel, block, 0);
+  if (sliced) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, shell_slice_kernel<true>, block, 0);
   else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, shell_run_kernel<true, 0>, block, 0);
   if (occ < 1) occ = 1;
   const int b = (blocks_per_sm > 0 && blocks_per_sm < occ) ? blocks_per_sm : occ;
@@ -670,9 +692,10 @@ cudaError_t launch_shell_run_compact(const ShellModel* d_models, WorkQueue q, Co
   return cudaGetLastError();
 }
 
-cudaError_t launch_shell_slice(const ShellModel* d_models, WorkQueue q, SlotState st, uint32_t budget,
-                               const float* d_ktab, int grid, int block, cudaStream_t s) {
-  shell_slice_kernel<<<grid, block, 0, s>>>(d_models, q, st, budget, d_ktab);
+cudaError_t launch_shell_slice(const ShellModel* d_models, WorkQueue q, SlotState in, SlotState out, uint32_t budget,
+                               const float* d_ktab, int grid, int block, bool mixed, cudaStream_t s) {
+  if (mixed) shell_slice_kernel<true><<<grid, block, 0, s>>>(d_models, q, in, out, budget, d_ktab);
+  else shell_slice_kernel<false><<<grid, block, 0, s>>>(d_models, q, in, out, budget, d_ktab);
   return cudaGetLastError();
 }
 

@@ -512,3 +512,42 @@ def test_mgii_outflow_parity(ctx, orc):
     c, dof = chi2_dof(r.spectrum, ro["counts"])
     assert c <= 1.2, (c, dof)
     assert mean_nscat_z(r.stats, n, ro, n) < 3.0
+
+
+def test_autotuner_picks_a_measured_shape(ctx, tmp_path, monkeypatch):
+    """The launch-shape autotuner times its candidates through the C ABI, keeps the fastest,
+    applies it, and caches the choice (results do not depend on the shape)."""
+    from paper_2507_11603_gb300 import autotune
+    monkeypatch.setattr(autotune, "CACHE", str(tmp_path / "autotune.json"))
+    g = ctx.shell(tau0=1e4, T=1e4, phase="dipole")
+    kw = dict(n_bins=40, X_min=-300.0, X_max=300.0)
+    best = autotune.tune_run(ctx, g, "sphere-1e4", n_photons=2000, candidates=[(128, 0), (64, 0)], **kw)
+    assert len(best["table"]) == 2 and best["ms"] == min(t["ms"] for t in best["table"])
+    again = autotune.tune_run(ctx, g, "sphere-1e4", n_photons=2000, candidates=[(128, 0), (64, 0)], **kw)
+    assert again["block"] == best["block"]  # served from the cache
+    a = ctx.run(g, n_photons=3000, seed=7, **kw)
+    ctx.set_launch(128, 0)
+    b = ctx.run(g, n_photons=3000, seed=7, **kw)
+    assert np.array_equal(a.spectrum, b.spectrum) and a.stats["n_scat"] == b.stats["n_scat"]
+    srv = autotune.tune_server(ctx, [dict(N_HI=1e18, T=1e4, v_max=100.0, n_photons=2000, seed=s) for s in (1, 2)],
+                               "two-requests", candidates=(64, 256), R_in=0.9, phase="dipole", sigma=50.0)
+    assert srv["events_per_round"] in (64, 256)
+
+
+def test_server_mixes_power_law_and_homologous_requests(ctx):
+    """A power-law (Sec. 5.1) request served next to homologous shells: each result equals
+    its one-launch run (the server switches to the mixed-profile round kernel)."""
+    common = dict(phase="dipole", sigma=50.0, n_bins=64, X_min=-1500.0, X_max=1500.0)
+    reqs = [dict(R_in=0.9, N_HI=3e18, T=1e4, v_max=150.0, tau_dust=0.3, n_photons=4000, seed=51),
+            dict(R_in=0.2, N_HI=10 ** 17.6, T=1e4, v_max=120.0, profile="power_law", alpha_rho=-1.0, alpha_v=0.5,
+                 n_photons=4000, seed=52)]
+    srv = ctx.server(max_requests=4, events_per_round=64)
+    tickets = [srv.submit(**r, **common) for r in reqs]
+    got = [srv.wait(t, timeout_ms=120000) for t in tickets]
+    srv.close()
+    for g_, r in zip(got, reqs):
+        kw = {k: v for k, v in r.items() if k not in ("n_photons", "seed")}
+        geo = ctx.shell(phase="dipole", **kw)
+        one = ctx.run(geo, n_photons=r["n_photons"], seed=r["seed"], sigma=50.0, n_bins=64, X_min=-1500.0,
+                      X_max=1500.0)
+        assert np.array_equal(one.spectrum, g_.spectrum) and one.stats["n_scat"] == g_.stats["n_scat"]
