@@ -78,9 +78,11 @@ struct PhotonRec {
   unsigned long long pid;
 };
 
-// Tail compaction: a launch first resumes saved packets, then takes fresh photons; once
-// both sources are empty, a warp with fewer than `spill_below` live lanes saves them to
-// `spill` and exits, so the next launch runs the survivors in full warps.
+// Tail compaction (optional, off by default): a launch first resumes saved packets, then
+// takes fresh photons; once the queue is drained, a warp with fewer than `spill_below` live
+// lanes saves them to `spill` and exits, and the next launch repacks the survivors
+// `per_warp` to a warp.  Also carries per_warp for the first launch (few photons spread
+// over all warps).
 struct Compact {
   const PhotonRec* resume;
   unsigned long long n_resume;

@@ -6,8 +6,9 @@
 // propagate to the interaction or the boundary, interact) for every live lane;
 // lanes whose packet finished are refilled from the photon work queue with one
 // warp-aggregated atomic (ballot of the idle lanes), so a warp stays full until the
-// queue drains.  The packet state lives in registers; the time-sliced variant
-// additionally loads/stores it from a slot array between launches (serving).
+// queue drains (runs with fewer photons than lanes fill per_warp lanes of every warp).
+// The packet state lives in registers; the time-sliced variant (serving) resumes its
+// packets from a list spread over all warps and appends the survivors to the next one.
 #include "thor_device.cuh"
 #include "thor_internal.h"
 

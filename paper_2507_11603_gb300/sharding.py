@@ -36,3 +36,18 @@ def merge_counts(counts, group=None):
     if dist.is_initialized() and dist.get_world_size(group) > 1:
         dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
     return t
+
+
+def merge_weights(hist, n_local: int, group=None):
+    """Reweighted spectra (Sec. 5.1 post-processing) over ranks: each rank's histogram is a
+    sum of weights divided by its own photon count n_local; the merged result is the sum of
+    the weights over all ranks divided by the total count (FP64 all-reduce)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.as_tensor(hist, dtype=torch.float64) * float(n_local)
+    n = torch.tensor([float(n_local)], dtype=torch.float64)
+    if dist.is_initialized() and dist.get_world_size(group) > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+        dist.all_reduce(n, op=dist.ReduceOp.SUM, group=group)
+    return t / n
+

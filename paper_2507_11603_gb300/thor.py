@@ -247,8 +247,9 @@ class Context:
     def set_launch(self, block_size: int, blocks_per_sm: int = 0):
         self._check(self.L.thor_ctx_set_launch(self.h, block_size, blocks_per_sm))
 
-    def set_tail(self, spill_below: int = 16, max_phases: int = 24):
-        """Tail compaction of the shell photon loop (0 = off); results do not depend on it."""
+    def set_tail(self, spill_below: int = 0, max_phases: int = 24):
+        """thor_ctx_set_tail: tail compaction of the shell photon loop (0 = off, the library's
+        default); results do not depend on it."""
         self._check(self.L.thor_ctx_set_tail(self.h, spill_below, max_phases))
 
     # -------------------------------------------------------------- geometries

@@ -69,3 +69,46 @@ def test_ranges_partition_ids():
         assert f0 == 5 + (world - 1) * 10 and n0 == 10
     with pytest.raises(ValueError):
         sharding.photon_range(2, 2, 10)
+
+
+PL = dict(dv_ratio=5.0, N_HI=10 ** 17.4, T=1e4, v_avg=120.0, alpha_rho=-1.0, alpha_v=0.5, sigma=800.0, ew=740.0,
+          C_cont=2500.0, seed=23, n_bins=30, X_min=-2500.0, X_max=2500.0, n_threads=2)
+SAMPLE, TARGET = (800.0, 740.0, 2500.0), (300.0, 24661.0, 2500.0)
+
+
+def _sweep_worker(rank, world, port, n_per_rank, q):
+    import torch.distributed as dist
+    import oracle
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    first, n = sharding.photon_range(rank, world, n_per_rank)
+    r = oracle.run_plshell(n_photons=n, first_id=first, **PL)
+    h = oracle.reweight(r["X0"], r["X"], r["col"], r["status"], sample=SAMPLE, target=TARGET, tau_d=0.4,
+                        n_bins=30, X_min=-2500.0, X_max=2500.0)
+    merged = sharding.merge_weights(h, n)
+    if rank == 0:
+        q.put(merged.numpy())
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_sweep_reweighting_over_two_gloo_ranks(orc):
+    """Sharded shell-model sweep: ranks run their photon ids of a power-law shell, reweight
+    their own escaped photons and merge the weighted spectra; the result equals a
+    single-rank run reweighted at once (up to the order of the FP64 sums)."""
+    world, n_per_rank = 2, 300
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_sweep_worker, args=(r, world, port, n_per_rank, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    merged = q.get(timeout=300)
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    r = orc.run_plshell(n_photons=world * n_per_rank, first_id=0, **PL)
+    single = orc.reweight(r["X0"], r["X"], r["col"], r["status"], sample=SAMPLE, target=TARGET, tau_d=0.4,
+                          n_bins=30, X_min=-2500.0, X_max=2500.0)
+    assert np.allclose(merged, single, rtol=1e-12, atol=1e-15)
