@@ -172,7 +172,7 @@ typedef struct {
   int32_t reserved;
   double peel_X_min, peel_X_max;
   float* cube;
-  /* optional per-photon records, indexed by photon id - first id (may be NULL) */
+  /* optional per-photon records (shells and grids), indexed by photon id - first id (may be NULL) */
   float* raw_X;          /* final lab X [km/s] */
   uint32_t* raw_nscat;   /* resonant scatterings */
   uint8_t* raw_status;   /* 1 escaped, 2 absorbed, 3 stopped at max_scat */

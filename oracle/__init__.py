@@ -126,7 +126,8 @@ def lib():
             L.orc_run_grid.restype = C.c_int
             L.orc_run_grid.argtypes = [P(C.c_float)] * 6 + [P(GridRun), C.c_uint64, C.c_uint64,
                                                              C.c_uint64, C.c_int32, P(C.c_uint64),
-                                                             P(C.c_double), P(Result)]
+                                                             P(C.c_double), P(Result), P(C.c_double),
+                                                             P(C.c_uint64), P(C.c_uint8)]
             L.orc_forest.restype = C.c_int
             L.orc_forest.argtypes = [P(C.c_float)] * 3 + [C.c_int32] * 3 + [P(C.c_int32), P(C.c_int32),
                                                                             C.c_int32, C.c_double,
@@ -318,7 +319,7 @@ def dda_trace(dims, origins, dirs, max_steps):
 
 def run_grid(fields: dict, *, cell_cm, n_photons, seed, first_id=0, phase="dipole", albedo=0.32,
              g_hg=0.73, n_bins=256, img_nx=None, X_min=-1000.0, X_max=1000.0, peel=True,
-             max_scat=0, n_threads=0):
+             max_scat=0, n_threads=0, raw=False):
     nHI = np.ascontiguousarray(fields["n_HI"], dtype=np.float32)
     nz, ny, nx = nHI.shape
     arrs = [nHI] + [np.ascontiguousarray(fields[k], dtype=np.float32)
@@ -329,13 +330,20 @@ def run_grid(fields: dict, *, cell_cm, n_photons, seed, first_id=0, phase="dipol
     spec = np.zeros(n_bins + 2, dtype=np.uint64)
     cube = np.zeros((3, img, img, n_bins)) if peel else None
     res = Result()
+    rX = np.zeros(n_photons) if raw else None
+    rn = np.zeros(n_photons, np.uint64) if raw else None
+    rs = np.zeros(n_photons, np.uint8) if raw else None
     lib().orc_run_grid(*[_p(a, C.c_float) for a in arrs], C.byref(run), first_id, n_photons, seed,
                        n_threads, _p(spec, C.c_uint64), _p(cube, C.c_double) if peel else None,
-                       C.byref(res))
-    return {"counts": spec[:n_bins], "underflow": int(spec[n_bins]), "overflow": int(spec[n_bins + 1]),
-            "cube": cube, "n_escaped": res.n_escaped, "n_absorbed": res.n_absorbed,
-            "n_capped": res.n_capped, "sum_scat": res.sum_scat, "sum_scat2": res.sum_scat2,
-            "sum_dust_scat": res.sum_dust_scat}
+                       C.byref(res), _p(rX, C.c_double) if raw else None, _p(rn, C.c_uint64) if raw else None,
+                       _p(rs, C.c_uint8) if raw else None)
+    out = {"counts": spec[:n_bins], "underflow": int(spec[n_bins]), "overflow": int(spec[n_bins + 1]),
+           "cube": cube, "n_escaped": res.n_escaped, "n_absorbed": res.n_absorbed,
+           "n_capped": res.n_capped, "sum_scat": res.sum_scat, "sum_scat2": res.sum_scat2,
+           "sum_dust_scat": res.sum_dust_scat}
+    if raw:
+        out.update(X=rX, nscat=rn, status=rs)
+    return out
 
 
 def forest(n_HI, T, v_los, sel_ix, sel_iy, *, ds_cm, dv_cell, n_bins, dv_bin, n_threads=0):

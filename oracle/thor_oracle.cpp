@@ -1257,7 +1257,8 @@ void peel_tau(const GridModel& g, const double p[3], int axis, double Xp, double
 
 extern "C" int orc_run_grid(const float* nHI, const float* T, const float* vx, const float* vy, const float* vz,
                  const float* kd, const orc_grid_run* run, uint64_t first_id, uint64_t n, uint64_t seed,
-                 int32_t n_threads, uint64_t* spec_counts, double* cube, orc_result* res) {
+                 int32_t n_threads, uint64_t* spec_counts, double* cube, orc_result* res, double* raw_X,
+                 uint64_t* raw_nscat, uint8_t* raw_status) {
   GridModel g;
   for (int a = 0; a < 3; ++a) g.n[a] = run->dims[a];
   int64_t nc = (int64_t)g.n[0] * g.n[1] * g.n[2];
@@ -1422,6 +1423,11 @@ extern "C" int orc_run_grid(const float* nHI, const float* T, const float* vx, c
     r.sum_scat2 += (double)nscat * (double)nscat;
     r.sum_dust_scat += ndust;
     r.sum_upar_iters += iters;
+    if (raw_X) {  // optional per-photon record: final lab X, scatterings, 1/2/3 = escaped/absorbed/capped
+      raw_X[i] = X;
+      raw_nscat[i] = nscat;
+      raw_status[i] = (uint8_t)status;
+    }
   });
   std::memset(res, 0, sizeof(orc_result));
   if (spec_counts) std::memset(spec_counts, 0, sizeof(uint64_t) * (size_t)(nb + 2));

@@ -554,6 +554,7 @@ extern "C" int thor_run(thor_ctx_t ctx, thor_geom_t g, const thor_source* src, u
     m.spectrum = o.spec; m.cube = o.cube; m.tally = d_tally;
     m.n_photons = n_photons; m.id_base = first_id;
     m.peel_rays = d_stats; m.peel_cells = d_stats + 1;
+    m.raw_X = o.raw_X; m.raw_nscat = o.raw_n; m.raw_status = o.raw_s;
     const int gsz = grid_grid(ctx->block, ctx->blocks_per_sm);
     // few photons: spread them so that each runs in a warp of its own where possible
     const unsigned long long warps = (unsigned long long)gsz * (ctx->block / 32);

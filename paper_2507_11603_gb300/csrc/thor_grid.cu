@@ -401,6 +401,12 @@ __global__ void __launch_bounds__(256) grid_run_kernel(GridModel m, WorkQueue q,
             atomicAdd(&m.spectrum[bin], 1ull);
           } else if (st == 2) ++ab;
           else ++cap;
+          if (m.raw_X) {
+            const unsigned long long j = ph.pid - m.id_base;
+            m.raw_X[j] = ph.X;
+            m.raw_nscat[j] = ph.nscat;
+            m.raw_status[j] = (uint8_t)st;
+          }
           sc += ph.nscat; du += ph.ndust; it += ph.iters; stp += ph.steps; ++dn;
           sc2 += (double)ph.nscat * (double)ph.nscat;
           active = false;

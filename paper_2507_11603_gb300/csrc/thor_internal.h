@@ -140,6 +140,9 @@ struct GridModel {
   unsigned long long* peel_rays;   // statistics: peel rays traced, cells visited
   unsigned long long* peel_cells;
   int32_t per_warp;       // lanes per warp that take photons (1..32): few photons spread over all schedulers
+  float* raw_X;           // optional per-photon records (NULL = off), indexed by pid - id_base
+  uint32_t* raw_nscat;
+  uint8_t* raw_status;
 };
 
 // ---- launchers (implemented in the .cu files) ------------------------------------

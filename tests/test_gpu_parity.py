@@ -206,6 +206,23 @@ def test_run_determinism_and_split_invariance(ctx):
     assert np.array_equal(a.spectrum, d.spectrum) and a.stats["n_scat"] == d.stats["n_scat"]
 
 
+def test_ragged_photon_counts_equal_photons_alone(ctx):
+    """A run of 37 photons (fewer than the resident warps, not a multiple of 32) gives each
+    photon exactly the history it has when run alone: raw status, scattering count and
+    escape frequency bit for bit, on a thick shell and on a small grid."""
+    g = ctx.shell(R_in=0.9, N_HI=1e19, T=1e4, v_max=200.0, tau_dust=0.5, phase="dipole")
+    f = _small_grid(n=8, seed=11)
+    gg = ctx.grid(f["n_HI"], f["T"], f["v"], f["kd"], 100 * 3.0856775814913673e18, phase="dipole")
+    for geom, kw in ((g, dict(sigma=50.0)), (gg, {})):
+        kw.update(seed=9, n_bins=16, X_min=-1500, X_max=1500, raw=True)
+        r = ctx.run(geom, n_photons=37, first_id=100, **kw)
+        assert r.raw_status.shape == (37,)
+        for k in (0, 1, 17, 31, 32, 36):
+            one = ctx.run(geom, n_photons=1, first_id=100 + k, **kw)
+            assert one.raw_status[0] == r.raw_status[k] and one.raw_nscat[0] == r.raw_nscat[k]
+            assert one.raw_X[0] == r.raw_X[k]
+
+
 def test_tail_compaction_does_not_change_results(ctx):
     """Tail compaction re-packs survivors between launches; every photon's history is
     keyed by its id, so the tallies must be bit-identical with it on and off."""
@@ -291,6 +308,27 @@ def test_grid_thick_cells_fast_path(ctx, orc):
     assert abs(tot_g / tot_o - 1) < 0.05, (tot_g, tot_o)
 
 
+def test_grid_same_stream_per_photon(ctx, orc):
+    """Same seed and photon ids on the grid: emission and every event draw the same words
+    on both sides, so photons with few events follow the same cell walk and interactions;
+    (status, n_scat) agree photon by photon except after an FP32 decision flip, and the
+    escape frequencies agree to FP32 rounding."""
+    f = _small_grid(n=16, seed=5)
+    cell = 100 * 3.0856775814913673e18
+    of = dict(n_HI=f["n_HI"], T=f["T"], vx=f["v"][0], vy=f["v"][1], vz=f["v"][2], kd=f["kd"])
+    g = ctx.grid(f["n_HI"], f["T"], f["v"], f["kd"], cell, phase="dipole", albedo=0.32, g_hg=0.73)
+    n = 4000
+    r = ctx.run(g, n_photons=n, seed=12, n_bins=16, X_min=-600, X_max=600, raw=True, max_scat=20000)
+    ro = orc.run_grid(of, cell_cm=cell, n_photons=n, seed=12, n_bins=16, X_min=-600, X_max=600, peel=False,
+                      max_scat=20000, raw=True)
+    few = ro["nscat"] < 5
+    assert few.sum() > 200
+    same = (r.raw_status == ro["status"]) & (r.raw_nscat.astype(np.uint64) == ro["nscat"])
+    assert same[few].mean() > 0.9, same[few].mean()
+    esc = few & same & (ro["status"] == 1)
+    assert np.median(np.abs(r.raw_X[esc] - ro["X"][esc])) < 0.05
+
+
 def test_grid_config4_full_size_builds(ctx):
     """Config 4 fields at 256^3 (packed on the device, emission CDF); a short run checks
     conservation on the full-size grid."""
@@ -313,6 +351,30 @@ def test_forest_small_box_elementwise(ctx, orc):
     ref = orc.forest(nHI, T, v, sel % 8, sel // 8, ds_cm=ds, dv_cell=2.0, n_bins=512, dv_bin=1.0)
     rel = np.abs(tau.astype(np.float64) - ref) / ref
     assert rel.max() < 1e-5, rel.max()
+
+
+def test_forest_ragged_chunks_and_subsets(ctx, orc):
+    """Ragged forest shapes, element by element against the FP64 oracle: nz = 1100 spans two
+    staged cell chunks (1024 + 76), n_bins = 300 leaves a ragged last bin pass, the box is
+    3 x 5 sightlines with a sub-range [4, 11), on host and device buffers; and the
+    degenerate one-cell, one-bin sightline (a single Voigt term)."""
+    import torch
+    from paper_2507_11603_gb300 import synth
+    nHI, T, v = synth.forest_fields_numpy((1100, 3, 5), seed=9)
+    ds = synth.forest_scale(2.0, 1.5)
+    kw = dict(ds_cm=ds, dv_cell=1.5, n_bins=300, dv_bin=5.5)
+    sel = np.arange(4, 11)
+    ref = orc.forest(nHI, T, v, sel % 5, sel // 5, **kw)
+    host = ctx.forest(nHI, T, v, first=4, count=7, **kw)
+    dev = ctx.forest(*(torch.as_tensor(a, device="cuda") for a in (nHI, T, v)), first=4, count=7, **kw)
+    for got in (host, dev.cpu().numpy()):
+        assert got.shape == (7, 300)
+        rel = np.abs(got.astype(np.float64) - ref) / ref
+        assert rel.max() < 1e-5, rel.max()
+    n1, T1, v1 = synth.forest_fields_numpy((1, 1, 2), seed=3)
+    one = ctx.forest(n1, T1, v1, ds_cm=ds, dv_cell=2.0, n_bins=1, dv_bin=2.0)
+    ref1 = orc.forest(n1, T1, v1, [0, 1], [0, 0], ds_cm=ds, dv_cell=2.0, n_bins=1, dv_bin=2.0)
+    assert (np.abs(one.astype(np.float64) - ref1) / ref1).max() < 1e-5
 
 
 def test_forest_full_size_sampled(ctx, orc):

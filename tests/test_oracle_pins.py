@@ -358,6 +358,27 @@ def test_peel_empty_grid(orc):
     assert abs(r["cube"].sum() - 3 * n / (4 * np.pi)) < 1e-9 * n
 
 
+def test_grid_raw_records_thermal_emission(orc):
+    """Per-photon records of a grid run without opacity: every photon escapes unscattered
+    with its emitted frequency, which in a static cell is the thermal N(0, v_th^2 / 2) of
+    Sec. 2.1; the records also rebuild the binned spectrum exactly."""
+    f = _uniform_fields(4, 1e-30, 0.0)
+    n = 4000
+    r = orc.run_grid(f, cell_cm=3.086e20, n_photons=n, seed=3, n_bins=32, X_min=-40, X_max=40, peel=False,
+                     raw=True)
+    assert np.all(r["status"] == 1) and np.all(r["nscat"] == 0)
+    vth = orc.line_params(1e4)["vth_kms"]
+    assert stats.kstest(r["X"], lambda t: stats.norm.cdf(t, 0.0, vth / np.sqrt(2.0))).pvalue > 1e-3
+    h = np.histogram(r["X"], bins=32, range=(-40, 40))[0]
+    assert np.array_equal(h, r["counts"].astype(np.int64))
+    # a thick dusty grid: the records partition the photons the way the tallies do
+    f = _uniform_fields(4, 1e-30, 0.5 / 3.086e18)
+    r = orc.run_grid(f, cell_cm=3.086e18, n_photons=n, seed=4, albedo=0.5, n_bins=8, peel=False, raw=True)
+    for code, key in ((1, "n_escaped"), (2, "n_absorbed"), (3, "n_capped")):
+        assert (r["status"] == code).sum() == r[key]
+    assert r["nscat"].sum() == r["sum_scat"]
+
+
 def test_peel_dust_attenuation(orc):
     # uniform absorbing dust, no HI opacity: E[exp(-k (L - z))] = (1 - exp(-k L)) / (k L)
     L, n = 8, 6000
