@@ -249,6 +249,8 @@ __device__ __forceinline__ float cot_pi(float t) {
 }
 
 // Iteration 0 takes words 1-3 of the event, iteration i >= 1 words 0-2 of block i + 2.
+// Iteration 0 is peeled out of the loop so that it shares a basic block with the work
+// the caller schedules around it (further iterations are rare in the core).
 __device__ __forceinline__ float sample_upar(float x, float a, const Rng& rng, uint32_t& iters) {
   const float sgn = (x < 0.0f) ? -1.0f : 1.0f;
   const float xr = fabsf(x);
@@ -258,17 +260,21 @@ __device__ __forceinline__ float sample_upar(float x, float a, const Rng& rng, u
   const float p1 = __fdividef(w1, __fmaf_rn(e0, kPiF - w1, w1));
   const float u02 = u0 * u0;
   const float w1p = w1 * (1.0f / kPiF);  // alpha in units of pi
-  uint32_t r1 = rng.v[W_UPAR0], r2 = rng.v[W_UPAR0 + 1], r3 = rng.v[W_UPAR0 + 2], spare, blk = 3u;
-  float u;
-  for (;;) {
+  auto trial = [&](uint32_t r1, uint32_t r2, uint32_t r3, float& u) {
     const float R1 = uni32(r1), R2 = uni32(r2), R3 = uni32(r3);
     const bool reg1 = R1 < p1;
     const float t = reg1 ? w1p * R2 : __fmaf_rn(1.0f - w1p, R2, w1p);
     u = __fmaf_rn(-a, cot_pi(t), xr);  // x - a cot(alpha)
     const float acc = reg1 ? __expf(-u * u) : __expf(u02 - u * u);
     ++iters;
-    if (R3 <= acc) break;
-    rng.block(blk++, r1, r2, r3, spare);
+    return R3 <= acc;
+  };
+  float u;
+  if (!trial(rng.v[W_UPAR0], rng.v[W_UPAR0 + 1], rng.v[W_UPAR0 + 2], u)) {
+    uint32_t r1, r2, r3, spare, blk = 3u;
+    do {
+      rng.block(blk++, r1, r2, r3, spare);
+    } while (!trial(r1, r2, r3, u));
   }
   return sgn * u;
 }
@@ -310,36 +316,42 @@ struct AtomFrame {  // what peeling-off needs from a resonant scattering
 // x_out = x_in + u . (k_out - k_in) and overwrites k with k_out.
 // Core-skipping (Sec. 3.4.2): for |x| < xcrit the perpendicular speed comes from the
 // Gaussian left-truncated at xcrit, r = sqrt(xcrit^2 - ln R) (xcrit = 0: plain Eq. 5).
-__device__ __forceinline__ float scatter_resonant(float x, float a, int phase, float3& k, const Rng& rng,
-                                                  uint32_t& iters, AtomFrame* af, float xcrit = 0.0f) {
-  const float upar = sample_upar(x, a, rng, iters);
-  const float xc = (fabsf(x) < xcrit) ? xcrit : 0.0f;
-  const float r = sqrt_approx(__fmaf_rn(xc, xc, -__logf(rng.u(W_BM_R))));
-  float sp1, cp1;
-  __sincosf(2.0f * kPiF * rng.u(W_BM_PHI), &sp1, &cp1);
-  const float u1 = r * cp1, u2 = r * sp1;
-  const bool core = fabsf(x - upar) < 0.2f;
-  float mu;
-  if (phase == PH_ISO) {
-    mu = __fmaf_rn(2.0f, rng.u(W_MU), -1.0f);
-  } else if (phase == PH_DIPOLE) {
-    mu = mu_dipole(rng.u(W_MU));
-  } else {
-    const float Rc = rng.u(W_MIXED);
-    const float Rm = rng.u(W_MU);
-    mu = (core && Rc < (1.0f / 3.0f)) ? __fmaf_rn(2.0f, Rm, -1.0f) : mu_dipole(Rm);
-  }
-  float sp, cp;
-  __sincosf(2.0f * kPiF * rng.u(W_PHI), &sp, &cp);
-  float3 e1, e2;
-  basis(k.x, k.y, k.z, e1, e2);
-  const float st = sqrt_approx(fmaxf(0.0f, 1.0f - mu * mu));
+// The perpendicular velocity, mu and the outgoing direction do not depend on u_par, so
+// they are formed before the rejection sampler and overlap with it; only the mixed phase
+// function's isotropic branch (core scatterings, Sec. 2.3) needs u_par and redoes the
+// direction afterwards.
+__device__ __forceinline__ float3 turn(const float3& k, const float3& e1, const float3& e2, float mu, float st,
+                                       float cp, float sp) {
   float3 ko;
   ko.x = mu * k.x + st * (cp * e1.x + sp * e2.x);
   ko.y = mu * k.y + st * (cp * e1.y + sp * e2.y);
   ko.z = mu * k.z + st * (cp * e1.z + sp * e2.z);
   const float inv = rsqrtf(ko.x * ko.x + ko.y * ko.y + ko.z * ko.z);
-  ko.x *= inv; ko.y *= inv; ko.z *= inv;
+  return make_float3(ko.x * inv, ko.y * inv, ko.z * inv);
+}
+
+__device__ __forceinline__ float scatter_resonant(float x, float a, int phase, float3& k, const Rng& rng,
+                                                  uint32_t& iters, AtomFrame* af, float xcrit = 0.0f) {
+  const float xc = (fabsf(x) < xcrit) ? xcrit : 0.0f;
+  const float r = sqrt_approx(__fmaf_rn(xc, xc, -__logf(rng.u(W_BM_R))));
+  float sp1, cp1;
+  __sincosf(2.0f * kPiF * rng.u(W_BM_PHI), &sp1, &cp1);
+  const float u1 = r * cp1, u2 = r * sp1;
+  const float Rm = rng.u(W_MU);
+  float mu = (phase == PH_ISO) ? __fmaf_rn(2.0f, Rm, -1.0f) : mu_dipole(Rm);
+  float sp, cp;
+  __sincosf(2.0f * kPiF * rng.u(W_PHI), &sp, &cp);
+  float3 e1, e2;
+  basis(k.x, k.y, k.z, e1, e2);
+  float st = sqrt_approx(fmaxf(0.0f, 1.0f - mu * mu));
+  float3 ko = turn(k, e1, e2, mu, st, cp, sp);
+  const float upar = sample_upar(x, a, rng, iters);
+  const bool core = fabsf(x - upar) < 0.2f;
+  if (phase == PH_MIXED && core && rng.u(W_MIXED) < (1.0f / 3.0f)) {
+    mu = __fmaf_rn(2.0f, Rm, -1.0f);
+    st = sqrt_approx(fmaxf(0.0f, 1.0f - mu * mu));
+    ko = turn(k, e1, e2, mu, st, cp, sp);
+  }
   if (af) { af->upar = upar; af->u1 = u1; af->u2 = u2; af->e1 = e1; af->e2 = e2; af->core = core; }
   k = ko;
   return x - upar + __fmaf_rn(upar, mu, st * __fmaf_rn(u1, cp, u2 * sp));
