@@ -236,16 +236,15 @@ __device__ __forceinline__ float u0_rule(float xr, float a) {
 __device__ __forceinline__ float cot_pi(float t) {
   const float s = (t > 0.5f) ? t - 1.0f : t;
   const float z = kPiF * s;
-  if (fabsf(z) <= 0.25f) {
-    const float z2 = z * z;
-    float g = __fmaf_rn(z2, 1.0f / 4725.0f, 2.0f / 945.0f);
-    g = __fmaf_rn(g, z2, 1.0f / 45.0f);
-    g = __fmaf_rn(g, z2, 1.0f / 3.0f);
-    return __fmaf_rn(-z, g, rcp_approx(z));
-  }
+  const float z2 = z * z;
+  float g = __fmaf_rn(z2, 1.0f / 4725.0f, 2.0f / 945.0f);
+  g = __fmaf_rn(g, z2, 1.0f / 45.0f);
+  g = __fmaf_rn(g, z2, 1.0f / 3.0f);
+  const float laurent = __fmaf_rn(-z, g, rcp_approx(z));
   float sn, cs;
   __sincosf(z, &sn, &cs);
-  return cs * rcp_approx(sn);
+  const float trig = cs * rcp_approx(sn);
+  return (fabsf(z) <= 0.25f) ? laurent : trig;  // both formed: a select instead of a branch
 }
 
 // Iteration 0 takes words 1-3 of the event, iteration i >= 1 words 0-2 of block i + 2.
