@@ -123,6 +123,8 @@ typedef struct {
   double alpha_v;        /* power law: velocity index */
 } thor_shell_params;
 
+/* Checks every parameter on the host: finite values, the ranges above, and FP32
+ * opacities that do not overflow; THOR_ERR_INVALID_ARG otherwise. */
 int thor_shell_create(thor_ctx_t ctx, const thor_shell_params* p, thor_geom_t* out);
 
 /* Uniform Cartesian grid (Sec. 3.3).  n_HI [cm^-3], T [K], v = 3 arrays (vx, vy, vz)
@@ -130,7 +132,10 @@ int thor_shell_create(thor_ctx_t ctx, const thor_shell_params* p, thor_geom_t* o
  * coefficient [cm^-1] (may be NULL = no dust).  dims = (nx, ny, nz).  Fields are
  * packed into one 32-byte record per cell on the device (zeroth-order cells,
  * Sec. 3.4) together with the emission CDF (emissivity proportional to n_HI^2).
- * The inputs are not referenced after the call. */
+ * The inputs are not referenced after the call.  Every cell needs T > 0, n_HI >= 0,
+ * dust >= 0 and finite values (also after conversion to FP32 opacities); the cells are
+ * checked on the device and any violation returns THOR_ERR_INVALID_ARG with the count,
+ * as does n_HI = 0 everywhere. */
 int thor_grid_create(thor_ctx_t ctx, const float* n_HI, const float* T, const float* v, const float* dust,
                      const int32_t dims[3], double cell_size_cm, int mem_kind, thor_geom_t* out);
 
@@ -307,11 +312,12 @@ int thor_voigt_eval(thor_ctx_t ctx, const float* a, const float* x, float* H, in
 int thor_dda_trace(thor_ctx_t ctx, const int32_t dims[3], const double* origins, const float* dirs, int32_t n,
                    int32_t max_steps, int64_t* cells, double* seg, int32_t* count, int mem_kind);
 /* n samples of u_par at fixed (x, a) (Eq. 6 by the rejection scheme of Eq. 10),
- * sample i from photon stream i of `seed`; *iters = total rejection iterations. */
+ * sample i from photon stream i of `seed`; *iters = total rejection iterations.
+ * Needs finite x and finite a > 0 (THOR_ERR_INVALID_ARG otherwise). */
 int thor_sample_upar(thor_ctx_t ctx, float x, float a, uint64_t seed, int64_t n, float* out, uint64_t* iters,
                      int mem_kind);
 /* One resonant scattering (Eq. 5-7) of n photons moving along +z at gas-frame x in
- * static gas: x_out and mu = k_in . k_out. */
+ * static gas: x_out and mu = k_in . k_out.  Needs finite x and finite a > 0. */
 int thor_scatter_once(thor_ctx_t ctx, float x, float a, int phase, uint64_t seed, int64_t n, float* x_out,
                       float* mu_out, int mem_kind);
 /* Philox4x32-10 blocks: ctr 4n words, key 2n words, out 4n words. */

@@ -198,6 +198,7 @@ static int fill_power_law(thor_ctx* ctx, const thor_shell_params* p, ShellModel*
   m->phase = p->phase;
   const double at = (double)m->a * tau0;
   m->xcrit = (p->core_skip && at >= 1.0) ? (float)(0.2 * cbrt(at)) : 0.0f;
+  if (!shell_record_finite(*m)) return ctx->fail(THOR_ERR_INVALID_ARG, "shell opacity or line parameters overflow FP32");
   return THOR_OK;
 }
 
@@ -218,6 +219,9 @@ int thor::fill_shell_source(thor_ctx* ctx, const thor_source* src, ShellModel* m
 
 int thor::fill_shell_model(thor_ctx* ctx, const thor_shell_params* p, ShellModel* m) {
   if (!p) return ctx->fail(THOR_ERR_INVALID_ARG, "shell parameters are NULL");
+  for (double q : {p->R_in, p->R_out, p->N_HI, p->tau0, p->T, p->v_max, p->tau_dust, p->albedo, p->g_hg, p->step_dx,
+                   p->alpha_rho, p->alpha_v})
+    if (!std::isfinite(q)) return ctx->fail(THOR_ERR_INVALID_ARG, "shell parameters must be finite");
   if (!(p->R_out > 0.0) || !(p->R_in >= 0.0) || !(p->R_in < p->R_out))
     return ctx->fail(THOR_ERR_INVALID_ARG, "shell radii must satisfy 0 <= R_in < R_out");
   if (!(p->T > 0.0)) return ctx->fail(THOR_ERR_INVALID_ARG, "temperature must be > 0");
@@ -254,6 +258,7 @@ int thor::fill_shell_model(thor_ctx* ctx, const thor_shell_params* p, ShellModel
   m->phase = p->phase;
   const double at = line_a(p->T) * tau0;
   m->xcrit = (p->core_skip && at >= 1.0) ? (float)(0.2 * cbrt(at)) : 0.0f;
+  if (!shell_record_finite(*m)) return ctx->fail(THOR_ERR_INVALID_ARG, "shell opacity or line parameters overflow FP32");
   return THOR_OK;
 }
 
@@ -296,7 +301,7 @@ extern "C" int thor_grid_create(thor_ctx_t ctx, const float* n_HI, const float* 
   int rc = THOR_OK;
   if (cudaMalloc(&g->cells, (size_t)n * sizeof(GridCell)) != cudaSuccess ||
       cudaMalloc(&g->cdf, (size_t)n * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&g->scan_tmp, scan_f64_scratch(n)) != cudaSuccess) {
+      cudaMalloc(&g->scan_tmp, scan_f64_scratch(n) + sizeof(unsigned long long)) != cudaSuccess) {
     delete g;
     return ctx->fail(THOR_ERR_OOM, "thor_grid_create: cannot allocate %lld cells", (long long)n);
   }
@@ -312,13 +317,29 @@ extern "C" int thor_grid_create(thor_ctx_t ctx, const float* n_HI, const float* 
     dn = stage; dT = stage + n; dvx = stage + 2 * n; dvy = stage + 3 * n; dvz = stage + 4 * n;
     dd = dust ? stage + 5 * n : nullptr;
   }
-  if (rc == THOR_OK) rc = ctx->cuda(launch_grid_pack(dn, dT, dvx, dvy, dvz, dd, n, cell_cm, g->cells, g->cdf, ctx->stream), "grid pack");
+  // unusable cells are counted on the device (the fields may be device-resident)
+  unsigned long long* d_bad =
+      reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(g->scan_tmp) + scan_f64_scratch(n));
+  if (rc == THOR_OK) rc = ctx->cuda(cudaMemsetAsync(d_bad, 0, sizeof(unsigned long long), ctx->stream), "grid check");
+  if (rc == THOR_OK)
+    rc = ctx->cuda(launch_grid_pack(dn, dT, dvx, dvy, dvz, dd, n, cell_cm, g->cells, g->cdf, d_bad, ctx->stream),
+                   "grid pack");
   if (rc == THOR_OK) rc = ctx->cuda(launch_scan_f64(g->cdf, n, g->scan_tmp, ctx->stream), "emission CDF");
   if (rc == THOR_OK) rc = ctx->cuda(cudaStreamSynchronize(ctx->stream), "grid create");
   if (stage) cudaFree(stage);
   if (rc != THOR_OK) { delete g; return rc; }
+  unsigned long long bad = 0;
   double total = 0.0;
-  cudaMemcpy(&total, g->cdf + (n - 1), sizeof(double), cudaMemcpyDeviceToHost);
+  if ((rc = ctx->cuda(cudaMemcpy(&bad, d_bad, sizeof bad, cudaMemcpyDeviceToHost), "grid check")) ||
+      (rc = ctx->cuda(cudaMemcpy(&total, g->cdf + (n - 1), sizeof(double), cudaMemcpyDeviceToHost), "grid CDF"))) {
+    delete g;
+    return rc;
+  }
+  if (bad) {
+    delete g;
+    return ctx->fail(THOR_ERR_INVALID_ARG,
+                     "thor_grid_create: %llu cells out of range (need T > 0, n_HI >= 0, dust >= 0, all finite)", bad);
+  }
   if (!(total > 0.0)) { delete g; return ctx->fail(THOR_ERR_INVALID_ARG, "thor_grid_create: n_HI is zero everywhere"); }
   *out = g;
   return THOR_OK;
@@ -787,7 +808,9 @@ extern "C" int thor_dda_trace(thor_ctx_t ctx, const int32_t dims[3], const doubl
 
 extern "C" int thor_sample_upar(thor_ctx_t ctx, float x, float a, uint64_t seed, int64_t n, float* out, uint64_t* iters,
                                 int mem_kind) {
-  if (!ctx || !out || n <= 0 || !(a >= 0.0f)) return ctx ? ctx->fail(THOR_ERR_INVALID_ARG, "thor_sample_upar") : THOR_ERR_INVALID_ARG;
+  if (!ctx || !out || n <= 0 || !(a > 0.0f) || !std::isfinite(a) || !std::isfinite(x))
+    return ctx ? ctx->fail(THOR_ERR_INVALID_ARG, "thor_sample_upar: needs n > 0, finite x, finite a > 0")
+               : THOR_ERR_INVALID_ARG;
   Stage st;
   if (int rc = stage_begin(ctx, mem_kind, (size_t)n * 4 + 4096, &st)) return rc;
   float* d = (float*)st.out(out, (size_t)n * 4);
@@ -804,8 +827,10 @@ extern "C" int thor_sample_upar(thor_ctx_t ctx, float x, float a, uint64_t seed,
 
 extern "C" int thor_scatter_once(thor_ctx_t ctx, float x, float a, int phase, uint64_t seed, int64_t n, float* x_out,
                                  float* mu_out, int mem_kind) {
-  if (!ctx || !x_out || !mu_out || n <= 0 || phase < 0 || phase > 2)
-    return ctx ? ctx->fail(THOR_ERR_INVALID_ARG, "thor_scatter_once") : THOR_ERR_INVALID_ARG;
+  if (!ctx || !x_out || !mu_out || n <= 0 || phase < 0 || phase > 2 || !(a > 0.0f) || !std::isfinite(a) ||
+      !std::isfinite(x))
+    return ctx ? ctx->fail(THOR_ERR_INVALID_ARG, "thor_scatter_once: needs n > 0, phase 0-2, finite x, finite a > 0")
+               : THOR_ERR_INVALID_ARG;
   Stage st;
   if (int rc = stage_begin(ctx, mem_kind, (size_t)n * 8 + 4096, &st)) return rc;
   float* dx = (float*)st.out(x_out, (size_t)n * 4);

@@ -249,7 +249,11 @@ __device__ __forceinline__ float cot_pi(float t) {
 
 // Iteration 0 takes words 1-3 of the event, iteration i >= 1 words 0-2 of block i + 2.
 // Iteration 0 is peeled out of the loop so that it shares a basic block with the work
-// the caller schedules around it (further iterations are rare in the core).
+// the caller schedules around it (further iterations are rare in the core).  The loop
+// stops after kMaxUparTrials trials: every trial accepts with probability above 1/5 for
+// a > 0 and finite x (the paper's expected counts are 2.1-4.2), so valid inputs never get
+// there (probability below 1e-390), and a NaN input cannot keep a lane spinning.
+constexpr uint32_t kMaxUparTrials = 4096u;
 __device__ __forceinline__ float sample_upar(float x, float a, const Rng& rng, uint32_t& iters) {
   const float sgn = (x < 0.0f) ? -1.0f : 1.0f;
   const float xr = fabsf(x);
@@ -273,12 +277,12 @@ __device__ __forceinline__ float sample_upar(float x, float a, const Rng& rng, u
     uint32_t r1, r2, r3, spare, blk = 3u;
     do {
       rng.block(blk++, r1, r2, r3, spare);
-    } while (!trial(r1, r2, r3, u));
+    } while (!trial(r1, r2, r3, u) && blk < 2u + kMaxUparTrials);
   }
   return sgn * u;
 }
 
-// Phase functions (Sec. 2.3): mu = k_in . k_out.
+// Phase functions (Sec. 2.3.1 resonant, Sec. 2.3.2 dust, Eq. 9): mu = k_in . k_out.
 enum : int { PH_ISO = 0, PH_DIPOLE = 1, PH_MIXED = 2 };
 __device__ __forceinline__ float mu_dipole(float R) {  // CDF (mu^3 + 3 mu + 4)/8, Cardano
   const float B = __fmaf_rn(4.0f, R, -2.0f);
@@ -317,7 +321,7 @@ struct AtomFrame {  // what peeling-off needs from a resonant scattering
 // Gaussian left-truncated at xcrit, r = sqrt(xcrit^2 - ln R) (xcrit = 0: plain Eq. 5).
 // The perpendicular velocity, mu and the outgoing direction do not depend on u_par, so
 // they are formed before the rejection sampler and overlap with it; only the mixed phase
-// function's isotropic branch (core scatterings, Sec. 2.3) needs u_par and redoes the
+// function's isotropic branch (core scatterings, Sec. 2.3.1) needs u_par and redoes the
 // direction afterwards.
 __device__ __forceinline__ float3 turn(const float3& k, const float3& e1, const float3& e2, float mu, float st,
                                        float cp, float sp) {

@@ -13,7 +13,8 @@ constexpr unsigned kFull = 0xffffffffu;
 __global__ void grid_pack_kernel(const float* __restrict__ nHI, const float* __restrict__ T,
                                  const float* __restrict__ vx, const float* __restrict__ vy,
                                  const float* __restrict__ vz, const float* __restrict__ dust, int64_t n,
-                                 double cell_cm, GridCell* __restrict__ out, double* __restrict__ w) {
+                                 double cell_cm, GridCell* __restrict__ out, double* __restrict__ w,
+                                 unsigned long long* __restrict__ bad) {
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
     const double Tc = (double)T[c];
     const double rT = 1.0 / sqrt(Tc);
@@ -25,6 +26,12 @@ __global__ void grid_pack_kernel(const float* __restrict__ nHI, const float* __r
     g.inv_vth = (float)(1.0 / (THOR_VTH1 * sqrt(Tc)));
     g.vx = vx[c]; g.vy = vy[c]; g.vz = vz[c];
     g.kd = dust ? (float)((double)dust[c] * cell_cm) : 0.0f;
+    // a cell the photon loop cannot use: T <= 0, negative density or dust, or anything
+    // non-finite (before or after the conversion to per-cell opacities)
+    const bool ok = Tc > 0.0 && nh >= 0.0 && g.kd >= 0.0f && isfinite(g.kap0) && isfinite(g.a) &&
+                    isfinite(g.vth) && g.vth > 0.0f && isfinite(g.inv_vth) && isfinite(g.vx) && isfinite(g.vy) &&
+                    isfinite(g.vz) && isfinite(g.kd) && isfinite(nh * nh);
+    if (!ok) atomicAdd(bad, 1ull);
     out[c] = g;
     w[c] = nh * nh;
   }
@@ -431,11 +438,11 @@ __global__ void __launch_bounds__(256) grid_run_kernel(GridModel m, WorkQueue q,
 
 cudaError_t launch_grid_pack(const float* nHI, const float* T, const float* vx, const float* vy, const float* vz,
                              const float* dust, int64_t n, double cell_cm, GridCell* out, double* w,
-                             cudaStream_t s) {
+                             unsigned long long* bad, cudaStream_t s) {
   const int block = 256;
   const int64_t want = (n + block - 1) / block;
   const int grid = (int)(want < 152 * 32 ? want : 152 * 32);
-  grid_pack_kernel<<<grid, block, 0, s>>>(nHI, T, vx, vy, vz, dust, n, cell_cm, out, w);
+  grid_pack_kernel<<<grid, block, 0, s>>>(nHI, T, vx, vy, vz, dust, n, cell_cm, out, w, bad);
   return cudaGetLastError();
 }
 

@@ -1,7 +1,9 @@
 // thor_internal.h -- plain structs shared by the host runtime and the kernels.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
+#include <initializer_list>
 #include <cuda_runtime.h>
 
 namespace thor {
@@ -51,6 +53,16 @@ struct ShellModel {
   float* raw_X0;             // optional per-photon emitted X and column
   float* raw_col;
 };
+
+// Every FP32 parameter of a shell record is finite and the thermal speed and Voigt a are
+// positive (a parameter set whose opacities overflow FP32 is rejected, since a photon
+// with an infinite opacity would never move).
+inline bool shell_record_finite(const ShellModel& m) {
+  for (float q : {m.kap0, m.kapd, m.vth, m.inv_vth, m.a, m.vgrad, m.gam, m.ds_core, m.xcrit, m.ar, m.av, m.v1, m.kapn,
+                  m.kapdn, m.invF, m.kapn2, m.a2, m.eps2})
+    if (!std::isfinite(q)) return false;
+  return m.vth > 0.0f && m.a > 0.0f && (m.n_lines < 2 || m.a2 > 0.0f);
+}
 
 // Photon work queue: photon g in [0, total) belongs to model m with
 // prefix[m] <= g < prefix[m+1] and has id first_id[m] + g - prefix[m].
@@ -160,7 +172,7 @@ cudaError_t launch_shell_slice(const ShellModel* d_models, WorkQueue q, SlotStat
                                const float* d_ktab, int grid, int block, bool mixed, cudaStream_t s);
 cudaError_t launch_grid_pack(const float* nHI, const float* T, const float* vx, const float* vy,
                              const float* vz, const float* dust, int64_t n, double cell_cm, GridCell* out,
-                             double* w, cudaStream_t s);
+                             double* w, unsigned long long* bad, cudaStream_t s);  // bad: count of unusable cells
 cudaError_t launch_scan_f64(double* data, int64_t n, double* scratch, cudaStream_t s);
 size_t scan_f64_scratch(int64_t n);
 cudaError_t launch_grid_run(GridModel m, WorkQueue q, const float* d_ktab, int grid, int block,

@@ -65,6 +65,8 @@ int setup(int dev, unsigned char** scratch, float** ktab) {
 
 // The shell's model record, as thor_shell_create builds it (same checks, no context).
 int model_from_params(const thor_shell_params* p, ShellModel* m) {
+  for (double q : {p->R_in, p->R_out, p->N_HI, p->tau0, p->T, p->v_max, p->tau_dust, p->albedo, p->g_hg, p->step_dx})
+    if (!std::isfinite(q)) return fail(THOR_ERR_INVALID_ARG, "thor_run_shell_noalloc: parameters must be finite");
   if (!(p->R_out > 0.0) || !(p->R_in >= 0.0) || !(p->R_in < p->R_out))
     return fail(THOR_ERR_INVALID_ARG, "thor_run_shell_noalloc: radii must satisfy 0 <= R_in < R_out");
   if (!(p->T > 0.0)) return fail(THOR_ERR_INVALID_ARG, "thor_run_shell_noalloc: temperature must be > 0");
@@ -98,6 +100,8 @@ int model_from_params(const thor_shell_params* p, ShellModel* m) {
   m->g_hg = (float)p->g_hg;
   m->phase = p->phase;
   m->xcrit = (p->core_skip && at >= 1.0) ? (float)(0.2 * cbrt(at)) : 0.0f;
+  if (!shell_record_finite(*m))
+    return fail(THOR_ERR_INVALID_ARG, "thor_run_shell_noalloc: opacity or line parameters overflow FP32");
   return THOR_OK;
 }
 
@@ -120,14 +124,14 @@ extern "C" int thor_run_shell_noalloc(const thor_shell_params* p, const thor_sou
   if (mem_kind == THOR_MEM_HOST && n_bins > THOR_NOALLOC_MAX_BINS)
     return fail(THOR_ERR_CAPACITY, "thor_run_shell_noalloc: host spectra are staged in the fixed scratch "
                                    "array and may have at most THOR_NOALLOC_MAX_BINS bins");
+  ShellModel m;  // every argument is checked before the device is touched
+  if (int rc = model_from_params(p, &m)) return rc;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
     return fail(THOR_ERR_DEVICE, "thor_run_shell_noalloc: no current CUDA device");
   unsigned char* scratch = nullptr;
   float* ktab = nullptr;
   if (int rc = setup(dev, &scratch, &ktab)) return rc;
-  ShellModel m;
-  if (int rc = model_from_params(p, &m)) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   unsigned long long* spec = (mem_kind == THOR_MEM_DEVICE) ? (unsigned long long*)spectrum
                                                            : (unsigned long long*)(scratch + kOffSpec);

@@ -43,6 +43,24 @@ def test_init_without_gpu_fails_cleanly():
     assert e.value.code == thor.ERR_DEVICE
 
 
+def test_shell_parameters_checked_before_the_device():
+    """Non-finite or out-of-range shell parameters are rejected with INVALID_ARG before any
+    CUDA call (so this runs without a GPU); valid ones get as far as the device."""
+    import torch
+    from paper_2507_11603_gb300 import thor
+    base = dict(T=1e4, tau0=1e4, n_photons=10, seed=1, n_bins=8)
+    for bad in (dict(T=float("inf")), dict(T=float("nan")), dict(T=0.0), dict(tau0=float("inf")),
+                dict(v_max=float("nan")), dict(tau_dust=float("inf")), dict(R_out=float("inf")),
+                dict(tau0=1e300), dict(step_dx=float("nan"))):
+        with pytest.raises(thor.ThorError) as e:
+            thor.run_shell_noalloc(**{**base, **bad})
+        assert e.value.code == thor.ERR_INVALID_ARG, bad
+    if not torch.cuda.is_available():
+        with pytest.raises(thor.ThorError) as e:
+            thor.run_shell_noalloc(**base)
+        assert e.value.code == thor.ERR_DEVICE
+
+
 def test_product_never_imports_oracle():
     pkg = os.path.join(ROOT, "paper_2507_11603_gb300")
     for dirpath, _, files in os.walk(pkg):

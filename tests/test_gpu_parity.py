@@ -454,9 +454,35 @@ def test_invalid_arguments_are_rejected(ctx):
     with pytest.raises(thor.ThorError):
         ctx.forest(np.ones((4, 2, 2), np.float32), np.ones((4, 2, 2), np.float32), np.zeros((4, 2, 2), np.float32),
                    ds_cm=1.0, dv_cell=2.0, n_bins=7, dv_bin=1.0)
+    with pytest.raises(thor.ThorError):
+        ctx.shell(T=float("inf"), tau0=1.0)
+    # unusable grid cells are found on the device, for host and device fields alike
+    import torch
+    f = _small_grid(n=8, seed=2)
+    cell = 100 * 3.0856775814913673e18
+    for field, idx, val in (("T", (1, 2, 3), 0.0), ("T", (0, 0, 0), float("nan")), ("n_HI", (7, 7, 7), -1.0),
+                            ("kd", (4, 0, 2), float("inf"))):
+        bad = {k: v.copy() for k, v in f.items()}
+        bad[field][idx] = val
+        for conv in (lambda a: a, lambda a: torch.as_tensor(a, device="cuda")):
+            with pytest.raises(thor.ThorError) as e:
+                ctx.grid(*(conv(bad[k]) for k in ("n_HI", "T", "v", "kd")), cell)
+            assert e.value.code == thor.ERR_INVALID_ARG and "out of range" in str(e.value)
+    bad = {k: v.copy() for k, v in f.items()}
+    bad["v"][1, 3, 3, 3] = float("nan")
+    with pytest.raises(thor.ThorError):
+        ctx.grid(bad["n_HI"], bad["T"], bad["v"], bad["kd"], cell)
+    for a in (0.0, float("nan")):
+        with pytest.raises(thor.ThorError):
+            ctx.sample_upar(1.0, a, 16, seed=1)
+        with pytest.raises(thor.ThorError):
+            ctx.scatter_once(1.0, a, 1, 16, seed=1)
     # the context is still usable afterwards
     r = ctx.run(g, n_photons=100, seed=1, n_bins=10, X_min=-100, X_max=100)
     assert r.stats["n_escaped"] == 100
+    gg = ctx.grid(f["n_HI"], f["T"], f["v"], f["kd"], cell)
+    st = ctx.run(gg, n_photons=100, seed=1, n_bins=10).stats
+    assert st["n_escaped"] + st["n_absorbed"] + st["n_capped"] == 100
 
 
 # --------------------------------------------------------- shell-model sweep (Sec. 5.1)
