@@ -332,26 +332,56 @@ double u0_rule(double xr, double a) {
   return (envelope_D(xr, a, c1) <= envelope_D(xr, a, u)) ? c1 : u;
 }
 
-// u_par from f(u) ~ exp(-u^2) / ((x-u)^2 + a^2) (Eq. 6) by rejection with the
-// piecewise comparison function of Eq. 10.  The Lorentzian part is sampled through
+// Split point u1 of the third piece (|x| > kUparThreePiece): the envelope mass
+// w0 e^{-u1^2} + (w1 - w0), w0 = atan2(a, x + u1), is stationary in u1 where
+// e^{u1^2} - 1 = 2 u1 (x + u1) (to leading order in a / (x + u1)); three fixed-point steps
+// of u1 = sqrt(ln(1 + 2 u1 (x + u1))) from u1 = 2.  Any u1 > 0 gives the exact
+// distribution; the rule only sets the rejection rate.
+constexpr double kUparThreePiece = 3.0;
+double u1_rule(double xr) {
+  double u = 2.0;
+  for (int it = 0; it < 3; ++it) u = std::sqrt(std::log1p(2.0 * u * (xr + u)));
+  return u;
+}
+
+// u_par from f(u) ~ exp(-u^2) / ((x-u)^2 + a^2) (Eq. 6) by rejection with a piecewise,
+// integrable comparison function (Eq. 10).  The Lorentzian part is sampled through
 // alpha = theta + pi/2 = atan2(a, x - u), uniform on its interval, u = x - a/tan(alpha).
-// Region 1 (u <= u0): alpha in (0, w1), accept with exp(-u^2).
-// Region 2 (u >  u0): alpha in (w1, pi), accept with exp(u0^2 - u^2).
-// Negative x by symmetry.  Three draws per iteration: region, alpha, acceptance.
+// Eq. 10 has two pieces:
+//   region 1 (u <= u0): alpha in (0, w1), envelope 1, accept with exp(-u^2);
+//   region 2 (u >  u0): alpha in (w1, pi), envelope e^{-u0^2}, accept with exp(u0^2 - u^2).
+// Region 1 then spans the Lorentzian mass down to u -> -inf, where e^{-u^2} vanishes, and
+// the acceptance falls as ~1.8/|x| in the far wing.  For |x| > kUparThreePiece a third
+// piece is split off below u = -u1 (u^2 >= u1^2 there):
+//   region 0 (u <= -u1): alpha in (0, w0), w0 = atan2(a, x + u1), envelope e^{-u1^2},
+//                        accept with exp(u1^2 - u^2);
+// region 1 shrinks to alpha in (w0, w1).  Regions are chosen in proportion to their
+// envelope masses w0 e^{-u1^2}, w1 - w0, (pi - w1) e^{-u0^2}; for |x| <= kUparThreePiece,
+// w0 = 0 and this is Eq. 10 as it stands.  Negative x by symmetry.  Three draws per
+// iteration: region, alpha, acceptance.
 double sample_upar(double x, double a, Stream& rng, uint64_t* iters) {
   // iteration 0 uses words 1-3, iteration i >= 1 words 0-2 of block i + 2
   double sgn = (x < 0.0) ? -1.0 : 1.0, xr = std::fabs(x);
   double u0 = u0_rule(xr, a);
   double w1 = std::atan2(a, xr - u0);
   double e0 = std::exp(-u0 * u0);
-  double p1 = w1 / (w1 + e0 * (kPi - w1));
+  double u1 = 0.0, w0 = 0.0, e1 = 0.0;
+  if (xr > kUparThreePiece) {
+    u1 = u1_rule(xr);
+    w0 = std::atan2(a, xr + u1);
+    e1 = std::exp(-u1 * u1);
+  }
+  const double m0 = w0 * e1, m1 = w1 - w0, m2 = e0 * (kPi - w1);
+  const double p0 = m0 / (m0 + m1 + m2), p01 = (m0 + m1) / (m0 + m1 + m2);
   for (uint64_t it = 1;; ++it) {
     const uint32_t w = (it == 1) ? (uint32_t)W_UPAR0 : 4u * (uint32_t)(it + 1);
     double R1 = rng.u(w), R2 = rng.u(w + 1), R3 = rng.u(w + 2);
-    bool reg1 = R1 < p1;
-    double alpha = reg1 ? w1 * R2 : w1 + (kPi - w1) * R2;
+    double alpha, shift;
+    if (R1 < p0) { alpha = w0 * R2; shift = u1 * u1; }                        // region 0
+    else if (R1 < p01) { alpha = w0 + (w1 - w0) * R2; shift = 0.0; }        // region 1
+    else { alpha = w1 + (kPi - w1) * R2; shift = u0 * u0; }                  // region 2
     double u = xr - a / std::tan(alpha);
-    double acc = reg1 ? std::exp(-u * u) : std::exp(u0 * u0 - u * u);
+    double acc = std::exp(shift - u * u);
     if (R3 <= acc) {
       if (iters) *iters += it;
       return sgn * u;

@@ -196,7 +196,8 @@ __device__ __forceinline__ float voigt(float a, float x, const float* __restrict
 //   w1 = atan2(a, x - u0), P(region 1) = w1 / (w1 + e^{-u0^2} (pi - w1)), u = x - a / tan(alpha).
 // Split point u0: the smaller-envelope candidate of (i) x - sqrt(a/(2 pi x)) e^{x^2/2}
 // and (ii) three Newton steps on u0^2 = ln(2 pi u0 (x - u0)^2 / a) (only for x > 2).
-// Three draws per iteration: region, alpha, acceptance.
+// Three draws per iteration: region, alpha, acceptance.  For |x| > 3 the comparison
+// function has a third piece below u = -u1 (sample_upar_far).
 // ------------------------------------------------------------------------------
 // atan2(a, d) for a, d >= 0: series when a/d <= 1/20 (relative error < 3e-9), else atan2f.
 __device__ __forceinline__ float atan2_pos(float a, float d) {
@@ -250,13 +251,68 @@ __device__ __forceinline__ float cot_pi(float t) {
 // Iteration 0 takes words 1-3 of the event, iteration i >= 1 words 0-2 of block i + 2.
 // Iteration 0 is peeled out of the loop so that it shares a basic block with the work
 // the caller schedules around it (further iterations are rare in the core).  The loop
-// stops after kMaxUparTrials trials: every trial accepts with probability above 1/5 for
-// a > 0 and finite x (the paper's expected counts are 2.1-4.2), so valid inputs never get
-// there (probability below 1e-390), and a NaN input cannot keep a lane spinning.
-constexpr uint32_t kMaxUparTrials = 4096u;
+// stops after kMaxUparTrials trials so that a NaN input cannot keep a lane spinning.  A
+// trial accepts with probability ~1 in the core and ~1.8/|x| in the far wing (the flat
+// region-1 envelope covers the Lorentzian mass down to u -> -inf), so at |x| = 1000 the
+// bound is reached with probability ~e^-1800: never, for any frequency a photon scatters at.
+constexpr uint32_t kMaxUparTrials = 1u << 20;
+
+// Far side (|x| > kUparThreePiece): Eq. 10's region 1 spans the Lorentzian mass down to
+// u -> -inf, where e^{-u^2} vanishes, so its acceptance falls as ~1.8/|x|.  A third piece
+// is split off below u = -u1 (envelope e^{-u1^2}, since u^2 >= u1^2 there):
+//   region 0: alpha in (0, w0), w0 = atan2(a, x + u1), accept with exp(u1^2 - u^2);
+//   region 1: alpha in (w0, w1), accept with exp(-u^2);
+//   region 2: alpha in (w1, pi), accept with exp(u0^2 - u^2);
+// each chosen in proportion to its envelope mass.  u1 makes that mass stationary,
+// e^{u1^2} - 1 = 2 u1 (x + u1), by three fixed-point steps from 2.  The width of region 1
+// is w1 - w0 = atan2(a (u0 + u1), (x - u0)(x + u1) + a^2), free of the cancellation of
+// the difference.  About 4-6 trials at every |x| > 3 (against ~0.57 |x| with two pieces).
+// Same words as the two-piece loop; kept out of line, as it is rare in optically thick gas
+// (everything passes by value, so the caller's stream state stays in registers).
+constexpr float kUparThreePiece = 3.0f;
+struct UparDraw { float u; uint32_t trials; };
+static __device__ __noinline__ UparDraw sample_upar_far(float xr, float a, Rng rng) {
+  uint32_t iters = 0;
+  const float u0 = u0_rule(xr, a);
+  float u1 = 2.0f;
+#pragma unroll
+  for (int it = 0; it < 3; ++it) u1 = sqrt_approx(__logf(__fmaf_rn(2.0f * u1, xr + u1, 1.0f)));
+  const float w1 = atan2_pos(a, xr - u0);
+  const float w0 = atan2_pos(a, xr + u1);
+  const float w01 = atan2_pos(a * (u0 + u1), __fmaf_rn(xr - u0, xr + u1, a * a));
+  const float s0 = u0 * u0, s1 = u1 * u1;
+  const float m0 = w0 * __expf(-s1), m2 = __expf(-s0) * (kPiF - w1);
+  const float inv = __frcp_rn(m0 + w01 + m2);
+  const float p0 = m0 * inv, p01 = (m0 + w01) * inv;
+  const float w0p = w0 * (1.0f / kPiF), w01p = w01 * (1.0f / kPiF), w1p = w1 * (1.0f / kPiF);
+  auto trial = [&](uint32_t r1, uint32_t r2, uint32_t r3, float& u) {
+    const float R1 = uni32(r1), R2 = uni32(r2), R3 = uni32(r3);
+    float t, sh;
+    if (R1 < p0) { t = w0p * R2; sh = s1; }
+    else if (R1 < p01) { t = __fmaf_rn(w01p, R2, w0p); sh = 0.0f; }
+    else { t = __fmaf_rn(1.0f - w1p, R2, w1p); sh = s0; }
+    u = __fmaf_rn(-a, cot_pi(t), xr);
+    ++iters;
+    return R3 <= __expf(sh - u * u);
+  };
+  float u;
+  if (!trial(rng.v[W_UPAR0], rng.v[W_UPAR0 + 1], rng.v[W_UPAR0 + 2], u)) {
+    uint32_t r1, r2, r3, spare, blk = 3u;
+    do {
+      rng.block(blk++, r1, r2, r3, spare);
+    } while (!trial(r1, r2, r3, u) && blk < 2u + kMaxUparTrials);
+  }
+  return UparDraw{u, iters};
+}
+
 __device__ __forceinline__ float sample_upar(float x, float a, const Rng& rng, uint32_t& iters) {
   const float sgn = (x < 0.0f) ? -1.0f : 1.0f;
   const float xr = fabsf(x);
+  if (xr > kUparThreePiece) {
+    const UparDraw d = sample_upar_far(xr, a, rng);
+    iters += d.trials;
+    return sgn * d.u;
+  }
   const float u0 = u0_rule(xr, a);
   const float w1 = atan2_pos(a, xr - u0);
   const float e0 = __expf(-u0 * u0);

@@ -112,10 +112,12 @@ def test_dda_bit_exact(ctx, orc, dims):
 
 # ------------------------------------------------------------------ samplers
 @pytest.mark.parametrize("x,a", [(0.0, 4.7e-4), (1.3, 4.7e-4), (2.5, 1e-3), (3.0, 1e-2), (6.0, 1e-3),
-                                 (-14.0, 4.7e-4)])
+                                 (-14.0, 4.7e-4), (3.5, 1e-4), (50.0, 4.7e-4), (-200.0, 1e-3)])
 def test_upar_sampler(ctx, orc, x, a):
     n = 100000
     u, it = ctx.sample_upar(x, a, n, seed=21)
+    if abs(x) >= 6.0:  # three-piece comparison function: bounded trial count in the wing
+        assert it / n < 7.0, it / n
     # distribution: Eq. 6 CDF by quadrature
     grid, cdf = A.upar_cdf_table(x, a)
     assert stats.kstest(u, lambda t: np.interp(t, grid, cdf)).pvalue > 1e-4

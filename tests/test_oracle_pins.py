@@ -113,7 +113,7 @@ def test_line_parameters(orc):
 
 # ------------------------------------------------------------------ samplers
 @pytest.mark.parametrize("a", [1e-2, 1e-3, 1e-4])
-@pytest.mark.parametrize("x", [0.0, 1.0, 2.0, 3.0, 4.0, 6.0, 10.0, -2.5])
+@pytest.mark.parametrize("x", [0.0, 1.0, 2.0, 3.0, 4.0, 6.0, 10.0, -2.5, 50.0, -200.0])
 def test_upar_distribution_matches_eq6(orc, x, a):
     n = 40000
     u, iters = orc.sample_upar(x, a, n, seed=11)
@@ -123,6 +123,17 @@ def test_upar_distribution_matches_eq6(orc, x, a):
     m = A.upar_mean(x, a)
     sd = np.std(u) / np.sqrt(n)
     assert abs(u.mean() - m) < 5 * sd + 1e-6
+
+
+def test_upar_far_wing_trials_stay_bounded(orc):
+    """Beyond |x| = 3 the comparison function has a third piece below -u1, so the expected
+    number of trials stays near 4-5 out to |x| = 1000 (two pieces need ~0.57 |x|: 9 at
+    x = 10, 115 at x = 200), while the draws still follow Eq. 6 (the KS pins above include
+    x = 50 and -200)."""
+    for a in (1e-2, 1e-3, 1e-4):
+        for x in (10.0, 50.0, 200.0, 1000.0):
+            _, it = orc.sample_upar(x, a, 20000, seed=5)
+            assert it / 20000 < 6.5, (x, a, it / 20000)
 
 
 def test_upar_degenerate_a_zero(orc):
