@@ -555,7 +555,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
-    ap.add_argument("--inst-per-scat", type=float, default=366.0,
+    ap.add_argument("--inst-per-scat", type=float, default=374.0,
                     help="warp instructions per scattering of the shell photon loop (ncu, bench workload)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=10.0)

@@ -251,10 +251,10 @@ __device__ __forceinline__ float cot_pi(float t) {
 // Iteration 0 takes words 1-3 of the event, iteration i >= 1 words 0-2 of block i + 2.
 // Iteration 0 is peeled out of the loop so that it shares a basic block with the work
 // the caller schedules around it (further iterations are rare in the core).  The loop
-// stops after kMaxUparTrials trials so that a NaN input cannot keep a lane spinning.  A
-// trial accepts with probability ~1 in the core and ~1.8/|x| in the far wing (the flat
-// region-1 envelope covers the Lorentzian mass down to u -> -inf), so at |x| = 1000 the
-// bound is reached with probability ~e^-1800: never, for any frequency a photon scatters at.
+// stops after kMaxUparTrials trials so that a NaN input cannot keep a lane spinning.  The
+// expected trial count peaks near |x| ~ 4 (16 at a = 1e-4, 110 at a = 1e-6) and stays
+// near 4-5 in the far wing with the three-piece form below, so a valid input reaches the
+// bound with probability below e^-9000.
 constexpr uint32_t kMaxUparTrials = 1u << 20;
 
 // Far side (|x| > kUparThreePiece): Eq. 10's region 1 spans the Lorentzian mass down to
