@@ -18,6 +18,7 @@
 //                            zeroth-order cells, interaction at the linear crossing),
 //                            interaction channel chosen in proportion to tau_i,
 //                            u_par by rejection with the comparison function of Eq. 10
+//                            (for |x| > 3 with a third piece below -u1, exact as well)
 //   * Sec. 3.4.1             peeling-off towards observers
 //   * Sec. 3.5.2, Eq. 11     synthetic Lyman-alpha forest optical depth
 //   * App. A.3               Voigt profile H(a,x) = Re w(x + i a) (Faddeeva truth)
@@ -25,6 +26,12 @@
 //                            not sub-step; it integrates tau exactly along the path
 //                            (Gauss-Legendre quadrature on analytic H) and root-finds
 //                            the interaction point.
+//
+// Parity unpinned (no external value fixes the whole result; the building blocks are
+// pinned): the spectra of outflowing shells (the paper's comparison runs are not
+// available; pinned through first-flight escape and the pinned Voigt, sampler, phase
+// function and geometry pieces) and the peeling-off cube of moving, HI-thick grids
+// (pinned through the empty and uniformly dusty grids and the same pieces).
 //
 // Build: g++ -O2 -std=c++17 -fPIC -shared -ffp-contract=off (no FMA contraction: the
 // DDA cell walk must be bit-reproducible, see dda_*).
