@@ -233,7 +233,8 @@ def run_shell_bench(args):
         r = step(args.warmup + args.steps + i, device_out=False)
         e2e_ms += (time.perf_counter() - t0) * 1000.0
         e2e_scat += r.stats["n_scat"]
-    e2e_value = sum_over_ranks(float(e2e_scat), world) / (max_over_ranks(e2e_ms, world) / 1000.0)
+    e2e_t = max_over_ranks(e2e_ms, world)
+    e2e_value = sum_over_ranks(float(e2e_scat), world) / (e2e_t / 1000.0) if args.e2e_steps > 0 else None
 
     if rank != 0:
         if world > 1:
@@ -248,6 +249,9 @@ def run_shell_bench(args):
     # workload (ncu smsp__inst_executed.sum / n_scat, profiles/shell_run_kernel_expanding_shell.md)
     peak_issue = 152 * 4 * sm_max * 1e6
     inst_per_scat = args.inst_per_scat
+    # DRAM bytes of one bench launch of the shell kernel (ncu dram__bytes_read.sum +
+    # dram__bytes_write.sum, one capture of the timed step; code, constants and tallies)
+    launch_dram_bytes = 858112 + 0
     achieved = (n_scat / args.steps) * inst_per_scat / (kern_avg_ms / 1000.0)
     line = {
         "metric": METRIC, "value": value, "unit": "scatterings/s", "n_gpus": world, "steps": args.steps,
@@ -260,7 +264,7 @@ def run_shell_bench(args):
                 "d2h_bytes_per_step": (RUN["n_bins"] + 2) * 8 + 96},
         "gpu_launches": launches,
         "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_issue / 1e9,
-                     "unit": "Gwarp-inst/s", "frac": achieved / peak_issue, "traffic": None,
+                     "unit": "Gwarp-inst/s", "frac": achieved / peak_issue, "traffic": launch_dram_bytes,
                      "per_unit": f"{inst_per_scat:g} warp instructions per scattering (ncu)",
                      "peak_source": f"152 SMs x 4 schedulers x {sm_max:.0f} MHz (max SM clock of measured peaks)"},
         "clocks": clk.summary(),
