@@ -127,7 +127,7 @@ def lib():
             L.orc_run_grid.argtypes = [P(C.c_float)] * 6 + [P(GridRun), C.c_uint64, C.c_uint64,
                                                              C.c_uint64, C.c_int32, P(C.c_uint64),
                                                              P(C.c_double), P(Result), P(C.c_double),
-                                                             P(C.c_uint64), P(C.c_uint8)]
+                                                             P(C.c_uint64), P(C.c_uint8), P(C.c_double)]
             L.orc_forest.restype = C.c_int
             L.orc_forest.argtypes = [P(C.c_float)] * 3 + [C.c_int32] * 3 + [P(C.c_int32), P(C.c_int32),
                                                                             C.c_int32, C.c_double,
@@ -333,16 +333,17 @@ def run_grid(fields: dict, *, cell_cm, n_photons, seed, first_id=0, phase="dipol
     rX = np.zeros(n_photons) if raw else None
     rn = np.zeros(n_photons, np.uint64) if raw else None
     rs = np.zeros(n_photons, np.uint8) if raw else None
+    rk = np.zeros((n_photons, 3)) if raw else None
     lib().orc_run_grid(*[_p(a, C.c_float) for a in arrs], C.byref(run), first_id, n_photons, seed,
                        n_threads, _p(spec, C.c_uint64), _p(cube, C.c_double) if peel else None,
                        C.byref(res), _p(rX, C.c_double) if raw else None, _p(rn, C.c_uint64) if raw else None,
-                       _p(rs, C.c_uint8) if raw else None)
+                       _p(rs, C.c_uint8) if raw else None, _p(rk, C.c_double) if raw else None)
     out = {"counts": spec[:n_bins], "underflow": int(spec[n_bins]), "overflow": int(spec[n_bins + 1]),
            "cube": cube, "n_escaped": res.n_escaped, "n_absorbed": res.n_absorbed,
            "n_capped": res.n_capped, "sum_scat": res.sum_scat, "sum_scat2": res.sum_scat2,
            "sum_dust_scat": res.sum_dust_scat}
     if raw:
-        out.update(X=rX, nscat=rn, status=rs)
+        out.update(X=rX, nscat=rn, status=rs, k=rk)
     return out
 
 

@@ -30,8 +30,7 @@
 // Parity unpinned (no external value fixes the whole result; the building blocks are
 // pinned): the spectra of outflowing shells (the paper's comparison runs are not
 // available; pinned through first-flight escape and the pinned Voigt, sampler, phase
-// function and geometry pieces) and the peeling-off cube of moving, HI-thick grids
-// (pinned through the empty and uniformly dusty grids and the same pieces).
+// function and geometry pieces).
 //
 // Build: g++ -O2 -std=c++17 -fPIC -shared -ffp-contract=off (no FMA contraction: the
 // DDA cell walk must be bit-reproducible, see dda_*).
@@ -1295,7 +1294,7 @@ void peel_tau(const GridModel& g, const double p[3], int axis, double Xp, double
 extern "C" int orc_run_grid(const float* nHI, const float* T, const float* vx, const float* vy, const float* vz,
                  const float* kd, const orc_grid_run* run, uint64_t first_id, uint64_t n, uint64_t seed,
                  int32_t n_threads, uint64_t* spec_counts, double* cube, orc_result* res, double* raw_X,
-                 uint64_t* raw_nscat, uint8_t* raw_status) {
+                 uint64_t* raw_nscat, uint8_t* raw_status, double* raw_k) {
   GridModel g;
   for (int a = 0; a < 3; ++a) g.n[a] = run->dims[a];
   int64_t nc = (int64_t)g.n[0] * g.n[1] * g.n[2];
@@ -1465,6 +1464,8 @@ extern "C" int orc_run_grid(const float* nHI, const float* T, const float* vx, c
       raw_nscat[i] = nscat;
       raw_status[i] = (uint8_t)status;
     }
+    if (raw_k)  // optional: final direction (the escape direction of escaped photons)
+      for (int a = 0; a < 3; ++a) raw_k[3 * i + a] = k[a];
   });
   std::memset(res, 0, sizeof(orc_result));
   if (spec_counts) std::memset(spec_counts, 0, sizeof(uint64_t) * (size_t)(nb + 2));

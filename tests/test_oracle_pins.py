@@ -390,6 +390,64 @@ def test_grid_raw_records_thermal_emission(orc):
     assert r["nscat"].sum() == r["sum_scat"]
 
 
+def test_peel_off_matches_direct_escape_counts(orc):
+    """Peeling-off (Sec. 3.4.1) is an unbiased estimator of the escaping flux per steradian
+    towards each observer, in any medium: in a moving, HI-opaque grid (line-centre depth 2
+    per cell, random 20 km/s velocities, dipole scattering) its total towards +x, +y, +z
+    must equal the count of photons escaping within a cone about those axes per unit solid
+    angle.  A cube's projected area has a cusp (a minimum) along each face normal, so the
+    cone count is biased high in proportion to the cone's opening angle; it is fitted
+    linearly in the angle over six cones and extrapolated to zero."""
+    sig0 = orc.line_params(1e4)["sigma0"]
+    rng = np.random.default_rng(7)
+    s = (8, 8, 8)
+    f = {"n_HI": np.full(s, 2.0 / (sig0 * 3.086e20), np.float32), "T": np.full(s, 1e4, np.float32),
+         "vx": rng.normal(0, 20, s).astype(np.float32), "vy": rng.normal(0, 20, s).astype(np.float32),
+         "vz": rng.normal(0, 20, s).astype(np.float32), "kd": np.zeros(s, np.float32)}
+    n = 1_000_000
+    r = orc.run_grid(f, cell_cm=3.086e20, n_photons=n, seed=3, n_bins=8, img_nx=4, X_min=-4000, X_max=4000,
+                     peel=True, phase="dipole", raw=True)
+    assert r["sum_scat"] / n > 2.0  # the scattering peels dominate the emission peels
+    peel = np.mean([r["cube"][ax].sum() / n for ax in range(3)])
+    k = r["k"][r["status"] == 1]
+    th, est, err = [], [], []
+    for c in (0.995, 0.99, 0.98, 0.96, 0.93, 0.9):
+        cnt = sum(int((k[:, ax] > c).sum()) for ax in range(3))
+        om = 2 * np.pi * (1 - c)
+        th.append(np.arccos(c)); est.append(cnt / (3 * n * om)); err.append(np.sqrt(cnt) / (3 * n * om))
+    A = np.vstack([np.ones(len(th)), th]).T / np.array(err)[:, None]
+    coef = np.linalg.lstsq(A, np.array(est) / np.array(err), rcond=None)[0]
+    sd = np.sqrt(np.linalg.inv(A.T @ A)[0, 0])
+    assert abs(peel - coef[0]) < 4 * sd, (peel, coef[0], sd)
+    assert coef[1] > 0  # the cusp: the cone count grows with the opening angle
+
+
+def test_peel_off_spectra_follow_the_bulk_flow(orc):
+    """Galilean invariance of the peeled spectra (no recoil, Eq. 7): in a uniform cube that
+    moves at V along x, the gas-frame problem is the same towards +x, +y and +z (the cube's
+    symmetry), and lab frequencies are gas-frame ones plus v . k_obs, so the spectrum peeled
+    towards +x is the one towards +y shifted by exactly +V, with the same total and width."""
+    sig0 = orc.line_params(1e4)["sigma0"]
+    s = (8, 8, 8)
+    z = np.zeros(s, np.float32)
+    V = 40.0
+    f = {"n_HI": np.full(s, 2.0 / (sig0 * 3.086e20), np.float32), "T": np.full(s, 1e4, np.float32),
+         "vx": np.full(s, V, np.float32), "vy": z, "vz": z, "kd": z}
+    n = 200_000
+    r = orc.run_grid(f, cell_cm=3.086e20, n_photons=n, seed=4, n_bins=600, img_nx=4, X_min=-300, X_max=300,
+                     peel=True, phase="dipole")
+    assert r["sum_scat"] / n > 2.0
+    edges = np.linspace(-300, 300, 601)
+    c = 0.5 * (edges[1:] + edges[:-1])
+    sp = r["cube"].sum(axis=(1, 2))
+    tot = sp.sum(axis=1)
+    mean = (sp * c).sum(axis=1) / tot
+    width = np.sqrt((sp * c ** 2).sum(axis=1) / tot - mean ** 2)
+    assert abs(mean[0] - mean[1] - V) < 0.5 and abs(mean[1]) < 0.5 and abs(mean[2]) < 0.5, mean
+    assert np.all(np.abs(tot / tot.mean() - 1) < 0.02), tot
+    assert np.all(np.abs(width / width.mean() - 1) < 0.02), width
+
+
 def test_peel_dust_attenuation(orc):
     # uniform absorbing dust, no HI opacity: E[exp(-k (L - z))] = (1 - exp(-k L)) / (k L)
     L, n = 8, 6000
