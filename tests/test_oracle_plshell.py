@@ -113,3 +113,28 @@ def test_mgii_first_flight_escape(orc, where):
     p = np.exp(-tau)
     f = float(np.mean(r["nscat"] == 0))
     assert abs(f - p) < 4 * np.sqrt(max(p * (1 - p), 1e-9) / n) + 1e-9, (where, f, p, tau)
+
+
+def test_power_law_first_flight_escape(orc):
+    """A monochromatic central source in a power-law shell (n ~ r^-1, v ~ r^0.5, dust
+    following the gas): the fraction of photons that escape without any interaction is
+    exp(-tau_HI(X0) - tau_d), with tau_HI = int k(r) H(a, (X0 - v(r)) / v_th) dr along the
+    radial ray, by scipy quadrature of the shell's profiles and scipy's Faddeeva function."""
+    from scipy.special import wofz
+    lp = orc.line_params(1e4)
+    kw = dict(dv_ratio=5.0, N_HI=3e14, T=1e4, v_avg=150.0, alpha_rho=-1.0, alpha_v=0.5)
+    tau_d, n = 0.3, 20000
+
+    def tau_hi(X0):
+        def f(r):
+            k, v = orc.plshell_profile(r=r, **kw)
+            return k * wofz((X0 - v) / lp["vth_kms"] + 1j * lp["a"]).real
+        return integrate.quad(f, 1.0 / kw["dv_ratio"], 1.0, limit=400, epsabs=0, epsrel=1e-9)[0]
+
+    for X0 in (100.0, 120.0, 160.0, 200.0, 240.0):
+        t = tau_hi(X0)
+        r = orc.run_plshell(**kw, tau_dust=tau_d, phase="dipole", sigma=1e-4, ew=1.0, C_cont=0.0, X0=X0,
+                            n_photons=n, seed=13)
+        f = float(np.mean((r["status"] == 1) & (r["nscat"] == 0)))
+        p = np.exp(-t - tau_d)
+        assert abs(f - p) < 4 * np.sqrt(p * (1 - p) / n), (X0, t, f, p)
