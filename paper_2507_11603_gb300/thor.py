@@ -190,6 +190,30 @@ def _ptr(x):
     raise TypeError("expected a numpy array or a torch tensor")
 
 
+def _arr(x, name, dtype, shape=None):
+    """An array argument checked before its pointer reaches the C ABI, which trusts the
+    sizes it derives from dims and counts: host numpy arrays are converted to a contiguous
+    array of `dtype`; tensors must already have that element type and be contiguous (a
+    device tensor is never copied here); `shape`, when given, must match exactly."""
+    if isinstance(x, np.ndarray):
+        x = np.ascontiguousarray(x, dtype=dtype)
+    else:
+        try:
+            import torch
+        except ImportError as e:  # pragma: no cover
+            raise TypeError(f"{name}: expected a numpy array or a torch tensor") from e
+        if not isinstance(x, torch.Tensor):
+            raise TypeError(f"{name}: expected a numpy array or a torch tensor")
+        want = {np.dtype(np.float32): torch.float32, np.dtype(np.uint8): torch.uint8}[np.dtype(dtype)]
+        if x.dtype != want:
+            raise TypeError(f"{name}: expected {want}, got {x.dtype}")
+        if not x.is_contiguous():
+            raise ValueError(f"{name}: tensor must be contiguous")
+    if shape is not None and tuple(x.shape) != tuple(shape):
+        raise ValueError(f"{name}: shape {tuple(x.shape)}, expected {tuple(shape)}")
+    return x
+
+
 def _same_kind(*arrs):
     kinds = {_ptr(a)[1] for a in arrs if a is not None}
     if len(kinds) > 1:
@@ -266,8 +290,15 @@ class Context:
 
     def grid(self, n_HI, T, v, dust, cell_cm, phase="dipole", albedo=0.32, g_hg=0.73):
         """Fields of shape (nz, ny, nx); v of shape (3, nz, ny, nx) (vx, vy, vz)."""
+        n_HI = _arr(n_HI, "n_HI", np.float32)
+        if len(n_HI.shape) != 3:
+            raise ValueError("n_HI must have shape (nz, ny, nx)")
+        shape = tuple(n_HI.shape)
+        T = _arr(T, "T", np.float32, shape)
+        v = _arr(v, "v", np.float32, (3,) + shape)
+        dust = None if dust is None else _arr(dust, "dust", np.float32, shape)
         kind = _same_kind(n_HI, T, v, dust)
-        nz, ny, nx = n_HI.shape
+        nz, ny, nx = shape
         dims = (C.c_int32 * 3)(nx, ny, nz)
         g = C.c_void_p()
         self._check(self.L.thor_grid_create(self.h, _ptr(n_HI)[0], _ptr(T)[0], _ptr(v)[0], _ptr(dust)[0], dims,
@@ -324,8 +355,14 @@ class Context:
         """thor_reweight: spectra of the escaped photons for each target (sigma, ew, C, tau_d),
         reweighted from the sampled intrinsic spectrum sample = (sigma, ew, C); shape
         (n_targets, n_bins + 2), sum of weights per bin / n."""
-        kind = _same_kind(X0, X, col, status)
+        X0 = _arr(X0, "X0", np.float32)
+        if len(X0.shape) != 1:
+            raise ValueError("X0 must be one-dimensional")
         n = int(X0.shape[0])
+        X = _arr(X, "X", np.float32, (n,))
+        col = _arr(col, "col", np.float32, (n,))
+        status = _arr(status, "status", np.uint8, (n,))
+        kind = _same_kind(X0, X, col, status)
         smp = (C.c_double * 3)(*[float(v) for v in sample])
         tg = np.ascontiguousarray(np.asarray(targets, dtype=np.float64).reshape(-1, 4))
         out = np.zeros((tg.shape[0], n_bins + 2))
@@ -335,8 +372,14 @@ class Context:
         return out
 
     def forest(self, n_HI, T, v_los, *, ds_cm, dv_cell, n_bins, dv_bin, first=0, count=None, out=None):
+        n_HI = _arr(n_HI, "n_HI", np.float32)
+        if len(n_HI.shape) != 3:
+            raise ValueError("n_HI must have shape (nz, ny, nx)")
+        shape = tuple(n_HI.shape)
+        T = _arr(T, "T", np.float32, shape)
+        v_los = _arr(v_los, "v_los", np.float32, shape)
         kind = _same_kind(n_HI, T, v_los)
-        nz, ny, nx = n_HI.shape
+        nz, ny, nx = shape
         count = nx * ny - first if count is None else count
         if out is None:
             if kind == MEM_DEVICE:
@@ -344,6 +387,14 @@ class Context:
                 out = torch.empty((count, n_bins), dtype=torch.float32, device=n_HI.device)
             else:
                 out = np.zeros((count, n_bins), np.float32)
+        elif isinstance(out, np.ndarray) and (out.dtype != np.float32 or not out.flags["C_CONTIGUOUS"]):
+            raise TypeError("out must be a C-contiguous float32 array")  # written in place: no conversion
+        else:
+            out = _arr(out, "out", np.float32, (count, n_bins))
+        if _same_kind(out) != kind:
+            raise ValueError("out must live where the fields live (host or device)")
+        if tuple(out.shape) != (count, n_bins):
+            raise ValueError(f"out: shape {tuple(out.shape)}, expected {(count, n_bins)}")
         dims = (C.c_int32 * 3)(nx, ny, nz)
         sp = ForestSpec(ds_cm, dv_cell, n_bins, 0, dv_bin, first, count)
         self._check(self.L.thor_forest(self.h, _ptr(n_HI)[0], _ptr(T)[0], _ptr(v_los)[0], dims, kind, C.byref(sp),
@@ -368,6 +419,8 @@ class Context:
         o = np.ascontiguousarray(origins, np.float64)
         d = np.ascontiguousarray(dirs, np.float32)
         n = o.shape[0]
+        if o.shape != (n, 3) or d.shape != (n, 3):
+            raise ValueError("origins and dirs must both have shape (n, 3)")
         cells = np.full((n, max_steps), -1, np.int64)
         seg = np.zeros((n, max_steps))
         cnt = np.zeros(n, np.int32)

@@ -81,3 +81,42 @@ def test_line_params_host_function():
     p = thor.line_params(1e4)
     assert abs(p["vth_kms"] - 12.845) < 1e-3
     assert abs(p["a"] - 4.718e-4) < 1e-6
+
+
+def test_binding_checks_arrays_before_the_call():
+    """The C ABI trusts the sizes it derives from dims and counts, so the binding checks
+    element types and shapes first: a short or half-precision field would otherwise be
+    read past its end on the device.  Host arrays of another float type are converted."""
+    import numpy as np
+    import torch
+    from paper_2507_11603_gb300 import thor
+    C = thor.Context  # unbound: every check below raises before the library is touched
+    f32 = np.zeros((4, 3, 2), np.float32)
+    v = np.zeros((3, 4, 3, 2), np.float32)
+    with pytest.raises(ValueError):
+        C.grid(object(), f32, f32, f32, None, 1.0)  # v without its leading axis of 3
+    with pytest.raises(ValueError):
+        C.grid(object(), f32, f32[:3], v, None, 1.0)
+    with pytest.raises(ValueError):
+        C.grid(object(), f32, f32, v, np.zeros(5, np.float32), 1.0)
+    with pytest.raises(TypeError):
+        C.grid(object(), torch.zeros((4, 3, 2), dtype=torch.float16), f32, v, None, 1.0)
+    with pytest.raises(ValueError):
+        C.forest(object(), f32, f32, np.zeros((4, 3), np.float32), ds_cm=1.0, dv_cell=1.0, n_bins=4, dv_bin=1.0)
+    with pytest.raises(TypeError):
+        C.forest(object(), f32, f32, f32, ds_cm=1.0, dv_cell=1.0, n_bins=4, dv_bin=1.0,
+                 out=np.zeros((6, 4), np.float64))
+    with pytest.raises(ValueError):
+        C.forest(object(), f32, f32, f32, ds_cm=1.0, dv_cell=1.0, n_bins=4, dv_bin=1.0,
+                 out=np.zeros((5, 4), np.float32))
+    x = np.zeros(10, np.float32)
+    with pytest.raises(ValueError):
+        C.reweight(object(), x, x[:9], x, np.zeros(10, np.uint8), sample=(1, 1, 1), targets=[1, 1, 1, 0],
+                   n_bins=4, X_min=-1, X_max=1)
+    with pytest.raises(TypeError):
+        C.reweight(object(), x, x, x, torch.zeros(10, dtype=torch.int32), sample=(1, 1, 1), targets=[1, 1, 1, 0],
+                   n_bins=4, X_min=-1, X_max=1)
+    with pytest.raises(ValueError):
+        C.dda(object(), (2, 2, 2), np.zeros((5, 3)), np.zeros((4, 3), np.float32), 8)
+    # a float64 host field is converted, not rejected
+    assert thor._arr(np.zeros((2, 2)), "x", np.float32).dtype == np.float32
