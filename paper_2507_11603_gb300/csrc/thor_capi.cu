@@ -204,6 +204,8 @@ static int fill_power_law(thor_ctx* ctx, const thor_shell_params* p, ShellModel*
 
 int thor::fill_shell_source(thor_ctx* ctx, const thor_source* src, ShellModel* m) {
   if (src->kind != 0) return ctx->fail(THOR_ERR_INVALID_ARG, "shells take source kind 0 (central point source)");
+  for (double q : {src->X0, src->sigma, src->ew, src->C})
+    if (!std::isfinite(q)) return ctx->fail(THOR_ERR_INVALID_ARG, "source parameters must be finite");
   if (!(src->sigma >= 0.0)) return ctx->fail(THOR_ERR_INVALID_ARG, "source sigma must be >= 0");
   if (!(src->C >= 0.0) || !(src->ew >= 0.0)) return ctx->fail(THOR_ERR_INVALID_ARG, "source ew and C must be >= 0");
   if (src->C > 0.0 && m->profile != THOR_PROFILE_POWER_LAW)

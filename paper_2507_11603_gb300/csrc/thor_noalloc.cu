@@ -116,7 +116,7 @@ extern "C" int thor_run_shell_noalloc(const thor_shell_params* p, const thor_sou
   if (!p || !src || !spectrum || !out) return fail(THOR_ERR_INVALID_ARG, "thor_run_shell_noalloc: NULL argument");
   if (n_photons == 0 || first_id + n_photons < first_id)
     return fail(THOR_ERR_INVALID_ARG, "thor_run_shell_noalloc: bad photon range");
-  if (src->kind != 0 || !(src->sigma >= 0.0) || src->C > 0.0)
+  if (src->kind != 0 || !(src->sigma >= 0.0) || src->C > 0.0 || !std::isfinite(src->X0) || !std::isfinite(src->sigma))
     return fail(THOR_ERR_INVALID_ARG, "thor_run_shell_noalloc: shells take a central point source (kind 0, no continuum)");
   if (n_bins <= 0 || !(X_max > X_min)) return fail(THOR_ERR_INVALID_ARG, "thor_run_shell_noalloc: bad binning");
   if (mem_kind != THOR_MEM_HOST && mem_kind != THOR_MEM_DEVICE)

@@ -51,7 +51,7 @@ def test_shell_parameters_checked_before_the_device():
     base = dict(T=1e4, tau0=1e4, n_photons=10, seed=1, n_bins=8)
     for bad in (dict(T=float("inf")), dict(T=float("nan")), dict(T=0.0), dict(tau0=float("inf")),
                 dict(v_max=float("nan")), dict(tau_dust=float("inf")), dict(R_out=float("inf")),
-                dict(tau0=1e300), dict(step_dx=float("nan"))):
+                dict(tau0=1e300), dict(step_dx=float("nan")), dict(X0=float("nan")), dict(sigma=float("inf"))):
         with pytest.raises(thor.ThorError) as e:
             thor.run_shell_noalloc(**{**base, **bad})
         assert e.value.code == thor.ERR_INVALID_ARG, bad
