@@ -515,3 +515,37 @@ def test_core_skipping_preserves_spectrum(orc):
     x0, x1 = np.abs(r0["X"]) / vt, np.abs(r1["X"]) / vt
     assert abs(x1.mean() / x0.mean() - 1) < 0.05
     assert stats.ks_2samp(x0, x1).pvalue > 1e-3
+
+
+@pytest.mark.parametrize("tau_c", [0.5, 3.0])
+def test_grid_first_flight_escape(orc, tau_c):
+    """First flight through a uniform grid that moves at a constant velocity (Sec. 3.4, zeroth-
+    order cells): a photon emitted at x ~ N(0, 1/2) in the gas frame keeps that x along its
+    ray (uniform flow), so it leaves without interacting with probability
+    E[exp(-(kappa_0 H(a, x) + kappa_d) l)], l the distance from a uniform point to the cube's
+    surface along an isotropic direction; the expectation is sampled here with numpy and
+    scipy's Faddeeva function, independently of the oracle's cell walk.  Dust absorbs
+    (albedo 0), so an escape with no HI scattering had no interaction at all."""
+    from scipy.special import wofz
+    lp = orc.line_params(1e4)
+    L, cell, tau_d = 8, 3.086e18, 0.05
+    s = (L, L, L)
+    f = {"n_HI": np.full(s, tau_c / (lp["sigma0"] * cell), np.float32), "T": np.full(s, 1e4, np.float32),
+         "vx": np.full(s, 30.0, np.float32), "vy": np.full(s, -20.0, np.float32), "vz": np.full(s, 10.0, np.float32),
+         "kd": np.full(s, tau_d / cell, np.float32)}
+    n = 200_000
+    r = orc.run_grid(f, cell_cm=cell, n_photons=n, seed=8, n_bins=8, peel=False, raw=True, albedo=0.0)
+    got = float(np.mean((r["status"] == 1) & (r["nscat"] == 0)))
+    rng = np.random.default_rng(1)
+    m = 2_000_000
+    p = rng.uniform(0, L, (m, 3))
+    mu, ph = rng.uniform(-1, 1, m), rng.uniform(0, 2 * np.pi, m)
+    st = np.sqrt(1 - mu ** 2)
+    k = np.stack([st * np.cos(ph), st * np.sin(ph), mu], 1)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        ell = np.where(k > 0, (L - p) / k, np.where(k < 0, -p / k, np.inf)).min(1)
+    x = rng.normal(0.0, np.sqrt(0.5), m)
+    e = np.exp(-(tau_c * wofz(x + 1j * lp["a"]).real + tau_d) * ell)
+    want = float(e.mean())
+    sd = np.sqrt(want * (1 - want) / n + e.var() / m)
+    assert abs(got - want) < 4 * sd, (got, want, sd)
