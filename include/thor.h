@@ -299,6 +299,9 @@ int thor_server_wait(thor_server_t s, int64_t ticket, int64_t timeout_ms, thor_r
 int thor_server_cancel(thor_server_t s, int64_t ticket);
 /* Statistics: rounds launched, photons resident per round (average). */
 int thor_server_stats(thor_server_t s, uint64_t* rounds, double* mean_resident, uint64_t* admitted);
+/* Stop the server thread (after its current round), free its device state and drop the
+ * requests that were not waited for.  No other thread may be inside a call on the same
+ * server while it runs (a waiter would be left on a destroyed object). */
 void thor_server_destroy(thor_server_t s);
 
 /* ---- diagnostics: the device building blocks, one at a time ------------------------- */
