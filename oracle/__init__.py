@@ -99,6 +99,12 @@ def lib():
             L.orc_voigt_batch.argtypes = [P(C.c_double), P(C.c_double), P(C.c_double), C.c_int64]
             L.orc_u0.restype = C.c_double
             L.orc_u0.argtypes = [C.c_double, C.c_double]
+            L.orc_u0_eq10.restype = C.c_double
+            L.orc_u0_eq10.argtypes = [C.c_double, C.c_double]
+            L.orc_eq10_mass.restype = C.c_double
+            L.orc_eq10_mass.argtypes = [C.c_double, C.c_double, C.c_double]
+            L.orc_set_upar_method.argtypes = [C.c_int]
+            L.orc_get_upar_method.restype = C.c_int
             L.orc_segment_tau.restype = C.c_double
             L.orc_segment_tau.argtypes = [C.c_double] * 7 + [P(C.c_double)]
             L.orc_sample_upar.argtypes = [C.c_double, C.c_double, C.c_uint64, C.c_int64,
@@ -110,7 +116,7 @@ def lib():
             L.orc_run_shell.argtypes = [P(Shell), P(Source), C.c_uint64, C.c_uint64, C.c_uint64,
                                         C.c_int32, C.c_double, C.c_double, C.c_uint64, C.c_int32,
                                         P(C.c_uint64), P(Result), P(C.c_double), P(C.c_uint64),
-                                        P(C.c_uint8)]
+                                        P(C.c_uint8), P(C.c_uint32)]
             L.orc_plshell_profile.argtypes = [P(PLShell), C.c_double, P(C.c_double), P(C.c_double)]
             L.orc_mgii_params.argtypes = [C.c_double, P(C.c_double)]
             L.orc_run_plshell.restype = C.c_int
@@ -127,7 +133,8 @@ def lib():
             L.orc_run_grid.argtypes = [P(C.c_float)] * 6 + [P(GridRun), C.c_uint64, C.c_uint64,
                                                              C.c_uint64, C.c_int32, P(C.c_uint64),
                                                              P(C.c_double), P(Result), P(C.c_double),
-                                                             P(C.c_uint64), P(C.c_uint8), P(C.c_double)]
+                                                             P(C.c_uint64), P(C.c_uint8), P(C.c_double),
+                                                             P(C.c_uint32)]
             L.orc_forest.restype = C.c_int
             L.orc_forest.argtypes = [P(C.c_float)] * 3 + [C.c_int32] * 3 + [P(C.c_int32), P(C.c_int32),
                                                                             C.c_int32, C.c_double,
@@ -140,6 +147,32 @@ def lib():
 
 def _p(arr, ctype):
     return arr.ctypes.data_as(C.POINTER(ctype))
+
+
+# Exact u_par samplers of the oracle (Sec. 3.4, Eq. 10).  "eq10" (the default) is the
+# two-piece comparison function as printed, with its split point chosen by minimising the
+# envelope mass; "envelope" is a three-piece variant that reads the random words exactly as
+# the CUDA sampler does, for tests that follow the same photon on both sides draw by draw.
+UPAR_SAMPLERS = {"envelope": 0, "eq10": 1}
+_sampler_lock = threading.RLock()
+
+
+class _sampler:
+    """Selects the oracle's u_par sampler for the duration of one call."""
+
+    def __init__(self, name: str):
+        if name not in UPAR_SAMPLERS:
+            raise ValueError(f"unknown u_par sampler {name!r}")
+        self.m = UPAR_SAMPLERS[name]
+
+    def __enter__(self):
+        _sampler_lock.acquire()
+        self.prev = lib().orc_get_upar_method()
+        lib().orc_set_upar_method(self.m)
+
+    def __exit__(self, *exc):
+        lib().orc_set_upar_method(self.prev)
+        _sampler_lock.release()
 
 
 # ---------------------------------------------------------------------------------
@@ -181,7 +214,18 @@ def voigt(a, x) -> np.ndarray:
 
 
 def u0_rule(x: float, a: float) -> float:
+    """Split point u0 of the three-piece ("envelope") sampler."""
     return lib().orc_u0(float(x), float(a))
+
+
+def u0_eq10(x: float, a: float) -> float:
+    """Split point u0 of the two-piece Eq. 10 sampler: the minimiser of its envelope mass."""
+    return lib().orc_u0_eq10(float(x), float(a))
+
+
+def eq10_envelope_mass(x: float, a: float, u0: float) -> float:
+    """Mass of the two-piece Eq. 10 comparison function times a."""
+    return lib().orc_eq10_mass(float(x), float(a), float(u0))
 
 
 def segment_tau(x0, gam, kap0, kapd, a, S, tau_rem=np.inf):
@@ -194,10 +238,11 @@ def segment_tau(x0, gam, kap0, kapd, a, S, tau_rem=np.inf):
 # ---------------------------------------------------------------------------------
 # Samplers (unit level)
 # ---------------------------------------------------------------------------------
-def sample_upar(x: float, a: float, n: int, seed: int = 0):
+def sample_upar(x: float, a: float, n: int, seed: int = 0, sampler: str = "eq10"):
     o = np.empty(n)
     it = C.c_uint64()
-    lib().orc_sample_upar(float(x), float(a), seed, n, _p(o, C.c_double), C.byref(it))
+    with _sampler(sampler):
+        lib().orc_sample_upar(float(x), float(a), seed, n, _p(o, C.c_double), C.byref(it))
     return o, it.value
 
 
@@ -208,11 +253,12 @@ def sample_mu(kind: str, n: int, g: float = 0.0, seed: int = 0) -> np.ndarray:
     return o
 
 
-def scatter_once(x_in: float, a: float, phase: int, n: int, seed: int = 0):
+def scatter_once(x_in: float, a: float, phase: int, n: int, seed: int = 0, sampler: str = "eq10"):
     xo = np.empty(n)
     mu = np.empty(n)
-    lib().orc_scatter_once(float(x_in), float(a), int(phase), seed, n, _p(xo, C.c_double),
-                           _p(mu, C.c_double))
+    with _sampler(sampler):
+        lib().orc_scatter_once(float(x_in), float(a), int(phase), seed, n, _p(xo, C.c_double),
+                               _p(mu, C.c_double))
     return xo, mu
 
 
@@ -225,22 +271,25 @@ PHASE = {"isotropic": 0, "dipole": 1, "mixed": 2}
 def run_shell(*, tau0, T, R_in=0.0, R_out=1.0, v_max=0.0, tau_dust=0.0, albedo=0.0, g_hg=0.73,
               phase="isotropic", geometry="shell", line="delta", X0=0.0, sigma=0.0,
               n_photons=1000, seed=0, first_id=0, n_bins=200, X_min=-500.0, X_max=500.0,
-              max_scat=0, n_threads=0, raw=False, core_skip=False):
+              max_scat=0, n_threads=0, raw=False, core_skip=False, sampler="eq10"):
     geo = Shell(0 if geometry == "shell" else 1, PHASE[phase], 1 if core_skip else 0, 0, R_in, R_out, tau0, T,
                 v_max, tau_dust, albedo, g_hg)
     src = Source(0 if line == "delta" else 1, 0, X0, sigma)
     counts = np.zeros(n_bins + 2, dtype=np.uint64)
     res = Result()
-    rx = rn = rs = None
+    rx = rn = rs = rd = None
     if raw:
         rx = np.zeros(n_photons)
         rn = np.zeros(n_photons, dtype=np.uint64)
         rs = np.zeros(n_photons, dtype=np.uint8)
-    rc = lib().orc_run_shell(C.byref(geo), C.byref(src), first_id, n_photons, seed, n_bins, X_min,
-                             X_max, max_scat, n_threads, _p(counts, C.c_uint64), C.byref(res),
-                             _p(rx, C.c_double) if raw else None,
-                             _p(rn, C.c_uint64) if raw else None,
-                             _p(rs, C.c_uint8) if raw else None)
+        rd = np.zeros(n_photons, dtype=np.uint32)
+    with _sampler(sampler):
+        rc = lib().orc_run_shell(C.byref(geo), C.byref(src), first_id, n_photons, seed, n_bins, X_min,
+                                 X_max, max_scat, n_threads, _p(counts, C.c_uint64), C.byref(res),
+                                 _p(rx, C.c_double) if raw else None,
+                                 _p(rn, C.c_uint64) if raw else None,
+                                 _p(rs, C.c_uint8) if raw else None,
+                                 _p(rd, C.c_uint32) if raw else None)
     if rc != 0:
         raise ValueError("orc_run_shell rejected its arguments")
     out = {"counts": counts[:n_bins], "underflow": int(counts[n_bins]), "overflow": int(counts[n_bins + 1]),
@@ -248,7 +297,7 @@ def run_shell(*, tau0, T, R_in=0.0, R_out=1.0, v_max=0.0, tau_dust=0.0, albedo=0
            "sum_scat": res.sum_scat, "sum_scat2": res.sum_scat2, "sum_dust_scat": res.sum_dust_scat,
            "sum_upar_iters": res.sum_upar_iters}
     if raw:
-        out.update(X=rx, nscat=rn, status=rs)
+        out.update(X=rx, nscat=rn, status=rs, ndust=rd)
     return out
 
 
@@ -270,7 +319,8 @@ def mgii_params(T):
 
 def run_plshell(*, dv_ratio, N_HI, T, v_avg, alpha_rho=0.0, alpha_v=1.0, tau_dust=0.0, phase="dipole",
                 sigma=800.0, ew=0.0, C_cont=0.0, n_photons=1000, seed=0, first_id=0, n_bins=200,
-                X_min=-2500.0, X_max=2500.0, max_scat=0, n_threads=0, species="HI", X0=0.0):
+                X_min=-2500.0, X_max=2500.0, max_scat=0, n_threads=0, species="HI", X0=0.0,
+                sampler="eq10"):
     """Power-law shell run (Sec. 5.1) with per-photon records X0, X, col (units of N_HI);
     species "MgII": the doublet, N_HI is then the Mg II column."""
     geo = PLShell(dv_ratio, N_HI, T, v_avg, alpha_rho, alpha_v, tau_dust, PHASE[phase], SPECIES[species])
@@ -280,9 +330,11 @@ def run_plshell(*, dv_ratio, N_HI, T, v_avg, alpha_rho=0.0, alpha_v=1.0, tau_dus
     x0, x, col = np.zeros(n_photons), np.zeros(n_photons), np.zeros(n_photons)
     rn = np.zeros(n_photons, dtype=np.uint64)
     rs = np.zeros(n_photons, dtype=np.uint8)
-    rc = lib().orc_run_plshell(C.byref(geo), C.byref(src), first_id, n_photons, seed, n_bins, X_min, X_max,
-                               max_scat, n_threads, _p(counts, C.c_uint64), C.byref(res), _p(x0, C.c_double),
-                               _p(x, C.c_double), _p(col, C.c_double), _p(rn, C.c_uint64), _p(rs, C.c_uint8))
+    with _sampler(sampler):
+        rc = lib().orc_run_plshell(C.byref(geo), C.byref(src), first_id, n_photons, seed, n_bins, X_min,
+                                   X_max, max_scat, n_threads, _p(counts, C.c_uint64), C.byref(res),
+                                   _p(x0, C.c_double), _p(x, C.c_double), _p(col, C.c_double),
+                                   _p(rn, C.c_uint64), _p(rs, C.c_uint8))
     if rc != 0:
         raise ValueError("orc_run_plshell rejected its arguments")
     return {"counts": counts[:n_bins], "underflow": int(counts[n_bins]), "overflow": int(counts[n_bins + 1]),
@@ -319,7 +371,7 @@ def dda_trace(dims, origins, dirs, max_steps):
 
 def run_grid(fields: dict, *, cell_cm, n_photons, seed, first_id=0, phase="dipole", albedo=0.32,
              g_hg=0.73, n_bins=256, img_nx=None, X_min=-1000.0, X_max=1000.0, peel=True,
-             max_scat=0, n_threads=0, raw=False):
+             max_scat=0, n_threads=0, raw=False, sampler="eq10"):
     nHI = np.ascontiguousarray(fields["n_HI"], dtype=np.float32)
     nz, ny, nx = nHI.shape
     arrs = [nHI] + [np.ascontiguousarray(fields[k], dtype=np.float32)
@@ -334,16 +386,19 @@ def run_grid(fields: dict, *, cell_cm, n_photons, seed, first_id=0, phase="dipol
     rn = np.zeros(n_photons, np.uint64) if raw else None
     rs = np.zeros(n_photons, np.uint8) if raw else None
     rk = np.zeros((n_photons, 3)) if raw else None
-    lib().orc_run_grid(*[_p(a, C.c_float) for a in arrs], C.byref(run), first_id, n_photons, seed,
-                       n_threads, _p(spec, C.c_uint64), _p(cube, C.c_double) if peel else None,
-                       C.byref(res), _p(rX, C.c_double) if raw else None, _p(rn, C.c_uint64) if raw else None,
-                       _p(rs, C.c_uint8) if raw else None, _p(rk, C.c_double) if raw else None)
+    rd = np.zeros(n_photons, np.uint32) if raw else None
+    with _sampler(sampler):
+        lib().orc_run_grid(*[_p(a, C.c_float) for a in arrs], C.byref(run), first_id, n_photons, seed,
+                           n_threads, _p(spec, C.c_uint64), _p(cube, C.c_double) if peel else None,
+                           C.byref(res), _p(rX, C.c_double) if raw else None,
+                           _p(rn, C.c_uint64) if raw else None, _p(rs, C.c_uint8) if raw else None,
+                           _p(rk, C.c_double) if raw else None, _p(rd, C.c_uint32) if raw else None)
     out = {"counts": spec[:n_bins], "underflow": int(spec[n_bins]), "overflow": int(spec[n_bins + 1]),
            "cube": cube, "n_escaped": res.n_escaped, "n_absorbed": res.n_absorbed,
            "n_capped": res.n_capped, "sum_scat": res.sum_scat, "sum_scat2": res.sum_scat2,
            "sum_dust_scat": res.sum_dust_scat}
     if raw:
-        out.update(X=rX, nscat=rn, status=rs, k=rk)
+        out.update(X=rX, nscat=rn, status=rs, k=rk, ndust=rd)
     return out
 
 

@@ -18,7 +18,8 @@
 //                            zeroth-order cells, interaction at the linear crossing),
 //                            interaction channel chosen in proportion to tau_i,
 //                            u_par by rejection with the comparison function of Eq. 10
-//                            (for |x| > 3 with a third piece below -u1, exact as well)
+//                            as printed (default), or with a three-piece variant that
+//                            uses the random words as the device does (same-stream tests)
 //   * Sec. 3.4.1             peeling-off towards observers
 //   * Sec. 3.5.2, Eq. 11     synthetic Lyman-alpha forest optical depth
 //   * App. A.3               Voigt profile H(a,x) = Re w(x + i a) (Faddeeva truth)
@@ -365,7 +366,7 @@ double u1_rule(double xr) {
 // envelope masses w0 e^{-u1^2}, w1 - w0, (pi - w1) e^{-u0^2}; for |x| <= kUparThreePiece,
 // w0 = 0 and this is Eq. 10 as it stands.  Negative x by symmetry.  Three draws per
 // iteration: region, alpha, acceptance.
-double sample_upar(double x, double a, Stream& rng, uint64_t* iters) {
+double sample_upar_envelope(double x, double a, Stream& rng, uint64_t* iters) {
   // iteration 0 uses words 1-3, iteration i >= 1 words 0-2 of block i + 2
   double sgn = (x < 0.0) ? -1.0 : 1.0, xr = std::fabs(x);
   double u0 = u0_rule(xr, a);
@@ -393,6 +394,89 @@ double sample_upar(double x, double a, Stream& rng, uint64_t* iters) {
       return sgn * u;
     }
   }
+}
+
+// u_par by Eq. 10 exactly as printed: two pieces and nothing else.  This is the oracle's
+// default sampler; it shares no design choice with the three-piece envelope above (no
+// third piece, no stationarity approximation, a different parameterisation), so spectra
+// computed with it check the device's sampler instead of mirroring it.
+//   theta = atan((u - x)/a) maps the Lorentzian 1/(a^2 + (x - u)^2) onto a uniform density
+//   on (-pi/2, pi/2) of total mass pi/a.  With th0 = theta(u0), 0 <= u0 <= x:
+//     piece 1 (u <= u0): envelope g1 = 1/(a^2 + (x-u)^2),          mass (th0 + pi/2)/a;
+//     piece 2 (u >  u0): envelope g2 = e^{-u0^2}/(a^2 + (x-u)^2), mass e^{-u0^2}(pi/2 - th0)/a.
+//   Both bound f(u) = e^{-u^2}/(a^2 + (x-u)^2) because e^{-u^2} <= 1 everywhere and
+//   e^{-u^2} <= e^{-u0^2} for u > u0 >= 0.  A trial picks a piece in proportion to its mass,
+//   theta uniformly on the piece's interval, u = x + a tan(theta), and accepts with
+//   f/g = e^{-u^2} (piece 1) or e^{u0^2 - u^2} (piece 2).
+// The paper leaves u0 to the implementation (the choice only sets the rejection rate); here
+// it is the point of [0, x] that minimises the envelope mass itself, found by a scan and a
+// golden-section refinement of the exact mass (no fitted or approximated rule).  The
+// expected number of trials is (envelope mass) / (pi H(a,x) / a).  Negative x by symmetry
+// (f(u; -x) = f(-u; x)).  Draws: words region, angle, acceptance of the trial (as above).
+double eq10_mass(double xr, double a, double u0) {  // envelope mass times a
+  const double th0 = std::atan((u0 - xr) / a);
+  return (th0 + 0.5 * kPi) + std::exp(-u0 * u0) * (0.5 * kPi - th0);
+}
+
+double eq10_u0(double xr, double a) {
+  if (!(xr > 0.0)) return 0.0;
+  // candidates: a fine grid (step 0.1) over [0, min(x, 6)], where the optimum lies for
+  // resonant and wing photons, and a coarse grid (step x/32) over the whole interval;
+  // the best candidate is no worse than its neighbours on its own grid, so a local
+  // minimum lies within one step of it, where golden-section search refines it
+  double ub = 0.0, mb = eq10_mass(xr, a, 0.0), h = 0.1;
+  for (int i = 1; i <= 60 && 0.1 * i <= xr; ++i) {
+    const double m = eq10_mass(xr, a, 0.1 * i);
+    if (m < mb) { mb = m; ub = 0.1 * i; h = 0.1; }
+  }
+  for (int j = 1; j <= 32; ++j) {
+    const double m = eq10_mass(xr, a, xr * j / 32.0);
+    if (m < mb) { mb = m; ub = xr * j / 32.0; h = xr / 32.0; }
+  }
+  double lo = std::max(0.0, ub - h), hi = std::min(xr, ub + h);
+  const double r = 0.6180339887498949;  // golden ratio conjugate
+  double p = hi - r * (hi - lo), q = lo + r * (hi - lo);
+  double fp = eq10_mass(xr, a, p), fq = eq10_mass(xr, a, q);
+  for (int it = 0; it < 32; ++it) {
+    if (fp < fq) { hi = q; q = p; fq = fp; p = hi - r * (hi - lo); fp = eq10_mass(xr, a, p); }
+    else { lo = p; p = q; fp = fq; q = lo + r * (hi - lo); fq = eq10_mass(xr, a, q); }
+  }
+  const double u = 0.5 * (lo + hi);
+  return (eq10_mass(xr, a, u) <= mb) ? u : ub;
+}
+
+double sample_upar_eq10(double x, double a, Stream& rng, uint64_t* iters) {
+  const double sgn = (x < 0.0) ? -1.0 : 1.0, xr = std::fabs(x);
+  if (!(a > 0.0)) {  // a -> 0: the Lorentzian is a delta at u = x
+    if (iters) *iters += 1;
+    return x;
+  }
+  const double u0 = eq10_u0(xr, a);
+  const double th0 = std::atan((u0 - xr) / a);
+  const double e0 = std::exp(-u0 * u0);
+  const double m1 = th0 + 0.5 * kPi, m2 = e0 * (0.5 * kPi - th0);
+  const double p1 = m1 / (m1 + m2);
+  for (uint64_t it = 1;; ++it) {
+    const uint32_t w = (it == 1) ? (uint32_t)W_UPAR0 : 4u * (uint32_t)(it + 1);
+    const double Rp = rng.u(w), Ra = rng.u(w + 1), Racc = rng.u(w + 2);
+    double th, bound;
+    if (Rp < p1) { th = -0.5 * kPi + m1 * Ra; bound = 1.0; }
+    else { th = th0 + (0.5 * kPi - th0) * Ra; bound = e0; }
+    const double u = xr + a * std::tan(th);
+    if (Racc * bound <= std::exp(-u * u)) {
+      if (iters) *iters += it;
+      return sgn * u;
+    }
+  }
+}
+
+// Which exact sampler the oracle uses (set by orc_set_upar_method before a run):
+// 1 = Eq. 10 as printed (default), 0 = the three-piece envelope, which consumes the same
+// words the same way as the device's sampler (for photon-by-photon same-stream tests).
+int g_upar_method = 1;
+
+double sample_upar(double x, double a, Stream& rng, uint64_t* iters) {
+  return (g_upar_method == 0) ? sample_upar_envelope(x, a, rng, iters) : sample_upar_eq10(x, a, rng, iters);
 }
 
 // Phase functions: mu = cos(angle between incoming and outgoing direction).
@@ -511,6 +595,11 @@ extern "C" void orc_voigt_batch(const double* a, const double* x, double* out, i
 }
 
 extern "C" double orc_u0(double x, double a) { return u0_rule(std::fabs(x), a); }
+extern "C" double orc_u0_eq10(double x, double a) { return eq10_u0(std::fabs(x), a); }
+extern "C" double orc_eq10_mass(double x, double a, double u0) { return eq10_mass(std::fabs(x), a, u0); }
+// 1: Eq. 10 as printed (default); 0: three-piece envelope with the device's word use.
+extern "C" void orc_set_upar_method(int m) { g_upar_method = (m == 0) ? 0 : 1; }
+extern "C" int orc_get_upar_method(void) { return g_upar_method; }
 
 // tau along a linear-drift segment (exposed to pin the quadrature): returns the total
 // tau over [0,S] and, if tau_rem < total, *s_star.
@@ -763,7 +852,7 @@ void parallel_photons(uint64_t n, int n_threads, F&& work) {
 extern "C" int orc_run_shell(const orc_shell* geo, const orc_source* src, uint64_t first_id, uint64_t n,
                   uint64_t seed, int32_t n_bins, double X_min, double X_max, uint64_t max_scat,
                   int32_t n_threads, uint64_t* counts, orc_result* res, double* raw_X,
-                  uint64_t* raw_nscat, uint8_t* raw_status) {
+                  uint64_t* raw_nscat, uint8_t* raw_status, uint32_t* raw_ndust) {
   if (!geo || !src || !res) return -1;
   ShellModel m = make_shell(*geo);
   if (!(m.vth > 0.0) || geo->R_out <= geo->R_in) return -1;
@@ -786,6 +875,7 @@ extern "C" int orc_run_shell(const orc_shell* geo, const orc_source* src, uint64
     if (raw_X) raw_X[i] = po.X;
     if (raw_nscat) raw_nscat[i] = po.nscat;
     if (raw_status) raw_status[i] = po.status;
+    if (raw_ndust) raw_ndust[i] = po.ndust;
   });
   std::memset(res, 0, sizeof(orc_result));
   if (counts) std::memset(counts, 0, sizeof(uint64_t) * (size_t)(n_bins + 2));
@@ -1294,7 +1384,7 @@ void peel_tau(const GridModel& g, const double p[3], int axis, double Xp, double
 extern "C" int orc_run_grid(const float* nHI, const float* T, const float* vx, const float* vy, const float* vz,
                  const float* kd, const orc_grid_run* run, uint64_t first_id, uint64_t n, uint64_t seed,
                  int32_t n_threads, uint64_t* spec_counts, double* cube, orc_result* res, double* raw_X,
-                 uint64_t* raw_nscat, uint8_t* raw_status, double* raw_k) {
+                 uint64_t* raw_nscat, uint8_t* raw_status, double* raw_k, uint32_t* raw_ndust) {
   GridModel g;
   for (int a = 0; a < 3; ++a) g.n[a] = run->dims[a];
   int64_t nc = (int64_t)g.n[0] * g.n[1] * g.n[2];
@@ -1466,6 +1556,7 @@ extern "C" int orc_run_grid(const float* nHI, const float* T, const float* vx, c
     }
     if (raw_k)  // optional: final direction (the escape direction of escaped photons)
       for (int a = 0; a < 3; ++a) raw_k[3 * i + a] = k[a];
+    if (raw_ndust) raw_ndust[i] = (uint32_t)ndust;  // optional: dust scatterings
   });
   std::memset(res, 0, sizeof(orc_result));
   if (spec_counts) std::memset(spec_counts, 0, sizeof(uint64_t) * (size_t)(nb + 2));

@@ -95,3 +95,81 @@ def upar_mean(x, a):
     num = integrate.quad(g, lo, hi, points=pts, limit=500, epsabs=0, epsrel=1e-10)[0]
     den = integrate.quad(f, lo, hi, points=pts, limit=500, epsabs=0, epsrel=1e-10)[0]
     return num / den
+
+
+# ----------------------------------------------------------------------- dust scattering
+def hg_density(mu, g):
+    """Henyey-Greenstein phase function per unit mu on [-1, 1] (Eq. 9)."""
+    return 0.5 * (1.0 - g * g) / (1.0 + g * g - 2.0 * g * mu) ** 1.5
+
+
+def dust_sphere_first_orders(kappa, g):
+    """Uniform dust sphere of radius 1 with extinction kappa per unit length (no gas
+    opacity) and a central point source.  Returns (P0, I1): P0 = exp(-kappa), the chance of
+    leaving without an interaction, and I1, the chance of leaving right after exactly one
+    interaction if that interaction always scatters (Eq. 8 with albedo 1):
+        I1 = int_0^1 kappa e^{-kappa r} int_{-1}^{1} p_HG(mu) e^{-kappa L(r, mu)} dmu dr,
+    L(r, mu) = -r mu + sqrt(1 - r^2 (1 - mu^2)) the distance to the surface from radius r
+    along a direction at cosine mu to the (radial) incoming direction."""
+    def inner(mu, r):
+        L = -r * mu + np.sqrt(max(0.0, 1.0 - r * r * (1.0 - mu * mu)))
+        return kappa * np.exp(-kappa * r) * hg_density(mu, g) * np.exp(-kappa * L)
+    I1 = integrate.dblquad(inner, 0.0, 1.0, -1.0, 1.0, epsabs=1e-12, epsrel=1e-10)[0]
+    return float(np.exp(-kappa)), float(I1)
+
+
+def _box_exit(p, k, side):
+    """Distance from points p inside [0, side]^3 along unit directions k to the box surface."""
+    with np.errstate(divide="ignore", invalid="ignore"):
+        t = np.where(k > 0, (side - p) / k, np.where(k < 0, -p / k, np.inf))
+    return t.min(axis=1)
+
+
+def _iso_dirs(u1, u2):
+    mu = 2.0 * u1 - 1.0
+    st = np.sqrt(np.maximum(0.0, 1.0 - mu * mu))
+    ph = 2.0 * np.pi * u2
+    return np.stack([st * np.cos(ph), st * np.sin(ph), mu], axis=1)
+
+
+def dust_cube_first_orders(kappa, side, g, m=20, seed=0):
+    """Uniform dust cube [0, side]^3 with extinction kappa per unit length, sources uniform
+    in the volume and isotropic.  Returns (P0, I1) as dust_sphere_first_orders does, by
+    scrambled Sobol quadrature over (position, direction) for P0 (5 dimensions) and
+    (position, direction, flight to the first interaction, scattering mu and phi) for I1
+    (8 dimensions, 2^m points).  The flight length is drawn from the exponential truncated at
+    the exit distance (weight 1 - e^{-kappa L0}), and mu uniformly on [-1, 1] with the weight
+    2 p_HG(mu), so the phase function enters only through its density."""
+    from scipy.stats import qmc
+    u = qmc.Sobol(d=5, scramble=True, seed=seed).random_base2(m)
+    p = side * u[:, :3]
+    k = _iso_dirs(u[:, 3], u[:, 4])
+    P0 = float(np.mean(np.exp(-kappa * _box_exit(p, k, side))))
+    u = qmc.Sobol(d=8, scramble=True, seed=seed + 1).random_base2(m)
+    p = side * u[:, :3]
+    k = _iso_dirs(u[:, 3], u[:, 4])
+    L0 = _box_exit(p, k, side)
+    w = -np.expm1(-kappa * L0)
+    r = -np.log1p(-u[:, 5] * w) / kappa
+    p1 = p + r[:, None] * k
+    mu = 2.0 * u[:, 6] - 1.0
+    ph = 2.0 * np.pi * u[:, 7]
+    # orthonormal pair perpendicular to k (cross products with the least aligned axis)
+    ref = np.zeros_like(k)
+    ref[np.arange(len(k)), np.argmin(np.abs(k), axis=1)] = 1.0
+    e1 = np.cross(k, ref)
+    e1 /= np.linalg.norm(e1, axis=1)[:, None]
+    e2 = np.cross(k, e1)
+    st = np.sqrt(np.maximum(0.0, 1.0 - mu * mu))
+    k1 = mu[:, None] * k + st[:, None] * (np.cos(ph)[:, None] * e1 + np.sin(ph)[:, None] * e2)
+    I1 = float(np.mean(w * 2.0 * hg_density(mu, g) * np.exp(-kappa * _box_exit(p1, k1, side))))
+    return P0, I1
+
+
+def dust_event_order_probabilities(P0, I1, albedo):
+    """Chances of (dust scatterings, fate) for a photon that interacts only with dust of
+    albedo A (Eq. 8), from P0 and I1: each interaction scatters with probability A.
+    Keys: (0, 'esc'), (0, 'abs'), (1, 'esc'), (1, 'abs'), ('2+', None)."""
+    A = albedo
+    return {(0, "esc"): P0, (0, "abs"): (1.0 - A) * (1.0 - P0), (1, "esc"): A * I1,
+            (1, "abs"): A * (1.0 - A) * (1.0 - P0 - I1), ("2+", None): A * A * (1.0 - P0 - I1)}

@@ -122,7 +122,7 @@ def test_upar_sampler(ctx, orc, x, a):
     grid, cdf = A.upar_cdf_table(x, a)
     assert stats.kstest(u, lambda t: np.interp(t, grid, cdf)).pvalue > 1e-4
     # same streams as the oracle: sample-by-sample agreement except rare FP32 decision flips
-    uo, ito = orc.sample_upar(x, a, 4000, seed=21)
+    uo, ito = orc.sample_upar(x, a, 4000, seed=21, sampler="envelope")
     same = np.abs(u[:4000] - uo) <= 1e-4 * max(1.0, abs(x))
     assert same.mean() > 0.97, same.mean()
 
@@ -184,7 +184,7 @@ def test_outflow_shell_same_stream_per_photon(ctx, orc):
     r = ctx.run(g, n_photons=n, seed=7, sigma=50.0, n_bins=10, X_min=-1500, X_max=1500, raw=True, max_scat=20000)
     ro = orc.run_shell(R_in=0.9, tau0=1e20 * orc.line_params(1e4)["sigma0"], T=1e4, v_max=200.0, tau_dust=0.5,
                        phase="dipole", line="gauss", sigma=50.0, n_photons=n, seed=7, n_bins=10, X_min=-1500,
-                       X_max=1500, max_scat=20000, raw=True)
+                       X_max=1500, max_scat=20000, raw=True, sampler="envelope")
     few = ro["nscat"] < 5
     same = (r.raw_status == ro["status"]) & (r.raw_nscat.astype(np.uint64) == ro["nscat"])
     assert same[few].mean() > 0.9, same[few].mean()
@@ -322,7 +322,7 @@ def test_grid_same_stream_per_photon(ctx, orc):
     n = 4000
     r = ctx.run(g, n_photons=n, seed=12, n_bins=16, X_min=-600, X_max=600, raw=True, max_scat=20000)
     ro = orc.run_grid(of, cell_cm=cell, n_photons=n, seed=12, n_bins=16, X_min=-600, X_max=600, peel=False,
-                      max_scat=20000, raw=True)
+                      max_scat=20000, raw=True, sampler="envelope")
     few = ro["nscat"] < 5
     assert few.sum() > 200
     same = (r.raw_status == ro["status"]) & (r.raw_nscat.astype(np.uint64) == ro["nscat"])

@@ -112,17 +112,42 @@ def test_line_parameters(orc):
 
 
 # ------------------------------------------------------------------ samplers
+@pytest.mark.parametrize("sampler", ["eq10", "envelope"])
 @pytest.mark.parametrize("a", [1e-2, 1e-3, 1e-4])
 @pytest.mark.parametrize("x", [0.0, 1.0, 2.0, 3.0, 4.0, 6.0, 10.0, -2.5, 50.0, -200.0])
-def test_upar_distribution_matches_eq6(orc, x, a):
+def test_upar_distribution_matches_eq6(orc, x, a, sampler):
+    """Both exact samplers of the oracle against the Eq. 6 CDF by quadrature."""
     n = 40000
-    u, iters = orc.sample_upar(x, a, n, seed=11)
+    u, iters = orc.sample_upar(x, a, n, seed=11, sampler=sampler)
     grid, cdf = A.upar_cdf_table(x, a)
     res = stats.kstest(u, lambda t: np.interp(t, grid, cdf))
     assert res.pvalue > 1e-4, (x, a, res)
     m = A.upar_mean(x, a)
     sd = np.std(u) / np.sqrt(n)
     assert abs(u.mean() - m) < 5 * sd + 1e-6
+
+
+@pytest.mark.parametrize("a", [1e-2, 1e-4])
+@pytest.mark.parametrize("x", [0.0, 0.7, 2.0, 3.0, 4.0, -9.0, 40.0])
+def test_eq10_trial_count_matches_envelope_mass(orc, x, a):
+    """Eq. 10 as printed: the mean number of trials equals the comparison function's mass
+    over the target's, M(u0) / (pi H(a,x) / a), with H from scipy's Faddeeva function; and the
+    split point u0 is no worse than any point of a dense grid on [0, |x|]."""
+    n = 40000
+    _, it = orc.sample_upar(x, a, n, seed=13, sampler="eq10")
+    u0 = orc.u0_eq10(x, a)
+    assert 0.0 <= u0 <= abs(x)
+    M = orc.eq10_envelope_mass(x, a, u0)
+    # the mass in closed form, written out here: (theta0 + pi/2) + e^{-u0^2} (pi/2 - theta0)
+    th0 = np.arctan((u0 - abs(x)) / a)
+    assert abs(M - ((th0 + np.pi / 2) + np.exp(-u0 * u0) * (np.pi / 2 - th0))) < 1e-12 * max(1.0, M)
+    expected = M / (np.pi * A.voigt_scipy(a, x))
+    # trials are geometric with success probability 1/expected
+    sd = np.sqrt(expected * (expected - 1.0) / n) + 1e-12
+    assert abs(it / n - expected) < 5 * sd, (it / n, expected)
+    grid = np.linspace(0.0, abs(x), 4001)
+    best = min(orc.eq10_envelope_mass(x, a, g) for g in grid)
+    assert M <= best * (1 + 1e-9)
 
 
 def test_upar_far_wing_trials_stay_bounded(orc):
@@ -132,13 +157,14 @@ def test_upar_far_wing_trials_stay_bounded(orc):
     x = 50 and -200)."""
     for a in (1e-2, 1e-3, 1e-4):
         for x in (10.0, 50.0, 200.0, 1000.0):
-            _, it = orc.sample_upar(x, a, 20000, seed=5)
+            _, it = orc.sample_upar(x, a, 20000, seed=5, sampler="envelope")
             assert it / 20000 < 6.5, (x, a, it / 20000)
 
 
-def test_upar_degenerate_a_zero(orc):
+@pytest.mark.parametrize("sampler", ["eq10", "envelope"])
+def test_upar_degenerate_a_zero(orc, sampler):
     # a -> 0: the absorbing atom is exactly resonant, u_par = x
-    u, _ = orc.sample_upar(1.7, 0.0, 100, seed=1)
+    u, _ = orc.sample_upar(1.7, 0.0, 100, seed=1, sampler=sampler)
     assert np.all(u == 1.7)
 
 
