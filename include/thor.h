@@ -263,6 +263,10 @@ int thor_reweight(thor_ctx_t ctx, int64_t n, const float* X0, const float* X, co
  *    coefficient table; make that first call before any stream capture.
  *  - All calls share the array, and each call clears what must start at zero.  Calls
  *    that overlap on the GPU race on it: serialise them.
+ *  - The set-up belongs to the device's current context: after a cudaDeviceReset of a
+ *    device, do not call this entry point on that device again in the same process.
+ *  - Parameters are checked as thor_shell_create and thor_run check them (homologous
+ *    profile only), before the device is touched.
  *  - Errors: INVALID_ARG, CAPACITY, DEVICE; message in thor_noalloc_last_error(). */
 #define THOR_NOALLOC_MAX_BINS 4096
 int thor_run_shell_noalloc(const thor_shell_params* p, const thor_source* src, uint64_t first_id,

@@ -141,14 +141,14 @@ static double pow_int(double alpha, double lo, double hi) {
 static const double kMgLamK = 2796.352e-8, kMgLamH = 2803.531e-8, kMgFK = 0.608, kMgFH = 0.303;
 static const double kMgAK = 2.60e8, kMgAH = 2.57e8, kMgMass = 24.305 * 1.66053906660e-24;
 
-static int fill_power_law(thor_ctx* ctx, const thor_shell_params* p, ShellModel* m) {
+static int fill_power_law(ErrSink err, const thor_shell_params* p, ShellModel* m) {
   using namespace thor;
-  if (!(p->R_in > 0.0)) return ctx->fail(THOR_ERR_INVALID_ARG, "power-law shells need R_in > 0");
+  if (!(p->R_in > 0.0)) return err.fail(THOR_ERR_INVALID_ARG, "power-law shells need R_in > 0");
   if (p->species != THOR_SPECIES_HI && p->species != THOR_SPECIES_MGII)
-    return ctx->fail(THOR_ERR_INVALID_ARG, "unknown species");
+    return err.fail(THOR_ERR_INVALID_ARG, "unknown species");
   if (!(fabs(p->alpha_rho) <= 8.0) || !(fabs(p->alpha_v) <= 8.0))
-    return ctx->fail(THOR_ERR_INVALID_ARG, "power-law indices out of range");
-  if (p->albedo != 0.0) return ctx->fail(THOR_ERR_INVALID_ARG, "power-law shells take albedo 0 (dust absorbs)");
+    return err.fail(THOR_ERR_INVALID_ARG, "power-law indices out of range");
+  if (p->albedo != 0.0) return err.fail(THOR_ERR_INVALID_ARG, "power-law shells take albedo 0 (dust absorbs)");
   const bool mg = p->species == THOR_SPECIES_MGII;
   // thermal speed, Voigt a and line-centre cross-section of the (first) transition
   const double vth = mg ? sqrt(2.0 * 1.380649e-16 * p->T / kMgMass) * 1e-5 : line_vth_kms(p->T);
@@ -156,7 +156,7 @@ static int fill_power_law(thor_ctx* ctx, const thor_shell_params* p, ShellModel*
   const double sig_K = mg ? kMgFK * esu2_mec * kMgLamK / (vth * 1e5) : line_sigma0(p->T);
   double tau0 = p->tau0;
   if (!(tau0 > 0.0)) {
-    if (!(p->N_HI >= 0.0)) return ctx->fail(THOR_ERR_INVALID_ARG, "N_HI must be >= 0");
+    if (!(p->N_HI >= 0.0)) return err.fail(THOR_ERR_INVALID_ARG, "N_HI must be >= 0");
     tau0 = p->N_HI * sig_K;
   }
   const double ri = p->R_in / p->R_out;
@@ -198,19 +198,19 @@ static int fill_power_law(thor_ctx* ctx, const thor_shell_params* p, ShellModel*
   m->phase = p->phase;
   const double at = (double)m->a * tau0;
   m->xcrit = (p->core_skip && at >= 1.0) ? (float)(0.2 * cbrt(at)) : 0.0f;
-  if (!shell_record_finite(*m)) return ctx->fail(THOR_ERR_INVALID_ARG, "shell opacity or line parameters overflow FP32");
+  if (!shell_record_finite(*m)) return err.fail(THOR_ERR_INVALID_ARG, "shell opacity or line parameters overflow FP32");
   return THOR_OK;
 }
 
-int thor::fill_shell_source(thor_ctx* ctx, const thor_source* src, ShellModel* m) {
-  if (src->kind != 0) return ctx->fail(THOR_ERR_INVALID_ARG, "shells take source kind 0 (central point source)");
+int thor::shell_source_into_model(ErrSink err, const thor_source* src, ShellModel* m) {
+  if (src->kind != 0) return err.fail(THOR_ERR_INVALID_ARG, "shells take source kind 0 (central point source)");
   for (double q : {src->X0, src->sigma, src->ew, src->C})
-    if (!std::isfinite(q)) return ctx->fail(THOR_ERR_INVALID_ARG, "source parameters must be finite");
-  if (!(src->sigma >= 0.0)) return ctx->fail(THOR_ERR_INVALID_ARG, "source sigma must be >= 0");
-  if (!(src->C >= 0.0) || !(src->ew >= 0.0)) return ctx->fail(THOR_ERR_INVALID_ARG, "source ew and C must be >= 0");
+    if (!std::isfinite(q)) return err.fail(THOR_ERR_INVALID_ARG, "source parameters must be finite");
+  if (!(src->sigma >= 0.0)) return err.fail(THOR_ERR_INVALID_ARG, "source sigma must be >= 0");
+  if (!(src->C >= 0.0) || !(src->ew >= 0.0)) return err.fail(THOR_ERR_INVALID_ARG, "source ew and C must be >= 0");
   if (src->C > 0.0 && m->profile != THOR_PROFILE_POWER_LAW)
-    return ctx->fail(THOR_ERR_INVALID_ARG, "a continuum source needs a power-law shell");
-  if (src->C > 0.0 && !(src->sigma > 0.0)) return ctx->fail(THOR_ERR_INVALID_ARG, "a continuum source needs sigma > 0");
+    return err.fail(THOR_ERR_INVALID_ARG, "a continuum source needs a power-law shell");
+  if (src->C > 0.0 && !(src->sigma > 0.0)) return err.fail(THOR_ERR_INVALID_ARG, "a continuum source needs sigma > 0");
   m->line = (src->sigma > 0.0) ? 1 : 0;
   m->X0 = (float)src->X0;
   m->sigma = (float)src->sigma;
@@ -219,27 +219,27 @@ int thor::fill_shell_source(thor_ctx* ctx, const thor_source* src, ShellModel* m
   return THOR_OK;
 }
 
-int thor::fill_shell_model(thor_ctx* ctx, const thor_shell_params* p, ShellModel* m) {
-  if (!p) return ctx->fail(THOR_ERR_INVALID_ARG, "shell parameters are NULL");
+int thor::shell_model_from_params(ErrSink err, const thor_shell_params* p, ShellModel* m) {
+  if (!p) return err.fail(THOR_ERR_INVALID_ARG, "shell parameters are NULL");
   for (double q : {p->R_in, p->R_out, p->N_HI, p->tau0, p->T, p->v_max, p->tau_dust, p->albedo, p->g_hg, p->step_dx,
                    p->alpha_rho, p->alpha_v})
-    if (!std::isfinite(q)) return ctx->fail(THOR_ERR_INVALID_ARG, "shell parameters must be finite");
+    if (!std::isfinite(q)) return err.fail(THOR_ERR_INVALID_ARG, "shell parameters must be finite");
   if (!(p->R_out > 0.0) || !(p->R_in >= 0.0) || !(p->R_in < p->R_out))
-    return ctx->fail(THOR_ERR_INVALID_ARG, "shell radii must satisfy 0 <= R_in < R_out");
-  if (!(p->T > 0.0)) return ctx->fail(THOR_ERR_INVALID_ARG, "temperature must be > 0");
+    return err.fail(THOR_ERR_INVALID_ARG, "shell radii must satisfy 0 <= R_in < R_out");
+  if (!(p->T > 0.0)) return err.fail(THOR_ERR_INVALID_ARG, "temperature must be > 0");
   if (!(p->tau_dust >= 0.0) || !(p->albedo >= 0.0 && p->albedo <= 1.0) || !(p->g_hg > -1.0 && p->g_hg < 1.0))
-    return ctx->fail(THOR_ERR_INVALID_ARG, "dust parameters out of range");
-  if (p->phase < 0 || p->phase > 2) return ctx->fail(THOR_ERR_INVALID_ARG, "unknown phase function");
-  if (!(p->v_max >= 0.0)) return ctx->fail(THOR_ERR_INVALID_ARG, "v_max must be >= 0");
+    return err.fail(THOR_ERR_INVALID_ARG, "dust parameters out of range");
+  if (p->phase < 0 || p->phase > 2) return err.fail(THOR_ERR_INVALID_ARG, "unknown phase function");
+  if (!(p->v_max >= 0.0)) return err.fail(THOR_ERR_INVALID_ARG, "v_max must be >= 0");
   if (p->profile != THOR_PROFILE_HOMOLOGOUS && p->profile != THOR_PROFILE_POWER_LAW)
-    return ctx->fail(THOR_ERR_INVALID_ARG, "unknown density/velocity profile");
+    return err.fail(THOR_ERR_INVALID_ARG, "unknown density/velocity profile");
   if (p->profile == THOR_PROFILE_HOMOLOGOUS && p->species != THOR_SPECIES_HI)
-    return ctx->fail(THOR_ERR_INVALID_ARG, "the Mg II doublet runs on power-law shells");
-  if (p->profile == THOR_PROFILE_POWER_LAW) return fill_power_law(ctx, p, m);
+    return err.fail(THOR_ERR_INVALID_ARG, "the Mg II doublet runs on power-law shells");
+  if (p->profile == THOR_PROFILE_POWER_LAW) return fill_power_law(err, p, m);
   const double L = (p->R_out - p->R_in) / p->R_out;  // in units of R_out
   double tau0 = p->tau0;
   if (!(tau0 > 0.0)) {
-    if (!(p->N_HI >= 0.0)) return ctx->fail(THOR_ERR_INVALID_ARG, "N_HI must be >= 0");
+    if (!(p->N_HI >= 0.0)) return err.fail(THOR_ERR_INVALID_ARG, "N_HI must be >= 0");
     tau0 = p->N_HI * line_sigma0(p->T);
   }
   std::memset(m, 0, sizeof(*m));
@@ -260,8 +260,20 @@ int thor::fill_shell_model(thor_ctx* ctx, const thor_shell_params* p, ShellModel
   m->phase = p->phase;
   const double at = line_a(p->T) * tau0;
   m->xcrit = (p->core_skip && at >= 1.0) ? (float)(0.2 * cbrt(at)) : 0.0f;
-  if (!shell_record_finite(*m)) return ctx->fail(THOR_ERR_INVALID_ARG, "shell opacity or line parameters overflow FP32");
+  if (!shell_record_finite(*m)) return err.fail(THOR_ERR_INVALID_ARG, "shell opacity or line parameters overflow FP32");
   return THOR_OK;
+}
+
+int thor::fill_shell_source(thor_ctx* ctx, const thor_source* src, ShellModel* m) {
+  char msg[256] = {0};
+  const int rc = shell_source_into_model(ErrSink{msg, sizeof msg}, src, m);
+  return rc ? ctx->fail(rc, "%s", msg) : THOR_OK;
+}
+
+int thor::fill_shell_model(thor_ctx* ctx, const thor_shell_params* p, ShellModel* m) {
+  char msg[256] = {0};
+  const int rc = shell_model_from_params(ErrSink{msg, sizeof msg}, p, m);
+  return rc ? ctx->fail(rc, "%s", msg) : THOR_OK;
 }
 
 extern "C" int thor_shell_create(thor_ctx_t ctx, const thor_shell_params* p, thor_geom_t* out) {
@@ -466,7 +478,6 @@ extern "C" int thor_run(thor_ctx_t ctx, thor_geom_t g, const thor_source* src, u
   q.first_id = (const unsigned long long*)(qb + offsetof(QHost, first_id));
   q.model = (const int32_t*)(qb + offsetof(QHost, model));
   q.n_entries = 1;
-  const float dX = (float)((spec->X_max - spec->X_min) / spec->n_bins);
   int rc = THOR_OK;
   if (!grid) {
     ShellModel m = g->shell;
@@ -475,7 +486,7 @@ extern "C" int thor_run(thor_ctx_t ctx, thor_geom_t g, const thor_source* src, u
       return ctx->fail(THOR_ERR_INVALID_ARG, "raw_col is recorded on power-law shells");
     m.raw_X0 = o.raw_X0; m.raw_col = o.raw_col;
     m.X_min = (float)spec->X_min;
-    m.inv_dX = 1.0f / dX;
+    m.inv_dX = spectrum_inv_dX(spec->n_bins, spec->X_min, spec->X_max);
     m.n_bins = spec->n_bins;
     m.seed_lo = (uint32_t)seed; m.seed_hi = (uint32_t)(seed >> 32);
     m.max_scat = spec->max_scat;
@@ -564,12 +575,13 @@ extern "C" int thor_run(thor_ctx_t ctx, thor_geom_t g, const thor_source* src, u
     m.nx = g->dims[0]; m.ny = g->dims[1]; m.nz = g->dims[2];
     m.phase = g->grid_phase;
     m.albedo = (float)g->grid_albedo; m.g_hg = (float)g->grid_g;
-    m.X_min = (float)spec->X_min; m.inv_dX = 1.0f / dX; m.n_bins = spec->n_bins;
+    m.X_min = (float)spec->X_min; m.inv_dX = spectrum_inv_dX(spec->n_bins, spec->X_min, spec->X_max);
+    m.n_bins = spec->n_bins;
     m.peel = (spec->peel && o.cube) ? 1 : 0;
     m.img_n = spec->img_n; m.peel_bins = spec->peel_bins;
     if (m.peel) {
       m.pX_min = (float)spec->peel_X_min;
-      m.pinv_dX = (float)(spec->peel_bins / (spec->peel_X_max - spec->peel_X_min));
+      m.pinv_dX = spectrum_inv_dX(spec->peel_bins, spec->peel_X_min, spec->peel_X_max);
     }
     m.tau_cut = 50.0f;
     m.max_scat = spec->max_scat;

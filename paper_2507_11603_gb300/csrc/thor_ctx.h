@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cstdio>
 #include <string>
 
 #include "../../include/thor.h"
@@ -65,7 +66,23 @@ struct OutBufs {
   float* raw_X0 = nullptr;
   float* raw_col = nullptr;
 };
-// Source fields of a shell model (line, continuum); validated against the profile.
+// Where the shell checks below report: fail() writes the message into buf (truncated to
+// cap bytes) and returns the code.  Needs no context, so the allocation-free entry point
+// runs exactly the same checks as thor_shell_create and the server.
+struct ErrSink {
+  char* buf;
+  size_t cap;
+  int fail(int code, const char* msg) const {
+    if (buf && cap) std::snprintf(buf, cap, "%s", msg);
+    return code;
+  }
+};
+// Shell model record from its parameters (homologous or power-law; HI or Mg II), every
+// parameter checked; and the source fields of a shell model (line, continuum), validated
+// against the profile.
+int shell_model_from_params(ErrSink err, const thor_shell_params* p, ShellModel* m);
+int shell_source_into_model(ErrSink err, const thor_source* src, ShellModel* m);
+// The same, reporting through the context's last error.
 int fill_shell_source(thor_ctx* ctx, const thor_source* src, ShellModel* m);
 int fill_shell_model(thor_ctx* ctx, const thor_shell_params* p, ShellModel* m);
 int prepare_outputs(thor_ctx* ctx, const thor_output_spec* spec, uint64_t n_photons, bool grid, OutBufs* o);

@@ -64,6 +64,13 @@ inline bool shell_record_finite(const ShellModel& m) {
   return m.vth > 0.0f && m.a > 0.0f && (m.n_lines < 2 || m.a2 > 0.0f);
 }
 
+// Scale from a lab frequency to a spectrum bin: bin = floor((X - X_min) * inv_dX).  Every
+// path that bins photons (the single run, the served stream, the allocation-free run, the
+// peel cubes) takes it from here, so identical arguments give identical bins.
+inline float spectrum_inv_dX(int n_bins, double X_min, double X_max) {
+  return 1.0f / (float)((X_max - X_min) / n_bins);
+}
+
 // Photon work queue: photon g in [0, total) belongs to model m with
 // prefix[m] <= g < prefix[m+1] and has id first_id[m] + g - prefix[m].
 struct WorkQueue {

@@ -9,6 +9,7 @@
 // file-scope device array.  Every GPU that loads the library holds that array until
 // the process exits.  All calls share it, so calls that overlap on the GPU (two host
 // threads, or two streams) race on it and must be serialised by the caller.
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 
@@ -38,70 +39,31 @@ float* g_ktab_ptr[kMaxDevices];
 char g_err[256];
 
 int fail(int code, const char* msg) {
-  std::strncpy(g_err, msg, sizeof g_err - 1);
+  std::snprintf(g_err, sizeof g_err, "thor_run_shell_noalloc: %s", msg);
   return code;
 }
 
 // Once per device, with that device current: device addresses of the two arrays (the
-// host-side symbols are stand-ins, not device addresses) and the coefficient table.
+// host-side symbols are stand-ins, not device addresses) and the coefficient table.  The
+// cached addresses and the uploaded table belong to the device's current context; a
+// cudaDeviceReset ends it, so this entry point must not be called again on a device after
+// a reset (the table would be gone and the addresses stale).
 int setup(int dev, unsigned char** scratch, float** ktab) {
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_scratch_ptr[dev]) {
     unsigned char* s = nullptr;
     float* k = nullptr;
     if (cudaGetSymbolAddress((void**)&s, g_scratch) != cudaSuccess || !s)
-      return fail(THOR_ERR_DEVICE, "thor_run_shell_noalloc: cudaGetSymbolAddress(scratch) failed");
+      return fail(THOR_ERR_DEVICE, "cudaGetSymbolAddress(scratch) failed");
     if (cudaGetSymbolAddress((void**)&k, g_ktab) != cudaSuccess || !k)
-      return fail(THOR_ERR_DEVICE, "thor_run_shell_noalloc: cudaGetSymbolAddress(table) failed");
+      return fail(THOR_ERR_DEVICE, "cudaGetSymbolAddress(table) failed");
     if (cudaMemcpy(k, kVoigtK, sizeof(kVoigtK), cudaMemcpyHostToDevice) != cudaSuccess)
-      return fail(THOR_ERR_DEVICE, "thor_run_shell_noalloc: table upload failed");
+      return fail(THOR_ERR_DEVICE, "table upload failed");
     g_ktab_ptr[dev] = k;
     g_scratch_ptr[dev] = s;
   }
   *scratch = g_scratch_ptr[dev];
   *ktab = g_ktab_ptr[dev];
-  return THOR_OK;
-}
-
-// The shell's model record, as thor_shell_create builds it (same checks, no context).
-int model_from_params(const thor_shell_params* p, ShellModel* m) {
-  for (double q : {p->R_in, p->R_out, p->N_HI, p->tau0, p->T, p->v_max, p->tau_dust, p->albedo, p->g_hg, p->step_dx})
-    if (!std::isfinite(q)) return fail(THOR_ERR_INVALID_ARG, "thor_run_shell_noalloc: parameters must be finite");
-  if (!(p->R_out > 0.0) || !(p->R_in >= 0.0) || !(p->R_in < p->R_out))
-    return fail(THOR_ERR_INVALID_ARG, "thor_run_shell_noalloc: radii must satisfy 0 <= R_in < R_out");
-  if (!(p->T > 0.0)) return fail(THOR_ERR_INVALID_ARG, "thor_run_shell_noalloc: temperature must be > 0");
-  if (!(p->tau_dust >= 0.0) || !(p->albedo >= 0.0 && p->albedo <= 1.0) || !(p->g_hg > -1.0 && p->g_hg < 1.0))
-    return fail(THOR_ERR_INVALID_ARG, "thor_run_shell_noalloc: dust parameters out of range");
-  if (p->phase < 0 || p->phase > 2) return fail(THOR_ERR_INVALID_ARG, "thor_run_shell_noalloc: unknown phase");
-  if (!(p->v_max >= 0.0)) return fail(THOR_ERR_INVALID_ARG, "thor_run_shell_noalloc: v_max must be >= 0");
-  if (p->profile != THOR_PROFILE_HOMOLOGOUS)
-    return fail(THOR_ERR_INVALID_ARG, "thor_run_shell_noalloc: homologous shells only");
-  double tau0 = p->tau0;
-  if (!(tau0 > 0.0)) {
-    if (!(p->N_HI >= 0.0)) return fail(THOR_ERR_INVALID_ARG, "thor_run_shell_noalloc: N_HI must be >= 0");
-    tau0 = p->N_HI * line_sigma0(p->T);
-  }
-  const double L = (p->R_out - p->R_in) / p->R_out;
-  const double vth = line_vth_kms(p->T);
-  const double f = (p->step_dx > 0.0) ? p->step_dx : 0.01;
-  const double at = line_a(p->T) * tau0;
-  std::memset(m, 0, sizeof(*m));
-  m->R_in = p->R_in / p->R_out;
-  m->R_out = 1.0;
-  m->kap0 = (float)(tau0 / L);
-  m->kapd = (float)(p->tau_dust / L);
-  m->vth = (float)vth;
-  m->inv_vth = (float)(1.0 / vth);
-  m->a = (float)line_a(p->T);
-  m->vgrad = (float)p->v_max;
-  m->gam = (float)(p->v_max / vth);
-  m->ds_core = (p->v_max > 0.0) ? (float)(f * vth / p->v_max) : 1e30f;
-  m->albedo = (float)p->albedo;
-  m->g_hg = (float)p->g_hg;
-  m->phase = p->phase;
-  m->xcrit = (p->core_skip && at >= 1.0) ? (float)(0.2 * cbrt(at)) : 0.0f;
-  if (!shell_record_finite(*m))
-    return fail(THOR_ERR_INVALID_ARG, "thor_run_shell_noalloc: opacity or line parameters overflow FP32");
   return THOR_OK;
 }
 
@@ -113,22 +75,25 @@ extern "C" int thor_run_shell_noalloc(const thor_shell_params* p, const thor_sou
                                       uint64_t n_photons, uint64_t seed, int32_t n_bins, double X_min, double X_max,
                                       uint64_t* spectrum, int mem_kind, void* stream, thor_result* out) {
   g_err[0] = 0;
-  if (!p || !src || !spectrum || !out) return fail(THOR_ERR_INVALID_ARG, "thor_run_shell_noalloc: NULL argument");
+  if (!p || !src || !spectrum || !out) return fail(THOR_ERR_INVALID_ARG, "NULL argument");
   if (n_photons == 0 || first_id + n_photons < first_id)
-    return fail(THOR_ERR_INVALID_ARG, "thor_run_shell_noalloc: bad photon range");
-  if (src->kind != 0 || !(src->sigma >= 0.0) || src->C > 0.0 || !std::isfinite(src->X0) || !std::isfinite(src->sigma))
-    return fail(THOR_ERR_INVALID_ARG, "thor_run_shell_noalloc: shells take a central point source (kind 0, no continuum)");
-  if (n_bins <= 0 || !(X_max > X_min)) return fail(THOR_ERR_INVALID_ARG, "thor_run_shell_noalloc: bad binning");
+    return fail(THOR_ERR_INVALID_ARG, "bad photon range");
+  if (n_bins <= 0 || !(X_max > X_min)) return fail(THOR_ERR_INVALID_ARG, "bad binning");
   if (mem_kind != THOR_MEM_HOST && mem_kind != THOR_MEM_DEVICE)
-    return fail(THOR_ERR_INVALID_ARG, "thor_run_shell_noalloc: bad mem_kind");
+    return fail(THOR_ERR_INVALID_ARG, "bad mem_kind");
   if (mem_kind == THOR_MEM_HOST && n_bins > THOR_NOALLOC_MAX_BINS)
-    return fail(THOR_ERR_CAPACITY, "thor_run_shell_noalloc: host spectra are staged in the fixed scratch "
+    return fail(THOR_ERR_CAPACITY, "host spectra are staged in the fixed scratch "
                                    "array and may have at most THOR_NOALLOC_MAX_BINS bins");
-  ShellModel m;  // every argument is checked before the device is touched
-  if (int rc = model_from_params(p, &m)) return rc;
+  // every argument is checked before the device is touched, by the same checks as
+  // thor_shell_create and thor_run
+  ShellModel m;
+  char msg[200] = {0};
+  if (int rc = shell_model_from_params(ErrSink{msg, sizeof msg}, p, &m)) return fail(rc, msg);
+  if (p->profile != THOR_PROFILE_HOMOLOGOUS) return fail(THOR_ERR_INVALID_ARG, "homologous shells only");
+  if (int rc = shell_source_into_model(ErrSink{msg, sizeof msg}, src, &m)) return fail(rc, msg);
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
-    return fail(THOR_ERR_DEVICE, "thor_run_shell_noalloc: no current CUDA device");
+    return fail(THOR_ERR_DEVICE, "no current CUDA device");
   unsigned char* scratch = nullptr;
   float* ktab = nullptr;
   if (int rc = setup(dev, &scratch, &ktab)) return rc;
@@ -136,16 +101,10 @@ extern "C" int thor_run_shell_noalloc(const thor_shell_params* p, const thor_sou
   unsigned long long* spec = (mem_kind == THOR_MEM_DEVICE) ? (unsigned long long*)spectrum
                                                            : (unsigned long long*)(scratch + kOffSpec);
   Tally* tally = (Tally*)(scratch + kOffTally);
-  m.line = (src->sigma > 0.0) ? 1 : 0;
-  m.X0 = (float)src->X0;
-  m.sigma = (float)src->sigma;
-  m.p_line = 1.0f;
-  m.cont_C = 0.0f;
-  m.profile = THOR_PROFILE_HOMOLOGOUS;
   m.raw_X0 = nullptr;
   m.raw_col = nullptr;
   m.X_min = (float)X_min;
-  m.inv_dX = (float)(n_bins / (X_max - X_min));
+  m.inv_dX = spectrum_inv_dX(n_bins, X_min, X_max);
   m.n_bins = n_bins;
   m.seed_lo = (uint32_t)seed; m.seed_hi = (uint32_t)(seed >> 32);
   m.spectrum = spec;
@@ -166,9 +125,15 @@ extern "C" int thor_run_shell_noalloc(const thor_shell_params* p, const thor_sou
   q.first_id = (const unsigned long long*)(qb + offsetof(QHost, first_id));
   q.model = (const int32_t*)(qb + offsetof(QHost, model));
   q.n_entries = 1;
+  // launch shape of thor_run with its default block: fewer photons than lanes are spread
+  // over all warps (each then runs closer to alone)
+  const int block = 128, gsz = shell_grid(block, 0, false);
+  const unsigned long long warps = (unsigned long long)gsz * (block / 32);
+  const unsigned long long pw = (n_photons + warps - 1) / warps;
+  const int per_warp = (int)(pw < 1 ? 1 : (pw > 32 ? 32 : pw));
   if (e == cudaSuccess)
-    e = launch_shell_run((const ShellModel*)(scratch + kOffModel), q, ktab, shell_grid(128, 0, false), 128,
-                         THOR_PROFILE_HOMOLOGOUS, 32, s);
+    e = launch_shell_run((const ShellModel*)(scratch + kOffModel), q, ktab, gsz, block, THOR_PROFILE_HOMOLOGOUS,
+                         per_warp, s);
   Tally t;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&t, tally, sizeof t, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess && mem_kind == THOR_MEM_HOST)
@@ -178,6 +143,6 @@ extern "C" int thor_run_shell_noalloc(const thor_shell_params* p, const thor_sou
   std::memset(out, 0, sizeof *out);
   tally_to_result(t, n_photons, out);
   out->n_launches = 1;
-  if (t.n_done != n_photons) return fail(THOR_ERR_DEVICE, "thor_run_shell_noalloc: photon loop did not finish");
+  if (t.n_done != n_photons) return fail(THOR_ERR_DEVICE, "photon loop did not finish");
   return THOR_OK;
 }

@@ -382,7 +382,7 @@ extern "C" int thor_server_submit(thor_server_t s, const thor_shell_params* p, c
   ShellModel& m = r->model;
   if (int rc = fill_shell_source(ctx, src, &m)) { delete r; return rc; }
   m.X_min = (float)spec->X_min;
-  m.inv_dX = (float)(spec->n_bins / (spec->X_max - spec->X_min));
+  m.inv_dX = spectrum_inv_dX(spec->n_bins, spec->X_min, spec->X_max);
   m.n_bins = spec->n_bins;
   m.seed_lo = (uint32_t)seed; m.seed_hi = (uint32_t)(seed >> 32);
   m.max_scat = spec->max_scat;

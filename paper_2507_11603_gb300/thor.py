@@ -149,7 +149,8 @@ def line_params(T: float) -> dict:
 
 def run_shell_noalloc(*, T, R_in=0.0, R_out=1.0, N_HI=0.0, tau0=0.0, v_max=0.0, tau_dust=0.0, albedo=0.0,
                       g_hg=0.73, phase="isotropic", step_dx=0.0, core_skip=False, n_photons, seed, first_id=0,
-                      X0=0.0, sigma=0.0, n_bins=200, X_min=-1000.0, X_max=1000.0, spectrum=None, stream=None):
+                      X0=0.0, sigma=0.0, ew=0.0, C_cont=0.0, species="HI", n_bins=200, X_min=-1000.0,
+                      X_max=1000.0, spectrum=None, stream=None):
     """thor_run_shell_noalloc: the shell photon loop on the current CUDA device without any
     device allocation by the library (its scratch is a fixed static device array).  For
     callers that cannot allocate device memory at the time of the run.  `spectrum`: a host
@@ -157,8 +158,8 @@ def run_shell_noalloc(*, T, R_in=0.0, R_out=1.0, N_HI=0.0, tau0=0.0, v_max=0.0, 
     array when omitted); calls that overlap on the GPU must be serialised."""
     L = load()
     p = ShellParams(R_in, R_out, N_HI, tau0, T, v_max, tau_dust, albedo, g_hg, PHASE[phase],
-                    1 if core_skip else 0, step_dx)
-    src = Source(0, 0, X0, sigma)
+                    1 if core_skip else 0, step_dx, PROFILE["homologous"], SPECIES[species])
+    src = Source(0, 0, X0, sigma, ew, C_cont)
     if spectrum is None:
         spectrum = np.zeros(n_bins + 2, dtype=np.uint64)
     ptr, kind, _ = _ptr(spectrum)

@@ -45,13 +45,18 @@ def test_init_without_gpu_fails_cleanly():
 
 def test_shell_parameters_checked_before_the_device():
     """Non-finite or out-of-range shell parameters are rejected with INVALID_ARG before any
-    CUDA call (so this runs without a GPU); valid ones get as far as the device."""
+    CUDA call (so this runs without a GPU); valid ones get as far as the device.  The
+    allocation-free entry point runs the checks of thor_shell_create and thor_run: negative
+    or non-finite continuum and equivalent width, a continuum on a homologous shell, and the
+    Mg II doublet on a homologous shell are all refused."""
     import torch
     from paper_2507_11603_gb300 import thor
     base = dict(T=1e4, tau0=1e4, n_photons=10, seed=1, n_bins=8)
     for bad in (dict(T=float("inf")), dict(T=float("nan")), dict(T=0.0), dict(tau0=float("inf")),
                 dict(v_max=float("nan")), dict(tau_dust=float("inf")), dict(R_out=float("inf")),
-                dict(tau0=1e300), dict(step_dx=float("nan")), dict(X0=float("nan")), dict(sigma=float("inf"))):
+                dict(tau0=1e300), dict(step_dx=float("nan")), dict(X0=float("nan")), dict(sigma=float("inf")),
+                dict(C_cont=-1.0), dict(C_cont=float("nan")), dict(ew=-1.0), dict(ew=float("inf")),
+                dict(C_cont=100.0, sigma=50.0), dict(species="MgII")):
         with pytest.raises(thor.ThorError) as e:
             thor.run_shell_noalloc(**{**base, **bad})
         assert e.value.code == thor.ERR_INVALID_ARG, bad

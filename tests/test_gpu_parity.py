@@ -432,6 +432,21 @@ def test_server_mixed_equals_alone(ctx):
         assert np.array_equal(one.spectrum, m.spectrum) and one.stats["n_scat"] == m.stats["n_scat"]
 
 
+def test_server_bins_like_thor_run(ctx):
+    """A served request bins escaped photons exactly as thor_run does, also for binnings whose
+    FP32 scale depends on how it is formed (300 bins over [-40, 40] km/s)."""
+    srv = ctx.server(max_requests=4, events_per_round=64)
+    geo = dict(N_HI=1e17, T=1e4, v_max=20.0, tau_dust=0.0)
+    for nb, lo, hi in ((300, -40.0, 40.0), (1000, -30.0, 30.0)):
+        t = srv.submit(**geo, R_in=0.9, phase="dipole", n_photons=20000, seed=3, sigma=10.0, n_bins=nb, X_min=lo,
+                       X_max=hi)
+        m = srv.wait(t, timeout_ms=120000)
+        one = ctx.run(ctx.shell(R_in=0.9, phase="dipole", **geo), n_photons=20000, seed=3, sigma=10.0, n_bins=nb,
+                      X_min=lo, X_max=hi)
+        assert np.array_equal(one.spectrum, m.spectrum), (nb, lo, hi)
+    srv.close()
+
+
 def test_server_cancel_and_errors(ctx):
     from paper_2507_11603_gb300 import thor
     srv = ctx.server(max_requests=2, events_per_round=16)

@@ -35,6 +35,27 @@ def test_noalloc_matches_thor_run_twice():
     assert c.stats["n_scat"] == ref.stats["n_scat"]
 
 
+def test_noalloc_bins_like_thor_run():
+    """Binnings whose scale rounds differently in FP32 depending on how it is formed (300 bins
+    over [-40, 40] km/s: 3.7499998 or 3.75 per km/s): photons at bin edges land in the same
+    bins as through thor_run, twice in a row."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2507_11603_gb300 import thor
+    geo = dict(tau0=1e4, T=1e4, phase="isotropic")
+    ctx = thor.Context(0)
+    g = ctx.shell(**geo)
+    for nb, lo, hi in ((300, -40.0, 40.0), (1000, -30.0, 30.0)):
+        run = dict(n_photons=20000, seed=5, n_bins=nb, X_min=lo, X_max=hi)
+        ref = ctx.run(g, **run)
+        for _ in range(2):
+            r = thor.run_shell_noalloc(**geo, **run)
+            assert np.array_equal(r.spectrum, ref.spectrum), (nb, lo, hi)
+            assert (r.underflow, r.overflow) == (ref.underflow, ref.overflow)
+    ctx.close()
+
+
 def test_noalloc_rejects_oversized_host_spectrum():
     import torch
     if not torch.cuda.is_available():
