@@ -32,6 +32,16 @@ def chi2_dof(c1, c2):
     return float(np.sum((c1[m] - c2[m]) ** 2 / (c1[m] + c2[m])) / max(1, m.sum())), int(m.sum())
 
 
+def assert_spectrum_parity(c_gpu, c_orc, min_dof=100):
+    """chi^2/dof <= 1.2 on at least min_dof populated bins.  With k populated bins the
+    statistic's standard deviation is sqrt(2/k) about its mean of 1, so the bar sits 2 sigma
+    out at k = 100 (1 sigma at k = 25): binnings are chosen fine enough for that."""
+    c, dof = chi2_dof(c_gpu, c_orc)
+    assert dof >= min_dof, f"{dof} populated bins: too few for the chi^2/dof <= 1.2 bar"
+    assert c <= 1.2, (c, dof)
+    return c, dof
+
+
 def mean_nscat_z(r_gpu, n_gpu, r_orc, n_orc):
     m1 = r_gpu["n_scat"] / n_gpu
     v1 = r_gpu["sum_scat2"] / n_gpu - m1 ** 2
@@ -137,27 +147,32 @@ def test_single_scatter_matches_oracle(ctx, orc, phase):
 
 
 # ------------------------------------------------------------ photon loops
-def _shell_pair(ctx, orc, n, seed_gpu, seed_orc, nb, lo, hi, **geo):
+def _shell_pair(ctx, orc, n, seed_gpu, seed_orc, nb, lo, hi, raw=False, **geo):
     g = ctx.shell(**{k: v for k, v in geo.items() if k not in ("X0", "sigma", "max_scat")})
     r = ctx.run(g, n_photons=n, seed=seed_gpu, X0=geo.get("X0", 0.0), sigma=geo.get("sigma", 0.0), n_bins=nb,
-                X_min=lo, X_max=hi, max_scat=geo.get("max_scat", 0))
+                X_min=lo, X_max=hi, max_scat=geo.get("max_scat", 0), raw=raw)
     ogeo = {k: v for k, v in geo.items() if k not in ("sigma", "X0", "max_scat", "step_dx", "N_HI")}
     if "N_HI" in geo:
         ogeo["tau0"] = geo["N_HI"] * orc.line_params(geo["T"])["sigma0"]
     line = "gauss" if geo.get("sigma", 0.0) > 0 else "delta"
     ro = orc.run_shell(**ogeo, line=line, X0=geo.get("X0", 0.0), sigma=geo.get("sigma", 0.0), n_photons=n,
-                       seed=seed_orc, n_bins=nb, X_min=lo, X_max=hi, max_scat=geo.get("max_scat", 0))
+                       seed=seed_orc, n_bins=nb, X_min=lo, X_max=hi, max_scat=geo.get("max_scat", 0), raw=raw)
     return r, ro
 
 
 def test_static_sphere_tau1e4(ctx, orc):
-    """Config 1: tau0 = 1e4, T = 1e4 K, isotropic, x = 0 source, 5e3 photons, 200 bins over x in [-40, 40]."""
+    """Config 1: tau0 = 1e4, T = 1e4 K, isotropic, x = 0 source, 5e3 photons.  The config's
+    200 bins over x in [-40, 40] populate only ~40 bins (the spectrum spans |x| < 8), too few
+    for the chi^2 bar, so the spectrum is compared on bins four times finer (0.1 in x), and
+    the escape frequencies and scattering counts photon by photon by KS (unbinned)."""
     vt = orc.line_params(1e4)["vth_kms"]
-    r, ro = _shell_pair(ctx, orc, 5000, 0, 1000, 200, -40 * vt, 40 * vt, tau0=1e4, T=1e4, phase="isotropic")
-    assert r.stats["n_escaped"] == 5000 and ro["n_escaped"] == 5000
-    c, dof = chi2_dof(r.spectrum, ro["counts"])
-    assert c <= 1.2, (c, dof)
-    assert mean_nscat_z(r.stats, 5000, ro, 5000) < 3.0
+    n = 5000
+    r, ro = _shell_pair(ctx, orc, n, 0, 1000, 800, -40 * vt, 40 * vt, raw=True, tau0=1e4, T=1e4, phase="isotropic")
+    assert r.stats["n_escaped"] == n and ro["n_escaped"] == n
+    assert_spectrum_parity(r.spectrum, ro["counts"])
+    assert mean_nscat_z(r.stats, n, ro, n) < 3.0
+    assert stats.ks_2samp(np.asarray(r.raw_X, np.float64), ro["X"]).pvalue > 1e-3
+    assert stats.ks_2samp(np.asarray(r.raw_nscat, np.float64), ro["nscat"].astype(np.float64)).pvalue > 1e-3
 
 
 def test_outflow_shell_config2_subset(ctx, orc):
@@ -172,8 +187,45 @@ def test_outflow_shell_config2_subset(ctx, orc):
         p1, p2 = r.stats[k] / n, ro[k] / n
         sd = np.sqrt((p1 * (1 - p1) + p2 * (1 - p2)) / n) + 1e-12
         assert abs(p1 - p2) < 4 * sd, (k, p1, p2)
-    c, dof = chi2_dof(r.spectrum, ro["counts"])
-    assert c <= 1.2, (c, dof)
+    assert_spectrum_parity(r.spectrum, ro["counts"])
+    assert mean_nscat_z(r.stats, n, ro, n) < 3.0
+
+
+def test_config2_full_histories_against_oracle(ctx):
+    """Config 2 with every photon run to escape or absorption, as the bench runs it: the
+    photons trapped in the line core for 1e5-1e7 scatterings (FP32 offsets inside the safety
+    ball, FP32 remaining optical depth, start-point rate on short steps, fast Voigt) against
+    the FP64 oracle's uncapped run of the same workload at another seed, stored by
+    tests/golden/make_config2_golden.py.  Equal photon counts; spectrum chi^2/dof <= 1.2,
+    mean scattering count within 3 sigma, escaped / absorbed fractions within 4 sigma, and
+    the per-photon scattering counts (whole distribution and its > 1e5 tail) by KS."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "config2_full_history.json")))
+    n = gold["photons"]
+    sh = gold["shell"]
+    g = ctx.shell(R_in=sh["R_in"], N_HI=sh["N_HI"], T=sh["T"], v_max=sh["v_max"], tau_dust=sh["tau_dust"],
+                  phase=sh["phase"])
+    b = gold["bins"]
+    r = ctx.run(g, n_photons=n, seed=1, sigma=gold["source"]["sigma"], n_bins=b["n_bins"], X_min=b["X_min"],
+                X_max=b["X_max"], raw=True)
+    assert r.stats["n_capped"] == 0 and r.stats["n_escaped"] + r.stats["n_absorbed"] == n
+    for k in ("n_escaped", "n_absorbed"):
+        p1, p2 = r.stats[k] / n, gold[k] / n
+        sd = np.sqrt((p1 * (1 - p1) + p2 * (1 - p2)) / n)
+        assert abs(p1 - p2) < 4 * sd, (k, p1, p2)
+    assert_spectrum_parity(r.spectrum, gold["counts"])
+    ro = {"sum_scat": gold["sum_scat"], "sum_scat2": gold["sum_scat2"]}
+    assert mean_nscat_z(r.stats, n, ro, n) < 3.0
+    ng = np.asarray(r.raw_nscat, dtype=np.float64)
+    no = np.asarray(gold["nscat"], dtype=np.float64)
+    assert int(ng.sum()) == r.stats["n_scat"]
+    assert stats.ks_2samp(ng, no).pvalue > 1e-3
+    tg, to = ng[ng > 1e5], no[no > 1e5]
+    p1, p2 = tg.size / n, to.size / n
+    assert abs(p1 - p2) < 4 * np.sqrt((p1 * (1 - p1) + p2 * (1 - p2)) / n) + 1e-12, (tg.size, to.size)
+    assert min(tg.size, to.size) >= 20, (tg.size, to.size)
+    assert stats.ks_2samp(tg, to).pvalue > 1e-3
 
 
 def test_outflow_shell_same_stream_per_photon(ctx, orc):
@@ -267,14 +319,15 @@ def test_grid_photon_loop_and_peeling(ctx, orc):
     cell = 100 * 3.0856775814913673e18
     g = ctx.grid(f["n_HI"], f["T"], f["v"], f["kd"], cell, phase="dipole", albedo=0.32, g_hg=0.73)
     n = 20000
-    r = ctx.run(g, n_photons=n, seed=4, n_bins=64, X_min=-600, X_max=600, peel=True, img_n=8, peel_bins=64,
-                peel_X_min=-600, peel_X_max=600)
+    r = ctx.run(g, n_photons=n, seed=4, n_bins=256, X_min=-600, X_max=600, peel=True, img_n=8, peel_bins=64,
+                peel_X_min=-600, peel_X_max=600, raw=True)
     of = {"n_HI": f["n_HI"], "T": f["T"], "vx": f["v"][0], "vy": f["v"][1], "vz": f["v"][2], "kd": f["kd"]}
-    ro = orc.run_grid(of, cell_cm=cell, n_photons=n, seed=1004, n_bins=64, img_nx=8, X_min=-600, X_max=600,
-                      phase="dipole", albedo=0.32, g_hg=0.73)
-    c, dof = chi2_dof(r.spectrum, ro["counts"])
-    assert c <= 1.2, (c, dof)
+    ro = orc.run_grid(of, cell_cm=cell, n_photons=n, seed=1004, n_bins=256, img_nx=8, X_min=-600, X_max=600,
+                      phase="dipole", albedo=0.32, g_hg=0.73, raw=True)
+    assert_spectrum_parity(r.spectrum, ro["counts"])
     assert mean_nscat_z(r.stats, n, ro, n) < 3.0
+    eg, eo = np.asarray(r.raw_status) == 1, ro["status"] == 1
+    assert stats.ks_2samp(np.asarray(r.raw_X, np.float64)[eg], ro["X"][eo]).pvalue > 1e-3
     # peel cubes: per-observer spectra (collapsed over pixels) and images (collapsed over frequency)
     cg = r.cube.astype(np.float64)
     co = ro["cube"]
@@ -298,14 +351,15 @@ def test_grid_thick_cells_fast_path(ctx, orc):
     cell = 100 * 3.0856775814913673e18
     g = ctx.grid(f["n_HI"], f["T"], f["v"], f["kd"], cell, phase="dipole", albedo=0.32, g_hg=0.73)
     n = 8000
-    r = ctx.run(g, n_photons=n, seed=4, n_bins=64, X_min=-600, X_max=600, peel=True, img_n=8, peel_bins=64,
-                peel_X_min=-600, peel_X_max=600)
+    r = ctx.run(g, n_photons=n, seed=4, n_bins=256, X_min=-600, X_max=600, peel=True, img_n=8, peel_bins=64,
+                peel_X_min=-600, peel_X_max=600, raw=True)
     of = {"n_HI": f["n_HI"], "T": f["T"], "vx": f["v"][0], "vy": f["v"][1], "vz": f["v"][2], "kd": f["kd"]}
-    ro = orc.run_grid(of, cell_cm=cell, n_photons=n, seed=1004, n_bins=64, img_nx=8, X_min=-600, X_max=600,
-                      phase="dipole", albedo=0.32, g_hg=0.73)
-    c, dof = chi2_dof(r.spectrum, ro["counts"])
-    assert c <= 1.2, (c, dof)
+    ro = orc.run_grid(of, cell_cm=cell, n_photons=n, seed=1004, n_bins=256, img_nx=8, X_min=-600, X_max=600,
+                      phase="dipole", albedo=0.32, g_hg=0.73, raw=True)
+    assert_spectrum_parity(r.spectrum, ro["counts"])
     assert mean_nscat_z(r.stats, n, ro, n) < 3.0
+    eg, eo = np.asarray(r.raw_status) == 1, ro["status"] == 1
+    assert stats.ks_2samp(np.asarray(r.raw_X, np.float64)[eg], ro["X"][eo]).pvalue > 1e-3
     tot_g, tot_o = float(r.cube.astype(np.float64).sum()), float(ro["cube"].sum())
     assert abs(tot_g / tot_o - 1) < 0.05, (tot_g, tot_o)
 
@@ -512,16 +566,18 @@ def test_power_law_shell_parity(ctx, orc):
     the oracle's exact-tau transport: spectra, scattering counts, emitted X0, columns."""
     g = ctx.shell(profile="power_law", tau_dust=0.3, phase="dipole", **_SWEEP)
     n = 20000
-    kw = dict(n_bins=100, X_min=-2500.0, X_max=2500.0)
-    r = ctx.run(g, n_photons=n, seed=21, sigma=_SAMPLE[0], ew=_SAMPLE[1], C_cont=_SAMPLE[2], raw=True,
-                raw_sweep=True, **kw)
+    kw = dict(n_bins=400, X_min=-2500.0, X_max=2500.0)
+    src = dict(sigma=_SAMPLE[0], ew=_SAMPLE[1], C_cont=_SAMPLE[2], raw=True, raw_sweep=True)
     ro = orc.run_plshell(dv_ratio=5.0, N_HI=_SWEEP["N_HI"], T=1e4, v_avg=120.0, alpha_rho=-1.0, alpha_v=0.5,
                          tau_dust=0.3, phase="dipole", sigma=_SAMPLE[0], ew=_SAMPLE[1], C_cont=_SAMPLE[2],
                          n_photons=n, seed=21, **kw)
-    # emission uses the same words on both sides: X0 photon by photon
-    assert np.abs(r.raw_X0.astype(np.float64) - ro["X0"]).max() < 0.05
-    c, dof = chi2_dof(r.spectrum, ro["counts"])
-    assert c <= 1.2, (c, dof)
+    # emission uses the same words on both sides: X0 photon by photon at the oracle's seed
+    r0 = ctx.run(g, n_photons=n, seed=21, **src, **kw)
+    assert np.abs(r0.raw_X0.astype(np.float64) - ro["X0"]).max() < 0.05
+    # transport at an independent seed (at the same seed, photons that never scatter would be
+    # identical on both sides and flatter the spectrum comparison)
+    r = ctx.run(g, n_photons=n, seed=22, **src, **kw)
+    assert_spectrum_parity(r.spectrum, ro["counts"])
     assert mean_nscat_z(r.stats, n, ro, n) < 3.0
     esc_g, esc_o = r.raw_status == 1, ro["status"] == 1
     cg, co = r.raw_col[esc_g].astype(np.float64), ro["col"][esc_o]
@@ -607,15 +663,14 @@ def test_mgii_outflow_parity(ctx, orc):
     """The paper's Mg II test geometry (uniform sphere, homologous outflow, N_MgII = 10^14.5,
     T = 1e4 K) lit by a flat continuum: P Cygni profiles of both transitions, device vs oracle."""
     n = 20000
-    kw = dict(n_bins=80, X_min=-2000.0, X_max=1000.0)
+    kw = dict(n_bins=300, X_min=-2000.0, X_max=1000.0)
     g = ctx.shell(profile="power_law", species="MgII", R_in=1e-3, R_out=1.0, N_HI=10 ** 14.5, T=1e4, v_max=100.0,
                   alpha_rho=0.0, alpha_v=1.0, phase="dipole")
-    r = ctx.run(g, n_photons=n, seed=17, X0=-400.0, sigma=100.0, ew=0.0, C_cont=1400.0, **kw)
+    r = ctx.run(g, n_photons=n, seed=18, X0=-400.0, sigma=100.0, ew=0.0, C_cont=1400.0, **kw)
     ro = orc.run_plshell(dv_ratio=1000.0, N_HI=10 ** 14.5, T=1e4, v_avg=100.0, alpha_rho=0.0, alpha_v=1.0,
                          phase="dipole", sigma=100.0, ew=0.0, C_cont=1400.0, X0=-400.0, n_photons=n, seed=17,
                          species="MgII", **kw)
-    c, dof = chi2_dof(r.spectrum, ro["counts"])
-    assert c <= 1.2, (c, dof)
+    assert_spectrum_parity(r.spectrum, ro["counts"])
     assert mean_nscat_z(r.stats, n, ro, n) < 3.0
 
 
