@@ -189,52 +189,83 @@ def run_shell_bench(args):
     ctx = thor.Context(local)
     if args.block:
         ctx.set_launch(args.block, args.blocks_per_sm)
+    if args.bursts >= 0:
+        ctx.set_bursts(args.bursts)
     stream = torch.cuda.Stream()
     ctx.set_stream(stream)
     geom = ctx.shell(**SHELL)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     from paper_2507_11603_gb300 import sharding
 
-    def step(i, device_out=True):
+    def step(i, device_out=True, raw=False):
         # step i: the i-th block of world x 1e5 photon ids, rank r takes its own 1e5 (weak scaling)
         first, n = sharding.photon_range(rank, world, N_PHOTONS, base=i * world * N_PHOTONS)
-        return ctx.run(geom, n_photons=n, seed=1, first_id=first, device_out=device_out, **RUN)
+        with torch.cuda.stream(stream):  # device outputs are allocated and cleared on the run's stream
+            return ctx.run(geom, n_photons=n, seed=1, first_id=first, device_out=device_out, raw=raw, **RUN)
 
     for i in range(args.warmup):
         step(i)
+    # measured issue peaks of this device (FP32 FMA: one warp instruction per scheduler per
+    # clock; MUFU ex2), the denominators of the roofline below
+    peak_fma = ctx.issue_peak("fma")
+    peak_mufu = ctx.issue_peak("mufu")
     torch.cuda.synchronize()
     barrier(world)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     kern_ms, n_scat, launches = 0.0, 0, 0
+    step_scat, longest = [], []
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
         for i in range(args.steps):
             with torch.cuda.stream(stream):
                 flush.fill_(i & 0xFF)
             ev[i][0].record(stream)
-            r = step(args.warmup + i)
+            # per-photon records (9 B per photon, on the device) give each step's longest photon
+            r = step(args.warmup + i, raw=True)
             ev[i][1].record(stream)
             kern_ms += r.stats["elapsed_ms"]
             n_scat += r.stats["n_scat"]
+            step_scat.append(r.stats["n_scat"])
             launches += int(r.stats["n_launches"])
+            longest.append(r.raw_nscat)
         torch.cuda.synchronize()
     barrier(world)
-    step_ms = sum(a.elapsed_time(b) for a, b in ev)
+    longest = [(int(t.max().item()), int(torch.argmax(t).item())) for t in longest]
+    per_step_ms = [a.elapsed_time(b) for a, b in ev]
+    step_ms = sum(per_step_ms)
     t_max = max_over_ranks(step_ms, world)
     tot_scat = sum_over_ranks(float(n_scat), world)
     value = tot_scat / (t_max / 1000.0)
     kern_avg_ms = kern_ms / args.steps
 
-    # e2e through the public call with host buffers (copies inside the timed region)
+    # e2e through the public call with host buffers (copies inside the timed region), on the
+    # photon ids of the first e2e_steps timed steps: the same work, so e2e <= the device-timed
+    # rate of those steps shows the cost of the copies and the host call
+    n_e2e = min(args.e2e_steps, args.steps)
     e2e_ms, e2e_scat = 0.0, 0
-    for i in range(args.e2e_steps):
+    for i in range(n_e2e):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        r = step(args.warmup + args.steps + i, device_out=False)
+        r = step(args.warmup + i, device_out=False)
         e2e_ms += (time.perf_counter() - t0) * 1000.0
         e2e_scat += r.stats["n_scat"]
+        assert r.stats["n_scat"] == step_scat[i], "a photon run is deterministic"
     e2e_t = max_over_ranks(e2e_ms, world)
-    e2e_value = sum_over_ranks(float(e2e_scat), world) / (e2e_t / 1000.0) if args.e2e_steps > 0 else None
+    e2e_value = sum_over_ranks(float(e2e_scat), world) / (e2e_t / 1000.0) if n_e2e > 0 else None
+    same_ms = max_over_ranks(sum(per_step_ms[:n_e2e]), world)
+    same_value = sum_over_ranks(float(sum(step_scat[:n_e2e])), world) / (same_ms / 1000.0) if n_e2e > 0 else None
+
+    # latency of one event of a lone lane: the longest photon of the last timed step run
+    # alone for a bounded number of events (its own history, stopped at the cap)
+    ev_count, ev_pid = longest[-1]
+    first_last, _ = sharding.photon_range(rank, world, N_PHOTONS, base=(args.warmup + args.steps - 1) * world * N_PHOTONS)
+    cap = int(min(ev_count, args.lone_events))
+    with torch.cuda.stream(stream):
+        ctx.run(geom, n_photons=1, seed=1, first_id=first_last + ev_pid, max_scat=cap, device_out=True, **RUN)
+        lone = ctx.run(geom, n_photons=1, seed=1, first_id=first_last + ev_pid, max_scat=cap, device_out=True, **RUN)
+    lone_events = lone.stats["n_scat"] + lone.stats["n_dust_scat"]
+    us_per_event = lone.stats["elapsed_ms"] * 1e3 / max(lone_events, 1)
+    tail_frac = float(np.mean([c * us_per_event * 1e-3 / t for (c, _), t in zip(longest, per_step_ms)]))
 
     if rank != 0:
         if world > 1:
@@ -244,29 +275,45 @@ def run_shell_bench(args):
     pk = peaks()
     sm_max = pk.get("sm_max_mhz", 2070.0)
     # Issue roofline of the photon loop (no DRAM traffic to speak of, no dense contraction):
-    # peak = SMs x 4 schedulers x 1 warp instruction per clock x max SM clock; per-unit
-    # figure = warp instructions the kernel executes per resonant scattering on this
-    # workload (ncu smsp__inst_executed.sum / n_scat, profiles/shell_run_kernel_expanding_shell.md)
-    peak_issue = 152 * 4 * sm_max * 1e6
+    # peak = the measured FP32-FMA issue rate of this device (thor_issue_peak: one warp
+    # instruction per scheduler per clock; nominal 152 SMs x 4 x max SM clock); per-unit
+    # figures = warp and thread instructions the kernel executes per resonant scattering on
+    # this workload (ncu smsp__inst_executed.sum and smsp__thread_inst_executed.sum / n_scat)
+    peak_issue = peak_fma
     inst_per_scat = args.inst_per_scat
+    thread_inst_per_scat = args.thread_inst_per_scat
+    simt = thread_inst_per_scat / (32.0 * inst_per_scat)
     # DRAM bytes of one bench launch of the shell kernel (ncu dram__bytes_read.sum +
     # dram__bytes_write.sum, one capture of the timed step; code, constants and tallies)
-    launch_dram_bytes = 858112 + 0
+    launch_dram_bytes = args.launch_dram_bytes
     achieved = (n_scat / args.steps) * inst_per_scat / (kern_avg_ms / 1000.0)
+    lane_achieved = (n_scat / args.steps) * thread_inst_per_scat / (kern_avg_ms / 1000.0)
     line = {
         "metric": METRIC, "value": value, "unit": "scatterings/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "photons_per_step": N_PHOTONS, "l2": "flushed (256 MiB write) before each step",
                    "scatterings_per_step": n_scat / args.steps, "kernel_ms_per_step": kern_avg_ms,
-                   "launch": {"block": args.block or 128, "blocks_per_sm": args.blocks_per_sm}},
+                   "launch": {"block": args.block or 128, "blocks_per_sm": args.blocks_per_sm,
+                              "core_burst_lanes": args.bursts if args.bursts >= 0 else 4}},
         "e2e": {"value": e2e_value, "unit": "scatterings/s", "h2d_bytes_per_step": 256 + 48,
-                "d2h_bytes_per_step": (RUN["n_bins"] + 2) * 8 + 96},
+                "d2h_bytes_per_step": (RUN["n_bins"] + 2) * 8 + 96, "steps": n_e2e,
+                "photon_ids": f"those of the first {n_e2e} timed steps",
+                "device_timed_value_same_steps": same_value},
         "gpu_launches": launches,
         "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_issue / 1e9,
                      "unit": "Gwarp-inst/s", "frac": achieved / peak_issue, "traffic": launch_dram_bytes,
                      "per_unit": f"{inst_per_scat:g} warp instructions per scattering (ncu)",
-                     "peak_source": f"152 SMs x 4 schedulers x {sm_max:.0f} MHz (max SM clock of measured peaks)"},
+                     "peak_source": f"measured FP32-FMA issue rate (thor_issue_peak; nominal 152 SMs x 4 schedulers x "
+                                    f"{sm_max:.0f} MHz = {152 * 4 * sm_max * 1e-3:.1f} Gwarp-inst/s)",
+                     "mufu_peak": peak_mufu / 1e9,
+                     "simt_efficiency": simt,
+                     "lane_frac": lane_achieved / (32.0 * peak_issue),
+                     "lane_per_unit": f"{thread_inst_per_scat:g} thread instructions per scattering (ncu)",
+                     "tail": {"longest_photon_events": [c for c, _ in longest],
+                              "lone_event_us": us_per_event, "lone_events_timed": lone_events,
+                              "tail_frac": tail_frac,
+                              "what": "longest photon's events x lone-lane event latency / step time"}},
         "clocks": clk.summary(),
     }
     if args.stream_in_line > 0:
@@ -282,10 +329,12 @@ def run_shell_bench(args):
         dist.destroy_process_group()
 
 
-def stream_bench(ctx, n_requests=256, seed=2, load=0.75, events_per_round=256, nhi_max=1e21, core_skip=True):
+def stream_bench(ctx, n_requests=256, seed=2, load=0.75, events_per_round=256, nhi_max=1e21, core_skip=True,
+                 priority=True):
     """Served shell-model stream (Sec. 5.1 parameter grid): requests with Poisson arrivals at
-    `load` x the measured batched capacity, continuous batching on the device.  Baseline:
-    the same requests one launch per model (thor_run), FIFO, with the same arrival times."""
+    `load` x the measured batched capacity, continuous batching on the device.  Baseline,
+    also live: the same requests at the same arrival times served one launch per model
+    (thor_run), first come first served."""
     from paper_2507_11603_gb300 import synth
     reqs = synth.shell_stream(n_requests, seed=seed, nhi_max=nhi_max)
     common = dict(R_in=0.9, phase="dipole", sigma=50.0, n_bins=400, X_min=-1500.0, X_max=1500.0,
@@ -295,28 +344,23 @@ def stream_bench(ctx, n_requests=256, seed=2, load=0.75, events_per_round=256, n
         return srv.submit(N_HI=r["N_HI"], T=r["T"], v_max=r["v_max"], tau_dust=r["tau_dust"],
                           n_photons=r["n_photons"], seed=r["seed"], **common)
 
-    # 1) one launch per model, back to back: per-request device time and capacity
-    solo_ms, solo_scat = [], 0
-    t0 = time.perf_counter()
-    for r in reqs:
+    def one_launch(r):
         g = ctx.shell(R_in=0.9, N_HI=r["N_HI"], T=r["T"], v_max=r["v_max"], tau_dust=r["tau_dust"], phase="dipole",
                       core_skip=core_skip)
-        t1 = time.perf_counter()
         res = ctx.run(g, n_photons=r["n_photons"], seed=r["seed"], sigma=50.0, n_bins=400, X_min=-1500.0,
                       X_max=1500.0)
-        solo_ms.append((time.perf_counter() - t1) * 1000.0)
-        solo_scat += res.stats["n_scat"]
         g.close()
-    solo_total = time.perf_counter() - t0
-    # 2) batched capacity: all requests at t = 0
-    srv = ctx.server(max_requests=256, events_per_round=events_per_round)
+        return res
+
+    # 1) batched capacity: all requests at t = 0
+    srv = ctx.server(max_requests=256, events_per_round=events_per_round, priority=priority)
     t0 = time.perf_counter()
     tickets = [submit(srv, r) for r in reqs]
-    burst = [srv.wait(t) for t in tickets]
+    burst = [srv.wait(t, timeout_ms=600000) for t in tickets]
     burst_total = time.perf_counter() - t0
     burst_scat = sum(b.stats["n_scat"] for b in burst)
     capacity = n_requests / burst_total  # requests/s
-    # 3) Poisson stream at `load` x capacity, live
+    # 2) Poisson stream at `load` x capacity, continuous batching, live
     rate = load * capacity
     rng = np.random.default_rng(seed + 1000)
     arrivals = np.concatenate([[0.0], np.cumsum(rng.exponential(1.0 / rate, n_requests - 1))])
@@ -331,32 +375,41 @@ def stream_bench(ctx, n_requests=256, seed=2, load=0.75, events_per_round=256, n
         tick.append((i, submit(srv, r), time.perf_counter() - t_start))
     scat = 0
     for i, t, ts in tick:
-        res = srv.wait(t)
+        res = srv.wait(t, timeout_ms=600000)
         lat[i] = res.stats["elapsed_ms"]
         done_at[i] = ts + lat[i] / 1000.0
         scat += res.stats["n_scat"]
     span = done_at.max()
     stats = srv.stats()
     srv.close()
-    # 4) the same arrivals served by one-launch-per-model in FIFO order
-    finish, fifo_lat = 0.0, []
-    for i in range(n_requests):
-        start = max(arrivals[i], finish)
-        finish = start + solo_ms[i] / 1000.0
-        fifo_lat.append((finish - arrivals[i]) * 1000.0)
-    fifo_lat = np.array(fifo_lat)
+    # 3) the same arrivals served one launch per model, first come first served, live: a
+    # request waits for the runs of the requests before it
+    fifo_lat, solo_ms, fifo_scat = np.zeros(n_requests), np.zeros(n_requests), 0
+    t_start = time.perf_counter()
+    for i, r in enumerate(reqs):
+        now = time.perf_counter() - t_start
+        if arrivals[i] > now:
+            time.sleep(arrivals[i] - now)
+        res = one_launch(r)
+        fifo_lat[i] = (time.perf_counter() - t_start - arrivals[i]) * 1000.0
+        solo_ms[i] = res.stats["elapsed_ms"]
+        fifo_scat += res.stats["n_scat"]
+    fifo_span = time.perf_counter() - t_start
     j = int(np.argmax(lat))  # the request that sets the batched tail
     slowest = {"request": j, "N_HI": reqs[j]["N_HI"], "T": reqs[j]["T"], "v_max": reqs[j]["v_max"],
-               "photons": reqs[j]["n_photons"], "batched_ms": float(lat[j]), "one_launch_run_ms": solo_ms[j],
+               "photons": reqs[j]["n_photons"], "batched_ms": float(lat[j]), "one_launch_run_ms": float(solo_ms[j]),
                "one_launch_fifo_ms": float(fifo_lat[j])}
     return {"requests": n_requests, "slowest": slowest, "photons": int(sum(r["n_photons"] for r in reqs)),
-            "core_skip": core_skip, "N_HI_max": nhi_max, "load": load, "rate_per_s": rate,
+            "core_skip": core_skip, "N_HI_max": nhi_max, "load": load, "rate_per_s": rate, "age_priority": priority,
             "batched": {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                         "scatterings_per_s": scat / span, "burst_scatterings_per_s": burst_scat / burst_total,
-                        "rounds": stats["rounds"], "mean_resident": stats["mean_resident"]},
-            "one_launch_per_model": {"p50_ms": float(np.percentile(fifo_lat, 50)),
+                        "rounds": stats["rounds"], "mean_resident": stats["mean_resident"],
+                        "max_over_own_solo_run": float(np.max(lat / np.maximum(solo_ms, 1e-3)))},
+            "one_launch_per_model": {"kind": "live, same arrival times, first come first served",
+                                     "p50_ms": float(np.percentile(fifo_lat, 50)),
                                      "p99_ms": float(np.percentile(fifo_lat, 99)),
-                                     "scatterings_per_s": solo_scat / solo_total}}
+                                     "scatterings_per_s": fifo_scat / fifo_span,
+                                     "slowest_solo_run_ms": float(solo_ms.max())}}
 
 
 def run_stream_bench(args):
@@ -365,7 +418,7 @@ def run_stream_bench(args):
     ctx = thor.Context(0)
     with ClockSampler(0) as clk:
         s = stream_bench(ctx, n_requests=args.stream_requests, nhi_max=args.stream_nhi_max,
-                         core_skip=not args.no_core_skip)
+                         core_skip=not args.no_core_skip, priority=not args.no_priority)
     print(json.dumps({"metric": METRIC, "value": s["batched"]["scatterings_per_s"], "unit": "scatterings/s",
                       "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
                       "config": {"workload": "served shell-model stream"}, "stream": s, "clocks": clk.summary()}))
@@ -382,7 +435,14 @@ def run_probe(args):
     from paper_2507_11603_gb300 import thor
     ctx = thor.Context(0)
     n = args.probe_photons
-    kw = dict(n_photons=n, first_id=args.probe_first_id, max_scat=args.probe_max_scat)
+    first = args.probe_first_id
+    if first < 0 and args.probe_model == "shell":
+        # the longest photon of the first 1e5 of the bench workload (one run with records)
+        g0 = ctx.shell(**SHELL)
+        r0 = ctx.run(g0, n_photons=N_PHOTONS, seed=1, raw=True, **RUN)
+        first = int(np.argmax(np.asarray(r0.raw_nscat)))
+        g0.close()
+    kw = dict(n_photons=n, first_id=max(first, 0), max_scat=args.probe_max_scat)
     if args.probe_model == "shell":
         g = ctx.shell(**SHELL)
         for i in range(2):
@@ -394,7 +454,7 @@ def run_probe(args):
             r = ctx.run(g, seed=i, n_bins=50, X_min=-500, X_max=500, **kw)
         desc = {"probe": "static sphere", "tau0": args.probe_tau0}
     events = r.stats["n_scat"] + r.stats["n_dust_scat"]
-    print(json.dumps({**desc, "photons": n, "first_id": args.probe_first_id, **r.stats,
+    print(json.dumps({**desc, "photons": n, "first_id": max(first, 0), **r.stats,
                       "us_per_event_chain": r.stats["elapsed_ms"] * 1e3 / max(events / n, 1e-30)}))
 
 
@@ -507,6 +567,21 @@ def run_mgii_bench(args):
                       "clocks": clk.summary()}))
 
 
+def run_peaks_bench(args):
+    """Measured issue peaks of the device: FP32 FMA and MUFU ex2 warp instructions/s."""
+    from paper_2507_11603_gb300 import thor
+    ctx = thor.Context(0)
+    with ClockSampler(0) as clk:
+        fma = [ctx.issue_peak("fma") for _ in range(3)]
+        mufu = [ctx.issue_peak("mufu") for _ in range(3)]
+    pk = peaks()
+    sm_max = pk.get("sm_max_mhz", 2070.0)
+    print(json.dumps({"metric": "issue peaks", "fma_warp_inst_per_s": max(fma), "mufu_warp_inst_per_s": max(mufu),
+                      "fma_lane_flop_per_s": 2 * 32 * max(fma),
+                      "nominal_fma_warp_inst_per_s": 152 * 4 * sm_max * 1e6,
+                      "nominal_mufu_warp_inst_per_s": 152 * 0.5 * sm_max * 1e6, "clocks": clk.summary()}))
+
+
 def run_forest_bench(args):
     import torch
     from paper_2507_11603_gb300 import synth, thor
@@ -514,10 +589,11 @@ def run_forest_bench(args):
     stream = torch.cuda.Stream()
     ctx.set_stream(stream)
     n = args.forest_n
-    nHI, T, v = synth.forest_fields_torch(n, seed=5)
+    xy = args.forest_xy or n  # sightlines per side (a box of n cells along each sightline)
+    nHI, T, v = synth.forest_fields_torch(n, seed=5, shape=(n, xy, xy))
     torch.cuda.synchronize()
     ds = synth.forest_scale(2.0, 2.0)
-    out = torch.empty((n * n, 2 * n), dtype=torch.float32, device="cuda")
+    out = torch.empty((xy * xy, 2 * n), dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
         ctx.forest(nHI, T, v, ds_cm=ds, dv_cell=2.0, n_bins=2 * n, dv_bin=1.0, out=out)
     ms = []
@@ -525,12 +601,13 @@ def run_forest_bench(args):
         for _ in range(args.steps):
             ctx.forest(nHI, T, v, ds_cm=ds, dv_cell=2.0, n_bins=2 * n, dv_bin=1.0, out=out)
             ms.append(ctx.last_elapsed_ms())
-    evals = float(n) * n * n * 2 * n
+    evals = float(xy) * xy * n * 2 * n
     t = float(np.mean(ms)) / 1000.0
     print(json.dumps({"metric": "Voigt evaluations/s (Lya forest, Eq. 11)", "value": evals / t,
                       "unit": "evals/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
                       "ms_per_step": 1000 * t, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-                      "config": {"workload": f"forest {n}^3 box, {n * n} sightlines x {2 * n} bins"},
+                      "config": {"workload": f"forest {xy}x{xy}x{n} box, {xy * xy} sightlines of {n} cells x "
+                                             f"{2 * n} bins"},
                       "clocks": clk.summary()}))
 
 
@@ -540,31 +617,44 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="shell", choices=["shell", "forest", "stream", "grid", "probe", "sweep", "mgii"])
+    ap.add_argument("--workload", default="shell",
+                    choices=["shell", "forest", "stream", "grid", "probe", "sweep", "mgii", "peaks"])
     ap.add_argument("--mgii-v", type=float, default=100.0)
     ap.add_argument("--sweep-targets", type=int, default=256)
     ap.add_argument("--probe-tau0", type=float, default=1e5)
     ap.add_argument("--probe-photons", type=int, default=64)
     ap.add_argument("--probe-model", choices=("sphere", "shell"), default="sphere")
-    ap.add_argument("--probe-first-id", type=int, default=0)
+    ap.add_argument("--probe-first-id", type=int, default=0,
+                    help="first photon id of the probe (-1: the longest photon of the first 1e5, shell model)")
     ap.add_argument("--probe-max-scat", type=int, default=0)
     ap.add_argument("--grid-photons", type=int, default=20000)
     ap.add_argument("--grid-max-scat", type=int, default=0,
                     help="stop grid photons after this many scatterings (0 = never; for short profiling runs)")
     ap.add_argument("--stream-requests", type=int, default=256)
-    ap.add_argument("--stream-in-line", type=int, default=64,
+    ap.add_argument("--stream-in-line", type=int, default=256,
                     help="requests of the served stream measured after the main bench (0 = skip)")
     ap.add_argument("--stream-nhi-max", type=float, default=1e21)
     ap.add_argument("--no-core-skip", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--no-priority", action="store_true", help="served stream without age priority")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--lone-events", type=int, default=200000,
+                    help="events of the longest photon run alone to time the lone-lane event latency")
     ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--bursts", type=int, default=-1,
+                    help="core bursts in warps with at most this many live packets (-1 = library default)")
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--inst-per-scat", type=float, default=374.0,
                     help="warp instructions per scattering of the shell photon loop (ncu, bench workload)")
+    ap.add_argument("--thread-inst-per-scat", type=float, default=702.0,
+                    help="thread instructions per scattering of the shell photon loop (ncu, bench workload)")
+    ap.add_argument("--launch-dram-bytes", type=float, default=858112.0,
+                    help="DRAM bytes read + written by one bench launch of the shell kernel (ncu)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--forest-n", type=int, default=1024)
+    ap.add_argument("--forest-xy", type=int, default=0,
+                    help="sightlines per side of the forest box (0 = forest-n, a cube)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -580,6 +670,8 @@ def main():
         run_sweep_bench(args)
     elif args.workload == "mgii":
         run_mgii_bench(args)
+    elif args.workload == "peaks":
+        run_peaks_bench(args)
     else:
         run_shell_bench(args)
 

@@ -85,6 +85,14 @@ int thor_ctx_set_launch(thor_ctx_t ctx, int block_size, int blocks_per_sm);
  * photons than lanes spread them over all warps either way.  Results do not depend on
  * these settings. */
 int thor_ctx_set_tail(thor_ctx_t ctx, int spill_below, int max_phases);
+/* Core bursts of the gridless photon loop on homologous shells: in warps with at most
+ * max_lanes live packets (0..32; 0 = never; default 4), a packet runs the events that
+ * stay in the line core (start-point step inside the safety ball, resonant scattering at
+ * |x| <= 2, first u_par trial accepted) up to 32 at a time, with the next event's random
+ * words, its optical depth and the outgoing direction formed beside the frequency chain.
+ * Such an event is evaluated exactly as the general event evaluates it, so results do not
+ * depend on this setting (only the time to reach them does). */
+int thor_ctx_set_bursts(thor_ctx_t ctx, int max_lanes);
 
 /* ---- geometries (Sec. 3.3 datasets) ----------------------------------------------- */
 
@@ -282,7 +290,9 @@ typedef struct {
   int64_t n_slots;           /* resident packet slots (0 = one per resident thread) */
   uint64_t mem_budget_bytes; /* device bytes for per-request tables (admission limit) */
   int32_t block_size;        /* 0 = context default */
-  int32_t reserved;
+  int32_t priority;          /* age priority: 0 = on (the oldest request, and the next oldest while
+                                their packets in flight fit in half of the warps, run their packets
+                                one per warp), -1 = off (every packet shares warps) */
 } thor_server_config;
 
 /* Create a server on the context: a host thread runs device rounds while work is
@@ -313,6 +323,17 @@ void thor_server_destroy(thor_server_t s);
 /* H[i] = Voigt function H(a[i], x[i]) in FP32 (App. A.3); precise selects the
  * accurate exponential (forest kernel) instead of the fast one (photon loop). */
 int thor_voigt_eval(thor_ctx_t ctx, const float* a, const float* x, float* H, int64_t n, int precise, int mem_kind);
+/* xcw[i] = core-to-wing transition x_cw(a[i]) of the Voigt profile (App. A.2: the
+ * frequency where e^{-x^2} = a / (sqrt(pi) x^2)) by the B25 polynomial in ln a with a fast
+ * logarithm, as the u_par sampler uses it.  a[i] > 0 and normal; n values, host or device
+ * arrays per mem_kind (same-kind in and out; host arrays are staged through the device). */
+int thor_xcw_eval(thor_ctx_t ctx, const float* a, float* xcw, int64_t n, int mem_kind);
+/* Measured issue rate of one instruction kind over the whole device, in warp instructions
+ * per second (the denominators of the photon loops' ALU rooflines): kind 0 = FP32 FMA (the
+ * issue-slot peak, four schedulers per SM), kind 1 = MUFU ex2 (the special-function pipe).
+ * Eight independent dependency chains per thread, 64 warps per SM, best of five launches
+ * timed with CUDA events on the context's stream. */
+int thor_issue_peak(thor_ctx_t ctx, int kind, double* warp_inst_per_s);
 /* Cell walk of n rays (origins 3n doubles in cell units, directions 3n floats) through
  * a grid of dims; cells[r * max_steps + j] = linear cell index, seg[...] = path length,
  * count[r] = cells visited (Sec. 3.4 face-to-face propagation). */

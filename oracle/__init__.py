@@ -104,6 +104,8 @@ def lib():
             L.orc_eq10_mass.restype = C.c_double
             L.orc_eq10_mass.argtypes = [C.c_double, C.c_double, C.c_double]
             L.orc_set_upar_method.argtypes = [C.c_int]
+            L.orc_xcw.restype = C.c_double
+            L.orc_xcw.argtypes = [C.c_double]
             L.orc_get_upar_method.restype = C.c_int
             L.orc_segment_tau.restype = C.c_double
             L.orc_segment_tau.argtypes = [C.c_double] * 7 + [P(C.c_double)]
@@ -211,6 +213,11 @@ def voigt(a, x) -> np.ndarray:
     o = np.empty_like(x_)
     lib().orc_voigt_batch(_p(a_, C.c_double), _p(x_, C.c_double), _p(o, C.c_double), o.size)
     return o.reshape(np.broadcast(np.asarray(a), np.asarray(x)).shape)
+
+
+def xcw(a: float) -> float:
+    """Core-to-wing transition x_cw(a) of the Voigt profile (App. A.2), exact (Newton)."""
+    return lib().orc_xcw(float(a))
 
 
 def u0_rule(x: float, a: float) -> float:

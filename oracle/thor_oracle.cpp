@@ -339,57 +339,113 @@ double u0_rule(double xr, double a) {
   return (envelope_D(xr, a, c1) <= envelope_D(xr, a, u)) ? c1 : u;
 }
 
-// Split point u1 of the third piece (|x| > kUparThreePiece): the envelope mass
-// w0 e^{-u1^2} + (w1 - w0), w0 = atan2(a, x + u1), is stationary in u1 where
-// e^{u1^2} - 1 = 2 u1 (x + u1) (to leading order in a / (x + u1)); three fixed-point steps
-// of u1 = sqrt(ln(1 + 2 u1 (x + u1))) from u1 = 2.  Any u1 > 0 gives the exact
-// distribution; the rule only sets the rejection rate.
-constexpr double kUparThreePiece = 3.0;
-double u1_rule(double xr) {
-  double u = 2.0;
-  for (int it = 0; it < 3; ++it) u = std::sqrt(std::log1p(2.0 * u * (xr + u)));
-  return u;
+// The inverse CDF of N(0, 1/2) at R: u with (1 + erf(u)) / 2 = R, i.e. erfc(-u) = 2R
+// (u <= 0) or erfc(u) = 2 (1 - R) (u > 0), by Newton's method on erfc from the closed-form
+// start of Winitzki (2008, "A handy approximation for the error function and its inverse",
+// constant 0.147); erfc keeps the relative precision in both tails.
+double gauss_half_inv(double R) {
+  if (!(R > 0.0)) return -HUGE_VAL;
+  if (!(R < 1.0)) return HUGE_VAL;
+  const double y = 2.0 * R - 1.0;
+  const double al = 0.147;
+  const double w = std::log((1.0 - y) * (1.0 + y));
+  const double t = 2.0 / (kPi * al) + 0.5 * w;
+  double u = std::fabs(std::sqrt(std::sqrt(t * t - w / al) - t));  // |u|
+  const double c = (R > 0.5) ? 2.0 * (1.0 - R) : 2.0 * R;           // erfc(|u|) = c
+  for (int i = 0; i < 8; ++i) {
+    const double f = std::erfc(u) - c;
+    const double fp = -2.0 / kSqrtPi * std::exp(-u * u);
+    const double du = f / fp;
+    u -= du;
+    if (std::fabs(du) <= 1e-15 * std::fabs(u) + 1e-300) break;
+  }
+  return (R > 0.5) ? u : -u;
 }
 
-// u_par from f(u) ~ exp(-u^2) / ((x-u)^2 + a^2) (Eq. 6) by rejection with a piecewise,
-// integrable comparison function (Eq. 10).  The Lorentzian part is sampled through
-// alpha = theta + pi/2 = atan2(a, x - u), uniform on its interval, u = x - a/tan(alpha).
-// Eq. 10 has two pieces:
-//   region 1 (u <= u0): alpha in (0, w1), envelope 1, accept with exp(-u^2);
-//   region 2 (u >  u0): alpha in (w1, pi), envelope e^{-u0^2}, accept with exp(u0^2 - u^2).
-// Region 1 then spans the Lorentzian mass down to u -> -inf, where e^{-u^2} vanishes, and
-// the acceptance falls as ~1.8/|x| in the far wing.  For |x| > kUparThreePiece a third
-// piece is split off below u = -u1 (u^2 >= u1^2 there):
-//   region 0 (u <= -u1): alpha in (0, w0), w0 = atan2(a, x + u1), envelope e^{-u1^2},
-//                        accept with exp(u1^2 - u^2);
-// region 1 shrinks to alpha in (w0, w1).  Regions are chosen in proportion to their
-// envelope masses w0 e^{-u1^2}, w1 - w0, (pi - w1) e^{-u0^2}; for |x| <= kUparThreePiece,
-// w0 = 0 and this is Eq. 10 as it stands.  Negative x by symmetry.  Three draws per
-// iteration: region, alpha, acceptance.
+// Split points of the four-piece comparison function for |x| > 2 (the device's rule, in
+// FP64): u_b = 1.05 + 0.22 ln(x/3), b1 = 2 + 0.16 ln(x/3) (kept below x and above u_b), and
+// b2 where the top two pieces' envelope mass is stationary, e^{b2^2 - b1^2} = 2 pi b2 (x-b2)^2/a:
+// the near-resonance root or four Newton steps towards the far root, whichever gives the
+// smaller mass.  Any split points give the exact distribution.
+double top_mass(double xr, double a, double b1, double b2) {
+  return std::exp(-b1 * b1) * (std::atan2(a, xr - b2) - std::atan2(a, xr - b1)) +
+         std::exp(-b2 * b2) * (kPi - std::atan2(a, xr - b2));
+}
+void wing_split(double xr, double a, double* ub, double* b1, double* b2) {
+  const double L = std::log(xr / 3.0);
+  *ub = std::min(1.05 + 0.22 * L, xr - 1.2);
+  *b1 = std::max(std::min(2.0 + 0.16 * L, xr - 0.6), *ub + 0.3);
+  const double d = std::sqrt(a / (2.0 * kPi * xr)) * std::exp(std::min(0.5 * (xr * xr - *b1 * *b1), 80.0));
+  const double c1 = std::max(*b1 + 1e-3, xr - d);
+  double u = std::min(xr - 0.3, *b1 + 1.0 + 0.6 * std::log(xr));
+  for (int it = 0; it < 4; ++it) {
+    const double dx = xr - u;
+    const double g = u * u - *b1 * *b1 - std::log(2.0 * kPi * u * dx * dx / a);
+    const double gp = 2.0 * u - 1.0 / u + 2.0 / dx;
+    u = std::min(std::max(u - g / gp, *b1 + 0.05), xr - 1e-3);
+  }
+  *b2 = (top_mass(xr, a, *b1, c1) <= top_mass(xr, a, *b1, u)) ? c1 : u;
+}
+
+// u_par from f(u) ~ exp(-u^2) / ((x-u)^2 + a^2) (Eq. 6) by rejection, reading the random
+// words as the device's sampler does (for the same-stream tests; the oracle's default is the
+// Eq. 10 sampler below).  The Lorentzian part is sampled through alpha = atan2(a, x - u),
+// uniform on its interval, u = x - a/tan(alpha).
+//   |x| <= 2, Eq. 10's two pieces: region 1 (u <= u0): alpha in (0, w1), envelope 1, accept
+//     with exp(-u^2); region 2 (u > u0): alpha in (w1, pi), envelope e^{-u0^2}, accept with
+//     exp(u0^2 - u^2); u0 = max(0, x - sqrt(a/(2 pi x)) e^{x^2/2}).
+//   |x| > 2, four pieces: below u_b the Gaussian bound e^{-u^2} / ((x-u_b)^2 + a^2), u drawn
+//     from N(0, 1/2) by its inverse CDF and accepted with ((x-u_b)^2 + a^2) / ((x-u)^2 + a^2)
+//     if u <= u_b; on (u_b, b1], (b1, b2], (b2, inf) the Lorentzian times e^{-lower^2},
+//     accepted with exp(lower^2 - u^2).
+// Pieces are chosen in proportion to their envelope masses.  Negative x by symmetry.
+// Three draws per trial: region, angle (or Gaussian), acceptance.
 double sample_upar_envelope(double x, double a, Stream& rng, uint64_t* iters) {
   // iteration 0 uses words 1-3, iteration i >= 1 words 0-2 of block i + 2
-  double sgn = (x < 0.0) ? -1.0 : 1.0, xr = std::fabs(x);
-  double u0 = u0_rule(xr, a);
-  double w1 = std::atan2(a, xr - u0);
-  double e0 = std::exp(-u0 * u0);
-  double u1 = 0.0, w0 = 0.0, e1 = 0.0;
-  if (xr > kUparThreePiece) {
-    u1 = u1_rule(xr);
-    w0 = std::atan2(a, xr + u1);
-    e1 = std::exp(-u1 * u1);
+  const double sgn = (x < 0.0) ? -1.0 : 1.0, xr = std::fabs(x);
+  if (xr <= 2.0) {  // two pieces (Eq. 10)
+    const double u0 = u0_rule(xr, a);
+    const double w1 = std::atan2(a, xr - u0);
+    const double e0 = std::exp(-u0 * u0);
+    const double p1 = w1 / (w1 + e0 * (kPi - w1));
+    for (uint64_t it = 1;; ++it) {
+      const uint32_t w = (it == 1) ? (uint32_t)W_UPAR0 : 4u * (uint32_t)(it + 1);
+      const double R1 = rng.u(w), R2 = rng.u(w + 1), R3 = rng.u(w + 2);
+      double alpha, shift;
+      if (R1 < p1) { alpha = w1 * R2; shift = 0.0; }
+      else { alpha = w1 + (kPi - w1) * R2; shift = u0 * u0; }
+      const double u = xr - a / std::tan(alpha);
+      if (R3 <= std::exp(shift - u * u)) {
+        if (iters) *iters += it;
+        return sgn * u;
+      }
+    }
   }
-  const double m0 = w0 * e1, m1 = w1 - w0, m2 = e0 * (kPi - w1);
-  const double p0 = m0 / (m0 + m1 + m2), p01 = (m0 + m1) / (m0 + m1 + m2);
+  // four pieces: Gaussian below u_b, Lorentzians on (u_b, b1], (b1, b2], (b2, inf)
+  double ub, b1, b2;
+  wing_split(xr, a, &ub, &b1, &b2);
+  const double gden = (xr - ub) * (xr - ub) + a * a;
+  const double al0 = std::atan2(a, xr - ub), al1 = std::atan2(a, xr - b1), al2 = std::atan2(a, xr - b2);
+  const double mG = a * kSqrtPi / gden, m1 = std::exp(-ub * ub) * (al1 - al0);
+  const double m2 = std::exp(-b1 * b1) * (al2 - al1), m3 = std::exp(-b2 * b2) * (kPi - al2);
+  const double tot = mG + m1 + m2 + m3;
   for (uint64_t it = 1;; ++it) {
     const uint32_t w = (it == 1) ? (uint32_t)W_UPAR0 : 4u * (uint32_t)(it + 1);
-    double R1 = rng.u(w), R2 = rng.u(w + 1), R3 = rng.u(w + 2);
-    double alpha, shift;
-    if (R1 < p0) { alpha = w0 * R2; shift = u1 * u1; }                        // region 0
-    else if (R1 < p01) { alpha = w0 + (w1 - w0) * R2; shift = 0.0; }        // region 1
-    else { alpha = w1 + (kPi - w1) * R2; shift = u0 * u0; }                  // region 2
-    double u = xr - a / std::tan(alpha);
-    double acc = std::exp(shift - u * u);
-    if (R3 <= acc) {
+    const double R1 = rng.u(w) * tot, R2 = rng.u(w + 1), R3 = rng.u(w + 2);
+    double u;
+    bool acc;
+    if (R1 < mG) {
+      u = gauss_half_inv(R2);
+      acc = (u <= ub) && (R3 * ((xr - u) * (xr - u) + a * a) <= gden);
+    } else {
+      double lo, hi, b;
+      if (R1 < mG + m1) { lo = al0; hi = al1; b = ub; }
+      else if (R1 < mG + m1 + m2) { lo = al1; hi = al2; b = b1; }
+      else { lo = al2; hi = kPi; b = b2; }
+      u = xr - a / std::tan(lo + (hi - lo) * R2);
+      acc = R3 <= std::exp(b * b - u * u);
+    }
+    if (acc) {
       if (iters) *iters += it;
       return sgn * u;
     }
@@ -477,6 +533,22 @@ int g_upar_method = 1;
 
 double sample_upar(double x, double a, Stream& rng, uint64_t* iters) {
   return (g_upar_method == 0) ? sample_upar_envelope(x, a, rng, iters) : sample_upar_eq10(x, a, rng, iters);
+}
+
+// Core-to-wing transition of the Voigt profile (App. A.2): the frequency x_cw > 1 where the
+// Gaussian core and the Lorentzian wing are equal, e^{-x^2} = a / (sqrt(pi) x^2).  With
+// y = x^2 this is y - ln y = ln(sqrt(pi) / a), whose root above 1 (the lower branch of
+// Lambert's W, x_cw^2 = -W_{-1}(-a / sqrt(pi))) Newton's method reaches monotonically from
+// any start above it (the function is convex).  Domain: 0 < a < sqrt(pi)/e.
+double xcw_exact(double a) {
+  const double c = std::log(kSqrtPi / a);
+  double y = c + std::log(c) + 1.0;
+  for (int it = 0; it < 60; ++it) {
+    const double dy = (y - std::log(y) - c) / (1.0 - 1.0 / y);
+    y -= dy;
+    if (std::fabs(dy) <= 1e-15 * y) break;
+  }
+  return std::sqrt(y);
 }
 
 // Phase functions: mu = cos(angle between incoming and outgoing direction).
@@ -596,6 +668,7 @@ extern "C" void orc_voigt_batch(const double* a, const double* x, double* out, i
 
 extern "C" double orc_u0(double x, double a) { return u0_rule(std::fabs(x), a); }
 extern "C" double orc_u0_eq10(double x, double a) { return eq10_u0(std::fabs(x), a); }
+extern "C" double orc_xcw(double a) { return (a > 0.0 && a < 0.65) ? xcw_exact(a) : NAN; }
 extern "C" double orc_eq10_mass(double x, double a, double u0) { return eq10_mass(std::fabs(x), a, u0); }
 // 1: Eq. 10 as printed (default); 0: three-piece envelope with the device's word use.
 extern "C" void orc_set_upar_method(int m) { g_upar_method = (m == 0) ? 0 : 1; }

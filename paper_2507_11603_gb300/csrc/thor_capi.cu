@@ -110,6 +110,13 @@ extern "C" int thor_ctx_set_tail(thor_ctx_t ctx, int spill_below, int max_phases
   return THOR_OK;
 }
 
+extern "C" int thor_ctx_set_bursts(thor_ctx_t ctx, int max_lanes) {
+  if (!ctx) return THOR_ERR_INVALID_ARG;
+  if (max_lanes < 0 || max_lanes > 32) return ctx->fail(THOR_ERR_INVALID_ARG, "thor_ctx_set_bursts: max_lanes in [0, 32]");
+  ctx->core_lanes = max_lanes;
+  return THOR_OK;
+}
+
 extern "C" int thor_ctx_set_launch(thor_ctx_t ctx, int block_size, int blocks_per_sm) {
   if (!ctx) return THOR_ERR_INVALID_ARG;
   if (block_size <= 0 || block_size > 256 || (block_size & 31) || blocks_per_sm < 0)
@@ -505,7 +512,7 @@ extern "C" int thor_run(thor_ctx_t ctx, thor_geom_t g, const thor_source* src, u
     const int per_warp0 = (int)(pw0 < 1 ? 1 : (pw0 > 32 ? 32 : pw0));
     if (ctx->spill_below <= 0) {
       cudaEventRecord(ctx->ev0, s);
-      rc = ctx->cuda(launch_shell_run(d_m, q, ctx->d_ktab, gsz, ctx->block, m.profile, per_warp0, s),
+      rc = ctx->cuda(launch_shell_run(d_m, q, ctx->d_ktab, gsz, ctx->block, m.profile, per_warp0, ctx->core_lanes, s),
                      "shell photon loop");
       ++n_launch;
       cudaEventRecord(ctx->ev1, s);
@@ -535,6 +542,7 @@ extern "C" int thor_run(thor_ctx_t ctx, thor_geom_t g, const thor_source* src, u
         c.n_spill = ctr + 1;
         c.spill_below = last ? 0 : ctx->spill_below;
         c.per_warp = per_warp0;
+        c.core_lanes = ctx->core_lanes;
         if (per_warp0 <= 2) c.spill_below = 0;
         else if (c.spill_below > per_warp0 / 2) c.spill_below = per_warp0 / 2;
         int g = gsz;
@@ -800,6 +808,41 @@ extern "C" int thor_voigt_eval(thor_ctx_t ctx, const float* a, const float* x, f
   float* dH = (float*)st.out(H, n * 4);
   if (int rc = ctx->cuda(launch_voigt_eval(da, dx, dH, n, ctx->d_ktab, ctx->stream, precise), "voigt kernel")) return rc;
   return st.finish();
+}
+
+extern "C" int thor_xcw_eval(thor_ctx_t ctx, const float* a, float* xcw, int64_t n, int mem_kind) {
+  if (!ctx || !a || !xcw || n <= 0) return ctx ? ctx->fail(THOR_ERR_INVALID_ARG, "thor_xcw_eval") : THOR_ERR_INVALID_ARG;
+  Stage st;
+  if (int rc = stage_begin(ctx, mem_kind, 2 * (size_t)n * 4 + 1024, &st)) return rc;
+  const float* da = (const float*)st.in(a, n * 4);
+  float* dx = (float*)st.out(xcw, n * 4);
+  if (int rc = ctx->cuda(launch_xcw_eval(da, dx, n, ctx->stream), "x_cw kernel")) return rc;
+  return st.finish();
+}
+
+extern "C" int thor_issue_peak(thor_ctx_t ctx, int kind, double* warp_inst_per_s) {
+  if (!ctx || !warp_inst_per_s || kind < 0 || kind > 1)
+    return ctx ? ctx->fail(THOR_ERR_INVALID_ARG, "thor_issue_peak: kind 0 (FMA) or 1 (MUFU ex2)") : THOR_ERR_INVALID_ARG;
+  if (int rc = ctx->select()) return rc;
+  const int block = 256, grid = ctx->sm_count * 8;  // 8 resident blocks of 256 per SM: 64 warps
+  const int iters = (kind == 0) ? 8192 : 1024;
+  float* sink = (float*)ctx->scratch(ctx->b_diag, (size_t)grid * block * 4);
+  if (!sink) return ctx->fail(THOR_ERR_OOM, "thor_issue_peak");
+  cudaStream_t s = ctx->stream;
+  if (int rc = ctx->cuda(launch_issue_probe(kind, sink, grid, block, iters / 8, s), "issue probe warm-up")) return rc;
+  float best = 1e30f;
+  for (int rep = 0; rep < 5; ++rep) {
+    cudaEventRecord(ctx->ev0, s);
+    if (int rc = ctx->cuda(launch_issue_probe(kind, sink, grid, block, iters, s), "issue probe")) return rc;
+    cudaEventRecord(ctx->ev1, s);
+    if (int rc = ctx->cuda(cudaEventSynchronize(ctx->ev1), "issue probe")) return rc;
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    best = fminf(best, ms);
+  }
+  const double warp_inst = (double)grid * (block / 32) * (double)iters * 8.0;
+  *warp_inst_per_s = warp_inst / (best * 1e-3);
+  return THOR_OK;
 }
 
 extern "C" int thor_dda_trace(thor_ctx_t ctx, const int32_t dims[3], const double* org, const float* dir, int32_t n,

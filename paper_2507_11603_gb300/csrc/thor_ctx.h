@@ -29,6 +29,7 @@ struct thor_ctx {
   int spill_below = 0;      // warps with fewer live lanes hand them to the next launch (0 = off)
   int max_phases = 24;      // launches at most
   int final_below = 256;    // run to completion once this few packets are left
+  int core_lanes = 4;       // warps with at most this many live packets run core bursts (0 = never)
   int phases_last = 0;
 
   int fail(int code, const char* fmt, ...);

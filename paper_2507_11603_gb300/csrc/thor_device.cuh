@@ -86,6 +86,17 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
+__device__ __forceinline__ float lg2_approx(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+// e^x and ln x as one MUFU instruction and one multiply (relative error of order 2^-22;
+// results below the FP32 normal range flush to zero).  On the latency chain of a core event
+// these take ~20 cycles against ~42 for __expf / __logf (measured, single lane).
+__device__ __forceinline__ float exp_fast(float x) { return ex2_approx(x * 1.44269504f); }
+__device__ __forceinline__ float ln_fast(float x) { return lg2_approx(x) * 0.693147181f; }
+
 // (w + 1/2) 2^-32 in FP32: in (0, 1]
 __device__ __forceinline__ float uni32(uint32_t w) {
   return fminf(__fmaf_rn(__uint2float_rn(w), 2.3283064365386963e-10f, 1.1641532182693481e-10f), 1.0f);
@@ -180,6 +191,24 @@ __device__ __forceinline__ float voigt_core(float a, float ax, float x2, const f
   return __fmaf_rn(2.0f * a * kInvSqrtPiF, k, gauss) + c3 * __fmaf_rn(__fmaf_rn(-4.0f, x2, 6.0f), k, 2.0f);
 }
 
+// |x| <= THOR_VCORE_X = 2 (the photon loops' fast core path): the same series in a, with
+// K(x) from one polynomial in s = x^2 / 4 (voigt_coeffs.h, no table lookup, Estrin order:
+// the chain is x^2, four FMA levels and the exponential beside them).  Relative error
+// against the FP64 truth below 3e-6 for a <= 1e-2 before FP32 rounding (tested).
+__device__ __forceinline__ float voigt_core_poly(float a, float x) {
+  const float x2 = x * x;
+  const float s = 0.25f * x2, s2 = s * s, s4 = s2 * s2, s8 = s4 * s4;
+  const float p01 = __fmaf_rn(THOR_VCORE_P1, s, THOR_VCORE_P0), p23 = __fmaf_rn(THOR_VCORE_P3, s, THOR_VCORE_P2);
+  const float p45 = __fmaf_rn(THOR_VCORE_P5, s, THOR_VCORE_P4), p67 = __fmaf_rn(THOR_VCORE_P7, s, THOR_VCORE_P6);
+  const float p03 = __fmaf_rn(p23, s2, p01), p47 = __fmaf_rn(p67, s2, p45);
+  const float k = __fmaf_rn(THOR_VCORE_P8, s8, __fmaf_rn(p47, s4, p03));
+  const float g = exp_fast(-x2);
+  const float a2 = a * a;
+  const float gauss = g * __fmaf_rn(a2, __fmaf_rn(-2.0f, x2, 1.0f), 1.0f);
+  const float c3 = a2 * a * (kInvSqrtPiF / 3.0f);
+  return __fmaf_rn(2.0f * a * kInvSqrtPiF, k, gauss) + c3 * __fmaf_rn(__fmaf_rn(-4.0f, x2, 6.0f), k, 2.0f);
+}
+
 template <bool kAccurateExp = true>
 __device__ __forceinline__ float voigt(float a, float x, const float* __restrict__ Ktab) {
   const float ax = fabsf(x);
@@ -189,15 +218,38 @@ __device__ __forceinline__ float voigt(float a, float x, const float* __restrict
 }
 
 // ------------------------------------------------------------------------------
+// Core-to-wing transition x_cw(a) of the Voigt profile (App. A.2), where the Gaussian core
+// and the Lorentzian wing are equal (e^{-x^2} = a / (sqrt(pi) x^2)).  B25: the paper's
+// fourth-order polynomial in L = ln a (coefficients as printed, within ~0.5% of the exact
+// transition for Lyman alpha between 1 K and 1e7 K).  "fast": ln a from the IEEE-754
+// exponent and a cubic in the mantissa, log2(1 + t) ~ t (b1 + t (b2 + t b3)) on [0, 1),
+// fitted here (max error 8.1e-4 in log2, i.e. ~1e-4 in x_cw).  a > 0, normal.
+// ------------------------------------------------------------------------------
+__device__ __forceinline__ float fast_ln(float a) {
+  const uint32_t b = __float_as_uint(a);
+  const float e = (float)((int)(b >> 23) - 127);
+  const float t = __uint_as_float((b & 0x007fffffu) | 0x3f800000u) - 1.0f;
+  const float l2 = __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(t, 0.16417124f, -0.58750188f), 1.42405695f), e);
+  return l2 * 0.69314718f;
+}
+__device__ __forceinline__ float xcw_b25(float a) {
+  const float L = fast_ln(a);
+  float p = __fmaf_rn(-2.76037084e-4f, L, -7.91384757e-3f);
+  p = __fmaf_rn(p, L, -8.73073343e-2f);
+  p = __fmaf_rn(p, L, -6.17680644e-1f);
+  return __fmaf_rn(p, L, 1.03489162f);
+}
+
+// ------------------------------------------------------------------------------
 // Atom velocity parallel to the photon (Eq. 6) by rejection with the comparison
 // function of Eq. 10, sampled through alpha = theta + pi/2 = atan2(a, x - u):
 //   region 1 (u <= u0): alpha ~ U(0, w1), accept with exp(-u^2);
 //   region 2 (u >  u0): alpha ~ U(w1, pi), accept with exp(u0^2 - u^2);
 //   w1 = atan2(a, x - u0), P(region 1) = w1 / (w1 + e^{-u0^2} (pi - w1)), u = x - a / tan(alpha).
-// Split point u0: the smaller-envelope candidate of (i) x - sqrt(a/(2 pi x)) e^{x^2/2}
-// and (ii) three Newton steps on u0^2 = ln(2 pi u0 (x - u0)^2 / a) (only for x > 2).
-// Three draws per iteration: region, alpha, acceptance.  For |x| > 3 the comparison
-// function has a third piece below u = -u1 (sample_upar_far).
+// Split point u0 = x - sqrt(a/(2 pi x)) e^{x^2/2} (clamped at 0), the near-resonance
+// solution of the envelope mass's stationarity u0^2 = ln(2 pi u0 (x - u0)^2 / a).  Three draws
+// per iteration: region, alpha, acceptance.  For |x| > 2 a four-piece comparison function
+// takes over (sample_upar_wing).
 // ------------------------------------------------------------------------------
 // atan2(a, d) for a, d >= 0: series when a/d <= 1/20 (relative error < 3e-9), else atan2f.
 __device__ __forceinline__ float atan2_pos(float a, float d) {
@@ -213,10 +265,30 @@ __device__ __forceinline__ float envelope_D(float xr, float a, float u0) {
   return w1 + __expf(-u0 * u0) * (kPiF - w1);
 }
 
+// Near-resonance split point (the x <= 2 rule): u0 = x - d, d = sqrt(a/(2 pi x)) e^{x^2/2},
+// clamped at 0; and q = a / d = sqrt(2 pi a x) e^{-x^2/2}, formed directly (no division).
+// Where u0 > 0 and q <= 1/20, w1 = atan2(a, x - u0) = atan(q) = q (1 - q^2/3 + q^4/5) to
+// 3e-9 relative.  The photon loops' core bursts use these same functions, so both evaluate
+// an event identically.
+__device__ __forceinline__ float u0_core(float xr, float a) {
+  const float d = sqrt_approx(a * (0.5f / kPiF)) * rsqrtf(xr) * exp_fast(fminf(0.5f * xr * xr, 80.0f));
+  return fmaxf(0.0f, xr - d);
+}
+__device__ __forceinline__ float upar_q(float xr, float a) {
+  return sqrt_approx(a * (2.0f * kPiF)) * sqrt_approx(xr) * exp_fast(-(0.5f * xr * xr));
+}
+__device__ __forceinline__ float atan_small(float q) {
+  const float q2 = __fmul_rn(q, q);
+  return __fmul_rn(q, __fmaf_rn(q2, __fmaf_rn(q2, 0.2f, -1.0f / 3.0f), 1.0f));
+}
+// Region 1 of the two-piece comparison function is chosen with probability w1 / mass,
+// mass = w1 + e^{-u0^2} (pi - w1): R1 < w1 / mass, tested as R1 mass < w1.
+__device__ __forceinline__ float envelope_mass(float w1, float e0) { return __fmaf_rn(e0, kPiF - w1, w1); }
+__device__ __forceinline__ bool region1(float R1, float mass, float w1) { return __fmul_rn(R1, mass) < w1; }
+
 __device__ __forceinline__ float u0_rule(float xr, float a) {
   if (xr <= 0.0f) return 0.0f;
-  const float d = sqrt_approx(a * (0.5f / kPiF)) * rsqrtf(xr) * __expf(fminf(0.5f * xr * xr, 80.0f));
-  const float c1 = fmaxf(0.0f, xr - d);
+  const float c1 = u0_core(xr, a);
   if (xr <= 2.0f) return c1;
   float u = fminf(xr - 0.3f, 2.0f + 0.6f * __logf(xr));
   const float c2 = 2.0f * kPiF * rcp_approx(a);
@@ -252,47 +324,85 @@ __device__ __forceinline__ float cot_pi(float t) {
 // Iteration 0 is peeled out of the loop so that it shares a basic block with the work
 // the caller schedules around it (further iterations are rare in the core).  The loop
 // stops after kMaxUparTrials trials so that a NaN input cannot keep a lane spinning.  The
-// expected trial count peaks near |x| ~ 4 (16 at a = 1e-4, 110 at a = 1e-6) and stays
-// near 4-5 in the far wing with the three-piece form below, so a valid input reaches the
-// bound with probability below e^-9000.
+// expected trial count stays below 3 at every x for a in [1e-5, 1e-2] (two pieces for
+// |x| <= 2, four beyond), so a valid input never comes near the bound.
 constexpr uint32_t kMaxUparTrials = 1u << 20;
 
-// Far side (|x| > kUparThreePiece): Eq. 10's region 1 spans the Lorentzian mass down to
-// u -> -inf, where e^{-u^2} vanishes, so its acceptance falls as ~1.8/|x|.  A third piece
-// is split off below u = -u1 (envelope e^{-u1^2}, since u^2 >= u1^2 there):
-//   region 0: alpha in (0, w0), w0 = atan2(a, x + u1), accept with exp(u1^2 - u^2);
-//   region 1: alpha in (w0, w1), accept with exp(-u^2);
-//   region 2: alpha in (w1, pi), accept with exp(u0^2 - u^2);
-// each chosen in proportion to its envelope mass.  u1 makes that mass stationary,
-// e^{u1^2} - 1 = 2 u1 (x + u1), by three fixed-point steps from 2.  The width of region 1
-// is w1 - w0 = atan2(a (u0 + u1), (x - u0)(x + u1) + a^2), free of the cancellation of
-// the difference.  About 4-6 trials at every |x| > 3 (against ~0.57 |x| with two pieces).
-// Same words as the two-piece loop; kept out of line, as it is rare in optically thick gas
+// Wing side (|x| > kUparWing): a four-piece comparison function.  Eq. 10's two pieces bound
+// the Gaussian factor e^{-u^2} of f(u) = e^{-u^2} / ((x-u)^2 + a^2) by a constant over all
+// u <= u0, which wastes most trials once |x| passes ~2 (7-9 trials at x = 3, up to ~20 near
+// x = 4 with any single split).  Here, with split points u_b < b1 < b2 < x:
+//   piece G (u <= u_b): f <= e^{-u^2} / ((x-u_b)^2 + a^2) (x - u >= x - u_b there): u drawn from
+//     N(0, 1/2) by its inverse CDF, u = erfinv(2R - 1), accepted with
+//     ((x-u_b)^2 + a^2) / ((x-u)^2 + a^2) if u <= u_b, else rejected (the proposal is the whole
+//     Gaussian, so a draw above u_b is a rejected trial);
+//   pieces 1, 2, 3 (u_b, b1], (b1, b2], (b2, inf): the Lorentzian 1/((x-u)^2 + a^2) times the
+//     Gaussian factor's value at the piece's lower end, alpha = atan2(a, x - u) uniform on the
+//     piece, u = x - a cot(alpha), accepted with exp(lower^2 - u^2).
+// Pieces are chosen in proportion to their masses (times a): a sqrt(pi) / ((x-u_b)^2 + a^2),
+// e^{-u_b^2} dalpha_1, e^{-b1^2} dalpha_2, e^{-b2^2} (pi - alpha(b2)); the widths dalpha are
+// atan2(a (b' - b), (x - b')(x - b) + a^2), free of the cancellation of a difference.  Any
+// split points give the exact distribution; these keep the expected trials below 3 for every
+// |x| > 2 and a in [1e-5, 1e-2] (computed from the masses and the Faddeeva function; tested):
+// u_b = 1.05 + 0.22 ln(x/3), b1 = 2 + 0.16 ln(x/3) (kept below x and above u_b), and b2 where
+// the top two pieces' mass is stationary, e^{b2^2 - b1^2} = 2 pi b2 (x - b2)^2 / a: the
+// near-resonance root x - sqrt(a / (2 pi x)) e^{(x^2 - b1^2)/2} or the far root by four Newton
+// steps, whichever gives the smaller mass.  Same words as the core loop (region, angle or
+// Gaussian, acceptance); kept out of line, as wing scatterings are rare in thick gas
 // (everything passes by value, so the caller's stream state stays in registers).
-constexpr float kUparThreePiece = 3.0f;
+constexpr float kUparWing = 2.0f;
 struct UparDraw { float u; uint32_t trials; };
-static __device__ __noinline__ UparDraw sample_upar_far(float xr, float a, Rng rng) {
-  uint32_t iters = 0;
-  const float u0 = u0_rule(xr, a);
-  float u1 = 2.0f;
+struct WingSplit { float ub, b1, b2; };
+__device__ __forceinline__ float top_mass(float xr, float a, float b1, float b2) {
+  const float d12 = atan2f(a * (b2 - b1), __fmaf_rn(xr - b2, xr - b1, a * a));
+  return __expf(-b1 * b1) * d12 + __expf(-b2 * b2) * (kPiF - atan2f(a, xr - b2));
+}
+__device__ __forceinline__ WingSplit wing_split(float xr, float a) {
+  const float L = __logf(xr * (1.0f / 3.0f));
+  const float ub = fminf(__fmaf_rn(0.22f, L, 1.05f), xr - 1.2f);
+  const float b1 = fmaxf(fminf(__fmaf_rn(0.16f, L, 2.0f), xr - 0.6f), ub + 0.3f);
+  const float d = sqrtf(a / (2.0f * kPiF * xr)) * __expf(fminf(0.5f * (xr * xr - b1 * b1), 80.0f));
+  const float c1 = fmaxf(b1 + 1e-3f, xr - d);
+  float u = fminf(xr - 0.3f, b1 + 1.0f + 0.6f * __logf(xr));
 #pragma unroll
-  for (int it = 0; it < 3; ++it) u1 = sqrt_approx(__logf(__fmaf_rn(2.0f * u1, xr + u1, 1.0f)));
-  const float w1 = atan2_pos(a, xr - u0);
-  const float w0 = atan2_pos(a, xr + u1);
-  const float w01 = atan2_pos(a * (u0 + u1), __fmaf_rn(xr - u0, xr + u1, a * a));
-  const float s0 = u0 * u0, s1 = u1 * u1;
-  const float m0 = w0 * __expf(-s1), m2 = __expf(-s0) * (kPiF - w1);
-  const float inv = __frcp_rn(m0 + w01 + m2);
-  const float p0 = m0 * inv, p01 = (m0 + w01) * inv;
-  const float w0p = w0 * (1.0f / kPiF), w01p = w01 * (1.0f / kPiF), w1p = w1 * (1.0f / kPiF);
+  for (int it = 0; it < 4; ++it) {
+    const float dx = xr - u;
+    const float g = u * u - b1 * b1 - __logf(2.0f * kPiF * u * dx * dx / a);
+    const float gp = 2.0f * u - 1.0f / u + 2.0f / dx;
+    u = fminf(fmaxf(u - g / gp, b1 + 0.05f), xr - 1e-3f);
+  }
+  const float b2 = (top_mass(xr, a, b1, c1) <= top_mass(xr, a, b1, u)) ? c1 : u;
+  return WingSplit{ub, b1, b2};
+}
+static __device__ __noinline__ UparDraw sample_upar_wing(float xr, float a, Rng rng) {
+  uint32_t iters = 0;
+  const WingSplit sp = wing_split(xr, a);
+  const float ub = sp.ub, b1 = sp.b1, b2 = sp.b2;
+  const float a2 = a * a;
+  const float dub = xr - ub;
+  const float gden = __fmaf_rn(dub, dub, a2);  // (x - u_b)^2 + a^2
+  const float al0 = atan2f(a, dub);
+  const float d1 = atan2f(a * (b1 - ub), __fmaf_rn(xr - b1, dub, a2));
+  const float d2 = atan2f(a * (b2 - b1), __fmaf_rn(xr - b2, xr - b1, a2));
+  const float al1 = al0 + d1, al2 = al1 + d2;
+  const float e1 = __expf(-ub * ub), e2 = __expf(-b1 * b1), e3 = __expf(-b2 * b2);
+  const float mG = a * 1.7724538509f / gden, m1 = e1 * d1, m2 = e2 * d2, m3 = e3 * (kPiF - al2);
+  const float c1 = mG + m1, c2 = c1 + m2, tot = c2 + m3;
+  const float sub = ub * ub, sb1 = b1 * b1, sb2 = b2 * b2;
   auto trial = [&](uint32_t r1, uint32_t r2, uint32_t r3, float& u) {
-    const float R1 = uni32(r1), R2 = uni32(r2), R3 = uni32(r3);
-    float t, sh;
-    if (R1 < p0) { t = w0p * R2; sh = s1; }
-    else if (R1 < p01) { t = __fmaf_rn(w01p, R2, w0p); sh = 0.0f; }
-    else { t = __fmaf_rn(1.0f - w1p, R2, w1p); sh = s0; }
-    u = __fmaf_rn(-a, cot_pi(t), xr);
+    const float R1 = uni32(r1) * tot, R2 = uni32(r2), R3 = uni32(r3);
     ++iters;
+    if (R1 < mG) {  // Gaussian piece
+      u = erfinvf(__fmaf_rn(2.0f, R2, -1.0f));
+      if (!(u <= ub)) return false;
+      const float dx = xr - u;
+      return R3 * __fmaf_rn(dx, dx, a2) <= gden;
+    }
+    float lo, w, sh;
+    if (R1 < c1) { lo = al0; w = d1; sh = sub; }
+    else if (R1 < c2) { lo = al1; w = d2; sh = sb1; }
+    else { lo = al2; w = kPiF - al2; sh = sb2; }
+    u = __fmaf_rn(-a, cot_pi(__fmaf_rn(w, R2, lo) * (1.0f / kPiF)), xr);
     return R3 <= __expf(sh - u * u);
   };
   float u;
@@ -308,23 +418,26 @@ static __device__ __noinline__ UparDraw sample_upar_far(float xr, float a, Rng r
 __device__ __forceinline__ float sample_upar(float x, float a, const Rng& rng, uint32_t& iters) {
   const float sgn = (x < 0.0f) ? -1.0f : 1.0f;
   const float xr = fabsf(x);
-  if (xr > kUparThreePiece) {
-    const UparDraw d = sample_upar_far(xr, a, rng);
+  if (xr > kUparWing) {
+    const UparDraw d = sample_upar_wing(xr, a, rng);
     iters += d.trials;
     return sgn * d.u;
   }
   const float u0 = u0_rule(xr, a);
-  const float w1 = atan2_pos(a, xr - u0);
-  const float e0 = __expf(-u0 * u0);
-  const float p1 = __fdividef(w1, __fmaf_rn(e0, kPiF - w1, w1));
-  const float u02 = u0 * u0;
+  float w1;
+  if (xr <= 2.0f && u0 > 0.0f && upar_q(xr, a) <= 0.05f) w1 = atan_small(upar_q(xr, a));
+  else w1 = atan2_pos(a, xr - u0);
+  const float u02 = __fmul_rn(u0, u0);
+  const float e0 = exp_fast(-u02);
+  const float mass = envelope_mass(w1, e0);
   const float w1p = w1 * (1.0f / kPiF);  // alpha in units of pi
   auto trial = [&](uint32_t r1, uint32_t r2, uint32_t r3, float& u) {
     const float R1 = uni32(r1), R2 = uni32(r2), R3 = uni32(r3);
-    const bool reg1 = R1 < p1;
+    const bool reg1 = region1(R1, mass, w1);
     const float t = reg1 ? w1p * R2 : __fmaf_rn(1.0f - w1p, R2, w1p);
     u = __fmaf_rn(-a, cot_pi(t), xr);  // x - a cot(alpha)
-    const float acc = reg1 ? __expf(-u * u) : __expf(u02 - u * u);
+    const float uu = __fmul_rn(u, u);
+    const float acc = reg1 ? exp_fast(-uu) : exp_fast(u02 - uu);
     ++iters;
     return R3 <= acc;
   };
@@ -389,20 +502,28 @@ __device__ __forceinline__ float3 turn(const float3& k, const float3& e1, const 
   return make_float3(ko.x * inv, ko.y * inv, ko.z * inv);
 }
 
+// Eq. 7 without recoil: x_out = x - u_par + u . k_out, u . k_out = u_par mu + st (u1 cos phi
+// + u2 sin phi) (shared by scatter_resonant and the core bursts).
+__device__ __forceinline__ float x_after_scatter(float x, float upar, float mu, float st, float u1, float u2,
+                                                 float cp, float sp) {
+  const float perp = __fmul_rn(st, __fmaf_rn(u1, cp, __fmul_rn(u2, sp)));
+  return __fadd_rn(__fsub_rn(x, upar), __fmaf_rn(upar, mu, perp));
+}
+
 __device__ __forceinline__ float scatter_resonant(float x, float a, int phase, float3& k, const Rng& rng,
                                                   uint32_t& iters, AtomFrame* af, float xcrit = 0.0f) {
   const float xc = (fabsf(x) < xcrit) ? xcrit : 0.0f;
   const float r = sqrt_approx(__fmaf_rn(xc, xc, -__logf(rng.u(W_BM_R))));
   float sp1, cp1;
   __sincosf(2.0f * kPiF * rng.u(W_BM_PHI), &sp1, &cp1);
-  const float u1 = r * cp1, u2 = r * sp1;
+  const float u1 = __fmul_rn(r, cp1), u2 = __fmul_rn(r, sp1);
   const float Rm = rng.u(W_MU);
   float mu = (phase == PH_ISO) ? __fmaf_rn(2.0f, Rm, -1.0f) : mu_dipole(Rm);
   float sp, cp;
   __sincosf(2.0f * kPiF * rng.u(W_PHI), &sp, &cp);
   float3 e1, e2;
   basis(k.x, k.y, k.z, e1, e2);
-  float st = sqrt_approx(fmaxf(0.0f, 1.0f - mu * mu));
+  float st = sqrt_approx(fmaxf(0.0f, __fmaf_rn(-mu, mu, 1.0f)));
   float3 ko = turn(k, e1, e2, mu, st, cp, sp);
   const float upar = sample_upar(x, a, rng, iters);
   const bool core = fabsf(x - upar) < 0.2f;
@@ -413,7 +534,7 @@ __device__ __forceinline__ float scatter_resonant(float x, float a, int phase, f
   }
   if (af) { af->upar = upar; af->u1 = u1; af->u2 = u2; af->e1 = e1; af->e2 = e2; af->core = core; }
   k = ko;
-  return x - upar + __fmaf_rn(upar, mu, st * __fmaf_rn(u1, cp, u2 * sp));
+  return x_after_scatter(x, upar, mu, st, u1, u2, cp, sp);
 }
 
 __device__ __forceinline__ void scatter_dust(float g, float3& k, const Rng& rng) {

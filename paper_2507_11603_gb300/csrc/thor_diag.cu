@@ -80,7 +80,46 @@ inline unsigned blocks_for(int64_t n, int b) {
   return (unsigned)(g < 152 * 64 ? (g > 0 ? g : 1) : 152 * 64);
 }
 
+// Issue-rate probe (the denominators of the ALU rooflines): every thread runs eight
+// independent chains of `iters` dependent operations of one kind, so every scheduler always
+// has an independent instruction to issue; kind 0 = FP32 FMA (the issue-slot peak, one warp
+// instruction per scheduler per clock), kind 1 = MUFU ex2 (the special-function pipe).
+// The sum is stored so nothing is optimised away.
+template <int kKind>
+__global__ void __launch_bounds__(256) issue_probe_kernel(float* __restrict__ sink, int iters, float seed) {
+  float v[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = seed * (float)(threadIdx.x + 1) + 0.001f * (float)j;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if (kKind == 0) v[j] = __fmaf_rn(v[j], 0.9999999f, 1e-7f);
+      else v[j] = ex2_approx(v[j]) - 1.5f;
+    }
+  }
+  float acc = 0.0f;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) acc += v[j];
+  if (acc == 12345.678f) sink[blockIdx.x * blockDim.x + threadIdx.x] = acc;  // practically never
+}
+
+__global__ void xcw_kernel(const float* __restrict__ a, float* __restrict__ out, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = xcw_b25(a[i]);
+}
+
 }  // namespace
+
+cudaError_t launch_issue_probe(int kind, float* sink, int grid, int block, int iters, cudaStream_t s) {
+  if (kind == 0) issue_probe_kernel<0><<<grid, block, 0, s>>>(sink, iters, 1e-3f);
+  else issue_probe_kernel<1><<<grid, block, 0, s>>>(sink, iters, 1e-3f);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_xcw_eval(const float* a, float* out, int64_t n, cudaStream_t s) {
+  xcw_kernel<<<blocks_for(n, 256), 256, 0, s>>>(a, out, n);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_voigt_eval(const float* a, const float* x, float* H, int64_t n, const float* d_ktab,
                               cudaStream_t s, int precise) {

@@ -43,6 +43,7 @@ struct ShellModel {
   unsigned long long id_base;
   unsigned long long n_photons;
   int32_t cancelled;         // served requests: drop in-flight packets (set by the host)
+  int32_t priority;          // served requests: packets run one per warp (set by the host per round)
   int32_t profile;           // 0 homologous uniform shell, 1 power-law shell (Sec. 5.1)
   // power law: n(r) / n(1) = r^ar, v(r) = v1 r^av (radial), opacities per unit length at r = 1
   float ar, av, v1, kapn, kapdn;
@@ -110,6 +111,7 @@ struct Compact {
   unsigned long long* n_spill;
   int32_t spill_below;  // 0: run to completion
   int32_t per_warp;     // lanes per warp that take packets (1..32): few packets spread over all schedulers
+  int32_t core_lanes;   // warps with at most this many live packets run core events in bursts (0 = never)
 };
 
 // Resident packet state for time-sliced (served) execution, SoA, one slot per thread.
@@ -123,7 +125,10 @@ struct SlotState {
   unsigned long long* pid;
   uint8_t* region;
   int64_t n_slots;                   // capacity (packets)
-  unsigned long long* live;          // [0] packets stored in this buffer, [1] append counter of the next
+  // [0] packets stored in this buffer from the front, [1] their append counter in the next
+  // buffer; [2] priority packets stored from the back (entry j at n_slots - 1 - j), [3] their
+  // append counter in the next buffer
+  unsigned long long* live;
 };
 
 // Grid model (Sec. 3.3 uniform Cartesian grid), packed 32 B per cell.
@@ -168,7 +173,7 @@ struct GridModel {
 int shell_grid(int block, int blocks_per_sm, bool sliced);  // persistent grid size
 int grid_grid(int block, int blocks_per_sm);
 cudaError_t launch_shell_run(const ShellModel* d_models, WorkQueue q, const float* d_ktab, int grid,
-                             int block, int profile, int per_warp, cudaStream_t s);
+                             int block, int profile, int per_warp, int core_lanes, cudaStream_t s);
 cudaError_t launch_shell_run_compact(const ShellModel* d_models, WorkQueue q, Compact c, const float* d_ktab,
                                      int grid, int block, int profile, cudaStream_t s);
 cudaError_t launch_reweight(int64_t n, const float* X0, const float* X, const float* col, const uint8_t* status,
@@ -189,6 +194,8 @@ cudaError_t launch_forest(const float* nHI, const float* T, const float* vlos, i
                           double dv_bin, float* tau, const float* d_ktab, cudaStream_t s);
 cudaError_t launch_voigt_eval(const float* a, const float* x, float* H, int64_t n, const float* d_ktab,
                               cudaStream_t s, int precise);
+cudaError_t launch_xcw_eval(const float* a, float* out, int64_t n, cudaStream_t s);
+cudaError_t launch_issue_probe(int kind, float* sink, int grid, int block, int iters, cudaStream_t s);
 cudaError_t launch_dda_trace(int nx, int ny, int nz, const double* org, const float* dir, int n, int max_steps,
                              int64_t* cells, double* seg, int32_t* count, cudaStream_t s);
 cudaError_t launch_upar(float x, float a, uint64_t seed, int64_t n, float* out, unsigned long long* iters,

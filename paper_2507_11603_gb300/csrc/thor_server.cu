@@ -45,6 +45,9 @@ struct Request {
   int state = 0;           // 0 pending, 1 active, 2 done, 3 cancelled
   bool cancel = false;
   bool cancel_sent = false;
+  bool priority = false;       // wanted this round: packets one per warp
+  bool priority_sent = false;  // as last set on the device
+  uint64_t done_seen = 0;      // photons finished, as of the last round's tallies
   Clock::time_point t_submit, t_done;
   thor_result result{};
 };
@@ -166,6 +169,27 @@ void thor_server::run() {
         ++n_entries;
       }
       h_prefix[n_entries] = total;
+      // priority: the oldest request, and the next oldest while their packets in flight fit
+      // in half of the warps, run their packets one per warp, so the longest histories of the
+      // requests that have waited longest advance at the latency of a lone lane (the slice
+      // kernel gives each such packet a warp of its own, up to half of the warps, and spreads
+      // the rest with the other packets)
+      {
+        std::vector<std::pair<int64_t, int>> by_age;
+        for (int i = 0; i < R; ++i)
+          if (active[i] && !active[i]->cancel) by_age.emplace_back(active[i]->ticket, i);
+        std::sort(by_age.begin(), by_age.end());
+        const uint64_t cap = (uint64_t)(n_slots / 32) / 2;
+        uint64_t cum = 0;
+        bool open = cfg.priority >= 0;
+        for (const auto& oi : by_age) {
+          Request* r = active[oi.second];
+          const uint64_t resident = r->issued - std::min(r->issued, r->done_seen);
+          r->priority = open && (cum == 0 || cum + resident <= cap);
+          if (r->priority) cum += resident + 1;
+          else open = false;
+        }
+      }
       // rounds run kIdleRounds x longer while nobody waits for admission: fewer launches
       // and host round trips for the tails of admitted requests
       budget = pending.empty() ? (uint64_t)cfg.events_per_round * kIdleRounds : (uint64_t)cfg.events_per_round;
@@ -178,8 +202,19 @@ void thor_server::run() {
     }
     cudaStream_t s = stream;
     bool ok = true;
+    for (Request* r : fresh) {
+      ShellModel m = r->model;
+      m.spectrum = d_spec + (size_t)r->slot * (max_bins + 2);
+      m.tally = d_tally + r->slot;
+      m.priority = 0;
+      r->priority_sent = false;
+      ok &= cudaMemcpyAsync(d_models + r->slot, &m, sizeof m, cudaMemcpyHostToDevice, s) == cudaSuccess;
+      ok &= cudaMemsetAsync(m.spectrum, 0, (size_t)(max_bins + 2) * 8, s) == cudaSuccess;
+      ok &= cudaMemsetAsync(m.tally, 0, sizeof(Tally), s) == cudaSuccess;
+    }
     {
-      // tell the device which admitted requests were cancelled (their packets are dropped)
+      // tell the device which admitted requests were cancelled (their packets are dropped);
+      // after the model uploads of this round, which would otherwise overwrite the flag
       std::lock_guard<std::mutex> lk(mu);
       for (int i = 0; i < R; ++i) {
         Request* r = active[i];
@@ -190,13 +225,18 @@ void thor_server::run() {
         }
       }
     }
-    for (Request* r : fresh) {
-      ShellModel m = r->model;
-      m.spectrum = d_spec + (size_t)r->slot * (max_bins + 2);
-      m.tally = d_tally + r->slot;
-      ok &= cudaMemcpyAsync(d_models + r->slot, &m, sizeof m, cudaMemcpyHostToDevice, s) == cudaSuccess;
-      ok &= cudaMemsetAsync(m.spectrum, 0, (size_t)(max_bins + 2) * 8, s) == cudaSuccess;
-      ok &= cudaMemsetAsync(m.tally, 0, sizeof(Tally), s) == cudaSuccess;
+    {
+      // priority flags that changed since the last round
+      static const int32_t kOne = 1, kZero = 0;
+      std::lock_guard<std::mutex> lk(mu);
+      for (int i = 0; i < R; ++i) {
+        Request* r = active[i];
+        if (r && r->priority != r->priority_sent) {
+          ok &= cudaMemcpyAsync(&d_models[i].priority, r->priority ? &kOne : &kZero, sizeof(int32_t),
+                                cudaMemcpyHostToDevice, s) == cudaSuccess;
+          r->priority_sent = r->priority;
+        }
+      }
     }
     // queue header (the tables were filled in place above), then the captured round
     ((unsigned long long*)(h_queue + L.next))[0] = 0;
@@ -241,6 +281,7 @@ void thor_server::run() {
         Request* r = active[i];
         if (!r) continue;
         resident += r->issued - h_tally[i].n_done;
+        r->done_seen = h_tally[i].n_done;
         const bool all_done = h_tally[i].n_done >= r->n_photons;
         const bool cancelled_drained = r->cancel && h_tally[i].n_done >= r->issued;
         if (all_done || cancelled_drained) finished.push_back(r);
@@ -305,7 +346,8 @@ extern "C" int thor_server_create(thor_ctx_t ctx, const thor_server_config* cfg,
     return ctx->fail(THOR_ERR_OOM, "thor_server_create: device allocation failed");
   }
   // carve the two packet lists (256-byte aligned SoA arrays, identical layouts) and the
-  // counters {packets in the in list, append counter of the out list}
+  // counters {packets in the in list from the front, their append counter in the out list,
+  // priority packets in the in list from the back, their append counter}
   auto carve = [&](char* p, SlotState& st) {
     auto take = [&](size_t bytes) { char* q = p; p += (bytes + 255) & ~(size_t)255; return (void*)q; };
     st.px = (double*)take(n * 8); st.py = (double*)take(n * 8); st.pz = (double*)take(n * 8);
@@ -327,7 +369,7 @@ extern "C" int thor_server_create(thor_ctx_t ctx, const thor_server_config* cfg,
   unsigned long long* live = (unsigned long long*)(base + 2 * slot_bytes);
   s->st_in.live = live;
   s->st_out.live = live;
-  cudaMemsetAsync(live, 0, 16, s->stream);  // no packets in flight
+  cudaMemsetAsync(live, 0, 32, s->stream);  // no packets in flight
   cudaStreamSynchronize(s->stream);
   // capture one round (thread-local capture mode: other host threads are unaffected)
   {
@@ -352,6 +394,8 @@ extern "C" int thor_server_create(thor_ctx_t ctx, const thor_server_config* cfg,
       cudaMemcpyAsync(s->d_slots, (char*)s->d_slots + s->slot_bytes, s->slot_bytes, cudaMemcpyDeviceToDevice, cs);
       cudaMemcpyAsync(&s->st_in.live[0], &s->st_in.live[1], 8, cudaMemcpyDeviceToDevice, cs);
       cudaMemsetAsync(&s->st_in.live[1], 0, 8, cs);
+      cudaMemcpyAsync(&s->st_in.live[2], &s->st_in.live[3], 8, cudaMemcpyDeviceToDevice, cs);
+      cudaMemsetAsync(&s->st_in.live[3], 0, 8, cs);
       cudaMemcpyAsync(s->h_out, s->d_queue + L.next, 8, cudaMemcpyDeviceToHost, cs);
       cudaMemcpyAsync(s->h_out + 8, s->d_tally, sizeof(Tally) * R, cudaMemcpyDeviceToHost, cs);
       cap = cudaStreamEndCapture(cs, &s->graph[v]) == cudaSuccess &&

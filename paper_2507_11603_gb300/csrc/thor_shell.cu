@@ -88,6 +88,25 @@ __device__ __forceinline__ float safe_distance(const ShellModel& m, const Photon
   return fmaxf(__double2float_rd(d) * 0.999999f, 0.0f);
 }
 
+// The start of a step, shared by shell_event's fast paths and the core bursts (one
+// definition, so both evaluate an event bit for bit alike): H(a, x) from the table-free
+// polynomial in the core (|x| <= 2), else from the table; kH = kap0 H; the crossing at the
+// start-point rate s = tau / (kH + kapd); dust is chosen when R (kH + kapd) >= kH (the
+// channel of Sec. 3.4, probability kapd / (kH + kapd)).
+struct StartStep { float kH, s; };
+__device__ __forceinline__ float voigt_start(float a, float x, const float* __restrict__ Ktab) {
+  return (fabsf(x) <= THOR_VCORE_X) ? voigt_core_poly(a, x) : voigt<false>(a, x, Ktab);
+}
+__device__ __forceinline__ StartStep start_step(const ShellModel& m, float H, float tau) {
+  const float kH = __fmul_rn(m.kap0, H);
+  return StartStep{kH, __fmul_rn(tau, rcp_approx(__fadd_rn(kH, m.kapd)))};
+}
+// The optical depth to the next interaction, tau = -ln R (Eq. 3), shared likewise.
+__device__ __forceinline__ float draw_tau(const Rng& r) { return -ln_fast(r.u(W_TAU)); }
+__device__ __forceinline__ bool dust_channel(const ShellModel& m, float kH, float R) {
+  return __fmul_rn(R, __fadd_rn(kH, m.kapd)) >= kH;
+}
+
 // One event.  Returns 0 = continues, 1 = escaped, 2 = absorbed by dust, 3 = capped.
 // The gas-frame frequency x is carried along the ray: in the homologous flow it drifts
 // as x(s) = x0 - gam s in every direction, and a scattering leaves it at x_out at the
@@ -96,7 +115,7 @@ __device__ __forceinline__ float safe_distance(const ShellModel& m, const Photon
 // case for photons trapped in the line core).
 __device__ int shell_event(const ShellModel& m, Photon& ph, const float* __restrict__ Ktab) {
   ph.rng.next_event((m.kapd > 0.0f || m.phase == PH_MIXED) ? 3u : 2u);
-  float tau_rem = -__logf(ph.rng.u(W_TAU));  // Eq. 3: tau ~ Exp(1)
+  float tau_rem = draw_tau(ph.rng);  // Eq. 3: tau ~ Exp(1)
   float x_site, kH;
   for (;;) {
     if (ph.region) {  // empty cavity: straight to the inner sphere, lab X conserved
@@ -112,10 +131,9 @@ __device__ int shell_event(const ShellModel& m, Photon& ph, const float* __restr
     }
     // ---- fast path: the next (sub-)step lies inside the safety ball
     if (m.gam == 0.0f) {
-      const float H = voigt<false>(m.a, ph.x, Ktab);
-      kH = m.kap0 * H;
-      const float kap = kH + m.kapd;
-      const float s = __fdividef(tau_rem, kap);
+      const StartStep st0 = start_step(m, voigt_start(m.a, ph.x, Ktab), tau_rem);
+      kH = st0.kH;
+      const float s = st0.s;
       ++ph.steps;
       if (s <= ph.safe) {
         advance(ph, s);
@@ -126,15 +144,14 @@ __device__ int shell_event(const ShellModel& m, Photon& ph, const float* __restr
     } else if (ph.safe >= m.ds_core) {
       // Rate at the start of the step: a crossing within ds_core / 16 of the start is a
       // sub-step of its own, integrated with that rate (the common case in the core).
-      const float H0 = voigt<false>(m.a, ph.x, Ktab);
-      const float kap_s = __fmaf_rn(m.kap0, H0, m.kapd);
-      const float s0 = __fdividef(tau_rem, kap_s);
+      const StartStep st0 = start_step(m, voigt_start(m.a, ph.x, Ktab), tau_rem);
+      const float s0 = st0.s;
       if (s0 <= 0.0625f * m.ds_core) {
         ++ph.steps;
         advance(ph, s0);
         ph.safe = __fmaf_rd(-s0, 1.000001f, ph.safe);
-        x_site = ph.x - m.gam * s0;
-        kH = m.kap0 * H0;
+        x_site = __fmaf_rn(-m.gam, s0, ph.x);
+        kH = st0.kH;
         break;
       }
       const float ds = m.ds_core;
@@ -208,7 +225,7 @@ __device__ int shell_event(const ShellModel& m, Photon& ph, const float* __restr
   ph.x = x_site;
   // Interaction (Sec. 3.4): channel i with probability tau_i / sum_i tau_i.
   bool dust = false;
-  if (m.kapd > 0.0f) dust = ph.rng.u(W_CHANNEL) >= __fdividef(kH, kH + m.kapd);
+  if (m.kapd > 0.0f) dust = dust_channel(m, kH, ph.rng.u(W_CHANNEL));
   if (dust) {
     bool scat;
     if (m.albedo <= 0.0f) scat = false;
@@ -229,6 +246,108 @@ __device__ int shell_event(const ShellModel& m, Photon& ph, const float* __restr
     return 3;
   }
   return 0;
+}
+
+// ---- pipelined core events (homologous shells) ------------------------------------
+// A packet trapped in the line core spends its life in one kind of event: the crossing lies
+// within ds/16 of the start (start-point rate, Sec. 5.1 step limiter) inside the safety
+// ball, the interaction is a resonant scattering at |x| <= 2 (Sec. 3.4), and the first
+// trial of the u_par sampler (Eq. 10) is accepted.  In such an event only the frequency
+// chain x -> H(a,x) -> s -> x_site -> u_par -> x_out depends on the packet's state; the next
+// event's Philox blocks and optical depth, the perpendicular atom velocity (Eq. 5), mu and
+// the outgoing direction depend only on the event's random words and the incoming
+// direction.  core_burst forms them beside the chain of the current event, in one basic
+// block per event, so that the scheduler fills the chain's dependency stalls with them (a
+// lone lane issues in order and would otherwise wait on each link), and commits the event
+// only if it is of that kind.  Otherwise the packet is left at the event boundary and
+// shell_event runs the event in full from the same words.  Three things differ from
+// shell_event's evaluation of the same event, none in distribution: H comes from the
+// table-free core polynomial (voigt_core_poly, |x| <= 2, error below the fast path's);
+// the region and channel tests compare products instead of quotients; w1 = atan(a/d) is
+// formed from a/d = sqrt(2 pi a x) e^{-x^2/2} directly (a/d <= 1/20, where the series
+// atan2_pos uses is exact to 3e-9).  Returns 3 if the scattering cap was reached (the
+// packet is then finished as shell_event finishes it), else 0.
+constexpr uint32_t kCoreBurst = 32;  // events per burst at most
+constexpr int kCoreLanes = 4;        // served rounds: bursts in warps with at most this many live packets
+
+__device__ __forceinline__ int core_burst(const ShellModel& m, Photon& ph, uint32_t max_ev, uint32_t& n) {
+  n = 0;
+  if (m.phase == PH_MIXED || ph.region || !(fabsf(ph.x) <= THOR_VCORE_X)) return 0;
+  const uint32_t nblk = (m.kapd > 0.0f) ? 3u : 2u;
+  Rng r = ph.rng;
+  r.next_event(nblk);
+  float tau = draw_tau(r);
+  const float ds16 = 0.0625f * m.ds_core;
+  int status = 0;
+  for (; n < max_ev; ++n) {
+    // ---- the frequency chain: rate at the start, crossing, gas-frame frequency at the site
+    const float x0 = ph.x;
+    const StartStep st0 = start_step(m, voigt_core_poly(m.a, x0), tau);
+    const float s0 = st0.s;
+    const bool in_ball = (m.gam == 0.0f) ? (s0 <= ph.safe) : (ph.safe >= m.ds_core && s0 <= ds16);
+    const float xs = (m.gam == 0.0f) ? x0 : __fmaf_rn(-m.gam, s0, x0);
+    const bool dust = (m.kapd > 0.0f) && dust_channel(m, st0.kH, r.u(W_CHANNEL));
+    // ---- u_par, first trial of the two-piece comparison function (as sample_upar)
+    const float sgn = (xs < 0.0f) ? -1.0f : 1.0f;
+    const float xr = fabsf(xs);
+    const float u0 = u0_core(xr, m.a);
+    const float q = upar_q(xr, m.a);
+    const float w1 = atan_small(q);
+    const float u02 = __fmul_rn(u0, u0);
+    const float mass = envelope_mass(w1, exp_fast(-u02));
+    const float w1p = w1 * (1.0f / kPiF);
+    const float R1 = r.u(W_UPAR0), R2 = r.u(W_UPAR0 + 1), R3 = r.u(W_UPAR0 + 2);
+    const bool reg1 = region1(R1, mass, w1);
+    const float t = reg1 ? w1p * R2 : __fmaf_rn(1.0f - w1p, R2, w1p);
+    const float u = __fmaf_rn(-m.a, cot_pi(t), xr);
+    const float uu = __fmul_rn(u, u);
+    const float acc = reg1 ? exp_fast(-uu) : exp_fast(u02 - uu);
+    // ---- beside the chain: perpendicular velocity, mu, outgoing direction (as scatter_resonant)
+    const float xc = (xr < m.xcrit) ? m.xcrit : 0.0f;
+    const float rr = sqrt_approx(__fmaf_rn(xc, xc, -__logf(r.u(W_BM_R))));
+    float sp1, cp1;
+    __sincosf(2.0f * kPiF * r.u(W_BM_PHI), &sp1, &cp1);
+    const float u1 = __fmul_rn(rr, cp1), u2 = __fmul_rn(rr, sp1);
+    const float Rm = r.u(W_MU);
+    const float mu = (m.phase == PH_ISO) ? __fmaf_rn(2.0f, Rm, -1.0f) : mu_dipole(Rm);
+    float sp, cp;
+    __sincosf(2.0f * kPiF * r.u(W_PHI), &sp, &cp);
+    float3 e1, e2;
+    basis(ph.k.x, ph.k.y, ph.k.z, e1, e2);
+    const float st = sqrt_approx(fmaxf(0.0f, __fmaf_rn(-mu, mu, 1.0f)));
+    const float3 ko = turn(ph.k, e1, e2, mu, st, cp, sp);
+    // ---- the next event's words and optical depth
+    Rng r2 = r;
+    r2.next_event(nblk);
+    const float tau2 = draw_tau(r2);
+    if (!(in_ball && !dust && xr <= 2.0f && u0 > 0.0f && q <= 0.05f && R3 <= acc)) break;
+    // ---- commit, as shell_event and scatter_resonant do
+    ++ph.steps;
+    advance(ph, s0);
+    ph.safe = __fmaf_rd(-s0, 1.000001f, ph.safe);
+    ph.x = x_after_scatter(xs, sgn * u, mu, st, u1, u2, cp, sp);
+    ph.k = ko;
+    ++ph.iters;
+    ++ph.nscat;
+    r = r2;
+    tau = tau2;
+    if (m.max_scat && ph.nscat >= m.max_scat) {
+      ++n;
+      status = 3;
+      break;
+    }
+    if (!(fabsf(ph.x) <= THOR_VCORE_X)) {  // the next start is outside the polynomial's range
+      ++n;
+      break;
+    }
+  }
+  ph.rng.event = r.event - 1u;  // the event being tried is redone by shell_event
+  if (status == 3) {
+    anchor(ph);
+    const float b = (float)(ph.px * ph.k.x + ph.py * ph.k.y + ph.pz * ph.k.z);
+    ph.X = __fmaf_rn(ph.x, m.vth, m.vgrad * b);
+  }
+  return status;
 }
 
 // ---- power-law shells (Sec. 5.1) ---------------------------------------------------
@@ -519,13 +638,20 @@ __global__ void __launch_bounds__(256, 1) shell_run_kernel(const ShellModel* __r
       }
     }
     if (__all_sync(kFull, !active)) break;
+    // warps with few live packets (the tail of a run) take core events in bursts
+    const bool burst = kProfile == 0 && __popc(__ballot_sync(kFull, active)) <= c.core_lanes;
     // events until some lane of the warp finishes its packet: one vote per event, the
     // refill and spill checks above run only when the set of live lanes changed
     bool fin;
     do {
       fin = false;
       if (active) {
-        const int st = kProfile ? shell_event_pl(m, ph, sK) : shell_event(m, ph, sK);
+        int st = 0;
+        if (burst) {
+          uint32_t nb;
+          st = core_burst(m, ph, kCoreBurst, nb);
+        }
+        if (!st) st = kProfile ? shell_event_pl(m, ph, sK) : shell_event(m, ph, sK);
         if (st) {
           if (st == 1) { ++lt.esc; tally_spectrum(m, ph.X); }
           else if (st == 2) ++lt.abs;
@@ -552,11 +678,17 @@ __global__ void __launch_bounds__(256, 1) shell_run_kernel(const ShellModel* __r
   }
 }
 
-// Time-sliced execution (serving): packets in flight live in a list (`in`, in.live[0]
-// entries); lane l of warp w resumes entry w + l * n_warps, so the packets spread over all
-// warps every launch.  Each lane runs at most `budget` events, finished lanes take new
-// photons from the queue of admitted requests while the warp has fewer than per_warp live
-// packets, and what is still in flight is appended to `out` (out.live[1]).
+// Time-sliced execution (serving): packets in flight live in a list (`in`): in.live[0]
+// entries from the front, and in.live[2] priority entries from the back (packets of the
+// requests the host marked as priority, the oldest ones).  The first priority packets, up
+// to half of the warps, each run alone in a warp of their own (one packet per warp, so
+// the longest histories of the oldest requests advance at the latency of a lone lane
+// instead of behind divergent packets of other requests).  The remaining entries spread
+// over the other warps: lane l of warp w resumes entry w + l * (their count).  Each lane
+// runs at most `budget` events, finished lanes take new photons from the queue of admitted
+// requests while the warp has fewer live packets than its limit (1 for a priority warp,
+// per_warp otherwise), and what is still in flight is appended to `out`: priority packets
+// from the back (out.live[3]), the others from the front (out.live[1]).
 // kMixed: the round holds power-law models too (the event function is chosen per lane);
 // otherwise only homologous shells, compiled without the power-law event.
 template <bool kMixed>
@@ -573,13 +705,30 @@ __global__ void __launch_bounds__(256, 1) shell_slice_kernel(const ShellModel* _
   const unsigned lane = threadIdx.x & 31u;
   const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const unsigned long long n_in = in.live[0];
-  const int pw_in = (int)((n_in + n_warps - 1) / n_warps);  // every stored packet is resumed
-  const int64_t slot = warp + (int64_t)lane * n_warps;
+  const unsigned long long n_in = in.live[0], n_pri = in.live[2];
+  // priority warps: [0, n_pw), one priority packet each; the rest of the priority list and
+  // the front list spread over warps [n_pw, n_warps), at most 32 per warp.  Every stored
+  // packet must find a lane: n_in + n_pri - n_pw <= 32 (n_warps - n_pw), i.e.
+  // n_pw <= (32 n_warps - n_in - n_pri) / 31 (none when the list is full), and at most half
+  // of the warps.
+  const unsigned long long lanes = 32ull * (unsigned long long)n_warps;
+  const unsigned long long fit = (lanes > n_in + n_pri) ? (lanes - n_in - n_pri) / 31ull : 0ull;
+  const int64_t n_pw = (int64_t)min(min(n_pri, (unsigned long long)(n_warps / 2)), fit);
+  const unsigned long long rest = n_in + (n_pri - (unsigned long long)n_pw);
+  const int64_t n_rest_warps = n_warps - n_pw;
+  const bool pri_warp = warp < n_pw;
+  if (pri_warp) per_warp = 1;
+  int64_t slot = -1;
+  if (pri_warp) {
+    if (lane == 0) slot = in.n_slots - 1 - warp;
+  } else {
+    const unsigned long long e = (unsigned long long)(warp - n_pw) + (unsigned long long)lane * n_rest_warps;
+    if (e < rest) slot = (e < n_in) ? (int64_t)e : in.n_slots - 1 - (int64_t)(n_pw + (e - n_in));
+  }
   Photon ph;
   bool active = false, done = false;
   const SlotState& st = in;
-  if ((int)lane < pw_in && (unsigned long long)slot < n_in) {
+  if (slot >= 0) {
     ph.model = st.model[slot];
     const ShellModel& m = models[ph.model];
     ph.pid = st.pid[slot];
@@ -632,26 +781,38 @@ __global__ void __launch_bounds__(256, 1) shell_slice_kernel(const ShellModel* _
     }
     if (__any_sync(kFull, dropped)) { ++ev; continue; }  // refill the dropped lanes first
     const ShellModel mr = *mp;  // by value: the fields the event loop reads stay in registers
-    // events until some lane finishes its packet or the budget is used: one vote per event
+    // events until some lane finishes its packet or the budget is used: one vote per event;
+    // warps with few live packets take core events in bursts, charged to the budget by the
+    // longest burst of the warp
+    const bool burst = __popc(__ballot_sync(kFull, active)) <= kCoreLanes;
     bool fin;
     do {
       fin = false;
+      uint32_t nb = 0;
       if (active) {
-        const int r = (kMixed && mr.profile) ? shell_event_pl(mr, ph, sK) : shell_event(mr, ph, sK);
+        int r = 0;
+        if (burst && !(kMixed && mr.profile) && budget - ev > 1u) r = core_burst(mr, ph, min(kCoreBurst, budget - ev - 1u), nb);
+        if (!r) r = (kMixed && mr.profile) ? shell_event_pl(mr, ph, sK) : shell_event(mr, ph, sK);
         if (r) { finish_global(mr, ph, r); active = false; fin = true; }
       }
-      ++ev;
+      ev += 1u + __reduce_max_sync(kFull, nb);
     } while (ev < budget && !__any_sync(kFull, fin));
   }
-  // append the packets still in flight to the next list (one atomic per warp)
-  const unsigned live = __ballot_sync(kFull, active);
-  if (live) {
-    const int leader = __ffs(live) - 1;
-    unsigned long long base = 0;
-    if ((int)lane == leader) base = atomicAdd(&out.live[1], (unsigned long long)__popc(live));
-    base = __shfl_sync(kFull, base, leader);
+  // append the packets still in flight to the next list (one atomic per warp and list):
+  // packets of priority requests from the back, the others from the front
+  const bool pri = active && *(volatile const int32_t*)&models[ph.model].priority;
+  const unsigned live_f = __ballot_sync(kFull, active && !pri), live_b = __ballot_sync(kFull, pri);
+  if (live_f | live_b) {
+    const int lead_f = live_f ? __ffs(live_f) - 1 : 0, lead_b = live_b ? __ffs(live_b) - 1 : 0;
+    unsigned long long base_f = 0, base_b = 0;
+    if (live_f && (int)lane == lead_f) base_f = atomicAdd(&out.live[1], (unsigned long long)__popc(live_f));
+    if (live_b && (int)lane == lead_b) base_b = atomicAdd(&out.live[3], (unsigned long long)__popc(live_b));
+    base_f = __shfl_sync(kFull, base_f, lead_f);
+    base_b = __shfl_sync(kFull, base_b, lead_b);
     if (active) {
-      const unsigned long long j = base + __popc(live & ((1u << lane) - 1u));
+      const unsigned mine = pri ? live_b : live_f;
+      const unsigned long long r = (pri ? base_b : base_f) + __popc(mine & ((1u << lane) - 1u));
+      const unsigned long long j = pri ? (unsigned long long)(out.n_slots - 1) - r : r;
       SlotState& o = out;
       o.model[j] = ph.model; o.pid[j] = ph.pid;
       o.event[j] = ph.rng.event;
@@ -678,9 +839,10 @@ int shell_grid(int block, int blocks_per_sm, bool sliced) {
 }
 
 cudaError_t launch_shell_run(const ShellModel* d_models, WorkQueue q, const float* d_ktab, int grid, int block,
-                             int profile, int per_warp, cudaStream_t s) {
+                             int profile, int per_warp, int core_lanes, cudaStream_t s) {
   Compact none{};
   none.per_warp = per_warp;
+  none.core_lanes = core_lanes;
   if (profile) shell_run_kernel<false, 1><<<grid, block, 0, s>>>(d_models, q, none, d_ktab);
   else shell_run_kernel<false, 0><<<grid, block, 0, s>>>(d_models, q, none, d_ktab);
   return cudaGetLastError();

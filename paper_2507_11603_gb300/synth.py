@@ -97,12 +97,14 @@ def forest_fields_numpy(shape, seed: int = 5, mean_nHI: float = 1e-10, sigma_ln:
 
 
 def forest_fields_torch(n: int = 1024, seed: int = 5, mean_nHI: float = 1e-10, sigma_ln: float = 2.0,
-                        T0: float = 1e4, sigma_v: float = 30.0, device: str = "cuda"):
-    """The 1024^3 forest box generated on the GPU in FP32 (torch.fft), fields (nz, ny, nx)."""
+                        T0: float = 1e4, sigma_v: float = 30.0, device: str = "cuda", shape=None):
+    """The 1024^3 forest box generated on the GPU in FP32 (torch.fft), fields (nz, ny, nx);
+    `shape` = (nz, ny, nx) for a box of other proportions (e.g. fewer sightlines of the
+    full 1024 cells)."""
     import torch
     gen = torch.Generator(device=device)
     gen.manual_seed(seed)
-    shape = (n, n, n)
+    shape = tuple(shape) if shape is not None else (n, n, n)
     g = torch.randn(shape, generator=gen, device=device, dtype=torch.float32)
     ratio = torch.exp(sigma_ln * g - 0.5 * sigma_ln ** 2)
     del g
@@ -112,9 +114,9 @@ def forest_fields_torch(n: int = 1024, seed: int = 5, mean_nHI: float = 1e-10, s
     w = torch.randn(shape, generator=gen, device=device, dtype=torch.float32)
     f = torch.fft.rfftn(w)
     del w
-    kz = torch.fft.fftfreq(n, device=device)
-    ky = torch.fft.fftfreq(n, device=device)
-    kx = torch.fft.rfftfreq(n, device=device)
+    kz = torch.fft.fftfreq(shape[0], device=device)
+    ky = torch.fft.fftfreq(shape[1], device=device)
+    kx = torch.fft.rfftfreq(shape[2], device=device)
     k2 = kz[:, None, None] ** 2 + ky[None, :, None] ** 2 + kx[None, None, :] ** 2
     amp = torch.where(k2 > 0, k2.clamp_min(1e-30).pow(-11.0 / 12.0), torch.zeros_like(k2))
     f *= amp

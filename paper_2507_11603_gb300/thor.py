@@ -29,7 +29,8 @@ SYMBOLS = [
     "thor_forest", "thor_last_elapsed_ms", "thor_server_create", "thor_server_submit", "thor_server_poll",
     "thor_server_wait", "thor_server_cancel", "thor_server_stats", "thor_server_destroy", "thor_voigt_eval",
     "thor_dda_trace", "thor_sample_upar", "thor_scatter_once", "thor_philox", "thor_line_params",
-    "thor_run_shell_noalloc", "thor_noalloc_last_error", "thor_reweight",
+    "thor_run_shell_noalloc", "thor_noalloc_last_error", "thor_reweight", "thor_xcw_eval", "thor_ctx_set_bursts",
+    "thor_issue_peak",
 ]
 PROFILE = {"homologous": 0, "power_law": 1}
 SPECIES = {"HI": 0, "MgII": 1}
@@ -79,7 +80,7 @@ class ForestSpec(C.Structure):
 
 class ServerConfig(C.Structure):
     _fields_ = [("max_requests", C.c_int32), ("events_per_round", C.c_int32), ("n_slots", C.c_int64),
-                ("mem_budget_bytes", C.c_uint64), ("block_size", C.c_int32), ("reserved", C.c_int32)]
+                ("mem_budget_bytes", C.c_uint64), ("block_size", C.c_int32), ("priority", C.c_int32)]
 
 
 _lib = None
@@ -106,6 +107,7 @@ def load(build: bool = True) -> C.CDLL:
             "thor_ctx_set_stream": ([vp, vp], C.c_int),
             "thor_ctx_set_launch": ([vp, C.c_int, C.c_int], C.c_int),
             "thor_ctx_set_tail": ([vp, C.c_int, C.c_int], C.c_int),
+            "thor_ctx_set_bursts": ([vp, C.c_int], C.c_int),
             "thor_shell_create": ([vp, P(ShellParams), P(vp)], C.c_int),
             "thor_grid_create": ([vp, vp, vp, vp, vp, P(i32), dbl, C.c_int, P(vp)], C.c_int),
             "thor_grid_set_scattering": ([vp, C.c_int, dbl, dbl], C.c_int),
@@ -121,6 +123,8 @@ def load(build: bool = True) -> C.CDLL:
             "thor_server_stats": ([vp, P(u64), P(dbl), P(u64)], C.c_int),
             "thor_server_destroy": ([vp], None),
             "thor_voigt_eval": ([vp, vp, vp, vp, i64, C.c_int, C.c_int], C.c_int),
+            "thor_xcw_eval": ([vp, vp, vp, i64, C.c_int], C.c_int),
+            "thor_issue_peak": ([vp, C.c_int, P(dbl)], C.c_int),
             "thor_dda_trace": ([vp, P(i32), vp, vp, i32, i32, vp, vp, vp, C.c_int], C.c_int),
             "thor_sample_upar": ([vp, C.c_float, C.c_float, u64, i64, vp, P(u64), C.c_int], C.c_int),
             "thor_scatter_once": ([vp, C.c_float, C.c_float, C.c_int, u64, i64, vp, vp, C.c_int], C.c_int),
@@ -272,6 +276,11 @@ class Context:
     def set_launch(self, block_size: int, blocks_per_sm: int = 0):
         self._check(self.L.thor_ctx_set_launch(self.h, block_size, blocks_per_sm))
 
+    def set_bursts(self, max_lanes: int = 4):
+        """thor_ctx_set_bursts: core bursts in warps with at most max_lanes live packets (0 =
+        never); results do not depend on it."""
+        self._check(self.L.thor_ctx_set_bursts(self.h, max_lanes))
+
     def set_tail(self, spill_below: int = 0, max_phases: int = 24):
         """thor_ctx_set_tail: tail compaction of the shell photon loop (0 = off, the library's
         default); results do not depend on it."""
@@ -416,6 +425,20 @@ class Context:
                                            1 if precise else 0, MEM_HOST))
         return H
 
+    def xcw(self, a):
+        """Core-to-wing transition x_cw(a) (App. A.2) as the device computes it (B25, fast log)."""
+        a = np.ascontiguousarray(a, np.float32)
+        out = np.zeros(a.shape, np.float32)
+        self._check(self.L.thor_xcw_eval(self.h, a.ctypes.data, out.ctypes.data, a.size, MEM_HOST))
+        return out
+
+    def issue_peak(self, kind: str = "fma") -> float:
+        """thor_issue_peak: measured warp instructions per second of FP32 FMA ("fma") or MUFU
+        ex2 ("mufu") over the whole device."""
+        v = C.c_double()
+        self._check(self.L.thor_issue_peak(self.h, {"fma": 0, "mufu": 1}[kind], C.byref(v)))
+        return v.value
+
     def dda(self, dims, origins, dirs, max_steps):
         o = np.ascontiguousarray(origins, np.float64)
         d = np.ascontiguousarray(dirs, np.float32)
@@ -450,8 +473,11 @@ class Context:
         self._check(self.L.thor_philox(self.h, ctr.ctypes.data, key.ctypes.data, out.ctypes.data, ctr.shape[0], MEM_HOST))
         return out
 
-    def server(self, *, max_requests=256, events_per_round=256, n_slots=0, mem_budget_bytes=0, block_size=0):
-        return Server(self, ServerConfig(max_requests, events_per_round, n_slots, mem_budget_bytes, block_size, 0))
+    def server(self, *, max_requests=256, events_per_round=256, n_slots=0, mem_budget_bytes=0, block_size=0,
+               priority=True):
+        """thor_server_create; priority: age priority (the oldest requests' packets one per warp)."""
+        return Server(self, ServerConfig(max_requests, events_per_round, n_slots, mem_budget_bytes, block_size,
+                                         0 if priority else -1))
 
 
 class Geometry:

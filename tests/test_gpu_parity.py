@@ -108,6 +108,37 @@ def _rays(rng, dims, n):
     return org, d.astype(np.float32)
 
 
+def test_issue_peaks_are_plausible(ctx):
+    """The measured FP32-FMA issue rate (the photon loops' roofline denominator) lies near
+    the nominal 4 warp instructions per SM per clock at the device's clocks, and MUFU ex2
+    well below it (measured on GB300: 0.26 of the FMA rate)."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    fma = ctx.issue_peak("fma")
+    mufu = ctx.issue_peak("mufu")
+    per_sm_clock_fma = fma / sms / 2.07e9
+    assert 2.0 < per_sm_clock_fma < 4.4, per_sm_clock_fma
+    assert 0.05 < mufu / fma < 0.6, mufu / fma
+
+
+def test_xcw_b25_fast_against_exact(ctx, orc):
+    """x_cw on the device (B25 polynomial of App. A.2 with the fast logarithm) against the
+    oracle's exact transition for Lyman alpha from 1 K to 1e7 K: within the paper's stated
+    accuracy (0.6%), and within 2e-4 of the same polynomial evaluated with an exact log."""
+    import os
+    T = np.logspace(0, 7, 200)
+    a = np.array([orc.line_params(t)["a"] for t in T])
+    got = ctx.xcw(a.astype(np.float32)).astype(np.float64)
+    exact = np.array([orc.xcw(v) for v in a])
+    assert np.max(np.abs(got / exact - 1)) < 0.006
+    rows = [l.split() for l in open(os.path.join(os.path.dirname(__file__), "golden", "b25_xcw.txt"))
+            if l.strip() and not l.startswith("#")]
+    c = [float(r[1]) for r in rows]
+    L = np.log(a.astype(np.float32).astype(np.float64))
+    b25 = sum(ci * L ** i for i, ci in enumerate(c))
+    assert np.max(np.abs(got - b25)) < 2e-4
+
+
 @pytest.mark.parametrize("dims", [(7, 5, 9), (32, 32, 32), (256, 4, 3)])
 def test_dda_bit_exact(ctx, orc, dims):
     rng = np.random.default_rng(sum(dims))
@@ -122,12 +153,13 @@ def test_dda_bit_exact(ctx, orc, dims):
 
 # ------------------------------------------------------------------ samplers
 @pytest.mark.parametrize("x,a", [(0.0, 4.7e-4), (1.3, 4.7e-4), (2.5, 1e-3), (3.0, 1e-2), (6.0, 1e-3),
-                                 (-14.0, 4.7e-4), (3.5, 1e-4), (50.0, 4.7e-4), (-200.0, 1e-3)])
+                                 (-14.0, 4.7e-4), (3.5, 1e-4), (4.0, 1e-5), (4.0, 4.7e-4), (50.0, 4.7e-4),
+                                 (-200.0, 1e-3)])
 def test_upar_sampler(ctx, orc, x, a):
     n = 100000
     u, it = ctx.sample_upar(x, a, n, seed=21)
-    if abs(x) >= 6.0:  # three-piece comparison function: bounded trial count in the wing
-        assert it / n < 7.0, it / n
+    if abs(x) > 2.0:  # four-piece comparison function: below 3.2 trials at every |x| > 2
+        assert it / n < 3.2, it / n
     # distribution: Eq. 6 CDF by quadrature
     grid, cdf = A.upar_cdf_table(x, a)
     assert stats.kstest(u, lambda t: np.interp(t, grid, cdf)).pvalue > 1e-4
@@ -277,6 +309,31 @@ def test_ragged_photon_counts_equal_photons_alone(ctx):
             assert one.raw_X[0] == r.raw_X[k]
 
 
+@pytest.mark.parametrize("geo", [dict(R_in=0.9, N_HI=3e19, T=1e4, v_max=200.0, tau_dust=0.5, phase="dipole"),
+                                 dict(tau0=1e6, T=1e4, phase="isotropic")])
+def test_core_bursts_do_not_change_results(ctx, geo):
+    """Core bursts (pipelined core events) evaluate each event exactly as the general event
+    does: per-photon records and every tally are bit-identical with bursts never, in warps
+    with at most 4 live packets (the default), and in every warp; on an outflowing dusty
+    shell (start-point sub-steps, dust channel) and a static sphere (safety-ball steps)."""
+    g = ctx.shell(**geo)
+    kw = dict(n_photons=3000, seed=41, sigma=50.0 if "N_HI" in geo else 0.0, n_bins=200, X_min=-1500.0,
+              X_max=1500.0, raw=True)
+    out = []
+    for lanes in (0, 4, 32):
+        ctx.set_bursts(lanes)
+        out.append(ctx.run(g, **kw))
+    ctx.set_bursts(4)
+    a = out[0]
+    assert a.stats["n_scat"] > 1e6
+    for b in out[1:]:
+        assert np.array_equal(a.spectrum, b.spectrum)
+        assert np.array_equal(np.asarray(a.raw_X).view(np.uint32), np.asarray(b.raw_X).view(np.uint32))
+        assert np.array_equal(np.asarray(a.raw_nscat), np.asarray(b.raw_nscat))
+        for k in ("n_escaped", "n_absorbed", "n_scat", "n_dust_scat", "n_upar_iters", "n_steps"):
+            assert a.stats[k] == b.stats[k], k
+
+
 def test_tail_compaction_does_not_change_results(ctx):
     """Tail compaction re-packs survivors between launches; every photon's history is
     keyed by its id, so the tallies must be bit-identical with it on and off."""
@@ -319,10 +376,10 @@ def test_grid_photon_loop_and_peeling(ctx, orc):
     cell = 100 * 3.0856775814913673e18
     g = ctx.grid(f["n_HI"], f["T"], f["v"], f["kd"], cell, phase="dipole", albedo=0.32, g_hg=0.73)
     n = 20000
-    r = ctx.run(g, n_photons=n, seed=4, n_bins=256, X_min=-600, X_max=600, peel=True, img_n=8, peel_bins=64,
-                peel_X_min=-600, peel_X_max=600, raw=True)
+    r = ctx.run(g, n_photons=n, seed=4, n_bins=400, X_min=-400, X_max=400, peel=True, img_n=8, peel_bins=400,
+                peel_X_min=-400, peel_X_max=400, raw=True)
     of = {"n_HI": f["n_HI"], "T": f["T"], "vx": f["v"][0], "vy": f["v"][1], "vz": f["v"][2], "kd": f["kd"]}
-    ro = orc.run_grid(of, cell_cm=cell, n_photons=n, seed=1004, n_bins=256, img_nx=8, X_min=-600, X_max=600,
+    ro = orc.run_grid(of, cell_cm=cell, n_photons=n, seed=1004, n_bins=400, img_nx=8, X_min=-400, X_max=400,
                       phase="dipole", albedo=0.32, g_hg=0.73, raw=True)
     assert_spectrum_parity(r.spectrum, ro["counts"])
     assert mean_nscat_z(r.stats, n, ro, n) < 3.0
@@ -333,8 +390,9 @@ def test_grid_photon_loop_and_peeling(ctx, orc):
     co = ro["cube"]
     tot_g, tot_o = cg.sum(), co.sum()
     assert abs(tot_g / tot_o - 1) < 0.03, (tot_g, tot_o)
-    sg = cg.sum(axis=(1, 2)).ravel()
-    so = co.sum(axis=(1, 2)).ravel()
+    # per-observer spectra in groups of 8 bins (50 per observer)
+    sg = cg.sum(axis=(1, 2)).reshape(3, -1, 8).sum(axis=2).ravel()
+    so = co.sum(axis=(1, 2)).reshape(3, -1, 8).sum(axis=2).ravel()
     rel = np.abs(sg - so) / np.maximum(so, 1e-3 * so.max())
     assert np.median(rel) < 0.08
 
@@ -351,10 +409,10 @@ def test_grid_thick_cells_fast_path(ctx, orc):
     cell = 100 * 3.0856775814913673e18
     g = ctx.grid(f["n_HI"], f["T"], f["v"], f["kd"], cell, phase="dipole", albedo=0.32, g_hg=0.73)
     n = 8000
-    r = ctx.run(g, n_photons=n, seed=4, n_bins=256, X_min=-600, X_max=600, peel=True, img_n=8, peel_bins=64,
-                peel_X_min=-600, peel_X_max=600, raw=True)
+    r = ctx.run(g, n_photons=n, seed=4, n_bins=400, X_min=-400, X_max=400, peel=True, img_n=8, peel_bins=400,
+                peel_X_min=-400, peel_X_max=400, raw=True)
     of = {"n_HI": f["n_HI"], "T": f["T"], "vx": f["v"][0], "vy": f["v"][1], "vz": f["v"][2], "kd": f["kd"]}
-    ro = orc.run_grid(of, cell_cm=cell, n_photons=n, seed=1004, n_bins=256, img_nx=8, X_min=-600, X_max=600,
+    ro = orc.run_grid(of, cell_cm=cell, n_photons=n, seed=1004, n_bins=400, img_nx=8, X_min=-400, X_max=400,
                       phase="dipole", albedo=0.32, g_hg=0.73, raw=True)
     assert_spectrum_parity(r.spectrum, ro["counts"])
     assert mean_nscat_z(r.stats, n, ro, n) < 3.0
@@ -362,6 +420,44 @@ def test_grid_thick_cells_fast_path(ctx, orc):
     assert stats.ks_2samp(np.asarray(r.raw_X, np.float64)[eg], ro["X"][eo]).pvalue > 1e-3
     tot_g, tot_o = float(r.cube.astype(np.float64).sum()), float(ro["cube"].sum())
     assert abs(tot_g / tot_o - 1) < 0.05, (tot_g, tot_o)
+
+
+def test_grid64_config4_density_peeling(ctx, orc):
+    """A 64^3 grid with the config-4 recipe (100 pc cells, lognormal n_HI with mean 1e-3 cm^-3
+    and sigma_ln 1.5, so tau0 ~ 1.8e4 per cell at the mean; lognormal T; k^-11/3 velocity
+    fields of 50 km/s per axis; dust 0.01 n_HI with albedo 0.32, g 0.73), peeled to three
+    observers on 32 x 32 images.  A photon here scatters ~6e5 times on average before it
+    leaves, too long for the FP64 oracle in a test, so both sides stop every photon after 2e4
+    scatterings (the same definition).  Compared: fates, mean scatterings, escape
+    frequencies (KS), the peeled totals, per-observer spectra and coarse image blocks."""
+    from paper_2507_11603_gb300 import synth
+    f = synth.grid_fields(n=64, seed=3)
+    cell = 100 * synth.PC_CM
+    g = ctx.grid(f["n_HI"], f["T"], f["v"], f["kd"], cell, phase="dipole", albedo=0.32, g_hg=0.73)
+    n, cap = 4000, 20000
+    kw = dict(n_bins=64, X_min=-1000.0, X_max=1000.0)
+    r = ctx.run(g, n_photons=n, seed=61, peel=True, img_n=32, peel_bins=64, peel_X_min=-1000.0, peel_X_max=1000.0,
+                raw=True, max_scat=cap, **kw)
+    of = {"n_HI": f["n_HI"], "T": f["T"], "vx": f["v"][0], "vy": f["v"][1], "vz": f["v"][2], "kd": f["kd"]}
+    ro = orc.run_grid(of, cell_cm=cell, n_photons=n, seed=1061, img_nx=32, phase="dipole", albedo=0.32, g_hg=0.73,
+                      raw=True, max_scat=cap, **kw)
+    for k in ("n_escaped", "n_absorbed", "n_capped"):
+        p1, p2 = r.stats[k] / n, ro[k] / n
+        sd = np.sqrt((p1 * (1 - p1) + p2 * (1 - p2)) / n) + 1e-12
+        assert abs(p1 - p2) < 4 * sd, (k, p1, p2)
+    assert mean_nscat_z(r.stats, n, ro, n) < 3.0
+    eg, eo = np.asarray(r.raw_status) == 1, ro["status"] == 1
+    assert min(eg.sum(), eo.sum()) > 100
+    assert stats.ks_2samp(np.asarray(r.raw_X, np.float64)[eg], ro["X"][eo]).pvalue > 1e-3
+    cg, co = r.cube.astype(np.float64), ro["cube"]
+    assert abs(cg.sum() / co.sum() - 1) < 0.05, (cg.sum(), co.sum())
+    for ax in range(3):
+        sg, so = cg[ax].sum(axis=(0, 1)).reshape(-1, 4).sum(1), co[ax].sum(axis=(0, 1)).reshape(-1, 4).sum(1)
+        main = so > 0.02 * so.max()
+        assert np.median(np.abs(sg[main] / so[main] - 1)) < 0.1, ax
+        ig = cg[ax].sum(axis=2).reshape(4, 8, 4, 8).sum(axis=(1, 3))
+        io = co[ax].sum(axis=2).reshape(4, 8, 4, 8).sum(axis=(1, 3))
+        assert np.median(np.abs(ig / io - 1)) < 0.1, ax
 
 
 def test_grid_same_stream_per_photon(ctx, orc):
@@ -484,6 +580,28 @@ def test_server_mixed_equals_alone(ctx):
         one = ctx.run(g, n_photons=r["n_photons"], seed=r["seed"], sigma=50.0, n_bins=128, X_min=-1500.0,
                       X_max=1500.0)
         assert np.array_equal(one.spectrum, m.spectrum) and one.stats["n_scat"] == m.stats["n_scat"]
+
+
+def test_server_priority_with_a_full_slot_list(ctx):
+    """A small server (2048 packet slots, 64 warps) under a burst: the oldest request is
+    small enough for priority (its packets one per warp) while the younger ones fill every
+    slot.  Every stored packet must be resumed (all requests finish within the timeout), and
+    each result equals thor_run's."""
+    srv = ctx.server(max_requests=8, events_per_round=32, n_slots=2048)
+    common = dict(R_in=0.9, phase="dipole", sigma=50.0, n_bins=64, X_min=-1500.0, X_max=1500.0)
+    reqs = [dict(N_HI=3e19, T=1e4, v_max=100.0, tau_dust=0.5, n_photons=12, seed=21),
+            dict(N_HI=1e18, T=2e4, v_max=50.0, tau_dust=0.2, n_photons=6000, seed=22),
+            dict(N_HI=5e18, T=5e3, v_max=300.0, tau_dust=1.0, n_photons=6000, seed=23)]
+    tickets = [srv.submit(**r, **common) for r in reqs]
+    res = [srv.wait(t, timeout_ms=120000) for t in tickets]
+    srv.close()
+    for r, m in zip(reqs, res):
+        g = ctx.shell(R_in=0.9, N_HI=r["N_HI"], T=r["T"], v_max=r["v_max"], tau_dust=r["tau_dust"], phase="dipole")
+        one = ctx.run(g, n_photons=r["n_photons"], seed=r["seed"], sigma=50.0, n_bins=64, X_min=-1500.0,
+                      X_max=1500.0)
+        assert np.array_equal(one.spectrum, m.spectrum)
+        for k in ("n_escaped", "n_absorbed", "n_scat", "n_dust_scat"):
+            assert one.stats[k] == m.stats[k], k
 
 
 def test_server_bins_like_thor_run(ctx):
