@@ -189,8 +189,8 @@ def run_shell_bench(args):
     ctx = thor.Context(local)
     if args.block:
         ctx.set_launch(args.block, args.blocks_per_sm)
-    if args.bursts >= 0:
-        ctx.set_bursts(args.bursts)
+    if args.pipe_lanes >= 0 or args.burst_lanes >= 0:
+        ctx.set_bursts(args.pipe_lanes if args.pipe_lanes >= 0 else 32, args.burst_lanes if args.burst_lanes >= 0 else 4)
     stream = torch.cuda.Stream()
     ctx.set_stream(stream)
     geom = ctx.shell(**SHELL)
@@ -295,7 +295,8 @@ def run_shell_bench(args):
         "config": {"workload": WORKLOAD, "photons_per_step": N_PHOTONS, "l2": "flushed (256 MiB write) before each step",
                    "scatterings_per_step": n_scat / args.steps, "kernel_ms_per_step": kern_avg_ms,
                    "launch": {"block": args.block or 128, "blocks_per_sm": args.blocks_per_sm,
-                              "core_burst_lanes": args.bursts if args.bursts >= 0 else 4}},
+                              "pipelined_event_lanes": args.pipe_lanes if args.pipe_lanes >= 0 else 32,
+                              "core_burst_lanes": args.burst_lanes if args.burst_lanes >= 0 else 4}},
         "e2e": {"value": e2e_value, "unit": "scatterings/s", "h2d_bytes_per_step": 256 + 48,
                 "d2h_bytes_per_step": (RUN["n_bins"] + 2) * 8 + 96, "steps": n_e2e,
                 "photon_ids": f"those of the first {n_e2e} timed steps",
@@ -603,11 +604,22 @@ def run_forest_bench(args):
             ms.append(ctx.last_elapsed_ms())
     evals = float(xy) * xy * n * 2 * n
     t = float(np.mean(ms)) / 1000.0
+    # e2e: the same box from host memory (staged through the library's reused buffers,
+    # copies overlapped with the kernel) and the optical depths back to host memory
+    hn, hT, hv = (x.cpu().numpy() for x in (nHI, T, v))
+    hout = np.empty((xy * xy, 2 * n), np.float32)
+    del out
+    torch.cuda.empty_cache()
+    t0 = time.perf_counter()
+    ctx.forest(hn, hT, hv, ds_cm=ds, dv_cell=2.0, n_bins=2 * n, dv_bin=1.0, out=hout)
+    e2e_s = time.perf_counter() - t0
     print(json.dumps({"metric": "Voigt evaluations/s (Lya forest, Eq. 11)", "value": evals / t,
                       "unit": "evals/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
                       "ms_per_step": 1000 * t, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
                       "config": {"workload": f"forest {xy}x{xy}x{n} box, {xy * xy} sightlines of {n} cells x "
                                              f"{2 * n} bins"},
+                      "e2e": {"value": evals / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": 3 * 4 * xy * xy * n,
+                              "d2h_bytes_per_step": 4 * xy * xy * 2 * n},
                       "clocks": clk.summary()}))
 
 
@@ -640,7 +652,9 @@ def main():
     ap.add_argument("--lone-events", type=int, default=200000,
                     help="events of the longest photon run alone to time the lone-lane event latency")
     ap.add_argument("--block", type=int, default=0)
-    ap.add_argument("--bursts", type=int, default=-1,
+    ap.add_argument("--pipe-lanes", type=int, default=-1,
+                    help="pipelined events in warps with at most this many live packets (-1 = library default)")
+    ap.add_argument("--burst-lanes", type=int, default=-1,
                     help="core bursts in warps with at most this many live packets (-1 = library default)")
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--inst-per-scat", type=float, default=374.0,

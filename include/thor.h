@@ -85,14 +85,17 @@ int thor_ctx_set_launch(thor_ctx_t ctx, int block_size, int blocks_per_sm);
  * photons than lanes spread them over all warps either way.  Results do not depend on
  * these settings. */
 int thor_ctx_set_tail(thor_ctx_t ctx, int spill_below, int max_phases);
-/* Core bursts of the gridless photon loop on homologous shells: in warps with at most
- * max_lanes live packets (0..32; 0 = never; default 4), a packet runs the events that
- * stay in the line core (start-point step inside the safety ball, resonant scattering at
- * |x| <= 2, first u_par trial accepted) up to 32 at a time, with the next event's random
- * words, its optical depth and the outgoing direction formed beside the frequency chain.
- * Such an event is evaluated exactly as the general event evaluates it, so results do not
- * depend on this setting (only the time to reach them does). */
-int thor_ctx_set_bursts(thor_ctx_t ctx, int max_lanes);
+/* Pipelined events of the gridless photon loop on homologous shells.  In warps with at
+ * most pipe_lanes live packets (0..32; 0 = never; default 32) each event first tries its
+ * line-core form (start-point step inside the safety ball, resonant scattering at |x| <= 2,
+ * first u_par trial accepted), with the next event's random words, its optical depth and
+ * the outgoing direction formed beside the frequency chain, and runs the general event
+ * from the same words otherwise.  In warps with at most burst_lanes live packets (0..32;
+ * default 4; only where events are pipelined) a packet runs up to 32 core events back to
+ * back in one tight loop, for the lone lanes of a run's tail.  Both forms evaluate an event
+ * exactly as the general event does, so results do not depend on these settings (only the
+ * time to reach them does). */
+int thor_ctx_set_bursts(thor_ctx_t ctx, int pipe_lanes, int burst_lanes);
 
 /* ---- geometries (Sec. 3.3 datasets) ----------------------------------------------- */
 
@@ -222,7 +225,7 @@ typedef struct {
   double ds_cm;           /* proper path length per cell [cm] */
   double dv_cell;         /* Hubble-flow velocity across one cell [km/s] */
   int32_t n_bins;         /* velocity bins, n_bins * dv_bin == nz * dv_cell (periodic) */
-  int32_t reserved;
+  int32_t stage_rows;     /* host arrays: rows of sightlines per staged chunk (0 = automatic) */
   double dv_bin;          /* km/s */
   int64_t first_sightline, n_sightlines;  /* sightline s = column (s % nx, s / nx) along z */
 } thor_forest_spec;
@@ -230,7 +233,10 @@ typedef struct {
 /* tau_out[s * n_bins + b] = sum over cells k of the column of
  * n_HI sigma_0(T) ds H(a(T), (v_b - v_k) / v_th(T)), v_k = (k + 1/2) dv_cell + v_los,
  * v_b = (b + 1/2) dv_bin, nearest periodic image.  Fields as for grids (v_los = the
- * z velocity); all pointers of kind mem_kind.  n_bins <= 2048 per call. */
+ * z velocity); all pointers of kind mem_kind.  n_bins <= 2048 per call.  Host arrays are
+ * streamed through two reused device buffers in chunks of stage_rows rows of sightlines
+ * (automatic: as many rows as fit in 1 GiB per buffer), each chunk computed while the next
+ * is copied in; the buffers stay with the context for later calls. */
 int thor_forest(thor_ctx_t ctx, const float* n_HI, const float* T, const float* v_los, const int32_t dims[3],
                 int mem_kind, const thor_forest_spec* spec, float* tau_out);
 

@@ -1,5 +1,6 @@
 // thor_capi.cu -- host runtime behind include/thor.h: contexts, geometry objects,
 // the single-model run, the forest ray-march and the diagnostic entry points.
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -48,8 +49,12 @@ void* thor_ctx::scratch(Buf& b, size_t bytes) {
 
 thor_ctx::~thor_ctx() {
   cudaSetDevice(device);
-  for (Buf* b : {&b_models, &b_tally, &b_queue, &b_spec, &b_cube, &b_raw, &b_raw2, &b_diag, &b_stats, &b_spill, &b_cmp})
+  for (Buf* b : {&b_models, &b_tally, &b_queue, &b_spec, &b_cube, &b_raw, &b_raw2, &b_diag, &b_stats, &b_spill, &b_cmp,
+                 &b_stage[0], &b_stage[1]})
     if (b->p) cudaFree(b->p);
+  for (cudaEvent_t e : {ev_copied[0], ev_copied[1], ev_done[0], ev_done[1]})
+    if (e) cudaEventDestroy(e);
+  if (copy_stream) cudaStreamDestroy(copy_stream);
   if (d_ktab) cudaFree(d_ktab);
   if (ev0) cudaEventDestroy(ev0);
   if (ev1) cudaEventDestroy(ev1);
@@ -110,10 +115,12 @@ extern "C" int thor_ctx_set_tail(thor_ctx_t ctx, int spill_below, int max_phases
   return THOR_OK;
 }
 
-extern "C" int thor_ctx_set_bursts(thor_ctx_t ctx, int max_lanes) {
+extern "C" int thor_ctx_set_bursts(thor_ctx_t ctx, int pipe_lanes, int burst_lanes) {
   if (!ctx) return THOR_ERR_INVALID_ARG;
-  if (max_lanes < 0 || max_lanes > 32) return ctx->fail(THOR_ERR_INVALID_ARG, "thor_ctx_set_bursts: max_lanes in [0, 32]");
-  ctx->core_lanes = max_lanes;
+  if (pipe_lanes < 0 || pipe_lanes > 32 || burst_lanes < 0 || burst_lanes > 32)
+    return ctx->fail(THOR_ERR_INVALID_ARG, "thor_ctx_set_bursts: pipe_lanes and burst_lanes in [0, 32]");
+  ctx->core_lanes = pipe_lanes;
+  ctx->burst_lanes = burst_lanes;
   return THOR_OK;
 }
 
@@ -512,7 +519,8 @@ extern "C" int thor_run(thor_ctx_t ctx, thor_geom_t g, const thor_source* src, u
     const int per_warp0 = (int)(pw0 < 1 ? 1 : (pw0 > 32 ? 32 : pw0));
     if (ctx->spill_below <= 0) {
       cudaEventRecord(ctx->ev0, s);
-      rc = ctx->cuda(launch_shell_run(d_m, q, ctx->d_ktab, gsz, ctx->block, m.profile, per_warp0, ctx->core_lanes, s),
+      rc = ctx->cuda(launch_shell_run(d_m, q, ctx->d_ktab, gsz, ctx->block, m.profile, per_warp0, ctx->core_lanes,
+                                      ctx->burst_lanes, s),
                      "shell photon loop");
       ++n_launch;
       cudaEventRecord(ctx->ev1, s);
@@ -543,6 +551,7 @@ extern "C" int thor_run(thor_ctx_t ctx, thor_geom_t g, const thor_source* src, u
         c.spill_below = last ? 0 : ctx->spill_below;
         c.per_warp = per_warp0;
         c.core_lanes = ctx->core_lanes;
+        c.burst_lanes = ctx->burst_lanes;
         if (per_warp0 <= 2) c.spill_below = 0;
         else if (c.spill_below > per_warp0 / 2) c.spill_below = per_warp0 / 2;
         int g = gsz;
@@ -659,30 +668,77 @@ extern "C" int thor_forest(thor_ctx_t ctx, const float* n_HI, const float* T, co
   if (mem_kind != THOR_MEM_HOST && mem_kind != THOR_MEM_DEVICE) return ctx->fail(THOR_ERR_INVALID_ARG, "mem_kind");
   if (int rc = ctx->select()) return rc;
   cudaStream_t s = ctx->stream;
-  const int64_t n = (int64_t)dims[0] * dims[1] * dims[2];
-  const size_t tb = (size_t)sp->n_sightlines * sp->n_bins * sizeof(float);
-  const float *dn = n_HI, *dT = T, *dv = v_los;
-  float* dtau = tau_out;
-  void* stage = nullptr;
   int rc = THOR_OK;
-  if (mem_kind == THOR_MEM_HOST) {
-    if (cudaMalloc(&stage, 3 * (size_t)n * 4 + tb) != cudaSuccess) return ctx->fail(THOR_ERR_OOM, "forest staging");
-    float* f = (float*)stage;
-    rc = copy_in(ctx, n_HI, (size_t)n * 4, THOR_MEM_HOST, f);
-    if (!rc) rc = copy_in(ctx, T, (size_t)n * 4, THOR_MEM_HOST, f + n);
-    if (!rc) rc = copy_in(ctx, v_los, (size_t)n * 4, THOR_MEM_HOST, f + 2 * n);
-    dn = f; dT = f + n; dv = f + 2 * n; dtau = f + 3 * n;
-  }
-  if (!rc) {
+  if (mem_kind == THOR_MEM_DEVICE) {
     cudaEventRecord(ctx->ev0, s);
-    rc = ctx->cuda(launch_forest(dn, dT, dv, dims[0], dims[1], dims[2], sp->first_sightline, sp->n_sightlines, sp->ds_cm,
-                                 sp->dv_cell, sp->n_bins, sp->dv_bin, dtau, ctx->d_ktab, s), "forest kernel");
+    rc = ctx->cuda(launch_forest(n_HI, T, v_los, dims[0], dims[1], dims[2], sp->first_sightline, sp->n_sightlines,
+                                 sp->ds_cm, sp->dv_cell, sp->n_bins, sp->dv_bin, tau_out, ctx->d_ktab, s),
+                   "forest kernel");
     cudaEventRecord(ctx->ev1, s);
+    if (!rc) rc = ctx->cuda(cudaStreamSynchronize(s), "forest");
+    if (!rc) cudaEventElapsedTime(&ctx->last_ms, ctx->ev0, ctx->ev1);
+    return rc;
   }
-  if (!rc && mem_kind == THOR_MEM_HOST) rc = ctx->cuda(cudaMemcpyAsync(tau_out, dtau, tb, cudaMemcpyDeviceToHost, s), "copy tau");
+  // Host arrays: the box is streamed through two reused staging buffers in chunks of rows
+  // (all z of rows iy in [y0, y1): per field one strided copy, nz runs of (y1 - y0) nx
+  // floats), each chunk's sightlines computed while the next chunk is copied in on a second
+  // stream; optical depths go back row chunk by row chunk.  No allocation per call once the
+  // buffers have grown to a chunk.
+  const int nx = dims[0], ny = dims[1], nz = dims[2];
+  constexpr size_t kStageBytes = (size_t)1 << 30;  // per buffer
+  const size_t row_bytes = (size_t)nx * ((size_t)3 * nz + (size_t)sp->n_bins) * 4;
+  if (sp->stage_rows < 0) return ctx->fail(THOR_ERR_INVALID_ARG, "thor_forest: stage_rows must be >= 0");
+  const int rows = sp->stage_rows > 0 ? std::min(sp->stage_rows, ny)
+                                      : (int)std::max<size_t>(1, std::min<size_t>((size_t)ny, kStageBytes / row_bytes));
+  if (!ctx->copy_stream) {
+    if (cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return ctx->fail(THOR_ERR_DEVICE, "thor_forest: copy stream");
+    for (int b = 0; b < 2; ++b)
+      if (cudaEventCreateWithFlags(&ctx->ev_copied[b], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&ctx->ev_done[b], cudaEventDisableTiming) != cudaSuccess)
+        return ctx->fail(THOR_ERR_DEVICE, "thor_forest: events");
+  }
+  char* buf[2];
+  for (int b = 0; b < 2; ++b) {
+    buf[b] = (char*)ctx->scratch(ctx->b_stage[b], (size_t)rows * row_bytes);
+    if (!buf[b]) return ctx->fail(THOR_ERR_OOM, "thor_forest: staging buffers");
+  }
+  const int64_t s_lo = sp->first_sightline, s_hi = sp->first_sightline + sp->n_sightlines;
+  const int y_first = (int)(s_lo / nx), y_last = (int)((s_hi - 1) / nx);
+  cudaStream_t cs = ctx->copy_stream;
+  const size_t plane = (size_t)nx * ny * 4;
+  cudaEventRecord(ctx->ev0, s);
+  int chunk = 0;
+  for (int y0 = y_first; y0 <= y_last && !rc; y0 += rows, ++chunk) {
+    const int y1 = std::min(y0 + rows, y_last + 1), nr = y1 - y0;
+    const int b = chunk & 1;
+    float* f = (float*)buf[b];
+    const size_t nf = (size_t)nr * nx * nz;
+    float* dtau = f + 3 * nf;
+    // the buffer's previous chunk must be computed and copied out before it is overwritten
+    if (chunk >= 2) rc = ctx->cuda(cudaStreamWaitEvent(cs, ctx->ev_done[b], 0), "forest order");
+    const float* src[3] = {n_HI, T, v_los};
+    for (int k = 0; k < 3 && !rc; ++k)
+      rc = ctx->cuda(cudaMemcpy2DAsync(f + k * nf, (size_t)nr * nx * 4, (const char*)src[k] + (size_t)y0 * nx * 4,
+                                       plane, (size_t)nr * nx * 4, (size_t)nz, cudaMemcpyHostToDevice, cs),
+                     "forest copy in");
+    if (!rc) rc = ctx->cuda(cudaEventRecord(ctx->ev_copied[b], cs), "forest order");
+    if (!rc) rc = ctx->cuda(cudaStreamWaitEvent(s, ctx->ev_copied[b], 0), "forest order");
+    // sightlines of this chunk inside the requested range, relative to the chunk's rows
+    const int64_t c_lo = std::max<int64_t>(s_lo, (int64_t)y0 * nx), c_hi = std::min<int64_t>(s_hi, (int64_t)y1 * nx);
+    if (!rc)
+      rc = ctx->cuda(launch_forest(f, f + nf, f + 2 * nf, nx, nr, nz, c_lo - (int64_t)y0 * nx, c_hi - c_lo, sp->ds_cm,
+                                   sp->dv_cell, sp->n_bins, sp->dv_bin, dtau, ctx->d_ktab, s),
+                     "forest kernel");
+    if (!rc)
+      rc = ctx->cuda(cudaMemcpyAsync(tau_out + (size_t)(c_lo - s_lo) * sp->n_bins, dtau,
+                                     (size_t)(c_hi - c_lo) * sp->n_bins * 4, cudaMemcpyDeviceToHost, s),
+                     "forest copy out");
+    if (!rc) rc = ctx->cuda(cudaEventRecord(ctx->ev_done[b], s), "forest order");
+  }
+  cudaEventRecord(ctx->ev1, s);
   if (!rc) rc = ctx->cuda(cudaStreamSynchronize(s), "forest");
   if (!rc) cudaEventElapsedTime(&ctx->last_ms, ctx->ev0, ctx->ev1);
-  if (stage) cudaFree(stage);
   return rc;
 }
 

@@ -25,11 +25,15 @@ struct thor_ctx {
   std::string last_error;
   // grow-only scratch buffers reused across calls
   Buf b_models, b_tally, b_queue, b_spec, b_cube, b_raw, b_raw2, b_diag, b_stats, b_spill, b_cmp;
+  Buf b_stage[2];                   // host-input staging, double-buffered (forest)
+  cudaStream_t copy_stream = nullptr;  // host<->device copies overlapped with kernels
+  cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_done[2] = {nullptr, nullptr};
   // tail compaction of the shell photon loop
   int spill_below = 0;      // warps with fewer live lanes hand them to the next launch (0 = off)
   int max_phases = 24;      // launches at most
   int final_below = 256;    // run to completion once this few packets are left
-  int core_lanes = 4;       // warps with at most this many live packets run core bursts (0 = never)
+  int core_lanes = 32;      // warps with at most this many live packets run pipelined events (0 = never)
+  int burst_lanes = 4;      // ... and, with at most this many, core bursts (0 = never)
   int phases_last = 0;
 
   int fail(int code, const char* fmt, ...);

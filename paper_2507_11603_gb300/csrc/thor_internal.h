@@ -111,7 +111,8 @@ struct Compact {
   unsigned long long* n_spill;
   int32_t spill_below;  // 0: run to completion
   int32_t per_warp;     // lanes per warp that take packets (1..32): few packets spread over all schedulers
-  int32_t core_lanes;   // warps with at most this many live packets run core events in bursts (0 = never)
+  int32_t core_lanes;   // warps with at most this many live packets run pipelined events (0 = never)
+  int32_t burst_lanes;  // ... and, with at most this many, core bursts (0 = never)
 };
 
 // Resident packet state for time-sliced (served) execution, SoA, one slot per thread.
@@ -173,7 +174,7 @@ struct GridModel {
 int shell_grid(int block, int blocks_per_sm, bool sliced);  // persistent grid size
 int grid_grid(int block, int blocks_per_sm);
 cudaError_t launch_shell_run(const ShellModel* d_models, WorkQueue q, const float* d_ktab, int grid,
-                             int block, int profile, int per_warp, int core_lanes, cudaStream_t s);
+                             int block, int profile, int per_warp, int core_lanes, int burst_lanes, cudaStream_t s);
 cudaError_t launch_shell_run_compact(const ShellModel* d_models, WorkQueue q, Compact c, const float* d_ktab,
                                      int grid, int block, int profile, cudaStream_t s);
 cudaError_t launch_reweight(int64_t n, const float* X0, const float* X, const float* col, const uint8_t* status,

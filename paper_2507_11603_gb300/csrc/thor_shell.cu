@@ -16,6 +16,9 @@ namespace thor {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kServedPipeLanes = 32;  // served rounds: pipelined events in every warp
+constexpr int kServedBurstLanes = 4;  // served rounds: core bursts in warps with at most this many live packets
+constexpr uint32_t kLongLived = 1u << 14;  // served rounds: packets past this many events run one per warp
 
 struct Photon {
   double px, py, pz;  // FP64 anchor; the position is anchor + offset
@@ -113,9 +116,12 @@ __device__ __forceinline__ bool dust_channel(const ShellModel& m, float kH, floa
 // same point.  A conservative safety distance to the shell boundaries lets events whose
 // interaction lies inside the safety ball skip the FP64 ray-sphere geometry (the common
 // case for photons trapped in the line core).
-__device__ int shell_event(const ShellModel& m, Photon& ph, const float* __restrict__ Ktab) {
-  ph.rng.next_event((m.kapd > 0.0f || m.phase == PH_MIXED) ? 3u : 2u);
-  float tau_rem = draw_tau(ph.rng);  // Eq. 3: tau ~ Exp(1)
+__device__ __forceinline__ uint32_t shell_blocks(const ShellModel& m) {
+  return (m.kapd > 0.0f || m.phase == PH_MIXED) ? 3u : 2u;
+}
+
+// The event whose words ph.rng holds, with the optical depth tau_rem drawn from them.
+__device__ int shell_event_words(const ShellModel& m, Photon& ph, const float* __restrict__ Ktab, float tau_rem) {
   float x_site, kH;
   for (;;) {
     if (ph.region) {  // empty cavity: straight to the inner sphere, lab X conserved
@@ -248,106 +254,134 @@ __device__ int shell_event(const ShellModel& m, Photon& ph, const float* __restr
   return 0;
 }
 
-// ---- pipelined core events (homologous shells) ------------------------------------
+__device__ int shell_event(const ShellModel& m, Photon& ph, const float* __restrict__ Ktab) {
+  ph.rng.next_event(shell_blocks(m));
+  return shell_event_words(m, ph, Ktab, draw_tau(ph.rng));  // Eq. 3: tau ~ Exp(1)
+}
+
+// ---- pipelined events (homologous shells) -------------------------------------------
 // A packet trapped in the line core spends its life in one kind of event: the crossing lies
 // within ds/16 of the start (start-point rate, Sec. 5.1 step limiter) inside the safety
 // ball, the interaction is a resonant scattering at |x| <= 2 (Sec. 3.4), and the first
 // trial of the u_par sampler (Eq. 10) is accepted.  In such an event only the frequency
 // chain x -> H(a,x) -> s -> x_site -> u_par -> x_out depends on the packet's state; the next
 // event's Philox blocks and optical depth, the perpendicular atom velocity (Eq. 5), mu and
-// the outgoing direction depend only on the event's random words and the incoming
-// direction.  core_burst forms them beside the chain of the current event, in one basic
-// block per event, so that the scheduler fills the chain's dependency stalls with them (a
-// lone lane issues in order and would otherwise wait on each link), and commits the event
-// only if it is of that kind.  Otherwise the packet is left at the event boundary and
-// shell_event runs the event in full from the same words.  Three things differ from
-// shell_event's evaluation of the same event, none in distribution: H comes from the
-// table-free core polynomial (voigt_core_poly, |x| <= 2, error below the fast path's);
-// the region and channel tests compare products instead of quotients; w1 = atan(a/d) is
-// formed from a/d = sqrt(2 pi a x) e^{-x^2/2} directly (a/d <= 1/20, where the series
-// atan2_pos uses is exact to 3e-9).  Returns 3 if the scattering cap was reached (the
-// packet is then finished as shell_event finishes it), else 0.
-constexpr uint32_t kCoreBurst = 32;  // events per burst at most
-constexpr int kCoreLanes = 4;        // served rounds: bursts in warps with at most this many live packets
+// the outgoing direction depend only on random words and the incoming direction.
+// shell_event_pipe evaluates that kind of event in one basic block, with the next event's
+// words formed beside the chain (a lone lane issues in order and would otherwise wait on
+// each link), and commits it only if the event is of that kind; otherwise it runs the
+// general event from the same words.  The general event evaluates these events with the
+// same helpers (voigt_start, start_step, dust_channel, u0_core, upar_q / atan_small,
+// region1, x_after_scatter), so both paths give bit-identical results.
+// In this mode ph.rng holds the words of the event about to run ("prepared"), and
+// tau_next its optical depth; pipe_prepare / pipe_unprepare switch between the modes.
+__device__ __forceinline__ void pipe_prepare(const ShellModel& m, Photon& ph, float& tau_next) {
+  ph.rng.next_event(shell_blocks(m));
+  tau_next = draw_tau(ph.rng);
+}
+__device__ __forceinline__ void pipe_unprepare(Photon& ph) { ph.rng.event -= 1u; }
 
-__device__ __forceinline__ int core_burst(const ShellModel& m, Photon& ph, uint32_t max_ev, uint32_t& n) {
-  n = 0;
-  if (m.phase == PH_MIXED || ph.region || !(fabsf(ph.x) <= THOR_VCORE_X)) return 0;
-  const uint32_t nblk = (m.kapd > 0.0f) ? 3u : 2u;
-  Rng r = ph.rng;
-  r.next_event(nblk);
-  float tau = draw_tau(r);
-  const float ds16 = 0.0625f * m.ds_core;
-  int status = 0;
-  for (; n < max_ev; ++n) {
-    // ---- the frequency chain: rate at the start, crossing, gas-frame frequency at the site
-    const float x0 = ph.x;
-    const StartStep st0 = start_step(m, voigt_core_poly(m.a, x0), tau);
-    const float s0 = st0.s;
-    const bool in_ball = (m.gam == 0.0f) ? (s0 <= ph.safe) : (ph.safe >= m.ds_core && s0 <= ds16);
-    const float xs = (m.gam == 0.0f) ? x0 : __fmaf_rn(-m.gam, s0, x0);
-    const bool dust = (m.kapd > 0.0f) && dust_channel(m, st0.kH, r.u(W_CHANNEL));
-    // ---- u_par, first trial of the two-piece comparison function (as sample_upar)
-    const float sgn = (xs < 0.0f) ? -1.0f : 1.0f;
-    const float xr = fabsf(xs);
-    const float u0 = u0_core(xr, m.a);
-    const float q = upar_q(xr, m.a);
-    const float w1 = atan_small(q);
-    const float u02 = __fmul_rn(u0, u0);
-    const float mass = envelope_mass(w1, exp_fast(-u02));
-    const float w1p = w1 * (1.0f / kPiF);
-    const float R1 = r.u(W_UPAR0), R2 = r.u(W_UPAR0 + 1), R3 = r.u(W_UPAR0 + 2);
-    const bool reg1 = region1(R1, mass, w1);
-    const float t = reg1 ? w1p * R2 : __fmaf_rn(1.0f - w1p, R2, w1p);
-    const float u = __fmaf_rn(-m.a, cot_pi(t), xr);
-    const float uu = __fmul_rn(u, u);
-    const float acc = reg1 ? exp_fast(-uu) : exp_fast(u02 - uu);
-    // ---- beside the chain: perpendicular velocity, mu, outgoing direction (as scatter_resonant)
-    const float xc = (xr < m.xcrit) ? m.xcrit : 0.0f;
-    const float rr = sqrt_approx(__fmaf_rn(xc, xc, -__logf(r.u(W_BM_R))));
-    float sp1, cp1;
-    __sincosf(2.0f * kPiF * r.u(W_BM_PHI), &sp1, &cp1);
-    const float u1 = __fmul_rn(rr, cp1), u2 = __fmul_rn(rr, sp1);
-    const float Rm = r.u(W_MU);
-    const float mu = (m.phase == PH_ISO) ? __fmaf_rn(2.0f, Rm, -1.0f) : mu_dipole(Rm);
-    float sp, cp;
-    __sincosf(2.0f * kPiF * r.u(W_PHI), &sp, &cp);
-    float3 e1, e2;
-    basis(ph.k.x, ph.k.y, ph.k.z, e1, e2);
-    const float st = sqrt_approx(fmaxf(0.0f, __fmaf_rn(-mu, mu, 1.0f)));
-    const float3 ko = turn(ph.k, e1, e2, mu, st, cp, sp);
-    // ---- the next event's words and optical depth
-    Rng r2 = r;
-    r2.next_event(nblk);
-    const float tau2 = draw_tau(r2);
-    if (!(in_ball && !dust && xr <= 2.0f && u0 > 0.0f && q <= 0.05f && R3 <= acc)) break;
-    // ---- commit, as shell_event and scatter_resonant do
-    ++ph.steps;
-    advance(ph, s0);
-    ph.safe = __fmaf_rd(-s0, 1.000001f, ph.safe);
-    ph.x = x_after_scatter(xs, sgn * u, mu, st, u1, u2, cp, sp);
-    ph.k = ko;
-    ++ph.iters;
-    ++ph.nscat;
-    r = r2;
-    tau = tau2;
-    if (m.max_scat && ph.nscat >= m.max_scat) {
-      ++n;
-      status = 3;
-      break;
-    }
-    if (!(fabsf(ph.x) <= THOR_VCORE_X)) {  // the next start is outside the polynomial's range
-      ++n;
-      break;
-    }
-  }
-  ph.rng.event = r.event - 1u;  // the event being tried is redone by shell_event
-  if (status == 3) {
+// The line-core form of the prepared event.  Always forms the next event's words and
+// optical depth (r2, tau2).  Returns 0 if the event is not of the core kind (the packet is
+// unchanged), 1 if it was committed, 3 if committed and the scattering cap was reached (the
+// packet is then finished as shell_event_words finishes it).  On commit the packet is
+// prepared for the next event.
+__device__ __forceinline__ int core_event(const ShellModel& m, Photon& ph, const float* __restrict__ Ktab,
+                                          float& tau_next, Rng& r2, float& tau2) {
+  const Rng& r = ph.rng;
+  const float tau = tau_next;
+  // ---- the frequency chain: rate at the start, crossing, gas-frame frequency at the site
+  const float x0 = ph.x;
+  const StartStep st0 = start_step(m, voigt_start(m.a, x0, Ktab), tau);
+  const float s0 = st0.s;
+  const bool in_ball = (m.gam == 0.0f) ? (s0 <= ph.safe) : (ph.safe >= m.ds_core && s0 <= 0.0625f * m.ds_core);
+  const float xs = (m.gam == 0.0f) ? x0 : __fmaf_rn(-m.gam, s0, x0);
+  const bool dust = (m.kapd > 0.0f) && dust_channel(m, st0.kH, r.u(W_CHANNEL));
+  // ---- u_par, first trial of the two-piece comparison function (as sample_upar)
+  const float sgn = (xs < 0.0f) ? -1.0f : 1.0f;
+  const float xr = fabsf(xs);
+  const float u0 = u0_core(xr, m.a);
+  const float q = upar_q(xr, m.a);
+  const float w1 = atan_small(q);
+  const float u02 = __fmul_rn(u0, u0);
+  const float mass = envelope_mass(w1, exp_fast(-u02));
+  const float w1p = w1 * (1.0f / kPiF);
+  const float R1 = r.u(W_UPAR0), R2 = r.u(W_UPAR0 + 1), R3 = r.u(W_UPAR0 + 2);
+  const bool reg1 = region1(R1, mass, w1);
+  const float t = reg1 ? w1p * R2 : __fmaf_rn(1.0f - w1p, R2, w1p);
+  const float u = __fmaf_rn(-m.a, cot_pi(t), xr);
+  const float uu = __fmul_rn(u, u);
+  const float acc = reg1 ? exp_fast(-uu) : exp_fast(u02 - uu);
+  // ---- beside the chain: perpendicular velocity, mu, outgoing direction (as scatter_resonant)
+  const float xc = (xr < m.xcrit) ? m.xcrit : 0.0f;
+  const float rr = sqrt_approx(__fmaf_rn(xc, xc, -__logf(r.u(W_BM_R))));
+  float sp1, cp1;
+  __sincosf(2.0f * kPiF * r.u(W_BM_PHI), &sp1, &cp1);
+  const float u1 = __fmul_rn(rr, cp1), u2 = __fmul_rn(rr, sp1);
+  const float Rm = r.u(W_MU);
+  const float mu = (m.phase == PH_ISO) ? __fmaf_rn(2.0f, Rm, -1.0f) : mu_dipole(Rm);
+  float sp, cp;
+  __sincosf(2.0f * kPiF * r.u(W_PHI), &sp, &cp);
+  float3 e1, e2;
+  basis(ph.k.x, ph.k.y, ph.k.z, e1, e2);
+  const float st = sqrt_approx(fmaxf(0.0f, __fmaf_rn(-mu, mu, 1.0f)));
+  const float3 ko = turn(ph.k, e1, e2, mu, st, cp, sp);
+  // ---- the next event's words and optical depth (valid whichever path runs this event)
+  r2 = r;
+  r2.next_event(shell_blocks(m));
+  tau2 = draw_tau(r2);
+  if (!(!ph.region && m.phase != PH_MIXED && in_ball && !dust && xr <= 2.0f && u0 > 0.0f && q <= 0.05f &&
+        R3 <= acc))
+    return 0;
+  // ---- commit, as shell_event_words and scatter_resonant do
+  ++ph.steps;
+  advance(ph, s0);
+  ph.safe = __fmaf_rd(-s0, 1.000001f, ph.safe);
+  ph.x = x_after_scatter(xs, sgn * u, mu, st, u1, u2, cp, sp);
+  ph.k = ko;
+  ++ph.iters;
+  ++ph.nscat;
+  ph.rng = r2;  // prepared: the next event's words
+  tau_next = tau2;
+  if (m.max_scat && ph.nscat >= m.max_scat) {
     anchor(ph);
     const float b = (float)(ph.px * ph.k.x + ph.py * ph.k.y + ph.pz * ph.k.z);
     ph.X = __fmaf_rn(ph.x, m.vth, m.vgrad * b);
+    return 3;
   }
+  return 1;
+}
+
+// One prepared event: its core form if it is of that kind, else the general event from the
+// same words; the packet is then prepared for the next event.  Returns as shell_event.
+__device__ __forceinline__ int shell_event_pipe(const ShellModel& m, Photon& ph, const float* __restrict__ Ktab,
+                                                float& tau_next) {
+  Rng r2;
+  float tau2;
+  const int c = core_event(m, ph, Ktab, tau_next, r2, tau2);
+  if (c == 1) return 0;
+  if (c == 3) return 3;
+  const int status = shell_event_words(m, ph, Ktab, tau_next);
+  ph.rng = r2;
+  tau_next = tau2;
   return status;
+}
+
+// A burst: core events of a prepared packet back to back, in one loop whose body is one
+// basic block (no vote or exchange between events), until an event is not of the core kind
+// (it is left prepared, for shell_event_pipe) or kCoreBurst events are done.  For warps with
+// few live packets, where a lone lane's latency is what counts.  Returns 3 if the cap was
+// reached, else 0.
+constexpr uint32_t kCoreBurst = 32;
+__device__ __forceinline__ int core_burst(const ShellModel& m, Photon& ph, const float* __restrict__ Ktab,
+                                          float& tau_next) {
+  for (uint32_t n = 0; n < kCoreBurst; ++n) {
+    Rng r2;
+    float tau2;
+    const int c = core_event(m, ph, Ktab, tau_next, r2, tau2);
+    if (c != 1) return c;  // 0: not a core event (still prepared); 3: capped
+  }
+  return 0;
 }
 
 // ---- power-law shells (Sec. 5.1) ---------------------------------------------------
@@ -591,6 +625,8 @@ __global__ void __launch_bounds__(256, 1) shell_run_kernel(const ShellModel* __r
   Photon ph;
   bool active = false, done = (int)lane >= c.per_warp;  // lanes above per_warp stay idle
   bool drained = false;  // warp-uniform: a refill found the photon queue exhausted
+  bool prepared = false;  // ph.rng holds the words of the next event (pipelined mode)
+  float tau_next = 0.0f;
   LaneTally lt;
   for (;;) {
     unsigned need = __ballot_sync(kFull, !active && !done);
@@ -601,7 +637,7 @@ __global__ void __launch_bounds__(256, 1) shell_run_kernel(const ShellModel* __r
       base = __shfl_sync(kFull, base, leader);
       if (!active && !done) {
         const unsigned long long g = base + __popc(need & ((1u << lane) - 1u));
-        if (g < c.n_resume) { load_rec(m, c.resume[g], ph); active = true; }
+        if (g < c.n_resume) { load_rec(m, c.resume[g], ph); active = true; prepared = false; }
       }
       need = __ballot_sync(kFull, !active && !done);
     }
@@ -618,6 +654,7 @@ __global__ void __launch_bounds__(256, 1) shell_run_kernel(const ShellModel* __r
           ph.pid = q.first_id[0] + g;
           shell_emit(m, ph);
           active = true;
+          prepared = false;
         } else {
           done = true;
         }
@@ -631,6 +668,7 @@ __global__ void __launch_bounds__(256, 1) shell_run_kernel(const ShellModel* __r
           unsigned long long base = 0;
           if ((int)lane == leader) base = atomicAdd(c.n_spill, (unsigned long long)__popc(live));
           base = __shfl_sync(kFull, base, leader);
+          if (active && prepared) pipe_unprepare(ph);
           if (active) save_rec(ph, c.spill[base + __popc(live & ((1u << lane) - 1u))]);
         }
         active = false;
@@ -638,8 +676,11 @@ __global__ void __launch_bounds__(256, 1) shell_run_kernel(const ShellModel* __r
       }
     }
     if (__all_sync(kFull, !active)) break;
-    // warps with few live packets (the tail of a run) take core events in bursts
-    const bool burst = kProfile == 0 && __popc(__ballot_sync(kFull, active)) <= c.core_lanes;
+    // pipelined events in warps with at most core_lanes live packets (homologous shells),
+    // and core bursts in warps with at most burst_lanes
+    const int n_live = __popc(__ballot_sync(kFull, active));
+    const bool pipe = kProfile == 0 && n_live <= c.core_lanes;
+    const bool burst = pipe && n_live <= c.burst_lanes;
     // events until some lane of the warp finishes its packet: one vote per event, the
     // refill and spill checks above run only when the set of live lanes changed
     bool fin;
@@ -647,11 +688,14 @@ __global__ void __launch_bounds__(256, 1) shell_run_kernel(const ShellModel* __r
       fin = false;
       if (active) {
         int st = 0;
-        if (burst) {
-          uint32_t nb;
-          st = core_burst(m, ph, kCoreBurst, nb);
+        if (pipe) {
+          if (!prepared) { pipe_prepare(m, ph, tau_next); prepared = true; }
+          if (burst) st = core_burst(m, ph, sK, tau_next);
+          if (!st) st = shell_event_pipe(m, ph, sK, tau_next);
+        } else {
+          if (prepared) { pipe_unprepare(ph); prepared = false; }
+          st = kProfile ? shell_event_pl(m, ph, sK) : shell_event(m, ph, sK);
         }
-        if (!st) st = kProfile ? shell_event_pl(m, ph, sK) : shell_event(m, ph, sK);
         if (st) {
           if (st == 1) { ++lt.esc; tally_spectrum(m, ph.X); }
           else if (st == 2) ++lt.abs;
@@ -727,6 +771,8 @@ __global__ void __launch_bounds__(256, 1) shell_slice_kernel(const ShellModel* _
   }
   Photon ph;
   bool active = false, done = false;
+  bool prepared = false;  // ph.rng holds the words of the next event (pipelined mode)
+  float tau_next = 0.0f;
   const SlotState& st = in;
   if (slot >= 0) {
     ph.model = st.model[slot];
@@ -764,6 +810,7 @@ __global__ void __launch_bounds__(256, 1) shell_slice_kernel(const ShellModel* _
           ph.pid = q.first_id[e] + (g - q.prefix[e]);
           shell_emit(models[ph.model], ph);
           active = true;
+          prepared = false;
         } else {
           done = true;
         }
@@ -782,25 +829,41 @@ __global__ void __launch_bounds__(256, 1) shell_slice_kernel(const ShellModel* _
     if (__any_sync(kFull, dropped)) { ++ev; continue; }  // refill the dropped lanes first
     const ShellModel mr = *mp;  // by value: the fields the event loop reads stay in registers
     // events until some lane finishes its packet or the budget is used: one vote per event;
-    // warps with few live packets take core events in bursts, charged to the budget by the
-    // longest burst of the warp
-    const bool burst = __popc(__ballot_sync(kFull, active)) <= kCoreLanes;
+    // homologous shells run pipelined events in warps with at most kServedPipeLanes live
+    // packets
+    const int n_live = __popc(__ballot_sync(kFull, active));
+    const bool pipe = n_live <= kServedPipeLanes;
+    const bool burst = n_live <= kServedBurstLanes;
     bool fin;
     do {
       fin = false;
       uint32_t nb = 0;
       if (active) {
         int r = 0;
-        if (burst && !(kMixed && mr.profile) && budget - ev > 1u) r = core_burst(mr, ph, min(kCoreBurst, budget - ev - 1u), nb);
-        if (!r) r = (kMixed && mr.profile) ? shell_event_pl(mr, ph, sK) : shell_event(mr, ph, sK);
+        if (pipe && !(kMixed && mr.profile)) {
+          if (!prepared) { pipe_prepare(mr, ph, tau_next); prepared = true; }
+          if (burst && budget - ev > kCoreBurst) {
+            const uint32_t before = ph.nscat;
+            r = core_burst(mr, ph, sK, tau_next);
+            nb = ph.nscat - before;
+          }
+          if (!r) r = shell_event_pipe(mr, ph, sK, tau_next);
+        } else {
+          if (prepared) { pipe_unprepare(ph); prepared = false; }
+          r = (kMixed && mr.profile) ? shell_event_pl(mr, ph, sK) : shell_event(mr, ph, sK);
+        }
         if (r) { finish_global(mr, ph, r); active = false; fin = true; }
       }
-      ev += 1u + __reduce_max_sync(kFull, nb);
+      ev += 1u + __reduce_max_sync(kFull, nb);  // a burst is charged its events
     } while (ev < budget && !__any_sync(kFull, fin));
   }
+  if (active && prepared) pipe_unprepare(ph);  // saved packets hold their last completed event
   // append the packets still in flight to the next list (one atomic per warp and list):
-  // packets of priority requests from the back, the others from the front
-  const bool pri = active && *(volatile const int32_t*)&models[ph.model].priority;
+  // priority packets from the back, the others from the front.  Priority: packets of the
+  // requests the host marked (the oldest), and long-lived packets (more than kLongLived
+  // events: photons trapped in the line core, whose histories set the requests' latency)
+  const bool pri = active && ((ph.nscat + ph.ndust) >= kLongLived ||
+                              *(volatile const int32_t*)&models[ph.model].priority);
   const unsigned live_f = __ballot_sync(kFull, active && !pri), live_b = __ballot_sync(kFull, pri);
   if (live_f | live_b) {
     const int lead_f = live_f ? __ffs(live_f) - 1 : 0, lead_b = live_b ? __ffs(live_b) - 1 : 0;
@@ -839,10 +902,11 @@ int shell_grid(int block, int blocks_per_sm, bool sliced) {
 }
 
 cudaError_t launch_shell_run(const ShellModel* d_models, WorkQueue q, const float* d_ktab, int grid, int block,
-                             int profile, int per_warp, int core_lanes, cudaStream_t s) {
+                             int profile, int per_warp, int core_lanes, int burst_lanes, cudaStream_t s) {
   Compact none{};
   none.per_warp = per_warp;
   none.core_lanes = core_lanes;
+  none.burst_lanes = burst_lanes;
   if (profile) shell_run_kernel<false, 1><<<grid, block, 0, s>>>(d_models, q, none, d_ktab);
   else shell_run_kernel<false, 0><<<grid, block, 0, s>>>(d_models, q, none, d_ktab);
   return cudaGetLastError();

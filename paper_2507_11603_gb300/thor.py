@@ -74,7 +74,7 @@ class Result(C.Structure):
 
 
 class ForestSpec(C.Structure):
-    _fields_ = [("ds_cm", C.c_double), ("dv_cell", C.c_double), ("n_bins", C.c_int32), ("reserved", C.c_int32),
+    _fields_ = [("ds_cm", C.c_double), ("dv_cell", C.c_double), ("n_bins", C.c_int32), ("stage_rows", C.c_int32),
                 ("dv_bin", C.c_double), ("first_sightline", C.c_int64), ("n_sightlines", C.c_int64)]
 
 
@@ -107,7 +107,7 @@ def load(build: bool = True) -> C.CDLL:
             "thor_ctx_set_stream": ([vp, vp], C.c_int),
             "thor_ctx_set_launch": ([vp, C.c_int, C.c_int], C.c_int),
             "thor_ctx_set_tail": ([vp, C.c_int, C.c_int], C.c_int),
-            "thor_ctx_set_bursts": ([vp, C.c_int], C.c_int),
+            "thor_ctx_set_bursts": ([vp, C.c_int, C.c_int], C.c_int),
             "thor_shell_create": ([vp, P(ShellParams), P(vp)], C.c_int),
             "thor_grid_create": ([vp, vp, vp, vp, vp, P(i32), dbl, C.c_int, P(vp)], C.c_int),
             "thor_grid_set_scattering": ([vp, C.c_int, dbl, dbl], C.c_int),
@@ -276,10 +276,11 @@ class Context:
     def set_launch(self, block_size: int, blocks_per_sm: int = 0):
         self._check(self.L.thor_ctx_set_launch(self.h, block_size, blocks_per_sm))
 
-    def set_bursts(self, max_lanes: int = 4):
-        """thor_ctx_set_bursts: core bursts in warps with at most max_lanes live packets (0 =
-        never); results do not depend on it."""
-        self._check(self.L.thor_ctx_set_bursts(self.h, max_lanes))
+    def set_bursts(self, pipe_lanes: int = 32, burst_lanes: int = 4):
+        """thor_ctx_set_bursts: pipelined events in warps with at most pipe_lanes live packets,
+        core bursts in warps with at most burst_lanes (0 = never); results do not depend on
+        them."""
+        self._check(self.L.thor_ctx_set_bursts(self.h, pipe_lanes, burst_lanes))
 
     def set_tail(self, spill_below: int = 0, max_phases: int = 24):
         """thor_ctx_set_tail: tail compaction of the shell photon loop (0 = off, the library's
@@ -381,7 +382,9 @@ class Context:
                                          float(X_max), out.ctypes.data_as(C.POINTER(C.c_double))))
         return out
 
-    def forest(self, n_HI, T, v_los, *, ds_cm, dv_cell, n_bins, dv_bin, first=0, count=None, out=None):
+    def forest(self, n_HI, T, v_los, *, ds_cm, dv_cell, n_bins, dv_bin, first=0, count=None, out=None,
+               stage_rows=0):
+        """thor_forest; stage_rows: rows of sightlines per staged chunk for host arrays (0 = automatic)."""
         n_HI = _arr(n_HI, "n_HI", np.float32)
         if len(n_HI.shape) != 3:
             raise ValueError("n_HI must have shape (nz, ny, nx)")
@@ -406,7 +409,7 @@ class Context:
         if tuple(out.shape) != (count, n_bins):
             raise ValueError(f"out: shape {tuple(out.shape)}, expected {(count, n_bins)}")
         dims = (C.c_int32 * 3)(nx, ny, nz)
-        sp = ForestSpec(ds_cm, dv_cell, n_bins, 0, dv_bin, first, count)
+        sp = ForestSpec(ds_cm, dv_cell, n_bins, int(stage_rows), dv_bin, first, count)
         self._check(self.L.thor_forest(self.h, _ptr(n_HI)[0], _ptr(T)[0], _ptr(v_los)[0], dims, kind, C.byref(sp),
                                        _ptr(out)[0]))
         return out

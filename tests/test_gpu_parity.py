@@ -312,18 +312,19 @@ def test_ragged_photon_counts_equal_photons_alone(ctx):
 @pytest.mark.parametrize("geo", [dict(R_in=0.9, N_HI=3e19, T=1e4, v_max=200.0, tau_dust=0.5, phase="dipole"),
                                  dict(tau0=1e6, T=1e4, phase="isotropic")])
 def test_core_bursts_do_not_change_results(ctx, geo):
-    """Core bursts (pipelined core events) evaluate each event exactly as the general event
-    does: per-photon records and every tally are bit-identical with bursts never, in warps
-    with at most 4 live packets (the default), and in every warp; on an outflowing dusty
-    shell (start-point sub-steps, dust channel) and a static sphere (safety-ball steps)."""
+    """Pipelined events and core bursts evaluate each event exactly as the general event
+    does: per-photon records and every tally are bit-identical with pipelining never, in
+    every warp or in warps of at most 4 live packets, and with bursts never, in warps of at
+    most 4 (the default) or in every warp; on an outflowing dusty shell (start-point
+    sub-steps, dust channel) and a static sphere (safety-ball steps)."""
     g = ctx.shell(**geo)
     kw = dict(n_photons=3000, seed=41, sigma=50.0 if "N_HI" in geo else 0.0, n_bins=200, X_min=-1500.0,
               X_max=1500.0, raw=True)
     out = []
-    for lanes in (0, 4, 32):
-        ctx.set_bursts(lanes)
+    for pipe, burst in ((0, 0), (32, 0), (4, 4), (32, 4), (32, 32)):
+        ctx.set_bursts(pipe, burst)
         out.append(ctx.run(g, **kw))
-    ctx.set_bursts(4)
+    ctx.set_bursts(32, 4)
     a = out[0]
     assert a.stats["n_scat"] > 1e6
     for b in out[1:]:
@@ -428,36 +429,64 @@ def test_grid64_config4_density_peeling(ctx, orc):
     fields of 50 km/s per axis; dust 0.01 n_HI with albedo 0.32, g 0.73), peeled to three
     observers on 32 x 32 images.  A photon here scatters ~6e5 times on average before it
     leaves, too long for the FP64 oracle in a test, so both sides stop every photon after 2e4
-    scatterings (the same definition).  Compared: fates, mean scatterings, escape
-    frequencies (KS), the peeled totals, per-observer spectra and coarse image blocks."""
+    scatterings (the same definition).  The peeled light comes from the few scatterings near
+    the box faces (tau ~ 1.8e4 per cell elsewhere), so its totals are heavy-tailed (the
+    oracle's own total varies by ~9% between seeds at this size): both sides run 8 batches of
+    500 photons, and the peeled totals, per-observer spectra and image blocks are compared
+    with standard errors from the spread between batches.  Also compared: fates, mean
+    scatterings and escape frequencies (KS) over all 4000 photons."""
     from paper_2507_11603_gb300 import synth
     f = synth.grid_fields(n=64, seed=3)
     cell = 100 * synth.PC_CM
     g = ctx.grid(f["n_HI"], f["T"], f["v"], f["kd"], cell, phase="dipole", albedo=0.32, g_hg=0.73)
-    n, cap = 4000, 20000
-    kw = dict(n_bins=64, X_min=-1000.0, X_max=1000.0)
-    r = ctx.run(g, n_photons=n, seed=61, peel=True, img_n=32, peel_bins=64, peel_X_min=-1000.0, peel_X_max=1000.0,
-                raw=True, max_scat=cap, **kw)
     of = {"n_HI": f["n_HI"], "T": f["T"], "vx": f["v"][0], "vy": f["v"][1], "vz": f["v"][2], "kd": f["kd"]}
-    ro = orc.run_grid(of, cell_cm=cell, n_photons=n, seed=1061, img_nx=32, phase="dipole", albedo=0.32, g_hg=0.73,
-                      raw=True, max_scat=cap, **kw)
-    for k in ("n_escaped", "n_absorbed", "n_capped"):
-        p1, p2 = r.stats[k] / n, ro[k] / n
+    nb, m, cap = 8, 500, 20000
+    n = nb * m
+    kw = dict(n_bins=64, X_min=-1000.0, X_max=1000.0)
+    keys = ("n_escaped", "n_absorbed", "n_capped")
+    tg = dict.fromkeys(keys + ("n_scat", "sum_scat2"), 0)
+    to = dict.fromkeys(keys + ("sum_scat", "sum_scat2"), 0)
+    Xg, Xo, cubes_g, cubes_o = [], [], [], []
+    for b in range(nb):
+        r = ctx.run(g, n_photons=m, first_id=b * m, seed=61, peel=True, img_n=32, peel_bins=64, peel_X_min=-1000.0,
+                    peel_X_max=1000.0, raw=True, max_scat=cap, **kw)
+        ro = orc.run_grid(of, cell_cm=cell, n_photons=m, first_id=b * m, seed=1061, img_nx=32, phase="dipole",
+                          albedo=0.32, g_hg=0.73, raw=True, max_scat=cap, **kw)
+        for k in keys:
+            tg[k] += r.stats[k]
+            to[k] += ro[k]
+        tg["n_scat"] += r.stats["n_scat"]; tg["sum_scat2"] += r.stats["sum_scat2"]
+        to["sum_scat"] += ro["sum_scat"]; to["sum_scat2"] += ro["sum_scat2"]
+        Xg.append(np.asarray(r.raw_X, np.float64)[np.asarray(r.raw_status) == 1])
+        Xo.append(ro["X"][ro["status"] == 1])
+        cubes_g.append(r.cube.astype(np.float64))
+        cubes_o.append(ro["cube"])
+    for k in keys:
+        p1, p2 = tg[k] / n, to[k] / n
         sd = np.sqrt((p1 * (1 - p1) + p2 * (1 - p2)) / n) + 1e-12
         assert abs(p1 - p2) < 4 * sd, (k, p1, p2)
-    assert mean_nscat_z(r.stats, n, ro, n) < 3.0
-    eg, eo = np.asarray(r.raw_status) == 1, ro["status"] == 1
-    assert min(eg.sum(), eo.sum()) > 100
-    assert stats.ks_2samp(np.asarray(r.raw_X, np.float64)[eg], ro["X"][eo]).pvalue > 1e-3
-    cg, co = r.cube.astype(np.float64), ro["cube"]
-    assert abs(cg.sum() / co.sum() - 1) < 0.05, (cg.sum(), co.sum())
+    assert mean_nscat_z(tg, n, to, n) < 3.0
+    Xg, Xo = np.concatenate(Xg), np.concatenate(Xo)
+    assert min(Xg.size, Xo.size) > 100
+    assert stats.ks_2samp(Xg, Xo).pvalue > 1e-3
+    cg, co = np.stack(cubes_g), np.stack(cubes_o)  # (batch, axis, iy, ix, bin)
+
+    def z_of(qg, qo):
+        """|difference of means| / combined standard error, batch statistics on axis 0."""
+        se = np.sqrt(qg.var(axis=0, ddof=1) / nb + qo.var(axis=0, ddof=1) / nb) + 1e-300
+        return np.abs(qg.mean(axis=0) - qo.mean(axis=0)) / se
+
+    assert z_of(cg.sum(axis=(1, 2, 3, 4)), co.sum(axis=(1, 2, 3, 4))) < 4.0
     for ax in range(3):
-        sg, so = cg[ax].sum(axis=(0, 1)).reshape(-1, 4).sum(1), co[ax].sum(axis=(0, 1)).reshape(-1, 4).sum(1)
-        main = so > 0.02 * so.max()
-        assert np.median(np.abs(sg[main] / so[main] - 1)) < 0.1, ax
-        ig = cg[ax].sum(axis=2).reshape(4, 8, 4, 8).sum(axis=(1, 3))
-        io = co[ax].sum(axis=2).reshape(4, 8, 4, 8).sum(axis=(1, 3))
-        assert np.median(np.abs(ig / io - 1)) < 0.1, ax
+        spec_g = cg[:, ax].sum(axis=(1, 2)).reshape(nb, -1, 4).sum(axis=2)
+        spec_o = co[:, ax].sum(axis=(1, 2)).reshape(nb, -1, 4).sum(axis=2)
+        main = spec_o.mean(axis=0) > 0.02 * spec_o.mean(axis=0).max()
+        zs = z_of(spec_g, spec_o)[main]
+        assert np.mean(zs ** 2) < 2.5 and zs.max() < 5.0, (ax, zs)
+        img_g = cg[:, ax].sum(axis=3).reshape(nb, 4, 8, 4, 8).sum(axis=(2, 4)).reshape(nb, -1)
+        img_o = co[:, ax].sum(axis=3).reshape(nb, 4, 8, 4, 8).sum(axis=(2, 4)).reshape(nb, -1)
+        zi = z_of(img_g, img_o)
+        assert np.mean(zi ** 2) < 2.5 and zi.max() < 5.0, (ax, zi)
 
 
 def test_grid_same_stream_per_photon(ctx, orc):
@@ -508,7 +537,8 @@ def test_forest_small_box_elementwise(ctx, orc):
 def test_forest_ragged_chunks_and_subsets(ctx, orc):
     """Ragged forest shapes, element by element against the FP64 oracle: nz = 1100 spans two
     staged cell chunks (1024 + 76), n_bins = 300 leaves a ragged last bin pass, the box is
-    3 x 5 sightlines with a sub-range [4, 11), on host and device buffers; and the
+    3 x 5 sightlines with a sub-range [4, 11), on host (staged whole and one or two rows of
+    sightlines at a time) and device buffers; and the
     degenerate one-cell, one-bin sightline (a single Voigt term)."""
     import torch
     from paper_2507_11603_gb300 import synth
@@ -519,7 +549,10 @@ def test_forest_ragged_chunks_and_subsets(ctx, orc):
     ref = orc.forest(nHI, T, v, sel % 5, sel // 5, **kw)
     host = ctx.forest(nHI, T, v, first=4, count=7, **kw)
     dev = ctx.forest(*(torch.as_tensor(a, device="cuda") for a in (nHI, T, v)), first=4, count=7, **kw)
-    for got in (host, dev.cpu().numpy()):
+    # host arrays staged one and two rows of sightlines at a time: the range [4, 11) spans
+    # rows 0 (one sightline), 1 and 2 (one), and three chunks reuse a staging buffer
+    staged = [ctx.forest(nHI, T, v, first=4, count=7, stage_rows=k, **kw) for k in (1, 2)]
+    for got in (host, dev.cpu().numpy(), *staged):
         assert got.shape == (7, 300)
         rel = np.abs(got.astype(np.float64) - ref) / ref
         assert rel.max() < 1e-5, rel.max()
