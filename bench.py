@@ -331,7 +331,7 @@ def run_shell_bench(args):
 
 
 def stream_bench(ctx, n_requests=256, seed=2, load=0.75, events_per_round=256, nhi_max=1e21, core_skip=True,
-                 priority=True):
+                 priority=True, presort=True):
     """Served shell-model stream (Sec. 5.1 parameter grid): requests with Poisson arrivals at
     `load` x the measured batched capacity, continuous batching on the device.  Baseline,
     also live: the same requests at the same arrival times served one launch per model
@@ -354,7 +354,7 @@ def stream_bench(ctx, n_requests=256, seed=2, load=0.75, events_per_round=256, n
         return res
 
     # 1) batched capacity: all requests at t = 0
-    srv = ctx.server(max_requests=256, events_per_round=events_per_round, priority=priority)
+    srv = ctx.server(max_requests=256, events_per_round=events_per_round, priority=priority, presort=presort)
     t0 = time.perf_counter()
     tickets = [submit(srv, r) for r in reqs]
     burst = [srv.wait(t, timeout_ms=600000) for t in tickets]
@@ -402,6 +402,7 @@ def stream_bench(ctx, n_requests=256, seed=2, load=0.75, events_per_round=256, n
                "one_launch_fifo_ms": float(fifo_lat[j])}
     return {"requests": n_requests, "slowest": slowest, "photons": int(sum(r["n_photons"] for r in reqs)),
             "core_skip": core_skip, "N_HI_max": nhi_max, "load": load, "rate_per_s": rate, "age_priority": priority,
+            "presort": presort,
             "batched": {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                         "scatterings_per_s": scat / span, "burst_scatterings_per_s": burst_scat / burst_total,
                         "rounds": stats["rounds"], "mean_resident": stats["mean_resident"],
@@ -419,7 +420,8 @@ def run_stream_bench(args):
     ctx = thor.Context(0)
     with ClockSampler(0) as clk:
         s = stream_bench(ctx, n_requests=args.stream_requests, nhi_max=args.stream_nhi_max,
-                         core_skip=not args.no_core_skip, priority=not args.no_priority)
+                         core_skip=not args.no_core_skip, priority=not args.no_priority,
+                         presort=not args.no_presort)
     print(json.dumps({"metric": METRIC, "value": s["batched"]["scatterings_per_s"], "unit": "scatterings/s",
                       "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
                       "config": {"workload": "served shell-model stream"}, "stream": s, "clocks": clk.summary()}))
@@ -648,6 +650,7 @@ def main():
     ap.add_argument("--stream-nhi-max", type=float, default=1e21)
     ap.add_argument("--no-core-skip", action="store_true")
     ap.add_argument("--no-priority", action="store_true", help="served stream without age priority")
+    ap.add_argument("--no-presort", action="store_true", help="served stream without frequency pre-sorting")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--lone-events", type=int, default=200000,
                     help="events of the longest photon run alone to time the lone-lane event latency")

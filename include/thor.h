@@ -299,6 +299,9 @@ typedef struct {
   int32_t priority;          /* age priority: 0 = on (the oldest request, and the next oldest while
                                 their packets in flight fit in half of the warps, run their packets
                                 one per warp), -1 = off (every packet shares warps) */
+  int32_t presort;           /* frequency pre-sorting of the packets in flight between rounds, so a
+                                warp's packets are of one kind: 0 = on, -1 = off */
+  int32_t reserved;
 } thor_server_config;
 
 /* Create a server on the context: a host thread runs device rounds while work is

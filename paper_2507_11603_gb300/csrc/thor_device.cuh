@@ -177,7 +177,7 @@ __device__ __forceinline__ float voigt_core(float a, float ax, float x2, const f
     k = __fmaf_rn(k, u, q1.x); k = __fmaf_rn(k, u, q0.w); k = __fmaf_rn(k, u, q0.z);
     k = __fmaf_rn(k, u, q0.y); k = __fmaf_rn(k, u, q0.x);
   } else {  // latency-bound callers (photon loops): Estrin, dependency depth 4 instead of 11
-    const float u2 = u * u, u4 = u2 * u2, u8 = u4 * u4;
+    const float u2 = u * u, u4 = u2 * u2;
     const float p01 = __fmaf_rn(q0.y, u, q0.x), p23 = __fmaf_rn(q0.w, u, q0.z);
     const float p45 = __fmaf_rn(q1.y, u, q1.x), p67 = __fmaf_rn(q1.w, u, q1.z);
     const float p89 = __fmaf_rn(q2.y, u, q2.x), pab = __fmaf_rn(q2.w, u, q2.z);

@@ -180,6 +180,7 @@ cudaError_t launch_shell_run_compact(const ShellModel* d_models, WorkQueue q, Co
 cudaError_t launch_reweight(int64_t n, const float* X0, const float* X, const float* col, const uint8_t* status,
                             const float* d_params, int n_targets, int n_bins, double X_min, double X_max,
                             double* d_out, int n_sm, cudaStream_t s);
+cudaError_t launch_slot_presort(SlotState from, SlotState to, unsigned long long* cnt, cudaStream_t s);
 cudaError_t launch_shell_slice(const ShellModel* d_models, WorkQueue q, SlotState in, SlotState out,
                                uint32_t event_budget,
                                const float* d_ktab, int grid, int block, bool mixed, cudaStream_t s);

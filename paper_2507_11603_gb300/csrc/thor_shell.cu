@@ -286,8 +286,18 @@ __device__ __forceinline__ void pipe_unprepare(Photon& ph) { ph.rng.event -= 1u;
 // unchanged), 1 if it was committed, 3 if committed and the scattering cap was reached (the
 // packet is then finished as shell_event_words finishes it).  On commit the packet is
 // prepared for the next event.
+__device__ __forceinline__ int core_event_with(const ShellModel& m, Photon& ph, const float* __restrict__ Ktab,
+                                               float& tau_next, const Rng& r2, float tau2);
 __device__ __forceinline__ int core_event(const ShellModel& m, Photon& ph, const float* __restrict__ Ktab,
                                           float& tau_next, Rng& r2, float& tau2) {
+  r2 = ph.rng;
+  r2.next_event(shell_blocks(m));
+  tau2 = draw_tau(r2);
+  return core_event_with(m, ph, Ktab, tau_next, r2, tau2);
+}
+// The same event with the next event's words (r2) and optical depth (tau2) given.
+__device__ __forceinline__ int core_event_with(const ShellModel& m, Photon& ph, const float* __restrict__ Ktab,
+                                               float& tau_next, const Rng& r2, float tau2) {
   const Rng& r = ph.rng;
   const float tau = tau_next;
   // ---- the frequency chain: rate at the start, crossing, gas-frame frequency at the site
@@ -326,10 +336,6 @@ __device__ __forceinline__ int core_event(const ShellModel& m, Photon& ph, const
   basis(ph.k.x, ph.k.y, ph.k.z, e1, e2);
   const float st = sqrt_approx(fmaxf(0.0f, __fmaf_rn(-mu, mu, 1.0f)));
   const float3 ko = turn(ph.k, e1, e2, mu, st, cp, sp);
-  // ---- the next event's words and optical depth (valid whichever path runs this event)
-  r2 = r;
-  r2.next_event(shell_blocks(m));
-  tau2 = draw_tau(r2);
   if (!(!ph.region && m.phase != PH_MIXED && in_ball && !dust && xr <= 2.0f && u0 > 0.0f && q <= 0.05f &&
         R3 <= acc))
     return 0;
@@ -382,6 +388,64 @@ __device__ __forceinline__ int core_burst(const ShellModel& m, Photon& ph, const
     if (c != 1) return c;  // 0: not a core event (still prepared); 3: capped
   }
   return 0;
+}
+
+// A cooperative burst, for warps with at most kCoopOwners packets in bursts.  Called by all
+// 32 lanes, converged; `mine` marks the lanes whose (prepared) packets burst.  In a core
+// event the next event's three Philox blocks are about half a lone lane's instructions, and
+// they depend on nothing but the key, the photon id and the event number.  So every lane
+// computes one block ahead -- for owner o, event d ahead, block b: D = 32 / (3 owners)
+// events deep -- and the owners take their words by shuffle, D events per round of blocks.
+// The words are the ones Rng::start_event forms, so the packets' histories are those of
+// core_burst, bit for bit.  Returns as core_burst (per lane; 0 for lanes not in the burst).
+constexpr int kCoopOwners = 10;
+__device__ __forceinline__ int core_burst_coop(const ShellModel& m, Photon& ph, const float* __restrict__ Ktab,
+                                               float& tau_next, bool mine) {
+  const int lane = (int)(threadIdx.x & 31u);
+  const unsigned owners = __ballot_sync(kFull, mine);
+  const int n_own = __popc(owners);
+  if (n_own == 0) return 0;
+  if (n_own > kCoopOwners) return mine ? core_burst(m, ph, Ktab, tau_next) : 0;
+  const int D = 32 / (3 * n_own);  // >= 1
+  const int span = 3 * D;
+  // as a block computer: owner rank oi (its lane src), event offset d, block b
+  const int oi = lane / span, rem = lane - oi * span;
+  const int d = rem / 3, b = rem - 3 * d;
+  unsigned o = owners;
+#pragma unroll
+  for (int k = 0; k < kCoopOwners - 1; ++k)
+    if (k < oi) o &= o - 1u;
+  const int src = o ? __ffs(o) - 1 : 0;  // lanes past the owners' spans compute a spare block
+  // as an owner: the first lane of its span
+  const int base = mine ? __popc(owners & ((1u << lane) - 1u)) * span : 0;
+  const bool b3 = shell_blocks(m) > 2u;  // else words 8..11 stay as start_event leaves them
+  bool go = mine;
+  int status = 0;
+  for (uint32_t n = 0; n < kCoreBurst; n += (uint32_t)D) {
+    // a round of blocks: events e+1 .. e+D of each owner (e = its prepared event now)
+    const uint32_t k0 = __shfl_sync(kFull, ph.rng.k0, src), k1 = __shfl_sync(kFull, ph.rng.k1, src);
+    uint32_t h0 = __shfl_sync(kFull, ph.rng.p0, src), h1 = __shfl_sync(kFull, ph.rng.p1, src);
+    uint32_t h2 = __shfl_sync(kFull, ph.rng.event, src) + 1u + (uint32_t)d, h3 = (uint32_t)b;
+    philox10(h0, h1, h2, h3, k0, k1);
+    for (int i = 0; i < D && n + (uint32_t)i < kCoreBurst; ++i) {
+      const int s0 = base + 3 * i;
+      Rng r2 = ph.rng;
+      r2.event = ph.rng.event + 1u;
+      r2.v[0] = __shfl_sync(kFull, h0, s0); r2.v[1] = __shfl_sync(kFull, h1, s0);
+      r2.v[2] = __shfl_sync(kFull, h2, s0); r2.v[3] = __shfl_sync(kFull, h3, s0);
+      r2.v[4] = __shfl_sync(kFull, h0, s0 + 1); r2.v[5] = __shfl_sync(kFull, h1, s0 + 1);
+      r2.v[6] = __shfl_sync(kFull, h2, s0 + 1); r2.v[7] = __shfl_sync(kFull, h3, s0 + 1);
+      const uint32_t w8 = __shfl_sync(kFull, h0, s0 + 2), w9 = __shfl_sync(kFull, h1, s0 + 2);
+      const uint32_t w10 = __shfl_sync(kFull, h2, s0 + 2), w11 = __shfl_sync(kFull, h3, s0 + 2);
+      if (b3) { r2.v[8] = w8; r2.v[9] = w9; r2.v[10] = w10; r2.v[11] = w11; }
+      if (go) {
+        const int c = core_event_with(m, ph, Ktab, tau_next, r2, draw_tau(r2));
+        if (c != 1) { go = false; status = c; }
+      }
+      if (!__any_sync(kFull, go)) return status;
+    }
+  }
+  return status;
 }
 
 // ---- power-law shells (Sec. 5.1) ---------------------------------------------------
@@ -683,14 +747,18 @@ __global__ void __launch_bounds__(256, 1) shell_run_kernel(const ShellModel* __r
     const bool burst = pipe && n_live <= c.burst_lanes;
     // events until some lane of the warp finishes its packet: one vote per event, the
     // refill and spill checks above run only when the set of live lanes changed
+    // (bursts are cooperative up to kCoopOwners live packets: all lanes, converged)
     bool fin;
     do {
       fin = false;
+      int st = 0;
+      if (burst) {
+        if (active && !prepared) { pipe_prepare(m, ph, tau_next); prepared = true; }
+        st = core_burst_coop(m, ph, sK, tau_next, active);
+      }
       if (active) {
-        int st = 0;
         if (pipe) {
           if (!prepared) { pipe_prepare(m, ph, tau_next); prepared = true; }
-          if (burst) st = core_burst(m, ph, sK, tau_next);
           if (!st) st = shell_event_pipe(m, ph, sK, tau_next);
         } else {
           if (prepared) { pipe_unprepare(ph); prepared = false; }
@@ -766,8 +834,11 @@ __global__ void __launch_bounds__(256, 1) shell_slice_kernel(const ShellModel* _
   if (pri_warp) {
     if (lane == 0) slot = in.n_slots - 1 - warp;
   } else {
-    const unsigned long long e = (unsigned long long)(warp - n_pw) + (unsigned long long)lane * n_rest_warps;
-    if (e < rest) slot = (e < n_in) ? (int64_t)e : in.n_slots - 1 - (int64_t)(n_pw + (e - n_in));
+    // contiguous entries per warp, counts differing by at most one: [w rest / W, (w+1) rest / W)
+    // (the list arrives sorted by frequency bucket, so a warp's packets are of one kind)
+    const unsigned long long wi = (unsigned long long)(warp - n_pw), W = (unsigned long long)n_rest_warps;
+    const unsigned long long e = wi * rest / W + lane, e1 = (wi + 1) * rest / W;
+    if (e < e1) slot = (e < n_in) ? (int64_t)e : in.n_slots - 1 - (int64_t)(n_pw + (e - n_in));
   }
   Photon ph;
   bool active = false, done = false;
@@ -838,15 +909,17 @@ __global__ void __launch_bounds__(256, 1) shell_slice_kernel(const ShellModel* _
     do {
       fin = false;
       uint32_t nb = 0;
+      int r = 0;
+      const bool pl = pipe && !(kMixed && mr.profile);  // this lane's packet runs pipelined events
+      if (burst && budget - ev > kCoreBurst) {  // cooperative burst: all lanes, converged
+        if (active && pl && !prepared) { pipe_prepare(mr, ph, tau_next); prepared = true; }
+        const uint32_t before = ph.nscat;
+        r = core_burst_coop(mr, ph, sK, tau_next, active && pl);
+        if (active && pl) nb = ph.nscat - before;
+      }
       if (active) {
-        int r = 0;
-        if (pipe && !(kMixed && mr.profile)) {
+        if (pl) {
           if (!prepared) { pipe_prepare(mr, ph, tau_next); prepared = true; }
-          if (burst && budget - ev > kCoreBurst) {
-            const uint32_t before = ph.nscat;
-            r = core_burst(mr, ph, sK, tau_next);
-            nb = ph.nscat - before;
-          }
           if (!r) r = shell_event_pipe(mr, ph, sK, tau_next);
         } else {
           if (prepared) { pipe_unprepare(ph); prepared = false; }
@@ -888,7 +961,65 @@ __global__ void __launch_bounds__(256, 1) shell_slice_kernel(const ShellModel* _
   }
 }
 
+// ---- frequency pre-sorting of resident packets between served rounds ----------------
+// Sorting packets by frequency before they are handed to warps groups those that take the
+// same branches (the paper's pre-sorting, App. A.1 and Sec. 7.1): here, between rounds, the
+// front list of `from` (from.live[1] packets) is copied into `to` by bucket -- line core
+// (|x| <= 2), near wing (|x| <= 5), far wing, empty cavity -- and the resume hands each warp
+// contiguous entries, so a warp's packets are of one kind (core packets then run the
+// pipelined core events in step, wing packets the general event).  The back (priority)
+// list is copied in place.  cnt[0..3]: bucket sizes, cnt[4..7]: cursors, zero on entry.
+// The order inside a bucket does not matter: a packet's history does not depend on its
+// warp or lane.
+__device__ __forceinline__ int slot_bucket(const SlotState& s, int64_t i) {
+  if (s.region[i]) return 3;
+  const float ax = fabsf(s.x[i]);
+  return ax <= 2.0f ? 0 : (ax <= 5.0f ? 1 : 2);
+}
+__device__ __forceinline__ void copy_slot(const SlotState& a, int64_t i, const SlotState& b, int64_t j) {
+  b.px[j] = a.px[i]; b.py[j] = a.py[i]; b.pz[j] = a.pz[i];
+  b.ox[j] = a.ox[i]; b.oy[j] = a.oy[i]; b.oz[j] = a.oz[i]; b.safe[j] = a.safe[i];
+  b.kx[j] = a.kx[i]; b.ky[j] = a.ky[i]; b.kz[j] = a.kz[i]; b.X[j] = a.X[i]; b.x[j] = a.x[i];
+  b.event[j] = a.event[i];
+  b.nscat[j] = a.nscat[i]; b.ndust[j] = a.ndust[i]; b.iters[j] = a.iters[i]; b.steps[j] = a.steps[i];
+  b.model[j] = a.model[i]; b.pid[j] = a.pid[i]; b.region[j] = a.region[i];
+}
+__global__ void slot_hist_kernel(SlotState from, unsigned long long* __restrict__ cnt) {
+  const unsigned long long n = from.live[1];
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool mine = (unsigned long long)i < n;
+  const int key = mine ? slot_bucket(from, i) : 4;
+  const unsigned peers = __match_any_sync(kFull, key);
+  if (mine && (int)(threadIdx.x & 31u) == __ffs(peers) - 1) atomicAdd(&cnt[key], (unsigned long long)__popc(peers));
+}
+__global__ void slot_sort_kernel(SlotState from, SlotState to, unsigned long long* __restrict__ cnt) {
+  const unsigned long long n = from.live[1], nb = from.live[3];
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned lane = threadIdx.x & 31u;
+  const bool mine = (unsigned long long)i < n;
+  const int key = mine ? slot_bucket(from, i) : 4;
+  const unsigned peers = __match_any_sync(kFull, key);
+  const int leader = __ffs(peers) - 1;
+  unsigned long long base = 0;
+  if (mine && (int)lane == leader) base = atomicAdd(&cnt[4 + key], (unsigned long long)__popc(peers));
+  base = __shfl_sync(kFull, base, leader);
+  if (mine) {
+    unsigned long long off = 0;
+    for (int k = 0; k < key; ++k) off += cnt[k];
+    copy_slot(from, i, to, (int64_t)(off + base + __popc(peers & ((1u << lane) - 1u))));
+  }
+  if ((unsigned long long)i < nb) copy_slot(from, from.n_slots - 1 - i, to, to.n_slots - 1 - i);
+}
+
 }  // namespace
+
+cudaError_t launch_slot_presort(SlotState from, SlotState to, unsigned long long* cnt, cudaStream_t s) {
+  const unsigned grid = (unsigned)((from.n_slots + 255) / 256);
+  cudaMemsetAsync(cnt, 0, 8 * sizeof(unsigned long long), s);
+  slot_hist_kernel<<<grid, 256, 0, s>>>(from, cnt);
+  slot_sort_kernel<<<grid, 256, 0, s>>>(from, to, cnt);
+  return cudaGetLastError();
+}
 
 int shell_grid(int block, int blocks_per_sm, bool sliced) {
   int dev = 0, sms = 0, occ = 0;

@@ -80,7 +80,8 @@ class ForestSpec(C.Structure):
 
 class ServerConfig(C.Structure):
     _fields_ = [("max_requests", C.c_int32), ("events_per_round", C.c_int32), ("n_slots", C.c_int64),
-                ("mem_budget_bytes", C.c_uint64), ("block_size", C.c_int32), ("priority", C.c_int32)]
+                ("mem_budget_bytes", C.c_uint64), ("block_size", C.c_int32), ("priority", C.c_int32),
+                ("presort", C.c_int32), ("reserved", C.c_int32)]
 
 
 _lib = None
@@ -477,10 +478,11 @@ class Context:
         return out
 
     def server(self, *, max_requests=256, events_per_round=256, n_slots=0, mem_budget_bytes=0, block_size=0,
-               priority=True):
-        """thor_server_create; priority: age priority (the oldest requests' packets one per warp)."""
+               priority=True, presort=True):
+        """thor_server_create; priority: age priority (the oldest requests' packets one per warp);
+        presort: frequency pre-sorting of the packets in flight between rounds."""
         return Server(self, ServerConfig(max_requests, events_per_round, n_slots, mem_budget_bytes, block_size,
-                                         0 if priority else -1))
+                                         0 if priority else -1, 0 if presort else -1, 0))
 
 
 class Geometry:

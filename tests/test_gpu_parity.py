@@ -615,6 +615,27 @@ def test_server_mixed_equals_alone(ctx):
         assert np.array_equal(one.spectrum, m.spectrum) and one.stats["n_scat"] == m.stats["n_scat"]
 
 
+def test_server_presort_and_priority_do_not_change_results(ctx):
+    """Pre-sorting the packets in flight by frequency between rounds, and age priority, change
+    only which warp and lane run a packet: every request's spectrum and tallies are
+    bit-identical with both on, both off and each alone."""
+    reqs = [dict(N_HI=3e19, T=1e4, v_max=150.0, tau_dust=0.5, n_photons=4000, seed=31),
+            dict(N_HI=1e18, T=3e4, v_max=50.0, tau_dust=0.2, n_photons=9000, seed=32),
+            dict(N_HI=5e17, T=2e3, v_max=400.0, tau_dust=1.0, n_photons=2500, seed=33)]
+    common = dict(R_in=0.9, phase="dipole", sigma=50.0, n_bins=128, X_min=-1500.0, X_max=1500.0)
+    out = []
+    for presort, priority in ((True, True), (False, False), (True, False), (False, True)):
+        srv = ctx.server(max_requests=8, events_per_round=48, presort=presort, priority=priority)
+        tickets = [srv.submit(**r, **common) for r in reqs]
+        out.append([srv.wait(t, timeout_ms=120000) for t in tickets])
+        srv.close()
+    for res in out[1:]:
+        for a, b in zip(out[0], res):
+            assert np.array_equal(a.spectrum, b.spectrum)
+            for k in ("n_escaped", "n_absorbed", "n_scat", "n_dust_scat", "n_upar_iters"):
+                assert a.stats[k] == b.stats[k], k
+
+
 def test_server_priority_with_a_full_slot_list(ctx):
     """A small server (2048 packet slots, 64 warps) under a burst: the oldest request is
     small enough for priority (its packets one per warp) while the younger ones fill every
