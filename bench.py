@@ -475,6 +475,8 @@ def run_grid_bench(args):
     t_build = time.perf_counter() - t0
     kw = dict(n_bins=256, X_min=-1000.0, X_max=1000.0, peel=True, img_n=128, peel_bins=256, peel_X_min=-1000.0,
               peel_X_max=1000.0, device_out=True, max_scat=args.grid_max_scat)
+    if args.grid_slots:
+        ctx.set_grid_exec(args.grid_slots, args.grid_handoff if args.grid_handoff >= 0 else args.grid_slots // 8)
     ctx.run(g, n_photons=max(256, args.grid_photons // 16), seed=4, first_id=10 ** 9, **kw)
     ms, scat, steps, rays, cells = [], 0, 0, 0, 0
     with ClockSampler(0) as clk:
@@ -491,7 +493,9 @@ def run_grid_bench(args):
                       "n_gpus": 1, "steps": args.steps, "ms_per_step": 1000 * t / args.steps,
                       "higher_is_better": True, "dtype": "f32", "data": "synthetic",
                       "config": {"workload": f"256^3 grid, {args.grid_photons} photons per step (subset of 1e7)",
-                                 "max_scat": args.grid_max_scat, "grid_build_s": t_build},
+                                 "max_scat": args.grid_max_scat, "grid_build_s": t_build,
+                                 "execution": (f"event-based, {args.grid_slots} slots" if args.grid_slots
+                                               else "one kernel")},
                       "cell_steps_per_s": steps / t, "peel_rays_per_s": rays / t, "peel_cells_per_s": cells / t,
                       # 32 B per cell step and per peel cell, whether the record comes from memory or,
                       # for the photon's current cell, from registers
@@ -642,6 +646,10 @@ def main():
                     help="first photon id of the probe (-1: the longest photon of the first 1e5, shell model)")
     ap.add_argument("--probe-max-scat", type=int, default=0)
     ap.add_argument("--grid-photons", type=int, default=20000)
+    ap.add_argument("--grid-slots", type=int, default=0,
+                    help="grid workload: event-based loop with this many packets in flight (0 = one kernel)")
+    ap.add_argument("--grid-handoff", type=int, default=-1,
+                    help="grid workload: packets left when the event-based loop hands over (default slots/8)")
     ap.add_argument("--grid-max-scat", type=int, default=0,
                     help="stop grid photons after this many scatterings (0 = never; for short profiling runs)")
     ap.add_argument("--stream-requests", type=int, default=256)

@@ -88,14 +88,27 @@ int thor_ctx_set_tail(thor_ctx_t ctx, int spill_below, int max_phases);
 /* Pipelined events of the gridless photon loop on homologous shells.  In warps with at
  * most pipe_lanes live packets (0..32; 0 = never; default 32) each event first tries its
  * line-core form (start-point step inside the safety ball, resonant scattering at |x| <= 2,
- * first u_par trial accepted), with the next event's random words, its optical depth and
+ * u_par sample accepted within two trials), with the next event's random words, its optical depth and
  * the outgoing direction formed beside the frequency chain, and runs the general event
  * from the same words otherwise.  In warps with at most burst_lanes live packets (0..32;
- * default 4; only where events are pipelined) a packet runs up to 32 core events back to
- * back in one tight loop, for the lone lanes of a run's tail.  Both forms evaluate an event
+ * default 1; only where events are pipelined) a packet runs up to 32 core events back to
+ * back in one tight loop, for the lone lanes of a run's tail; with at most 10 such packets
+ * the warp's other lanes form their next events' random words ahead (cooperative burst).  Both forms evaluate an event
  * exactly as the general event does, so results do not depend on these settings (only the
  * time to reach them does). */
 int thor_ctx_set_bursts(thor_ctx_t ctx, int pipe_lanes, int burst_lanes);
+/* Event-based execution of the grid photon loop (the propagate / interact split that
+ * Sec. 7.2.2 proposes against divergence).  With slots > 0, thor_run on a grid keeps up to
+ * `slots` packets in device memory and advances all of them one event per round, in three
+ * kernels: the move to the interaction site (with emission into free slots, dust
+ * interactions and escapes), the resonant scatterings of the packets that reached one,
+ * and the peel-off rays that leave their first cell.  Once no new photons are left and at
+ * most `handoff` packets remain in flight (the run's tail, where rounds would hold few
+ * packets each), the survivors finish in the one-kernel loop.  slots = 0 (the default)
+ * runs the one-kernel loop throughout.  slots in [0, 2^26], handoff in [0, slots].  Photon
+ * histories, spectra, counters and per-photon records are identical either way; peel-off
+ * images agree up to the order of their floating-point sums. */
+int thor_ctx_set_grid_exec(thor_ctx_t ctx, int64_t slots, int64_t handoff);
 
 /* ---- geometries (Sec. 3.3 datasets) ----------------------------------------------- */
 

@@ -20,6 +20,11 @@ ROOT = os.path.dirname(PKG)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr", "-Xptxas", "-v"]
+# Per-file flags.  The grid photon loop runs the same event code in one kernel or split over
+# three (the event-based loop), and the two must give bit-identical histories: without
+# contraction every multiply and add rounds on its own, whatever the surrounding code lets
+# the compiler fuse (the hot expressions use explicit fused multiply-adds instead).
+FILE_FLAGS = {"thor_grid.cu": ["-fmad=false"]}
 
 
 def nvcc() -> str:
@@ -35,7 +40,7 @@ def sources():
 
 def _deps():
     return sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + \
-        [os.path.join(ROOT, "include", "thor.h")]
+        [os.path.join(ROOT, "include", "thor.h"), os.path.abspath(__file__)]
 
 
 def up_to_date() -> bool:
@@ -53,7 +58,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src).replace(".cu", ".o"))
-        cmd = [cc, *ARCH, *FLAGS, "-I", os.path.join(ROOT, "include"), "-c", src, "-o", obj]
+        extra = FILE_FLAGS.get(os.path.basename(src), [])
+        cmd = [cc, *ARCH, *FLAGS, *extra, "-I", os.path.join(ROOT, "include"), "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {os.path.basename(src)}:\n{r.stderr}")

@@ -50,7 +50,7 @@ void* thor_ctx::scratch(Buf& b, size_t bytes) {
 thor_ctx::~thor_ctx() {
   cudaSetDevice(device);
   for (Buf* b : {&b_models, &b_tally, &b_queue, &b_spec, &b_cube, &b_raw, &b_raw2, &b_diag, &b_stats, &b_spill, &b_cmp,
-                 &b_stage[0], &b_stage[1]})
+                 &b_stage[0], &b_stage[1], &b_gslots})
     if (b->p) cudaFree(b->p);
   for (cudaEvent_t e : {ev_copied[0], ev_copied[1], ev_done[0], ev_done[1]})
     if (e) cudaEventDestroy(e);
@@ -121,6 +121,15 @@ extern "C" int thor_ctx_set_bursts(thor_ctx_t ctx, int pipe_lanes, int burst_lan
     return ctx->fail(THOR_ERR_INVALID_ARG, "thor_ctx_set_bursts: pipe_lanes and burst_lanes in [0, 32]");
   ctx->core_lanes = pipe_lanes;
   ctx->burst_lanes = burst_lanes;
+  return THOR_OK;
+}
+
+extern "C" int thor_ctx_set_grid_exec(thor_ctx_t ctx, int64_t slots, int64_t handoff) {
+  if (!ctx) return THOR_ERR_INVALID_ARG;
+  if (slots < 0 || slots > ((int64_t)1 << 26) || handoff < 0 || handoff > slots)
+    return ctx->fail(THOR_ERR_INVALID_ARG, "thor_ctx_set_grid_exec: slots in [0, 2^26], handoff in [0, slots]");
+  ctx->grid_slots = slots;
+  ctx->grid_handoff = handoff;
   return THOR_OK;
 }
 
@@ -458,6 +467,54 @@ void thor::tally_to_result(const Tally& t, uint64_t n_photons, thor_result* r) {
   r->n_steps = t.n_steps; r->sum_scat2 = t.sum_scat2;
 }
 
+// Event-based grid loop (thor_ctx_set_grid_exec): rounds of (move, resonant scatterings,
+// peel rays) over the slots until no new photons are left and at most grid_handoff packets
+// remain, then the one-kernel loop finishes them.  The host checks the counters every
+// kCheck rounds (one small copy and a sync); between checks rounds are queued back to back.
+template <class PerWarp>
+static int run_grid_events(thor_ctx* ctx, thor::GridModel m, thor::WorkQueue q, int gsz,
+                           PerWarp per_warp, unsigned long long* n_launch) {
+  using namespace thor;
+  constexpr int kCheck = 8;
+  cudaStream_t s = ctx->stream;
+  const int64_t n = ctx->grid_slots;
+  void* base = ctx->scratch(ctx->b_gslots, grid_slots_bytes(n));
+  if (!base) return ctx->fail(THOR_ERR_OOM, "event-based grid loop: %lld slots", (long long)n);
+  GridSlots S = grid_slots_carve(base, n);
+  int rc;
+  if ((rc = ctx->cuda(cudaMemsetAsync(S.live, 0, (size_t)n, s), "clear slots"))) return rc;
+  if ((rc = ctx->cuda(cudaMemsetAsync(S.ctr, 0, 16 * 8, s), "clear slot counters"))) return rc;
+  if ((rc = ctx->cuda(cudaMemsetAsync(S.slab, 0, (size_t)kGridSlabBlocks * sizeof(TallySlab), s), "clear slab")))
+    return rc;
+  cudaEventRecord(ctx->ev0, s);
+  int64_t r = 0;
+  unsigned long long h[2] = {0, 0};  // packets in flight, photons taken from the queue
+  for (;;) {
+    for (int k = 0; k < kCheck; ++k, ++r) {
+      if ((rc = ctx->cuda(launch_grid_round(m, q, S, (int)(r & 1), ctx->d_ktab, ctx->block, s), "grid round")))
+        return rc;
+      *n_launch += 3;
+    }
+    if ((rc = ctx->cuda(cudaMemcpyAsync(&h[0], S.ctr, 8, cudaMemcpyDeviceToHost, s), "slot counters"))) return rc;
+    if ((rc = ctx->cuda(cudaMemcpyAsync(&h[1], q.next, 8, cudaMemcpyDeviceToHost, s), "queue counter"))) return rc;
+    if ((rc = ctx->cuda(cudaStreamSynchronize(s), "grid rounds"))) return rc;
+    if (h[1] >= q.total && (long long)h[0] <= ctx->grid_handoff) break;
+  }
+  ctx->grid_rounds_last = r;
+  if ((rc = ctx->cuda(launch_grid_slab_sum(m, S, s), "round counters"))) return rc;
+  ++*n_launch;
+  if (h[0] > 0) {  // the tail: the one-kernel loop resumes the packets in flight
+    if ((rc = ctx->cuda(cudaMemsetAsync(S.ctr + 2, 0, 16, s), "clear resume list"))) return rc;
+    if ((rc = ctx->cuda(launch_grid_list_live(S, s), "list packets in flight"))) return rc;
+    m.per_warp = per_warp(h[0]);
+    if ((rc = ctx->cuda(launch_grid_resume(m, q, S, ctx->d_ktab, gsz, ctx->block, s), "grid photon loop (tail)")))
+      return rc;
+    *n_launch += 2;
+  }
+  cudaEventRecord(ctx->ev1, s);
+  return THOR_OK;
+}
+
 extern "C" int thor_run(thor_ctx_t ctx, thor_geom_t g, const thor_source* src, uint64_t first_id, uint64_t n_photons,
                         uint64_t seed, const thor_output_spec* spec, thor_result* out) {
   if (!ctx || !g || !src || !out) return ctx ? ctx->fail(THOR_ERR_INVALID_ARG, "thor_run: NULL argument") : THOR_ERR_INVALID_ARG;
@@ -610,12 +667,20 @@ extern "C" int thor_run(thor_ctx_t ctx, thor_geom_t g, const thor_source* src, u
     const int gsz = grid_grid(ctx->block, ctx->blocks_per_sm);
     // few photons: spread them so that each runs in a warp of its own where possible
     const unsigned long long warps = (unsigned long long)gsz * (ctx->block / 32);
-    const unsigned long long pw = (n_photons + warps - 1) / warps;
-    m.per_warp = (int)(pw < 1 ? 1 : (pw > 32 ? 32 : pw));
-    cudaEventRecord(ctx->ev0, s);
-    rc = ctx->cuda(launch_grid_run(m, q, ctx->d_ktab, gsz, ctx->block, s), "grid photon loop");
-    ++n_launch;
-    cudaEventRecord(ctx->ev1, s);
+    auto per_warp = [&](unsigned long long n) {
+      const unsigned long long pw = (n + warps - 1) / warps;
+      return (int)(pw < 1 ? 1 : (pw > 32 ? 32 : pw));
+    };
+    m.per_warp = per_warp(n_photons);
+    ctx->grid_rounds_last = 0;
+    if (ctx->grid_slots <= 0) {
+      cudaEventRecord(ctx->ev0, s);
+      rc = ctx->cuda(launch_grid_run(m, q, ctx->d_ktab, gsz, ctx->block, s), "grid photon loop");
+      ++n_launch;
+      cudaEventRecord(ctx->ev1, s);
+    } else {
+      rc = run_grid_events(ctx, m, q, gsz, per_warp, &n_launch);
+    }
   }
   if (rc) return rc;
   Tally t;

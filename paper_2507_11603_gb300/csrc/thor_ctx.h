@@ -33,7 +33,12 @@ struct thor_ctx {
   int max_phases = 24;      // launches at most
   int final_below = 256;    // run to completion once this few packets are left
   int core_lanes = 32;      // warps with at most this many live packets run pipelined events (0 = never)
-  int burst_lanes = 4;      // ... and, with at most this many, core bursts (0 = never)
+  int burst_lanes = 1;      // ... and, with at most this many, core bursts (0 = never)
+  // event-based grid loop (0 slots = the one-kernel loop throughout)
+  int64_t grid_slots = 0;
+  int64_t grid_handoff = 0;  // packets in flight at which the tail goes to the one-kernel loop
+  Buf b_gslots;
+  int64_t grid_rounds_last = 0;
   int phases_last = 0;
 
   int fail(int code, const char* fmt, ...);

@@ -252,11 +252,12 @@ __device__ __forceinline__ float xcw_b25(float a) {
 // takes over (sample_upar_wing).
 // ------------------------------------------------------------------------------
 // atan2(a, d) for a, d >= 0: series when a/d <= 1/20 (relative error < 3e-9), else atan2f.
+__device__ __forceinline__ float atan2_series(float a, float d) {  // for a <= d / 20
+  const float t = __fdividef(a, d), t2 = __fmul_rn(t, t);
+  return __fmul_rn(t, __fmaf_rn(t2, __fmaf_rn(t2, 0.2f, -1.0f / 3.0f), 1.0f));
+}
 __device__ __forceinline__ float atan2_pos(float a, float d) {
-  if (a <= 0.05f * d) {
-    const float t = __fdividef(a, d), t2 = t * t;
-    return t * __fmaf_rn(t2, __fmaf_rn(t2, 0.2f, -1.0f / 3.0f), 1.0f);
-  }
+  if (a <= 0.05f * d) return atan2_series(a, d);
   return atan2f(a, d);
 }
 
@@ -318,6 +319,20 @@ __device__ __forceinline__ float cot_pi(float t) {
   __sincosf(z, &sn, &cs);
   const float trig = cs * rcp_approx(sn);
   return (fabsf(z) <= 0.25f) ? laurent : trig;  // both formed: a select instead of a branch
+}
+
+// One trial of the two-piece comparison function (R1: region, R2: angle, R3: acceptance):
+// u = x - a cot(alpha) with alpha uniform on the region's part of (0, pi); accepted with
+// e^{-u^2} in region 1 (u <= u0), e^{u0^2 - u^2} in region 2.  Every operation is an explicit
+// intrinsic, so the photon loops' core form rounds exactly as this sampler does.
+__device__ __forceinline__ bool upar_trial(float xr, float a, float w1, float w1p, float mass, float u02,
+                                           float R1, float R2, float R3, float& u) {
+  const bool reg1 = region1(R1, mass, w1);
+  const float t = reg1 ? __fmul_rn(w1p, R2) : __fmaf_rn(__fsub_rn(1.0f, w1p), R2, w1p);
+  u = __fmaf_rn(-a, cot_pi(t), xr);  // x - a cot(alpha)
+  const float uu = __fmul_rn(u, u);
+  const float acc = reg1 ? exp_fast(-uu) : exp_fast(__fsub_rn(u02, uu));
+  return R3 <= acc;
 }
 
 // Iteration 0 takes words 1-3 of the event, iteration i >= 1 words 0-2 of block i + 2.
@@ -430,16 +445,10 @@ __device__ __forceinline__ float sample_upar(float x, float a, const Rng& rng, u
   const float u02 = __fmul_rn(u0, u0);
   const float e0 = exp_fast(-u02);
   const float mass = envelope_mass(w1, e0);
-  const float w1p = w1 * (1.0f / kPiF);  // alpha in units of pi
+  const float w1p = __fmul_rn(w1, 1.0f / kPiF);  // alpha in units of pi
   auto trial = [&](uint32_t r1, uint32_t r2, uint32_t r3, float& u) {
-    const float R1 = uni32(r1), R2 = uni32(r2), R3 = uni32(r3);
-    const bool reg1 = region1(R1, mass, w1);
-    const float t = reg1 ? w1p * R2 : __fmaf_rn(1.0f - w1p, R2, w1p);
-    u = __fmaf_rn(-a, cot_pi(t), xr);  // x - a cot(alpha)
-    const float uu = __fmul_rn(u, u);
-    const float acc = reg1 ? exp_fast(-uu) : exp_fast(u02 - uu);
     ++iters;
-    return R3 <= acc;
+    return upar_trial(xr, a, w1, w1p, mass, u02, uni32(r1), uni32(r2), uni32(r3), u);
   };
   float u;
   if (!trial(rng.v[W_UPAR0], rng.v[W_UPAR0 + 1], rng.v[W_UPAR0 + 2], u)) {

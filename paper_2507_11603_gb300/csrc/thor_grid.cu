@@ -143,6 +143,11 @@ __device__ __forceinline__ GridCell load_cell(const GridCell* __restrict__ cells
   return g;
 }
 
+// Gas velocity along the direction, v . k (one rounding per fused step).
+__device__ __forceinline__ float v_dot_k(const GridCell& g, float3 k) {
+  return __fmaf_rn(g.vx, k.x, __fmaf_rn(g.vy, k.y, __fmul_rn(g.vz, k.z)));
+}
+
 __device__ __forceinline__ int64_t cell_index(const GridModel& m, int ix, int iy, int iz) {
   return (int64_t)ix + (int64_t)m.nx * ((int64_t)iy + (int64_t)m.ny * iz);
 }
@@ -218,7 +223,7 @@ __device__ void grid_emit(const GridModel& m, GPhoton& ph, const float* Ktab, ui
   const float R1 = ph.rng.u(6), R2 = ph.rng.u(7);
   const float xe = sqrtf(-__logf(R1)) * cospif(2.0f * R2);
   const GridCell g = load_cell(m.cells, c);
-  ph.X = __fmaf_rn(xe, g.vth, g.vx * ph.k.x + g.vy * ph.k.y + g.vz * ph.k.z);
+  ph.X = __fmaf_rn(xe, g.vth, v_dot_k(g, ph.k));
   ph.nscat = 0; ph.ndust = 0; ph.iters = 0; ph.steps = 0;
   if (m.peel) {
     const float vv[3] = {g.vx, g.vy, g.vz};
@@ -235,8 +240,20 @@ __device__ void grid_emit(const GridModel& m, GPhoton& ph, const float* Ktab, ui
 // Peel-off from the current position towards +axis (Sec. 3.4.1): the first segment runs
 // through the current cell, whose record is known (no load); only a ray that leaves it
 // with tau <= tau_cut walks on.  Weights below e^-tau_cut are not deposited.
+// The rest of such a ray (beyond the current cell) goes to `walk`: traced on the spot in the
+// one-kernel loop (WalkHere), or queued for the ray kernel in the event-based loop.
+struct WalkHere {
+  const GridModel& m;
+  const float* Ktab;
+  uint32_t& pc;
+  __device__ __forceinline__ void operator()(const double p[3], int ax, float Xp, float w0, float tau) const {
+    tau = peel_tau_from(m, p, ax, Xp, Ktab, pc, 1, tau);
+    if (tau <= m.tau_cut) deposit(m, p, ax, Xp, w0 * __expf(-tau));
+  }
+};
+template <class Walk>
 __device__ __forceinline__ void peel_from_cell(const GridModel& m, const GPhoton& ph, int ax, float Xp, float w0,
-                                               const float* Ktab, uint32_t& pr, uint32_t& pc) {
+                                               const float* Ktab, uint32_t& pr, uint32_t& pc, const Walk& walk) {
   const GridCell& g = ph.gc;
   const float v = (ax == 0) ? g.vx : (ax == 1) ? g.vy : g.vz;
   const float x = (Xp - v) * g.inv_vth;
@@ -246,24 +263,30 @@ __device__ __forceinline__ void peel_from_cell(const GridModel& m, const GPhoton
   ++pc;
   if (tau > m.tau_cut) return;  // blocked inside the current cell: no FP64, no gather
   const double p[3] = {ph.p[0] + (double)ph.o[0], ph.p[1] + (double)ph.o[1], ph.p[2] + (double)ph.o[2]};
-  tau = peel_tau_from(m, p, ax, Xp, Ktab, pc, 1, tau);
-  if (tau <= m.tau_cut) deposit(m, p, ax, Xp, w0 * __expf(-tau));
+  walk(p, ax, Xp, w0, tau);
 }
 
-// One event; returns 0 continue, 1 escaped, 2 absorbed, 3 capped.
+// An event is two halves: grid_move, then grid_interact.  grid_event runs them in sequence;
+// the event-based loop runs them in separate kernels, with the packet in memory between them
+// (bit-identical histories).
+//
+// The propagation half: the event's words, then the move to the interaction site.  Returns
+// 1 if the packet left the box, else 0 with x (gas-frame frequency at the site) and kH
+// (HI opacity there) set, and the packet's cell record in ph.gc.
 // Fast path: while the photon is known to be inside a cell (safe > 0) and the sampled
 // interaction lies within the safety distance, the event needs neither the cell walk nor
 // any FP64 arithmetic (the common case for photons trapped in optically thick cells).
 // Otherwise the cell walk runs from the current position (FP64, the bit-reproducible
 // contract of Dda) and re-establishes the cell frame at the interaction point.
-__device__ int grid_event(const GridModel& m, GPhoton& ph, const float* Ktab, uint32_t& pr, uint32_t& pc) {
+__device__ __forceinline__ int grid_move(const GridModel& m, GPhoton& ph, const float* Ktab, float& x_out,
+                                         float& kH_out) {
   ph.rng.next_event(3u);
   float tau_rem = -__logf(ph.rng.u(W_TAU));
   float x = 0.0f, kH = 0.0f;
   bool fast = false;
   if (ph.safe > 0.0f) {
     const GridCell& g = ph.gc;
-    x = (ph.X - (g.vx * ph.k.x + g.vy * ph.k.y + g.vz * ph.k.z)) * g.inv_vth;
+    x = (ph.X - v_dot_k(g, ph.k)) * g.inv_vth;
     kH = g.kap0 * voigt<false>(g.a, x, Ktab);
     const float kt = kH + g.kd;
     const float sdist = __fdividef(tau_rem, kt);
@@ -286,7 +309,7 @@ __device__ int grid_event(const GridModel& m, GPhoton& ph, const float* Ktab, ui
       double tn;
       const int ax = w.next_axis(tn);
       g = load_cell(m.cells, cell_index(m, w.i[0], w.i[1], w.i[2]));
-      x = (ph.X - (g.vx * ph.k.x + g.vy * ph.k.y + g.vz * ph.k.z)) * g.inv_vth;
+      x = (ph.X - v_dot_k(g, ph.k)) * g.inv_vth;
       kH = g.kap0 * voigt<false>(g.a, x, Ktab);
       const float kt = kH + g.kd;
       const float dt = (float)(tn - w.t);
@@ -308,30 +331,49 @@ __device__ int grid_event(const GridModel& m, GPhoton& ph, const float* Ktab, ui
     ph.gc = g;
     g_cell_frame(ph, w.i);
   }
+  x_out = x;
+  kH_out = kH;
+  return 0;
+}
+
+// The interaction channel at the site (Sec. 3.4): dust with probability kd / (kH + kd).
+__device__ __forceinline__ bool grid_dust_channel(const GPhoton& ph, float kH) {
+  const GridCell& g = ph.gc;
+  return g.kd > 0.0f && ph.rng.u(W_CHANNEL) >= __fdividef(kH, kH + g.kd);
+}
+// A dust interaction: absorbed with probability 1 - albedo (returns 2), else scattered by the
+// Henyey-Greenstein phase function (Eq. 8-9) with its peel-off (returns 0).
+template <class Walk>
+__device__ __forceinline__ int grid_dust(const GridModel& m, GPhoton& ph, const float* Ktab, uint32_t& pr,
+                                         uint32_t& pc, const Walk& walk) {
   const GridCell& g = ph.gc;
   const float vv[3] = {g.vx, g.vy, g.vz};
-  const float vk_in = g.vx * ph.k.x + g.vy * ph.k.y + g.vz * ph.k.z;
-  bool dust = false;
-  if (g.kd > 0.0f) dust = ph.rng.u(W_CHANNEL) >= __fdividef(kH, kH + g.kd);
-  if (dust) {
-    bool scat;
-    if (m.albedo <= 0.0f) scat = false;
-    else if (m.albedo >= 1.0f) scat = true;
-    else scat = ph.rng.u(W_ALBEDO) < m.albedo;
-    if (!scat) return 2;
-    if (m.peel) {
-      const float kin[3] = {ph.k.x, ph.k.y, ph.k.z};
+  const float vk_in = v_dot_k(g, ph.k);
+  bool scat;
+  if (m.albedo <= 0.0f) scat = false;
+  else if (m.albedo >= 1.0f) scat = true;
+  else scat = ph.rng.u(W_ALBEDO) < m.albedo;
+  if (!scat) return 2;
+  if (m.peel) {
+    const float kin[3] = {ph.k.x, ph.k.y, ph.k.z};
 #pragma unroll
-      for (int ax = 0; ax < 3; ++ax) {
-        const float Xp = ph.X + vv[ax] - vk_in;
-        peel_from_cell(m, ph, ax, Xp, P_hg(kin[ax], m.g_hg) * (0.5f / kPiF), Ktab, pr, pc);
-      }
+    for (int ax = 0; ax < 3; ++ax) {
+      const float Xp = ph.X + vv[ax] - vk_in;
+      peel_from_cell(m, ph, ax, Xp, P_hg(kin[ax], m.g_hg) * (0.5f / kPiF), Ktab, pr, pc, walk);
     }
-    scatter_dust(m.g_hg, ph.k, ph.rng);
-    ph.X += (g.vx * ph.k.x + g.vy * ph.k.y + g.vz * ph.k.z) - vk_in;
-    ++ph.ndust;
-    return 0;
   }
+  scatter_dust(m.g_hg, ph.k, ph.rng);
+  ph.X += v_dot_k(g, ph.k) - vk_in;
+  ++ph.ndust;
+  return 0;
+}
+// A resonant scattering at gas-frame frequency x (Eq. 5-7) with its peel-off.  Returns 3
+// if it reached the scattering cap, else 0.
+template <class Walk>
+__device__ __forceinline__ int grid_resonant(const GridModel& m, GPhoton& ph, float x, const float* Ktab,
+                                             uint32_t& pr, uint32_t& pc, const Walk& walk) {
+  const GridCell& g = ph.gc;
+  const float vv[3] = {g.vx, g.vy, g.vz};
   const float kin[3] = {ph.k.x, ph.k.y, ph.k.z};
   AtomFrame af;
   const float xo = scatter_resonant(x, g.a, m.phase, ph.k, ph.rng, ph.iters, &af);
@@ -346,13 +388,99 @@ __device__ int grid_event(const GridModel& m, GPhoton& ph, const float* Ktab, ui
       if (m.phase == PH_ISO) P = 0.5f;
       else if (m.phase == PH_DIPOLE) P = P_dipole(mu);
       else P = af.core ? (0.5f / 3.0f + 2.0f * P_dipole(mu) / 3.0f) : P_dipole(mu);
-      peel_from_cell(m, ph, ax, Xp, P * (0.5f / kPiF), Ktab, pr, pc);
+      peel_from_cell(m, ph, ax, Xp, P * (0.5f / kPiF), Ktab, pr, pc, walk);
     }
   }
-  ph.X = __fmaf_rn(xo, g.vth, g.vx * ph.k.x + g.vy * ph.k.y + g.vz * ph.k.z);
+  ph.X = __fmaf_rn(xo, g.vth, v_dot_k(g, ph.k));
   ++ph.nscat;
   if (m.max_scat && ph.nscat >= m.max_scat) return 3;
   return 0;
+}
+
+// The interaction half, from the words of the current event: channel, then dust or
+// resonant scattering, each with its peel-off (Sec. 3.4.1).  Returns 0 continue,
+// 2 absorbed, 3 capped.
+template <class Walk>
+__device__ __forceinline__ int grid_interact(const GridModel& m, GPhoton& ph, float x, float kH, const float* Ktab,
+                                             uint32_t& pr, uint32_t& pc, const Walk& walk) {
+  if (grid_dust_channel(ph, kH)) return grid_dust(m, ph, Ktab, pr, pc, walk);
+  return grid_resonant(m, ph, x, Ktab, pr, pc, walk);
+}
+
+// One event; returns 0 continue, 1 escaped, 2 absorbed, 3 capped.
+__device__ int grid_event(const GridModel& m, GPhoton& ph, const float* Ktab, uint32_t& pr, uint32_t& pc) {
+  float x, kH;
+  if (grid_move(m, ph, Ktab, x, kH)) return 1;
+  return grid_interact(m, ph, x, kH, Ktab, pr, pc, WalkHere{m, Ktab, pc});
+}
+
+// ---- event-based loop: packets in device memory between its kernels -----------------
+// A packet's state in its slot.  The cell record is not stored: it is re-read from the
+// cell under the anchor (the anchor lies in the packet's cell whenever the record is used).
+__device__ __forceinline__ void slot_save(const GridSlots& S, int64_t i, const GPhoton& ph) {
+  S.px[i] = ph.p[0]; S.py[i] = ph.p[1]; S.pz[i] = ph.p[2];
+  S.ox[i] = ph.o[0]; S.oy[i] = ph.o[1]; S.oz[i] = ph.o[2];
+  S.fx[i] = ph.fhi[0]; S.fy[i] = ph.fhi[1]; S.fz[i] = ph.fhi[2];
+  S.safe[i] = ph.safe;
+  S.kx[i] = ph.k.x; S.ky[i] = ph.k.y; S.kz[i] = ph.k.z; S.X[i] = ph.X;
+  S.nscat[i] = ph.nscat; S.ndust[i] = ph.ndust; S.iters[i] = ph.iters; S.steps[i] = ph.steps;
+  S.event[i] = ph.rng.event;
+  S.pid[i] = ph.pid;
+}
+// with_cell: re-read the cell record (always for the interaction half; for the move only
+// where the fast path may use it, safe > 0)
+__device__ __forceinline__ void slot_load(const GridModel& m, const GridSlots& S, int64_t i, GPhoton& ph,
+                                          bool with_cell) {
+  ph.p[0] = S.px[i]; ph.p[1] = S.py[i]; ph.p[2] = S.pz[i];
+  ph.o[0] = S.ox[i]; ph.o[1] = S.oy[i]; ph.o[2] = S.oz[i];
+  ph.fhi[0] = S.fx[i]; ph.fhi[1] = S.fy[i]; ph.fhi[2] = S.fz[i];
+  ph.safe = S.safe[i];
+  ph.k = make_float3(S.kx[i], S.ky[i], S.kz[i]);
+  ph.X = S.X[i];
+  ph.nscat = S.nscat[i]; ph.ndust = S.ndust[i]; ph.iters = S.iters[i]; ph.steps = S.steps[i];
+  ph.pid = S.pid[i];
+  ph.rng.keys(((uint64_t)m.seed_hi << 32) | m.seed_lo, ph.pid);
+  ph.rng.event = S.event[i];
+  if (with_cell || ph.safe > 0.0f)
+    ph.gc = load_cell(m.cells, cell_index(m, (int)floor(ph.p[0]), (int)floor(ph.p[1]), (int)floor(ph.p[2])));
+}
+// Peel rays past their first cell go to the ray queue.
+struct WalkQueue {
+  PeelRay* rays;
+  unsigned long long* n;
+  __device__ __forceinline__ void operator()(const double p[3], int ax, float Xp, float w0, float tau) const {
+    const unsigned long long j = atomicAdd(n, 1ull);
+    PeelRay r;
+    r.px = p[0]; r.py = p[1]; r.pz = p[2];
+    r.Xp = Xp; r.w0 = w0; r.tau = tau; r.ax = ax;
+    rays[j] = r;
+  }
+};
+// Counters of finished packets, per lane, flushed once per warp.
+struct GTally {
+  unsigned long long esc = 0, ab = 0, cap = 0, sc = 0, du = 0, it = 0, stp = 0, dn = 0;
+  double sc2 = 0.0;
+  uint32_t pr = 0, pc = 0;
+};
+__device__ __forceinline__ void grid_finish(const GridModel& m, const GPhoton& ph, int st, GTally& t) {
+  if (st == 1) {
+    ++t.esc;
+    const float f = (ph.X - m.X_min) * m.inv_dX;
+    int bin = !(f >= 0.0f) ? m.n_bins : (f >= (float)m.n_bins ? m.n_bins + 1 : (int)f);
+    atomicAdd(&m.spectrum[bin], 1ull);
+  } else if (st == 2) {
+    ++t.ab;
+  } else {
+    ++t.cap;
+  }
+  if (m.raw_X) {
+    const unsigned long long j = ph.pid - m.id_base;
+    m.raw_X[j] = ph.X;
+    m.raw_nscat[j] = ph.nscat;
+    m.raw_status[j] = (uint8_t)st;
+  }
+  t.sc += ph.nscat; t.du += ph.ndust; t.it += ph.iters; t.stp += ph.steps; ++t.dn;
+  t.sc2 += (double)ph.nscat * (double)ph.nscat;
 }
 
 __device__ __forceinline__ unsigned long long wsum(unsigned long long v) {
@@ -366,17 +494,99 @@ __device__ __forceinline__ double wsum(double v) {
   return v;
 }
 
-__global__ void __launch_bounds__(256) grid_run_kernel(GridModel m, WorkQueue q, const float* __restrict__ gK) {
+// Flush per-lane counters: warp reduce, one atomic per warp and field.
+__device__ __forceinline__ void flush_tally(const GridModel& m, const GTally& t) {
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned long long esc = wsum(t.esc), ab = wsum(t.ab), cap = wsum(t.cap), sc = wsum(t.sc), du = wsum(t.du),
+                           it = wsum(t.it), stp = wsum(t.stp), dn = wsum(t.dn);
+  const double sc2 = wsum(t.sc2);
+  const unsigned long long prs = wsum((unsigned long long)t.pr), pcs = wsum((unsigned long long)t.pc);
+  if (lane == 0 && (dn || prs || pcs)) {
+    Tally* T = m.tally;
+    atomicAdd(&T->n_escaped, esc); atomicAdd(&T->n_absorbed, ab); atomicAdd(&T->n_capped, cap);
+    atomicAdd(&T->n_scat, sc); atomicAdd(&T->n_dust_scat, du); atomicAdd(&T->n_upar_iters, it);
+    atomicAdd(&T->n_steps, stp); atomicAdd(&T->n_done, dn); atomicAdd(&T->sum_scat2, sc2);
+    if (m.peel_rays) { atomicAdd(m.peel_rays, prs); atomicAdd(m.peel_cells, pcs); }
+  }
+}
+
+// The event-based loop's kernels run thousands of times per run: their counters go to the
+// block's own slab entry (warp and block reduction, then plain adds -- kernels of one stream
+// never overlap, so no two blocks with the same index run at once), summed once at the end.
+__device__ __forceinline__ void flush_slab(TallySlab* slab, const GTally& t) {
+  __shared__ unsigned long long sh[8][10];
+  __shared__ double sh2[8];
+  const unsigned lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+  const unsigned long long v[10] = {wsum(t.esc), wsum(t.ab), wsum(t.cap), wsum(t.sc), wsum(t.du), wsum(t.it),
+                                    wsum(t.stp), wsum(t.dn), wsum((unsigned long long)t.pr),
+                                    wsum((unsigned long long)t.pc)};
+  const double v2 = wsum(t.sc2);
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < 10; ++k) sh[w][k] = v[k];
+    sh2[w] = v2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long a[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    double a2 = 0.0;
+    for (unsigned j = 0; j < (blockDim.x >> 5); ++j) {
+#pragma unroll
+      for (int k = 0; k < 10; ++k) a[k] += sh[j][k];
+      a2 += sh2[j];
+    }
+    TallySlab& e = slab[blockIdx.x];
+    e.esc += a[0]; e.ab += a[1]; e.cap += a[2]; e.sc += a[3]; e.du += a[4]; e.it += a[5]; e.stp += a[6];
+    e.dn += a[7]; e.pr += a[8]; e.pc += a[9]; e.sc2 += a2;
+  }
+}
+
+__global__ void grid_slab_sum_kernel(GridModel m, GridSlots S) {
+  unsigned long long a[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  double a2 = 0.0;
+  for (int b = threadIdx.x; b < kGridSlabBlocks; b += blockDim.x) {
+    const TallySlab& e = S.slab[b];
+    a[0] += e.esc; a[1] += e.ab; a[2] += e.cap; a[3] += e.sc; a[4] += e.du; a[5] += e.it; a[6] += e.stp;
+    a[7] += e.dn; a[8] += e.pr; a[9] += e.pc; a2 += e.sc2;
+  }
+#pragma unroll
+  for (int k = 0; k < 10; ++k) a[k] = wsum(a[k]);
+  a2 = wsum(a2);
+  if ((threadIdx.x & 31u) == 0) {
+    Tally* T = m.tally;
+    atomicAdd(&T->n_escaped, a[0]); atomicAdd(&T->n_absorbed, a[1]); atomicAdd(&T->n_capped, a[2]);
+    atomicAdd(&T->n_scat, a[3]); atomicAdd(&T->n_dust_scat, a[4]); atomicAdd(&T->n_upar_iters, a[5]);
+    atomicAdd(&T->n_steps, a[6]); atomicAdd(&T->n_done, a[7]); atomicAdd(&T->sum_scat2, a2);
+    if (m.peel_rays) { atomicAdd(m.peel_rays, a[8]); atomicAdd(m.peel_cells, a[9]); }
+  }
+}
+
+// The one-kernel loop: persistent warps, one event per lane per iteration, idle lanes
+// refilled from the photon queue (warp-aggregated).  kResume: lanes first take the packets
+// on the resume list of S (the tail handed over by the event-based loop).
+template <bool kResume>
+__global__ void __launch_bounds__(256) grid_run_kernel(GridModel m, WorkQueue q, const float* __restrict__ gK,
+                                                       GridSlots S) {
   __shared__ __align__(16) float sK[THOR_VOIGT_NINT * THOR_VOIGT_NCOEF];
   load_ktab(sK, gK);
   const unsigned lane = threadIdx.x & 31u;
   GPhoton ph;
   bool active = false, done = (int)lane >= m.per_warp;
-  unsigned long long esc = 0, ab = 0, cap = 0, sc = 0, du = 0, it = 0, stp = 0, dn = 0;
-  double sc2 = 0.0;
-  uint32_t pr = 0, pc = 0;
+  GTally t;
   for (;;) {
-    const unsigned need = __ballot_sync(kFull, !active && !done);
+    unsigned need = __ballot_sync(kFull, !active && !done);
+    if (kResume && need) {
+      const unsigned long long n_res = S.ctr[2];
+      const int leader = __ffs(need) - 1;
+      unsigned long long base = 0;
+      if ((int)lane == leader) base = atomicAdd(&S.ctr[3], (unsigned long long)__popc(need));
+      base = __shfl_sync(kFull, base, leader);
+      if (!active && !done) {
+        const unsigned long long g = base + __popc(need & ((1u << lane) - 1u));
+        if (g < n_res) { slot_load(m, S, S.rq[g], ph, false); active = true; }
+      }
+      need = __ballot_sync(kFull, !active && !done);
+    }
     if (need) {
       const int leader = __ffs(need) - 1;
       unsigned long long base = 0;
@@ -386,7 +596,7 @@ __global__ void __launch_bounds__(256) grid_run_kernel(GridModel m, WorkQueue q,
         const unsigned long long g = base + __popc(need & ((1u << lane) - 1u));
         if (g < q.total) {
           ph.pid = q.first_id[0] + g;
-          grid_emit(m, ph, sK, pr, pc);
+          grid_emit(m, ph, sK, t.pr, t.pc);
           active = true;
         } else {
           done = true;
@@ -399,38 +609,156 @@ __global__ void __launch_bounds__(256) grid_run_kernel(GridModel m, WorkQueue q,
     do {
       fin = false;
       if (active) {
-        const int st = grid_event(m, ph, sK, pr, pc);
+        const int st = grid_event(m, ph, sK, t.pr, t.pc);
         if (st) {
-          if (st == 1) {
-            ++esc;
-            const float f = (ph.X - m.X_min) * m.inv_dX;
-            int bin = !(f >= 0.0f) ? m.n_bins : (f >= (float)m.n_bins ? m.n_bins + 1 : (int)f);
-            atomicAdd(&m.spectrum[bin], 1ull);
-          } else if (st == 2) ++ab;
-          else ++cap;
-          if (m.raw_X) {
-            const unsigned long long j = ph.pid - m.id_base;
-            m.raw_X[j] = ph.X;
-            m.raw_nscat[j] = ph.nscat;
-            m.raw_status[j] = (uint8_t)st;
-          }
-          sc += ph.nscat; du += ph.ndust; it += ph.iters; stp += ph.steps; ++dn;
-          sc2 += (double)ph.nscat * (double)ph.nscat;
+          grid_finish(m, ph, st, t);
           active = false;
           fin = true;
         }
       }
     } while (!__any_sync(kFull, fin));
   }
-  esc = wsum(esc); ab = wsum(ab); cap = wsum(cap); sc = wsum(sc); du = wsum(du); it = wsum(it);
-  stp = wsum(stp); dn = wsum(dn); sc2 = wsum(sc2);
-  const unsigned long long prs = wsum((unsigned long long)pr), pcs = wsum((unsigned long long)pc);
-  if (lane == 0 && (dn || prs)) {
-    Tally* T = m.tally;
-    atomicAdd(&T->n_escaped, esc); atomicAdd(&T->n_absorbed, ab); atomicAdd(&T->n_capped, cap);
-    atomicAdd(&T->n_scat, sc); atomicAdd(&T->n_dust_scat, du); atomicAdd(&T->n_upar_iters, it);
-    atomicAdd(&T->n_steps, stp); atomicAdd(&T->n_done, dn); atomicAdd(&T->sum_scat2, sc2);
-    if (m.peel_rays) { atomicAdd(m.peel_rays, prs); atomicAdd(m.peel_cells, pcs); }
+  flush_tally(m, t);
+}
+
+// ---- event-based loop (Sec. 7.2.2): one event per packet per round, three kernels ----
+// Round kernel 1: the move.  Free slots first take new photons (emission with its
+// peel-off); then every packet moves to its interaction site.  Escapes finish here; dust
+// interactions run here (rare, and their rays go to the ray queue); packets at a resonant
+// scattering are queued for kernel 2.  Also clears the other parity's queue counters for the
+// next round.
+__global__ void __launch_bounds__(256) grid_move_kernel(GridModel m, WorkQueue q, GridSlots S, int parity,
+                                                        const float* __restrict__ gK) {
+  __shared__ __align__(16) float sK[THOR_VOIGT_NINT * THOR_VOIGT_NCOEF];
+  load_ktab(sK, gK);
+  unsigned long long* cnt = S.ctr + 4 + 4 * parity;
+  if (blockIdx.x == 0 && threadIdx.x < 2) S.ctr[4 + 4 * (parity ^ 1) + threadIdx.x] = 0ull;
+  const unsigned lane = threadIdx.x & 31u;
+  const WalkQueue walk{S.rays, cnt + 1};
+  GTally t;
+  long long dlive = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < S.n; b0 += stride) {  // warp-uniform
+    const int64_t i = b0 + threadIdx.x;
+    const bool in = i < S.n;
+    bool live = in && S.live[i];
+    GPhoton ph;
+    if (live) slot_load(m, S, i, ph, false);
+    const unsigned need = __ballot_sync(kFull, in && !live);
+    if (need) {
+      const int leader = __ffs(need) - 1;
+      unsigned long long base = 0;
+      if ((int)lane == leader)  // once the queue is drained, free slots stop touching its counter
+        base = (*(volatile const unsigned long long*)q.next < q.total)
+                   ? atomicAdd(q.next, (unsigned long long)__popc(need)) : q.total;
+      base = __shfl_sync(kFull, base, leader);
+      if (in && !live) {
+        const unsigned long long g = base + __popc(need & ((1u << lane) - 1u));
+        if (g < q.total) {
+          ph.pid = q.first_id[0] + g;
+          grid_emit(m, ph, sK, t.pr, t.pc);
+          live = true;
+          ++dlive;
+        }
+      }
+    }
+    if (!live) continue;
+    float x, kH;
+    int st = grid_move(m, ph, sK, x, kH);
+    bool queued = false;
+    if (st == 0) {
+      if (grid_dust_channel(ph, kH)) {
+        st = grid_dust(m, ph, sK, t.pr, t.pc, walk);
+      } else {
+        queued = true;
+        S.xs[i] = x;
+      }
+    }
+    const unsigned qb = __ballot_sync(__activemask(), queued);
+    if (queued) {
+      const int leader = __ffs(qb) - 1;
+      unsigned long long base = 0;
+      if ((int)lane == leader) base = atomicAdd(cnt, (unsigned long long)__popc(qb));
+      base = __shfl_sync(qb, base, leader);
+      S.rq[base + __popc(qb & ((1u << lane) - 1u))] = (int32_t)i;
+    }
+    if (st) {
+      grid_finish(m, ph, st, t);
+      --dlive;
+      S.live[i] = 0;
+    } else {
+      S.live[i] = 1;
+      slot_save(S, i, ph);
+    }
+  }
+  flush_slab(S.slab, t);
+  const long long dl = (long long)wsum((unsigned long long)dlive);
+  if (lane == 0 && dl) atomicAdd(&S.ctr[0], (unsigned long long)dl);
+}
+
+// Round kernel 2: the resonant scatterings queued by kernel 1, from the words of the same
+// event (regenerated), with their peel-off; packets at the scattering cap finish.
+__global__ void __launch_bounds__(256) grid_scatter_kernel(GridModel m, GridSlots S, int parity,
+                                                           const float* __restrict__ gK) {
+  __shared__ __align__(16) float sK[THOR_VOIGT_NINT * THOR_VOIGT_NCOEF];
+  load_ktab(sK, gK);
+  const unsigned long long* cnt = S.ctr + 4 + 4 * parity;
+  const unsigned long long n = cnt[0];
+  const WalkQueue walk{S.rays, S.ctr + 5 + 4 * parity};
+  GTally t;
+  long long dlive = 0;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+    const int64_t i = S.rq[j];
+    GPhoton ph;
+    slot_load(m, S, i, ph, true);
+    ph.rng.start_event(ph.rng.event, 3u);
+    const int st = grid_resonant(m, ph, S.xs[i], sK, t.pr, t.pc, walk);
+    if (st) {
+      grid_finish(m, ph, st, t);
+      --dlive;
+      S.live[i] = 0;
+    } else {
+      S.kx[i] = ph.k.x; S.ky[i] = ph.k.y; S.kz[i] = ph.k.z; S.X[i] = ph.X;
+      S.nscat[i] = ph.nscat; S.iters[i] = ph.iters;
+    }
+  }
+  flush_slab(S.slab, t);
+  const long long dl = (long long)wsum((unsigned long long)dlive);
+  if ((threadIdx.x & 31u) == 0 && dl) atomicAdd(&S.ctr[0], (unsigned long long)dl);
+}
+
+// Round kernel 3: peel rays past their first cell, walked to the box face and deposited.
+__global__ void __launch_bounds__(256) grid_ray_kernel(GridModel m, GridSlots S, int parity,
+                                                       const float* __restrict__ gK) {
+  __shared__ __align__(16) float sK[THOR_VOIGT_NINT * THOR_VOIGT_NCOEF];
+  load_ktab(sK, gK);
+  const unsigned long long n = S.ctr[5 + 4 * parity];
+  GTally t;
+  const WalkHere here{m, sK, t.pc};
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+    const PeelRay r = S.rays[j];
+    const double p[3] = {r.px, r.py, r.pz};
+    here(p, r.ax, r.Xp, r.w0, r.tau);
+  }
+  flush_slab(S.slab, t);
+}
+
+// The packets in flight, listed (in slot order) for the hand-off to the one-kernel loop.
+__global__ void grid_list_kernel(GridSlots S) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const unsigned lane = threadIdx.x & 31u;
+  for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < S.n; b0 += stride) {
+    const int64_t i = b0 + threadIdx.x;
+    const bool live = i < S.n && S.live[i];
+    const unsigned lb = __ballot_sync(kFull, live);
+    if (!lb) continue;
+    const int leader = __ffs(lb) - 1;
+    unsigned long long base = 0;
+    if ((int)lane == leader) base = atomicAdd(&S.ctr[2], (unsigned long long)__popc(lb));
+    base = __shfl_sync(kFull, base, leader);
+    if (live) S.rq[base + __popc(lb & ((1u << lane) - 1u))] = (int32_t)i;
   }
 }
 
@@ -469,15 +797,80 @@ int grid_grid(int block, int blocks_per_sm) {
   int dev = 0, sms = 0, occ = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, grid_run_kernel, block, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, grid_run_kernel<false>, block, 0);
   if (occ < 1) occ = 1;
   const int b = (blocks_per_sm > 0 && blocks_per_sm < occ) ? blocks_per_sm : occ;
   return sms * b;
 }
 
 cudaError_t launch_grid_run(GridModel m, WorkQueue q, const float* d_ktab, int grid, int block, cudaStream_t s) {
-  grid_run_kernel<<<grid, block, 0, s>>>(m, q, d_ktab);
+  grid_run_kernel<false><<<grid, block, 0, s>>>(m, q, d_ktab, GridSlots{});
   return cudaGetLastError();
+}
+
+cudaError_t launch_grid_resume(GridModel m, WorkQueue q, GridSlots S, const float* d_ktab, int grid, int block,
+                               cudaStream_t s) {
+  grid_run_kernel<true><<<grid, block, 0, s>>>(m, q, d_ktab, S);
+  return cudaGetLastError();
+}
+
+// Kernel 1 covers every slot (grid-stride); kernels 2 and 3 read their queue lengths on the
+// device, so a round needs no host round trip.
+cudaError_t launch_grid_round(GridModel m, WorkQueue q, GridSlots S, int parity, const float* d_ktab, int block,
+                              cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t want = (S.n + 255) / 256;
+  const int gmax = sms * 8 < kGridSlabBlocks ? sms * 8 : kGridSlabBlocks;  // one slab entry per block
+  const int g1 = (int)(want < (int64_t)gmax ? want : (int64_t)gmax);
+  grid_move_kernel<<<g1, 256, 0, s>>>(m, q, S, parity, d_ktab);
+  grid_scatter_kernel<<<gmax, block, 0, s>>>(m, S, parity, d_ktab);
+  grid_ray_kernel<<<gmax, block, 0, s>>>(m, S, parity, d_ktab);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grid_slab_sum(GridModel m, GridSlots S, cudaStream_t s) {
+  grid_slab_sum_kernel<<<1, 1024, 0, s>>>(m, S);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grid_list_live(GridSlots S, cudaStream_t s) {
+  const int64_t want = (S.n + 255) / 256;
+  grid_list_kernel<<<(unsigned)(want < 4096 ? want : 4096), 256, 0, s>>>(S);
+  return cudaGetLastError();
+}
+
+// Layout of the slot buffer (each array 256-byte aligned), as grid_slots_carve takes it:
+// 4 arrays of 8-byte entries (anchor, photon id), 18 of 4-byte entries (offsets, face
+// distances, safety distance, direction, frequencies, counters, event, resonant queue), the
+// live flags, 3 n peel rays, the counters and the tally slab.
+size_t grid_slots_bytes(int64_t n) {
+  auto r = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  return 4 * r((size_t)n * 8) + 18 * r((size_t)n * 4) + r((size_t)n) + r((size_t)3 * n * sizeof(PeelRay)) +
+         r(16 * 8) + r((size_t)kGridSlabBlocks * sizeof(TallySlab));
+}
+
+GridSlots grid_slots_carve(void* base, int64_t n) {
+  char* p = (char*)base;
+  auto take = [&](size_t bytes) { char* q = p; p += (bytes + 255) & ~(size_t)255; return (void*)q; };
+  GridSlots S;
+  S.n = n;
+  S.px = (double*)take(n * 8); S.py = (double*)take(n * 8); S.pz = (double*)take(n * 8);
+  S.ox = (float*)take(n * 4); S.oy = (float*)take(n * 4); S.oz = (float*)take(n * 4);
+  S.fx = (float*)take(n * 4); S.fy = (float*)take(n * 4); S.fz = (float*)take(n * 4);
+  S.safe = (float*)take(n * 4);
+  S.kx = (float*)take(n * 4); S.ky = (float*)take(n * 4); S.kz = (float*)take(n * 4); S.X = (float*)take(n * 4);
+  S.xs = (float*)take(n * 4);
+  S.nscat = (uint32_t*)take(n * 4); S.ndust = (uint32_t*)take(n * 4); S.iters = (uint32_t*)take(n * 4);
+  S.steps = (uint32_t*)take(n * 4); S.event = (uint32_t*)take(n * 4);
+  S.pid = (unsigned long long*)take(n * 8);
+  S.live = (uint8_t*)take(n);
+  S.rq = (int32_t*)take(n * 4);
+  S.rays = (PeelRay*)take((size_t)3 * n * sizeof(PeelRay));
+  S.ctr = (unsigned long long*)take(16 * 8);
+  S.slab = (TallySlab*)take((size_t)kGridSlabBlocks * sizeof(TallySlab));
+  return S;
 }
 
 }  // namespace thor

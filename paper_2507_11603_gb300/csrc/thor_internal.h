@@ -170,6 +170,38 @@ struct GridModel {
   uint8_t* raw_status;
 };
 
+// Event-based grid loop: packets in flight, one slot each (SoA, device memory), and the
+// queues between its kernels.
+struct PeelRay {  // a peel-off ray past its first cell (the walk resumes at the next cell)
+  double px, py, pz;
+  float Xp, w0, tau;
+  int32_t ax;
+};
+struct TallySlab {  // counters of one block index of the event-based loop's kernels
+  unsigned long long esc, ab, cap, sc, du, it, stp, dn, pr, pc;
+  double sc2;
+  unsigned long long pad;
+};
+struct GridSlots {
+  int64_t n;                   // slots
+  double *px, *py, *pz;        // FP64 anchor (cell units)
+  float *ox, *oy, *oz;         // FP32 offset from the anchor
+  float *fx, *fy, *fz;         // distances from the anchor to the cell's + faces
+  float* safe;
+  float *kx, *ky, *kz, *X;
+  float* xs;                   // gas-frame frequency at the interaction site (move -> interact)
+  uint32_t *nscat, *ndust, *iters, *steps, *event;
+  unsigned long long* pid;
+  uint8_t* live;               // 1 = a packet in flight
+  int32_t* rq;                 // slots awaiting a resonant scattering (n entries)
+  PeelRay* rays;               // peel rays past their first cell (3 n entries)
+  // [0] packets in flight; [2] entries of the resume list (in rq) and [3] its cursor;
+  // round parity r: [4 + 4r] resonant queue length, [5 + 4r] ray queue length
+  unsigned long long* ctr;
+  TallySlab* slab;             // one entry per block index (kGridSlabBlocks), summed at the end
+};
+constexpr int kGridSlabBlocks = 4096;
+
 // ---- launchers (implemented in the .cu files) ------------------------------------
 int shell_grid(int block, int blocks_per_sm, bool sliced);  // persistent grid size
 int grid_grid(int block, int blocks_per_sm);
@@ -191,6 +223,17 @@ cudaError_t launch_scan_f64(double* data, int64_t n, double* scratch, cudaStream
 size_t scan_f64_scratch(int64_t n);
 cudaError_t launch_grid_run(GridModel m, WorkQueue q, const float* d_ktab, int grid, int block,
                             cudaStream_t s);
+// Event-based grid loop: one round (move, resonant scatterings, peel rays) with counters of
+// parity `parity`; the list of packets in flight (for the hand-off); the one-kernel loop
+// resuming that list first.
+cudaError_t launch_grid_round(GridModel m, WorkQueue q, GridSlots S, int parity, const float* d_ktab, int block,
+                              cudaStream_t s);
+cudaError_t launch_grid_list_live(GridSlots S, cudaStream_t s);
+cudaError_t launch_grid_slab_sum(GridModel m, GridSlots S, cudaStream_t s);
+cudaError_t launch_grid_resume(GridModel m, WorkQueue q, GridSlots S, const float* d_ktab, int grid, int block,
+                               cudaStream_t s);
+size_t grid_slots_bytes(int64_t n);
+GridSlots grid_slots_carve(void* base, int64_t n);
 cudaError_t launch_forest(const float* nHI, const float* T, const float* vlos, int nx, int ny, int nz,
                           int64_t first, int64_t count, double ds_cm, double dv_cell, int n_bins,
                           double dv_bin, float* tau, const float* d_ktab, cudaStream_t s);

@@ -133,7 +133,7 @@ extern "C" int thor_run_shell_noalloc(const thor_shell_params* p, const thor_sou
   const int per_warp = (int)(pw < 1 ? 1 : (pw > 32 ? 32 : pw));
   if (e == cudaSuccess)
     e = launch_shell_run((const ShellModel*)(scratch + kOffModel), q, ktab, gsz, block, THOR_PROFILE_HOMOLOGOUS,
-                         per_warp, 32, 4, s);
+                         per_warp, 32, 1, s);  // the context defaults of thor_ctx_set_bursts
   Tally t;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&t, tally, sizeof t, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess && mem_kind == THOR_MEM_HOST)

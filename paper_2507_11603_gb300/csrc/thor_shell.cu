@@ -17,7 +17,7 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kServedPipeLanes = 32;  // served rounds: pipelined events in every warp
-constexpr int kServedBurstLanes = 4;  // served rounds: core bursts in warps with at most this many live packets
+constexpr int kServedBurstLanes = 1;  // served rounds: core bursts for lone packets
 constexpr uint32_t kLongLived = 1u << 14;  // served rounds: packets past this many events run one per warp
 
 struct Photon {
@@ -262,8 +262,8 @@ __device__ int shell_event(const ShellModel& m, Photon& ph, const float* __restr
 // ---- pipelined events (homologous shells) -------------------------------------------
 // A packet trapped in the line core spends its life in one kind of event: the crossing lies
 // within ds/16 of the start (start-point rate, Sec. 5.1 step limiter) inside the safety
-// ball, the interaction is a resonant scattering at |x| <= 2 (Sec. 3.4), and the first
-// trial of the u_par sampler (Eq. 10) is accepted.  In such an event only the frequency
+// ball, the interaction is a resonant scattering at |x| <= 2 (Sec. 3.4), and the u_par
+// sampler (Eq. 10) accepts within two trials.  In such an event only the frequency
 // chain x -> H(a,x) -> s -> x_site -> u_par -> x_out depends on the packet's state; the next
 // event's Philox blocks and optical depth, the perpendicular atom velocity (Eq. 5), mu and
 // the outgoing direction depend only on random words and the incoming direction.
@@ -295,13 +295,24 @@ __device__ __forceinline__ int core_event(const ShellModel& m, Photon& ph, const
   tau2 = draw_tau(r2);
   return core_event_with(m, ph, Ktab, tau_next, r2, tau2);
 }
-// The same event with the next event's words (r2) and optical depth (tau2) given.
-__device__ __forceinline__ int core_event_with(const ShellModel& m, Photon& ph, const float* __restrict__ Ktab,
-                                               float& tau_next, const Rng& r2, float tau2) {
+// The core form of the prepared event, evaluated (nothing committed): the frequency chain,
+// the u_par sampler's first trial (and its second, when the first is rejected) and, beside
+// them, the perpendicular velocity, mu and the outgoing direction.  ok: the event is of the
+// core kind.
+struct CoreEval {
+  float s0, xs, upar, mu, st, u1, u2, cp, sp;
+  float3 ko;
+  uint32_t trials;  // u_par trials (one or two)
+  bool ok;
+};
+// live = false: a lane of a cooperative burst without a packet in it; it evaluates at line
+// centre and skips the rare second trial, so that it takes the owners' branches.
+__device__ __forceinline__ CoreEval core_eval(const ShellModel& m, const Photon& ph, const float* __restrict__ Ktab,
+                                              float tau, bool live = true) {
   const Rng& r = ph.rng;
-  const float tau = tau_next;
+  CoreEval e;
   // ---- the frequency chain: rate at the start, crossing, gas-frame frequency at the site
-  const float x0 = ph.x;
+  const float x0 = live ? ph.x : 0.0f;
   const StartStep st0 = start_step(m, voigt_start(m.a, x0, Ktab), tau);
   const float s0 = st0.s;
   const bool in_ball = (m.gam == 0.0f) ? (s0 <= ph.safe) : (ph.safe >= m.ds_core && s0 <= 0.0625f * m.ds_core);
@@ -312,43 +323,70 @@ __device__ __forceinline__ int core_event_with(const ShellModel& m, Photon& ph, 
   const float xr = fabsf(xs);
   const float u0 = u0_core(xr, m.a);
   const float q = upar_q(xr, m.a);
-  const float w1 = atan_small(q);
+  // w1 = atan2(a, x - u0) as sample_upar forms it: the q form where u0 > 0, else (u0 = 0,
+  // within ~0.04 of line centre) the series in a / x
+  const bool split = u0 > 0.0f;
+  const float w1 = split ? atan_small(q) : atan2_series(m.a, xr);
   const float u02 = __fmul_rn(u0, u0);
   const float mass = envelope_mass(w1, exp_fast(-u02));
-  const float w1p = w1 * (1.0f / kPiF);
-  const float R1 = r.u(W_UPAR0), R2 = r.u(W_UPAR0 + 1), R3 = r.u(W_UPAR0 + 2);
-  const bool reg1 = region1(R1, mass, w1);
-  const float t = reg1 ? w1p * R2 : __fmaf_rn(1.0f - w1p, R2, w1p);
-  const float u = __fmaf_rn(-m.a, cot_pi(t), xr);
-  const float uu = __fmul_rn(u, u);
-  const float acc = reg1 ? exp_fast(-uu) : exp_fast(u02 - uu);
+  const float w1p = __fmul_rn(w1, 1.0f / kPiF);
+  float u;
+  bool accepted = upar_trial(xr, m.a, w1, w1p, mass, u02, r.u(W_UPAR0), r.u(W_UPAR0 + 1), r.u(W_UPAR0 + 2), u);
+  e.trials = 1u;
+  if (!accepted && live) {  // rare: the second trial, from block 3 of the event as sample_upar takes it
+    uint32_t b0, b1, b2, b3;
+    r.block(3u, b0, b1, b2, b3);
+    accepted = upar_trial(xr, m.a, w1, w1p, mass, u02, uni32(b0), uni32(b1), uni32(b2), u);
+    e.trials = 2u;
+  }
   // ---- beside the chain: perpendicular velocity, mu, outgoing direction (as scatter_resonant)
   const float xc = (xr < m.xcrit) ? m.xcrit : 0.0f;
   const float rr = sqrt_approx(__fmaf_rn(xc, xc, -__logf(r.u(W_BM_R))));
   float sp1, cp1;
   __sincosf(2.0f * kPiF * r.u(W_BM_PHI), &sp1, &cp1);
-  const float u1 = __fmul_rn(rr, cp1), u2 = __fmul_rn(rr, sp1);
+  e.u1 = __fmul_rn(rr, cp1);
+  e.u2 = __fmul_rn(rr, sp1);
   const float Rm = r.u(W_MU);
-  const float mu = (m.phase == PH_ISO) ? __fmaf_rn(2.0f, Rm, -1.0f) : mu_dipole(Rm);
-  float sp, cp;
-  __sincosf(2.0f * kPiF * r.u(W_PHI), &sp, &cp);
+  e.mu = (m.phase == PH_ISO) ? __fmaf_rn(2.0f, Rm, -1.0f) : mu_dipole(Rm);
+  __sincosf(2.0f * kPiF * r.u(W_PHI), &e.sp, &e.cp);
   float3 e1, e2;
   basis(ph.k.x, ph.k.y, ph.k.z, e1, e2);
-  const float st = sqrt_approx(fmaxf(0.0f, __fmaf_rn(-mu, mu, 1.0f)));
-  const float3 ko = turn(ph.k, e1, e2, mu, st, cp, sp);
-  if (!(!ph.region && m.phase != PH_MIXED && in_ball && !dust && xr <= 2.0f && u0 > 0.0f && q <= 0.05f &&
-        R3 <= acc))
-    return 0;
-  // ---- commit, as shell_event_words and scatter_resonant do
-  ++ph.steps;
-  advance(ph, s0);
-  ph.safe = __fmaf_rd(-s0, 1.000001f, ph.safe);
-  ph.x = x_after_scatter(xs, sgn * u, mu, st, u1, u2, cp, sp);
-  ph.k = ko;
-  ++ph.iters;
-  ++ph.nscat;
-  ph.rng = r2;  // prepared: the next event's words
-  tau_next = tau2;
+  e.st = sqrt_approx(fmaxf(0.0f, __fmaf_rn(-e.mu, e.mu, 1.0f)));
+  e.ko = turn(ph.k, e1, e2, e.mu, e.st, e.cp, e.sp);
+  e.s0 = s0;
+  e.xs = xs;
+  e.upar = sgn * u;
+  e.ok = !ph.region && m.phase != PH_MIXED && in_ball && !dust && xr <= 2.0f &&
+         (split ? q <= 0.05f : m.a <= 0.05f * xr) && accepted;
+  return e;
+}
+// Commit an evaluated core event where `ok` (selects, no branch), as shell_event_words and
+// scatter_resonant do: the packet is then prepared with the next event's words r2 and
+// optical depth tau2.
+__device__ __forceinline__ void core_commit(Photon& ph, const CoreEval& e, bool ok, const Rng& r2, float tau2,
+                                            float& tau_next) {
+  ph.steps += ok ? 1u : 0u;
+  ph.ox = ok ? __fmaf_rn(e.s0, ph.k.x, ph.ox) : ph.ox;  // advance(ph, s0)
+  ph.oy = ok ? __fmaf_rn(e.s0, ph.k.y, ph.oy) : ph.oy;
+  ph.oz = ok ? __fmaf_rn(e.s0, ph.k.z, ph.oz) : ph.oz;
+  ph.safe = ok ? __fmaf_rd(-e.s0, 1.000001f, ph.safe) : ph.safe;
+  ph.x = ok ? x_after_scatter(e.xs, e.upar, e.mu, e.st, e.u1, e.u2, e.cp, e.sp) : ph.x;
+  ph.k.x = ok ? e.ko.x : ph.k.x;
+  ph.k.y = ok ? e.ko.y : ph.k.y;
+  ph.k.z = ok ? e.ko.z : ph.k.z;
+  ph.iters += ok ? e.trials : 0u;
+  ph.nscat += ok ? 1u : 0u;
+  ph.rng.event = ok ? r2.event : ph.rng.event;
+#pragma unroll
+  for (int j = 0; j < 12; ++j) ph.rng.v[j] = ok ? r2.v[j] : ph.rng.v[j];
+  tau_next = ok ? tau2 : tau_next;
+}
+// The same event with the next event's words (r2) and optical depth (tau2) given.
+__device__ __forceinline__ int core_event_with(const ShellModel& m, Photon& ph, const float* __restrict__ Ktab,
+                                               float& tau_next, const Rng& r2, float tau2) {
+  const CoreEval e = core_eval(m, ph, Ktab, tau_next);
+  if (!e.ok) return 0;
+  core_commit(ph, e, true, r2, tau2, tau_next);
   if (m.max_scat && ph.nscat >= m.max_scat) {
     anchor(ph);
     const float b = (float)(ph.px * ph.k.x + ph.py * ph.k.y + ph.pz * ph.k.z);
@@ -397,7 +435,8 @@ __device__ __forceinline__ int core_burst(const ShellModel& m, Photon& ph, const
 // computes one block ahead -- for owner o, event d ahead, block b: D = 32 / (3 owners)
 // events deep -- and the owners take their words by shuffle, D events per round of blocks.
 // The words are the ones Rng::start_event forms, so the packets' histories are those of
-// core_burst, bit for bit.  Returns as core_burst (per lane; 0 for lanes not in the burst).
+// core_burst, bit for bit.  Returns 0: a packet leaves the burst prepared, before its first
+// event that is not of the core kind, or one scattering short of the cap.
 constexpr int kCoopOwners = 10;
 __device__ __forceinline__ int core_burst_coop(const ShellModel& m, Photon& ph, const float* __restrict__ Ktab,
                                                float& tau_next, bool mine) {
@@ -419,8 +458,10 @@ __device__ __forceinline__ int core_burst_coop(const ShellModel& m, Photon& ph, 
   // as an owner: the first lane of its span
   const int base = mine ? __popc(owners & ((1u << lane) - 1u)) * span : 0;
   const bool b3 = shell_blocks(m) > 2u;  // else words 8..11 stay as start_event leaves them
-  bool go = mine;
-  int status = 0;
+  // a burst stops one scattering short of the cap: the event that reaches it runs as
+  // shell_event_pipe (which finishes the packet)
+  const uint32_t room = m.max_scat ? (m.max_scat > ph.nscat + 1u ? m.max_scat - ph.nscat - 1u : 0u) : kCoreBurst;
+  bool go = mine && room > 0u;
   for (uint32_t n = 0; n < kCoreBurst; n += (uint32_t)D) {
     // a round of blocks: events e+1 .. e+D of each owner (e = its prepared event now)
     const uint32_t k0 = __shfl_sync(kFull, ph.rng.k0, src), k1 = __shfl_sync(kFull, ph.rng.k1, src);
@@ -438,14 +479,15 @@ __device__ __forceinline__ int core_burst_coop(const ShellModel& m, Photon& ph, 
       const uint32_t w8 = __shfl_sync(kFull, h0, s0 + 2), w9 = __shfl_sync(kFull, h1, s0 + 2);
       const uint32_t w10 = __shfl_sync(kFull, h2, s0 + 2), w11 = __shfl_sync(kFull, h3, s0 + 2);
       if (b3) { r2.v[8] = w8; r2.v[9] = w9; r2.v[10] = w10; r2.v[11] = w11; }
-      if (go) {
-        const int c = core_event_with(m, ph, Ktab, tau_next, r2, draw_tau(r2));
-        if (c != 1) { go = false; status = c; }
-      }
-      if (!__any_sync(kFull, go)) return status;
+      // every lane evaluates (the owners' events; garbage elsewhere, never committed) and
+      // commits by select: the loop body is one basic block
+      const CoreEval e = core_eval(m, ph, Ktab, tau_next, go);
+      go = go && e.ok && n + (uint32_t)i < room;
+      core_commit(ph, e, go, r2, draw_tau(r2), tau_next);
+      if (!__any_sync(kFull, go)) return 0;
     }
   }
-  return status;
+  return 0;
 }
 
 // ---- power-law shells (Sec. 5.1) ---------------------------------------------------

@@ -30,7 +30,7 @@ SYMBOLS = [
     "thor_server_wait", "thor_server_cancel", "thor_server_stats", "thor_server_destroy", "thor_voigt_eval",
     "thor_dda_trace", "thor_sample_upar", "thor_scatter_once", "thor_philox", "thor_line_params",
     "thor_run_shell_noalloc", "thor_noalloc_last_error", "thor_reweight", "thor_xcw_eval", "thor_ctx_set_bursts",
-    "thor_issue_peak",
+    "thor_issue_peak", "thor_ctx_set_grid_exec",
 ]
 PROFILE = {"homologous": 0, "power_law": 1}
 SPECIES = {"HI": 0, "MgII": 1}
@@ -109,6 +109,7 @@ def load(build: bool = True) -> C.CDLL:
             "thor_ctx_set_launch": ([vp, C.c_int, C.c_int], C.c_int),
             "thor_ctx_set_tail": ([vp, C.c_int, C.c_int], C.c_int),
             "thor_ctx_set_bursts": ([vp, C.c_int, C.c_int], C.c_int),
+            "thor_ctx_set_grid_exec": ([vp, C.c_int64, C.c_int64], C.c_int),
             "thor_shell_create": ([vp, P(ShellParams), P(vp)], C.c_int),
             "thor_grid_create": ([vp, vp, vp, vp, vp, P(i32), dbl, C.c_int, P(vp)], C.c_int),
             "thor_grid_set_scattering": ([vp, C.c_int, dbl, dbl], C.c_int),
@@ -277,11 +278,19 @@ class Context:
     def set_launch(self, block_size: int, blocks_per_sm: int = 0):
         self._check(self.L.thor_ctx_set_launch(self.h, block_size, blocks_per_sm))
 
-    def set_bursts(self, pipe_lanes: int = 32, burst_lanes: int = 4):
+    def set_bursts(self, pipe_lanes: int = 32, burst_lanes: int = 1):
         """thor_ctx_set_bursts: pipelined events in warps with at most pipe_lanes live packets,
         core bursts in warps with at most burst_lanes (0 = never); results do not depend on
         them."""
         self._check(self.L.thor_ctx_set_bursts(self.h, pipe_lanes, burst_lanes))
+
+    def set_grid_exec(self, slots: int = 0, handoff: int | None = None):
+        """thor_ctx_set_grid_exec: event-based grid loop with `slots` packets in flight
+        (0 = the one-kernel loop), handing the last `handoff` (default slots // 8) to the
+        one-kernel loop; results do not depend on it."""
+        if handoff is None:
+            handoff = slots // 8
+        self._check(self.L.thor_ctx_set_grid_exec(self.h, int(slots), int(handoff)))
 
     def set_tail(self, spill_below: int = 0, max_phases: int = 24):
         """thor_ctx_set_tail: tail compaction of the shell photon loop (0 = off, the library's

@@ -314,17 +314,18 @@ def test_ragged_photon_counts_equal_photons_alone(ctx):
 def test_core_bursts_do_not_change_results(ctx, geo):
     """Pipelined events and core bursts evaluate each event exactly as the general event
     does: per-photon records and every tally are bit-identical with pipelining never, in
-    every warp or in warps of at most 4 live packets, and with bursts never, in warps of at
-    most 4 (the default) or in every warp; on an outflowing dusty shell (start-point
-    sub-steps, dust channel) and a static sphere (safety-ball steps)."""
+    every warp or in warps of at most 4 live packets, and with bursts never, for lone packets
+    (the default), in warps of at most 4 or 10 (cooperative bursts with several owners) or in
+    every warp (plain bursts beyond 10); on an outflowing dusty shell (start-point sub-steps,
+    dust channel) and a static sphere (safety-ball steps)."""
     g = ctx.shell(**geo)
     kw = dict(n_photons=3000, seed=41, sigma=50.0 if "N_HI" in geo else 0.0, n_bins=200, X_min=-1500.0,
               X_max=1500.0, raw=True)
     out = []
-    for pipe, burst in ((0, 0), (32, 0), (4, 4), (32, 4), (32, 32)):
+    for pipe, burst in ((0, 0), (32, 0), (32, 1), (4, 4), (32, 4), (32, 10), (32, 32)):
         ctx.set_bursts(pipe, burst)
         out.append(ctx.run(g, **kw))
-    ctx.set_bursts(32, 4)
+    ctx.set_bursts(32, 1)
     a = out[0]
     assert a.stats["n_scat"] > 1e6
     for b in out[1:]:
