@@ -501,8 +501,10 @@ static int run_grid_events(thor_ctx* ctx, thor::GridModel m, thor::WorkQueue q, 
     if (h[1] >= q.total && (long long)h[0] <= ctx->grid_handoff) break;
   }
   ctx->grid_rounds_last = r;
+  // peel rays still walking after the last round (parity (r - 1) & 1) are in the other queue
+  if ((rc = ctx->cuda(launch_grid_ray_drain(m, S, (int)(r & 1), ctx->d_ktab, ctx->block, s), "peel rays"))) return rc;
   if ((rc = ctx->cuda(launch_grid_slab_sum(m, S, s), "round counters"))) return rc;
-  ++*n_launch;
+  *n_launch += 2;
   if (h[0] > 0) {  // the tail: the one-kernel loop resumes the packets in flight
     if ((rc = ctx->cuda(cudaMemsetAsync(S.ctr + 2, 0, 16, s), "clear resume list"))) return rc;
     if ((rc = ctx->cuda(launch_grid_list_live(S, s), "list packets in flight"))) return rc;

@@ -154,29 +154,55 @@ __device__ __forceinline__ int64_t cell_index(const GridModel& m, int ix, int iy
 
 // Optical depth from p to the box face along +axis at lab frequency Xp (Sec. 3.4.1),
 // cell by cell, stopping once tau > tau_cut.
-__device__ __forceinline__ float peel_tau_from(const GridModel& m, const double p[3], int axis, float Xp,
-                                               const float* Ktab, uint32_t& ncell, int skip, float tau0) {
-  // walk along +axis: the cell index advances by `stride` elements per step; the first
-  // `skip` cells (0 or 1) are already in tau0
+// A peel ray's walk along +axis from cell index i (t: its entry distance from the start,
+// tau: the optical depth so far), cell by cell, stopping once tau > tau_cut.  Cells are
+// loaded four at a time (their addresses do not depend on the walk), so a long walk waits on
+// memory once per four cells; the optical depth is summed in the same order as one at a
+// time.  Walks at most max_cells cells (all when max_cells <= 0).  Returns true when the walk
+// is over (tau > tau_cut, or the box face reached).
+struct PeelWalk {
+  int i;     // next cell along the axis
+  double t;  // distance from the ray's start to that cell's entry face
+  float tau;
+};
+__device__ __forceinline__ bool peel_walk(const GridModel& m, const double p[3], int axis, float Xp,
+                                          const float* Ktab, uint32_t& ncell, PeelWalk& w, int max_cells) {
   const int ix = (int)floor(p[0]), iy = (int)floor(p[1]), iz = (int)floor(p[2]);
   const int n_ax = (axis == 0) ? m.nx : (axis == 1) ? m.ny : m.nz;
-  const int i0 = ((axis == 0) ? ix : (axis == 1) ? iy : iz) + skip;
+  const int ia = (axis == 0) ? ix : (axis == 1) ? iy : iz;
   const double pa = (axis == 0) ? p[0] : (axis == 1) ? p[1] : p[2];
   const int64_t stride = (axis == 0) ? 1 : (axis == 1) ? (int64_t)m.nx : (int64_t)m.nx * m.ny;
-  int64_t c = cell_index(m, ix, iy, iz) + (int64_t)skip * stride;
-  double t = skip ? __dadd_rn((double)i0, -pa) : 0.0;
-  float tau = tau0;
-  for (int i = i0; i < n_ax; ++i, c += stride) {
-    const double tn = __dadd_rn((double)(i + 1), -pa);
-    const GridCell g = load_cell(m.cells, c);
-    const float v = (axis == 0) ? g.vx : (axis == 1) ? g.vy : g.vz;
-    const float x = (Xp - v) * g.inv_vth;
-    tau = __fmaf_rn(__fmaf_rn(g.kap0, voigt<false>(g.a, x, Ktab), g.kd), (float)(tn - t), tau);
-    ++ncell;
-    if (tau > m.tau_cut) break;
-    t = tn;
+  int64_t c = cell_index(m, ix, iy, iz) + (int64_t)(w.i - ia) * stride;
+  const int end = (max_cells > 0 && w.i + max_cells < n_ax) ? w.i + max_cells : n_ax;
+  while (w.i < end) {
+    GridCell g[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) g[k] = load_cell(m.cells, c + (int64_t)min(k, end - 1 - w.i) * stride);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (w.i >= end) break;
+      const double tn = __dadd_rn((double)(w.i + 1), -pa);
+      const float v = (axis == 0) ? g[k].vx : (axis == 1) ? g[k].vy : g[k].vz;
+      const float x = (Xp - v) * g[k].inv_vth;
+      w.tau = __fmaf_rn(__fmaf_rn(g[k].kap0, voigt<false>(g[k].a, x, Ktab), g[k].kd), (float)(tn - w.t), w.tau);
+      ++ncell;
+      ++w.i;
+      c += stride;
+      if (w.tau > m.tau_cut) return true;
+      w.t = tn;
+    }
   }
-  return tau;
+  return w.i >= n_ax;
+}
+// Optical depth from p to the box face along +axis at lab frequency Xp (Sec. 3.4.1); the
+// first `skip` cells (0 or 1) are already in tau0.
+__device__ __forceinline__ float peel_tau_from(const GridModel& m, const double p[3], int axis, float Xp,
+                                               const float* Ktab, uint32_t& ncell, int skip, float tau0) {
+  const int ia = (int)floor((axis == 0) ? p[0] : (axis == 1) ? p[1] : p[2]);
+  const double pa = (axis == 0) ? p[0] : (axis == 1) ? p[1] : p[2];
+  PeelWalk w{ia + skip, skip ? __dadd_rn((double)(ia + skip), -pa) : 0.0, tau0};
+  peel_walk(m, p, axis, Xp, Ktab, ncell, w, 0);
+  return w.tau;
 }
 __device__ __forceinline__ float peel_tau(const GridModel& m, const double p[3], int axis, float Xp, const float* Ktab,
                                           uint32_t& ncell) {
@@ -444,16 +470,35 @@ __device__ __forceinline__ void slot_load(const GridModel& m, const GridSlots& S
   if (with_cell || ph.safe > 0.0f)
     ph.gc = load_cell(m.cells, cell_index(m, (int)floor(ph.p[0]), (int)floor(ph.p[1]), (int)floor(ph.p[2])));
 }
-// Peel rays past their first cell go to the ray queue.
+// Peel rays past their first cell go to the ray queue of the round (walked there in chunks);
+// a ray that finds the queue full is walked to the end on the spot.
+__device__ __forceinline__ void queue_ray(const GridModel& m, PeelRay* rays, unsigned long long* n, int64_t cap,
+                                          const PeelRay& r, const float* Ktab, uint32_t& pc) {
+  const unsigned long long j = atomicAdd(n, 1ull);
+  if (j < (unsigned long long)cap) {
+    rays[j] = r;
+    return;
+  }
+  const double p[3] = {r.px, r.py, r.pz};
+  PeelWalk w{r.i, r.t, r.tau};
+  peel_walk(m, p, r.ax, r.Xp, Ktab, pc, w, 0);
+  if (w.tau <= m.tau_cut) deposit(m, p, r.ax, r.Xp, r.w0 * __expf(-w.tau));
+}
 struct WalkQueue {
+  const GridModel& m;
   PeelRay* rays;
   unsigned long long* n;
+  int64_t cap;
+  const float* Ktab;
+  uint32_t& pc;
   __device__ __forceinline__ void operator()(const double p[3], int ax, float Xp, float w0, float tau) const {
-    const unsigned long long j = atomicAdd(n, 1ull);
+    // the state after the first cell, as peel_tau_from(..., skip = 1, tau) starts
+    const int ia = (int)floor(p[ax]);
     PeelRay r;
     r.px = p[0]; r.py = p[1]; r.pz = p[2];
-    r.Xp = Xp; r.w0 = w0; r.tau = tau; r.ax = ax;
-    rays[j] = r;
+    r.t = __dadd_rn((double)(ia + 1), -p[ax]);
+    r.Xp = Xp; r.w0 = w0; r.tau = tau; r.ax = ax; r.i = ia + 1; r.pad = 0;
+    queue_ray(m, rays, n, cap, r, Ktab, pc);
   }
 };
 // Counters of finished packets, per lane, flushed once per warp.
@@ -634,8 +679,8 @@ __global__ void __launch_bounds__(256) grid_move_kernel(GridModel m, WorkQueue q
   unsigned long long* cnt = S.ctr + 4 + 4 * parity;
   if (blockIdx.x == 0 && threadIdx.x < 2) S.ctr[4 + 4 * (parity ^ 1) + threadIdx.x] = 0ull;
   const unsigned lane = threadIdx.x & 31u;
-  const WalkQueue walk{S.rays, cnt + 1};
   GTally t;
+  const WalkQueue walk{m, S.rays[parity], cnt + 1, (int64_t)kRayCap * S.n, sK, t.pc};
   long long dlive = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < S.n; b0 += stride) {  // warp-uniform
@@ -704,8 +749,8 @@ __global__ void __launch_bounds__(256) grid_scatter_kernel(GridModel m, GridSlot
   load_ktab(sK, gK);
   const unsigned long long* cnt = S.ctr + 4 + 4 * parity;
   const unsigned long long n = cnt[0];
-  const WalkQueue walk{S.rays, S.ctr + 5 + 4 * parity};
   GTally t;
+  const WalkQueue walk{m, S.rays[parity], S.ctr + 5 + 4 * parity, (int64_t)kRayCap * S.n, sK, t.pc};
   long long dlive = 0;
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
   for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
@@ -728,19 +773,31 @@ __global__ void __launch_bounds__(256) grid_scatter_kernel(GridModel m, GridSlot
   if ((threadIdx.x & 31u) == 0 && dl) atomicAdd(&S.ctr[0], (unsigned long long)dl);
 }
 
-// Round kernel 3: peel rays past their first cell, walked to the box face and deposited.
-__global__ void __launch_bounds__(256) grid_ray_kernel(GridModel m, GridSlots S, int parity,
+// Round kernel 3: the round's peel rays advance up to kRayChunk cells each (one ray per
+// thread); a ray that is done is deposited, the others go on in the next round's queue, so a
+// round waits for no ray's whole walk.  drain: walk every ray to its end (after the last
+// round).
+__global__ void __launch_bounds__(256) grid_ray_kernel(GridModel m, GridSlots S, int parity, int drain,
                                                        const float* __restrict__ gK) {
   __shared__ __align__(16) float sK[THOR_VOIGT_NINT * THOR_VOIGT_NCOEF];
   load_ktab(sK, gK);
-  const unsigned long long n = S.ctr[5 + 4 * parity];
+  const int64_t cap = (int64_t)kRayCap * S.n;
+  const unsigned long long n0 = S.ctr[5 + 4 * parity];
+  const unsigned long long n = n0 < (unsigned long long)cap ? n0 : (unsigned long long)cap;
+  PeelRay* next = S.rays[parity ^ 1];
+  unsigned long long* n_next = S.ctr + 5 + 4 * (parity ^ 1);
   GTally t;
-  const WalkHere here{m, sK, t.pc};
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
   for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
-    const PeelRay r = S.rays[j];
+    PeelRay r = S.rays[parity][j];
     const double p[3] = {r.px, r.py, r.pz};
-    here(p, r.ax, r.Xp, r.w0, r.tau);
+    PeelWalk w{r.i, r.t, r.tau};
+    if (peel_walk(m, p, r.ax, r.Xp, sK, t.pc, w, drain ? 0 : kRayChunk)) {
+      if (w.tau <= m.tau_cut) deposit(m, p, r.ax, r.Xp, r.w0 * __expf(-w.tau));
+    } else {
+      r.i = w.i; r.t = w.t; r.tau = w.tau;
+      queue_ray(m, next, n_next, cap, r, sK, t.pc);
+    }
   }
   flush_slab(S.slab, t);
 }
@@ -826,7 +883,18 @@ cudaError_t launch_grid_round(GridModel m, WorkQueue q, GridSlots S, int parity,
   const int g1 = (int)(want < (int64_t)gmax ? want : (int64_t)gmax);
   grid_move_kernel<<<g1, 256, 0, s>>>(m, q, S, parity, d_ktab);
   grid_scatter_kernel<<<gmax, block, 0, s>>>(m, S, parity, d_ktab);
-  grid_ray_kernel<<<gmax, block, 0, s>>>(m, S, parity, d_ktab);
+  grid_ray_kernel<<<gmax, block, 0, s>>>(m, S, parity, 0, d_ktab);
+  return cudaGetLastError();
+}
+
+// After the last round: the rays still in flight (in the next parity's queue) walk to their end.
+cudaError_t launch_grid_ray_drain(GridModel m, GridSlots S, int parity, const float* d_ktab, int block,
+                                  cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int gmax = sms * 8 < kGridSlabBlocks ? sms * 8 : kGridSlabBlocks;
+  grid_ray_kernel<<<gmax, block, 0, s>>>(m, S, parity, 1, d_ktab);
   return cudaGetLastError();
 }
 
@@ -844,11 +912,11 @@ cudaError_t launch_grid_list_live(GridSlots S, cudaStream_t s) {
 // Layout of the slot buffer (each array 256-byte aligned), as grid_slots_carve takes it:
 // 4 arrays of 8-byte entries (anchor, photon id), 18 of 4-byte entries (offsets, face
 // distances, safety distance, direction, frequencies, counters, event, resonant queue), the
-// live flags, 3 n peel rays, the counters and the tally slab.
+// live flags, two queues of kRayCap n peel rays, the counters and the tally slab.
 size_t grid_slots_bytes(int64_t n) {
   auto r = [](size_t b) { return (b + 255) & ~(size_t)255; };
-  return 4 * r((size_t)n * 8) + 18 * r((size_t)n * 4) + r((size_t)n) + r((size_t)3 * n * sizeof(PeelRay)) +
-         r(16 * 8) + r((size_t)kGridSlabBlocks * sizeof(TallySlab));
+  return 4 * r((size_t)n * 8) + 18 * r((size_t)n * 4) + r((size_t)n) +
+         2 * r((size_t)kRayCap * n * sizeof(PeelRay)) + r(16 * 8) + r((size_t)kGridSlabBlocks * sizeof(TallySlab));
 }
 
 GridSlots grid_slots_carve(void* base, int64_t n) {
@@ -867,7 +935,8 @@ GridSlots grid_slots_carve(void* base, int64_t n) {
   S.pid = (unsigned long long*)take(n * 8);
   S.live = (uint8_t*)take(n);
   S.rq = (int32_t*)take(n * 4);
-  S.rays = (PeelRay*)take((size_t)3 * n * sizeof(PeelRay));
+  S.rays[0] = (PeelRay*)take((size_t)kRayCap * n * sizeof(PeelRay));
+  S.rays[1] = (PeelRay*)take((size_t)kRayCap * n * sizeof(PeelRay));
   S.ctr = (unsigned long long*)take(16 * 8);
   S.slab = (TallySlab*)take((size_t)kGridSlabBlocks * sizeof(TallySlab));
   return S;

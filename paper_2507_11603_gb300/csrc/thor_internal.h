@@ -172,10 +172,12 @@ struct GridModel {
 
 // Event-based grid loop: packets in flight, one slot each (SoA, device memory), and the
 // queues between its kernels.
-struct PeelRay {  // a peel-off ray past its first cell (the walk resumes at the next cell)
+struct PeelRay {  // a peel-off ray in flight: its start, frequency, weight and walk state
   double px, py, pz;
+  double t;        // distance from the start to the entry face of cell i
   float Xp, w0, tau;
-  int32_t ax;
+  int32_t ax, i;   // axis, next cell along it
+  int32_t pad;
 };
 struct TallySlab {  // counters of one block index of the event-based loop's kernels
   unsigned long long esc, ab, cap, sc, du, it, stp, dn, pr, pc;
@@ -194,13 +196,15 @@ struct GridSlots {
   unsigned long long* pid;
   uint8_t* live;               // 1 = a packet in flight
   int32_t* rq;                 // slots awaiting a resonant scattering (n entries)
-  PeelRay* rays;               // peel rays past their first cell (3 n entries)
+  PeelRay* rays[2];            // peel rays in flight, per round parity (kRayCap n entries each)
   // [0] packets in flight; [2] entries of the resume list (in rq) and [3] its cursor;
   // round parity r: [4 + 4r] resonant queue length, [5 + 4r] ray queue length
   unsigned long long* ctr;
   TallySlab* slab;             // one entry per block index (kGridSlabBlocks), summed at the end
 };
 constexpr int kGridSlabBlocks = 4096;
+constexpr int kRayCap = 6;       // ray queue entries per slot and parity (3 new per round + carried)
+constexpr int kRayChunk = 32;    // cells a queued ray advances per round
 
 // ---- launchers (implemented in the .cu files) ------------------------------------
 int shell_grid(int block, int blocks_per_sm, bool sliced);  // persistent grid size
@@ -230,6 +234,8 @@ cudaError_t launch_grid_round(GridModel m, WorkQueue q, GridSlots S, int parity,
                               cudaStream_t s);
 cudaError_t launch_grid_list_live(GridSlots S, cudaStream_t s);
 cudaError_t launch_grid_slab_sum(GridModel m, GridSlots S, cudaStream_t s);
+cudaError_t launch_grid_ray_drain(GridModel m, GridSlots S, int parity, const float* d_ktab, int block,
+                                  cudaStream_t s);
 cudaError_t launch_grid_resume(GridModel m, WorkQueue q, GridSlots S, const float* d_ktab, int grid, int block,
                                cudaStream_t s);
 size_t grid_slots_bytes(int64_t n);

@@ -27,8 +27,9 @@ def ctx():
 
 def _fields(kind):
     from paper_2507_11603_gb300 import synth
-    if kind == "thin":  # optically thin cells with dusty gas: cell walks, escapes and dust events
-        f = synth.grid_fields(n=16, seed=3, mean_nHI=2e-7, sigma_ln=1.0, sigma_v=50.0, dust_ratio=1.0,
+    if kind in ("thin", "thin64"):  # optically thin cells with dusty gas: cell walks, escapes, dust
+        n = 16 if kind == "thin" else 64  # 64 cells: peel rays walk longer than one round's chunk
+        f = synth.grid_fields(n=n, seed=3, mean_nHI=2e-7 * 16 / n, sigma_ln=1.0, sigma_v=50.0, dust_ratio=1.0,
                               sigma_dust=4e-22)
         f["kd"] = (f["kd"] * 2e4).astype(np.float32)
     else:  # the config-4 recipe on 32^3: tau0 ~ 1.8e4 per cell, the in-cell fast path
@@ -68,6 +69,7 @@ def _assert_same(r0, r1):
     ("thin", 3000, 1000, 0, 0),       # slot count not a multiple of a warp or block; all in rounds
     ("thin", 100, 8192, 0, 0),        # fewer photons than slots
     ("thick", 3000, 2048, 256, 2000),  # thick cells (fast path), scattering cap
+    ("thin64", 20000, 4096, 512, 0),  # peel rays carried over several rounds
 ])
 def test_event_based_grid_loop_identical(ctx, kind, n, slots, handoff, cap):
     f = _fields(kind)
@@ -78,7 +80,7 @@ def test_event_based_grid_loop_identical(ctx, kind, n, slots, handoff, cap):
     r1 = _run(ctx, g, slots, handoff, **kw)
     assert r1.stats["n_escaped"] + r1.stats["n_absorbed"] + r1.stats["n_capped"] == n
     assert r1.stats["n_peel_rays"] > 0
-    if kind == "thin" and n >= 3000:
+    if kind.startswith("thin") and n >= 3000:
         assert r1.stats["n_dust_scat"] > 0
     if cap:
         assert r1.stats["n_capped"] > 0
