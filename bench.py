@@ -190,7 +190,9 @@ def run_shell_bench(args):
     if args.block:
         ctx.set_launch(args.block, args.blocks_per_sm)
     if args.pipe_lanes >= 0 or args.burst_lanes >= 0:
-        ctx.set_bursts(args.pipe_lanes if args.pipe_lanes >= 0 else 32, args.burst_lanes if args.burst_lanes >= 0 else 4)
+        ctx.set_bursts(args.pipe_lanes if args.pipe_lanes >= 0 else 32, args.burst_lanes if args.burst_lanes >= 0 else 1)
+    if args.no_tail_share:
+        ctx.set_tail_share(False)
     stream = torch.cuda.Stream()
     ctx.set_stream(stream)
     geom = ctx.shell(**SHELL)
@@ -296,7 +298,8 @@ def run_shell_bench(args):
                    "scatterings_per_step": n_scat / args.steps, "kernel_ms_per_step": kern_avg_ms,
                    "launch": {"block": args.block or 128, "blocks_per_sm": args.blocks_per_sm,
                               "pipelined_event_lanes": args.pipe_lanes if args.pipe_lanes >= 0 else 32,
-                              "core_burst_lanes": args.burst_lanes if args.burst_lanes >= 0 else 4}},
+                              "core_burst_lanes": args.burst_lanes if args.burst_lanes >= 0 else 1,
+                              "tail_work_sharing": not args.no_tail_share}},
         "e2e": {"value": e2e_value, "unit": "scatterings/s", "h2d_bytes_per_step": 256 + 48,
                 "d2h_bytes_per_step": (RUN["n_bins"] + 2) * 8 + 96, "steps": n_e2e,
                 "photon_ids": f"those of the first {n_e2e} timed steps",
@@ -665,6 +668,8 @@ def main():
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--pipe-lanes", type=int, default=-1,
                     help="pipelined events in warps with at most this many live packets (-1 = library default)")
+    ap.add_argument("--no-tail-share", action="store_true",
+                    help="shell workload: no work sharing in the tail of the one-launch run")
     ap.add_argument("--burst-lanes", type=int, default=-1,
                     help="core bursts in warps with at most this many live packets (-1 = library default)")
     ap.add_argument("--blocks-per-sm", type=int, default=0)

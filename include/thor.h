@@ -97,6 +97,13 @@ int thor_ctx_set_tail(thor_ctx_t ctx, int spill_below, int max_phases);
  * exactly as the general event does, so results do not depend on these settings (only the
  * time to reach them does). */
 int thor_ctx_set_bursts(thor_ctx_t ctx, int pipe_lanes, int burst_lanes);
+/* Work sharing in the tail of a one-launch gridless run (share 1, the default; 0 = off).
+ * Once no new photons are left, a warp whose packets have all finished waits (sleeping)
+ * for a packet that a warp with several live packets gives away, and runs it alone, so
+ * the longest histories of a run run at a lone lane's latency as soon as there is room.
+ * Packets move with their complete state (as tail compaction saves them), so results do
+ * not depend on this setting.  Applies when tail compaction is off (thor_ctx_set_tail). */
+int thor_ctx_set_tail_share(thor_ctx_t ctx, int share);
 /* Event-based execution of the grid photon loop (the propagate / interact split that
  * Sec. 7.2.2 proposes against divergence).  With slots > 0, thor_run on a grid keeps up to
  * `slots` packets in device memory and advances all of them one event per round, in three

@@ -50,7 +50,7 @@ void* thor_ctx::scratch(Buf& b, size_t bytes) {
 thor_ctx::~thor_ctx() {
   cudaSetDevice(device);
   for (Buf* b : {&b_models, &b_tally, &b_queue, &b_spec, &b_cube, &b_raw, &b_raw2, &b_diag, &b_stats, &b_spill, &b_cmp,
-                 &b_stage[0], &b_stage[1], &b_gslots})
+                 &b_stage[0], &b_stage[1], &b_gslots, &b_share})
     if (b->p) cudaFree(b->p);
   for (cudaEvent_t e : {ev_copied[0], ev_copied[1], ev_done[0], ev_done[1]})
     if (e) cudaEventDestroy(e);
@@ -121,6 +121,13 @@ extern "C" int thor_ctx_set_bursts(thor_ctx_t ctx, int pipe_lanes, int burst_lan
     return ctx->fail(THOR_ERR_INVALID_ARG, "thor_ctx_set_bursts: pipe_lanes and burst_lanes in [0, 32]");
   ctx->core_lanes = pipe_lanes;
   ctx->burst_lanes = burst_lanes;
+  return THOR_OK;
+}
+
+extern "C" int thor_ctx_set_tail_share(thor_ctx_t ctx, int share) {
+  if (!ctx) return THOR_ERR_INVALID_ARG;
+  if (share != 0 && share != 1) return ctx->fail(THOR_ERR_INVALID_ARG, "thor_ctx_set_tail_share: share must be 0 or 1");
+  ctx->share_tail = share;
   return THOR_OK;
 }
 
@@ -577,11 +584,54 @@ extern "C" int thor_run(thor_ctx_t ctx, thor_geom_t g, const thor_source* src, u
     const unsigned long long pw0 = (n_photons + warps0 - 1) / warps0;
     const int per_warp0 = (int)(pw0 < 1 ? 1 : (pw0 > 32 ? 32 : pw0));
     if (ctx->spill_below <= 0) {
+      // work sharing in the tail: a pool of one record per photon, its ready flags, counters
+      Compact sh{};
+      const bool share = ctx->share_tail != 0;
+      if (share) {
+        auto r256 = [](size_t b) { return (b + 255) & ~(size_t)255; };
+        const size_t b_pool = r256((size_t)n_photons * sizeof(PhotonRec)), b_ready = r256((size_t)n_photons * 4);
+        char* sb = (char*)ctx->scratch(ctx->b_share, b_pool + b_ready + 64);
+        if (!sb) return ctx->fail(THOR_ERR_OOM, "tail work-sharing pool");
+        sh.pool = (PhotonRec*)sb;
+        sh.ready = (uint32_t*)(sb + b_pool);
+        sh.share = (unsigned long long*)(sb + b_pool + b_ready);
+        sh.n_total = n_photons;
+        if ((rc = ctx->cuda(cudaMemsetAsync(sh.ready, 0, b_ready + 64, s), "clear sharing pool"))) return rc;
+      }
       cudaEventRecord(ctx->ev0, s);
       rc = ctx->cuda(launch_shell_run(d_m, q, ctx->d_ktab, gsz, ctx->block, m.profile, per_warp0, ctx->core_lanes,
-                                      ctx->burst_lanes, s),
+                                      ctx->burst_lanes, s, share ? &sh : nullptr),
                      "shell photon loop");
       ++n_launch;
+      if (!rc && share) {
+        // packets left in the pool (every waiting warp gave up first) finish in a relaunch
+        unsigned long long h[5];
+        if ((rc = ctx->cuda(cudaMemcpyAsync(h, sh.share, sizeof h, cudaMemcpyDeviceToHost, s), "sharing counters")))
+          return rc;
+        if ((rc = ctx->cuda(cudaStreamSynchronize(s), "shell photon loop"))) return rc;
+        if (h[4]) return ctx->fail(THOR_ERR_DEVICE, "tail work sharing: a packet given away was never written");
+        if (h[1] < h[0]) {
+          unsigned long long* ctr = (unsigned long long*)ctx->scratch(ctx->b_cmp, 4 * sizeof(unsigned long long));
+          if (!ctr) return ctx->fail(THOR_ERR_OOM, "resume counters");
+          if ((rc = ctx->cuda(cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned long long), s), "clear counters"))) return rc;
+          Compact c{};
+          c.resume = sh.pool + h[1];
+          c.n_resume = h[0] - h[1];
+          c.resume_next = ctr;
+          c.spill = nullptr;
+          c.n_spill = ctr + 1;
+          c.spill_below = 0;
+          c.per_warp = 1;
+          c.core_lanes = ctx->core_lanes;
+          c.burst_lanes = ctx->burst_lanes;
+          const unsigned long long want = (c.n_resume * 32 + ctx->block - 1) / ctx->block;
+          const int g = (int)(want < (unsigned long long)gsz ? want : gsz);
+          if ((rc = ctx->cuda(launch_shell_run_compact(d_m, q, c, ctx->d_ktab, g, ctx->block, m.profile, s),
+                              "shell photon loop (pool)")))
+            return rc;
+          ++n_launch;
+        }
+      }
       cudaEventRecord(ctx->ev1, s);
     } else {
       // Tail compaction: launch, then relaunch over the saved survivors until none are

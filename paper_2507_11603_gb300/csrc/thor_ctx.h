@@ -34,6 +34,8 @@ struct thor_ctx {
   int final_below = 256;    // run to completion once this few packets are left
   int core_lanes = 32;      // warps with at most this many live packets run pipelined events (0 = never)
   int burst_lanes = 1;      // ... and, with at most this many, core bursts (0 = never)
+  int share_tail = 1;       // work sharing in the tail of a one-launch shell run
+  Buf b_share;
   // event-based grid loop (0 slots = the one-kernel loop throughout)
   int64_t grid_slots = 0;
   int64_t grid_handoff = 0;  // packets in flight at which the tail goes to the one-kernel loop

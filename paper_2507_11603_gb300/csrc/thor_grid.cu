@@ -165,6 +165,43 @@ struct PeelWalk {
   double t;  // distance from the ray's start to that cell's entry face
   float tau;
 };
+struct WalkOut {
+  PeelWalk w;
+  uint32_t cells;  // cells walked
+  bool done;
+};
+// Kept out of line: every peel-off site (emission, dust and resonant scatterings, the ray
+// kernel) calls this one copy, which keeps the photon loop's code within the instruction
+// cache.  c: the index of cell w.i; pa: the start's coordinate along the axis.
+__device__ __noinline__ WalkOut peel_walk_cells(const GridCell* __restrict__ cells, int n_ax, int64_t stride,
+                                                int64_t c, double pa, float Xp, int axis, float tau_cut,
+                                                const float* __restrict__ Ktab, PeelWalk w, int max_cells) {
+  WalkOut o;
+  o.cells = 0;
+  o.done = false;
+  const int end = (max_cells > 0 && w.i + max_cells < n_ax) ? w.i + max_cells : n_ax;
+  while (w.i < end && !o.done) {
+    GridCell g[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) g[k] = load_cell(cells, c + (int64_t)min(k, end - 1 - w.i) * stride);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (w.i >= end || o.done) break;
+      const double tn = __dadd_rn((double)(w.i + 1), -pa);
+      const float v = (axis == 0) ? g[k].vx : (axis == 1) ? g[k].vy : g[k].vz;
+      const float x = (Xp - v) * g[k].inv_vth;
+      w.tau = __fmaf_rn(__fmaf_rn(g[k].kap0, voigt<false>(g[k].a, x, Ktab), g[k].kd), (float)(tn - w.t), w.tau);
+      ++o.cells;
+      ++w.i;
+      c += stride;
+      if (w.tau > tau_cut) o.done = true;
+      else w.t = tn;
+    }
+  }
+  o.done = o.done || w.i >= n_ax;
+  o.w = w;
+  return o;
+}
 __device__ __forceinline__ bool peel_walk(const GridModel& m, const double p[3], int axis, float Xp,
                                           const float* Ktab, uint32_t& ncell, PeelWalk& w, int max_cells) {
   const int ix = (int)floor(p[0]), iy = (int)floor(p[1]), iz = (int)floor(p[2]);
@@ -172,27 +209,11 @@ __device__ __forceinline__ bool peel_walk(const GridModel& m, const double p[3],
   const int ia = (axis == 0) ? ix : (axis == 1) ? iy : iz;
   const double pa = (axis == 0) ? p[0] : (axis == 1) ? p[1] : p[2];
   const int64_t stride = (axis == 0) ? 1 : (axis == 1) ? (int64_t)m.nx : (int64_t)m.nx * m.ny;
-  int64_t c = cell_index(m, ix, iy, iz) + (int64_t)(w.i - ia) * stride;
-  const int end = (max_cells > 0 && w.i + max_cells < n_ax) ? w.i + max_cells : n_ax;
-  while (w.i < end) {
-    GridCell g[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) g[k] = load_cell(m.cells, c + (int64_t)min(k, end - 1 - w.i) * stride);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      if (w.i >= end) break;
-      const double tn = __dadd_rn((double)(w.i + 1), -pa);
-      const float v = (axis == 0) ? g[k].vx : (axis == 1) ? g[k].vy : g[k].vz;
-      const float x = (Xp - v) * g[k].inv_vth;
-      w.tau = __fmaf_rn(__fmaf_rn(g[k].kap0, voigt<false>(g[k].a, x, Ktab), g[k].kd), (float)(tn - w.t), w.tau);
-      ++ncell;
-      ++w.i;
-      c += stride;
-      if (w.tau > m.tau_cut) return true;
-      w.t = tn;
-    }
-  }
-  return w.i >= n_ax;
+  const int64_t c = cell_index(m, ix, iy, iz) + (int64_t)(w.i - ia) * stride;
+  const WalkOut o = peel_walk_cells(m.cells, n_ax, stride, c, pa, Xp, axis, m.tau_cut, Ktab, w, max_cells);
+  w = o.w;
+  ncell += o.cells;
+  return o.done;
 }
 // Optical depth from p to the box face along +axis at lab frequency Xp (Sec. 3.4.1); the
 // first `skip` cells (0 or 1) are already in tau0.

@@ -113,6 +113,14 @@ struct Compact {
   int32_t per_warp;     // lanes per warp that take packets (1..32): few packets spread over all schedulers
   int32_t core_lanes;   // warps with at most this many live packets run pipelined events (0 = never)
   int32_t burst_lanes;  // ... and, with at most this many, core bursts (0 = never)
+  // Work sharing in the tail of a one-launch run (pool = NULL: off).  Once the queue is
+  // drained, a warp whose lanes are all done waits for a packet that a warp with several
+  // live packets gives away, and runs it alone.
+  PhotonRec* pool;              // given-away packets (one entry per photon at most)
+  uint32_t* ready;              // pool entry i written (1), set after the record
+  unsigned long long* share;    // [0] entries reserved, [1] taken, [2] empty warps waiting,
+                                // [3] photons finished, [4] a taken entry never became ready
+  unsigned long long n_total;   // photons of the run
 };
 
 // Resident packet state for time-sliced (served) execution, SoA, one slot per thread.
@@ -210,7 +218,8 @@ constexpr int kRayChunk = 32;    // cells a queued ray advances per round
 int shell_grid(int block, int blocks_per_sm, bool sliced);  // persistent grid size
 int grid_grid(int block, int blocks_per_sm);
 cudaError_t launch_shell_run(const ShellModel* d_models, WorkQueue q, const float* d_ktab, int grid,
-                             int block, int profile, int per_warp, int core_lanes, int burst_lanes, cudaStream_t s);
+                             int block, int profile, int per_warp, int core_lanes, int burst_lanes, cudaStream_t s,
+                             const Compact* share = nullptr);
 cudaError_t launch_shell_run_compact(const ShellModel* d_models, WorkQueue q, Compact c, const float* d_ktab,
                                      int grid, int block, int profile, cudaStream_t s);
 cudaError_t launch_reweight(int64_t n, const float* X0, const float* X, const float* col, const uint8_t* status,

@@ -715,6 +715,41 @@ __device__ __forceinline__ void load_rec(const ShellModel& m, const PhotonRec& r
   ph.rng.event = r.event;
 }
 
+// ---- work sharing in the tail of a one-launch run -----------------------------------------
+// Lane 0 of a warp whose lanes are all done (queue drained) waits for a given-away packet:
+// takes the next pool entry (compare-and-swap on the taken counter), or gives up once every
+// photon of the run has finished or after kPollMax polls (a packet still in the pool then is
+// resumed by the host).  Between polls it sleeps, backing off to 32 us, so that a thousand
+// waiting warps load the counters' cache lines little.  Returns the pool index, or -1.
+constexpr uint32_t kPollMax = 1u << 24;
+constexpr uint32_t kShareEvents = 512;  // a warp with several live packets checks for waiting warps this often
+__device__ __forceinline__ unsigned long long vload(const unsigned long long* p) {
+  return *(volatile const unsigned long long*)p;
+}
+__device__ long long share_take(const Compact& c) {
+  atomicAdd(&c.share[2], 1ull);
+  long long got = -1;
+  unsigned ns = 64;
+  for (uint32_t it = 0; it < kPollMax; ++it) {
+    const unsigned long long t = vload(&c.share[1]), n = vload(&c.share[0]);
+    if (t < n) {
+      if (atomicCAS(&c.share[1], t, t + 1ull) == t) { got = (long long)t; break; }
+      continue;
+    }
+    if (vload(&c.share[3]) >= c.n_total) break;
+    __nanosleep(ns);
+    ns = ns < 32768u ? 2u * ns : 32768u;
+  }
+  atomicAdd(&c.share[2], ~0ull);  // -1
+  if (got >= 0) {  // the giver writes the record, then the flag: wait for the flag (short)
+    uint32_t it = 0;
+    while (*(volatile const uint32_t*)&c.ready[got] == 0u && ++it < kPollMax) __nanosleep(32);
+    if (it >= kPollMax) { atomicAdd(&c.share[4], 1ull); return -1; }
+    __threadfence();
+  }
+  return got;
+}
+
 // Run-to-completion: all queue entries belong to one model (thor_run).  With kCompact,
 // lanes first resume saved packets, and a warp whose sources are empty and whose live
 // lanes drop below c.spill_below saves them and exits (tail compaction across launches).
@@ -781,10 +816,49 @@ __global__ void __launch_bounds__(256, 1) shell_run_kernel(const ShellModel* __r
         break;
       }
     }
+    if (c.pool && drained) {
+      const unsigned live = __ballot_sync(kFull, active);
+      if (live == 0u) {  // an empty warp: take a packet that a crowded warp gives away
+        long long got = -1;
+        if (lane == 0) got = share_take(c);
+        got = __shfl_sync(kFull, got, 0);
+        if (got < 0) break;
+        if (lane == 0) { load_rec(m, c.pool[got], ph); active = true; prepared = false; }
+        continue;
+      }
+      if (__popc(live) >= 2) {  // give packets away while empty warps wait, keeping the lowest lane's
+        const int leader = __ffs(live) - 1;
+        long long give = 0;
+        if ((int)lane == leader) {
+          const long long waiting = (long long)vload(&c.share[2]) -
+                                    (long long)(vload(&c.share[0]) - vload(&c.share[1]));
+          give = min((long long)(__popc(live) - 1), waiting);
+        }
+        give = __shfl_sync(kFull, give, leader);
+        if (give > 0) {
+          // the `give` highest live lanes: their rank from the top
+          const int from_top = __popc(live & ~((2u << lane) - 1u));
+          const bool giver = active && from_top < (int)give;
+          unsigned long long base = 0;
+          if ((int)lane == leader) base = atomicAdd(&c.share[0], (unsigned long long)give);
+          base = __shfl_sync(kFull, base, leader);
+          if (giver) {
+            const unsigned long long j = base + (unsigned long long)from_top;
+            if (prepared) { pipe_unprepare(ph); prepared = false; }
+            save_rec(ph, c.pool[j]);
+            __threadfence();
+            *(volatile uint32_t*)&c.ready[j] = 1u;
+            active = false;
+          }
+        }
+      }
+    }
     if (__all_sync(kFull, !active)) break;
     // pipelined events in warps with at most core_lanes live packets (homologous shells),
     // and core bursts in warps with at most burst_lanes
     const int n_live = __popc(__ballot_sync(kFull, active));
+    const bool check_share = c.pool && drained && n_live >= 2;
+    uint32_t n_ev = 0;
     const bool pipe = kProfile == 0 && n_live <= c.core_lanes;
     const bool burst = pipe && n_live <= c.burst_lanes;
     // events until some lane of the warp finishes its packet: one vote per event, the
@@ -813,11 +887,12 @@ __global__ void __launch_bounds__(256, 1) shell_run_kernel(const ShellModel* __r
           lt.scat += ph.nscat; lt.dust += ph.ndust; lt.iters += ph.iters; lt.steps += ph.steps; ++lt.done;
           lt.scat2 += (double)ph.nscat * (double)ph.nscat;
           write_raw(m, ph, st);
+          if (c.pool) atomicAdd(&c.share[3], 1ull);
           active = false;
           fin = true;
         }
       }
-    } while (!__any_sync(kFull, fin));
+    } while (!__any_sync(kFull, fin) && !(check_share && ++n_ev >= kShareEvents));
   }
   // flush lane tallies: warp reduce, one atomic per warp and field
   const unsigned long long e = warp_sum(lt.esc), a = warp_sum(lt.abs), cp = warp_sum(lt.cap),
@@ -1075,8 +1150,15 @@ int shell_grid(int block, int blocks_per_sm, bool sliced) {
 }
 
 cudaError_t launch_shell_run(const ShellModel* d_models, WorkQueue q, const float* d_ktab, int grid, int block,
-                             int profile, int per_warp, int core_lanes, int burst_lanes, cudaStream_t s) {
+                             int profile, int per_warp, int core_lanes, int burst_lanes, cudaStream_t s,
+                             const Compact* share) {
   Compact none{};
+  if (share) {  // the work-sharing fields
+    none.pool = share->pool;
+    none.ready = share->ready;
+    none.share = share->share;
+    none.n_total = share->n_total;
+  }
   none.per_warp = per_warp;
   none.core_lanes = core_lanes;
   none.burst_lanes = burst_lanes;

@@ -30,7 +30,7 @@ SYMBOLS = [
     "thor_server_wait", "thor_server_cancel", "thor_server_stats", "thor_server_destroy", "thor_voigt_eval",
     "thor_dda_trace", "thor_sample_upar", "thor_scatter_once", "thor_philox", "thor_line_params",
     "thor_run_shell_noalloc", "thor_noalloc_last_error", "thor_reweight", "thor_xcw_eval", "thor_ctx_set_bursts",
-    "thor_issue_peak", "thor_ctx_set_grid_exec",
+    "thor_issue_peak", "thor_ctx_set_grid_exec", "thor_ctx_set_tail_share",
 ]
 PROFILE = {"homologous": 0, "power_law": 1}
 SPECIES = {"HI": 0, "MgII": 1}
@@ -110,6 +110,7 @@ def load(build: bool = True) -> C.CDLL:
             "thor_ctx_set_tail": ([vp, C.c_int, C.c_int], C.c_int),
             "thor_ctx_set_bursts": ([vp, C.c_int, C.c_int], C.c_int),
             "thor_ctx_set_grid_exec": ([vp, C.c_int64, C.c_int64], C.c_int),
+            "thor_ctx_set_tail_share": ([vp, C.c_int], C.c_int),
             "thor_shell_create": ([vp, P(ShellParams), P(vp)], C.c_int),
             "thor_grid_create": ([vp, vp, vp, vp, vp, P(i32), dbl, C.c_int, P(vp)], C.c_int),
             "thor_grid_set_scattering": ([vp, C.c_int, dbl, dbl], C.c_int),
@@ -291,6 +292,11 @@ class Context:
         if handoff is None:
             handoff = slots // 8
         self._check(self.L.thor_ctx_set_grid_exec(self.h, int(slots), int(handoff)))
+
+    def set_tail_share(self, share: bool = True):
+        """thor_ctx_set_tail_share: work sharing in the tail of a one-launch shell run (on by
+        default); results do not depend on it."""
+        self._check(self.L.thor_ctx_set_tail_share(self.h, 1 if share else 0))
 
     def set_tail(self, spill_below: int = 0, max_phases: int = 24):
         """thor_ctx_set_tail: tail compaction of the shell photon loop (0 = off, the library's

@@ -336,6 +336,29 @@ def test_core_bursts_do_not_change_results(ctx, geo):
             assert a.stats[k] == b.stats[k], k
 
 
+@pytest.mark.parametrize("geo,n", [(dict(R_in=0.9, N_HI=3e19, T=1e4, v_max=200.0, tau_dust=0.5, phase="dipole"), 30000),
+                                   (dict(tau0=1e5, T=1e4, phase="isotropic"), 5000)])
+def test_tail_share_does_not_change_results(ctx, geo, n):
+    """Work sharing in the tail moves packets, with their complete state, from warps with
+    several live packets to warps that ran dry: per-photon records and every tally are
+    bit-identical with it on and off (a dusty outflowing shell whose core-trapped photons
+    crowd the tail; a static sphere, fewer photons than lanes)."""
+    g = ctx.shell(**geo)
+    kw = dict(n_photons=n, seed=29, sigma=50.0 if "N_HI" in geo else 0.0, n_bins=200, X_min=-1500.0,
+              X_max=1500.0, raw=True)
+    ctx.set_tail_share(False)
+    a = ctx.run(g, **kw)
+    ctx.set_tail_share(True)
+    b = ctx.run(g, **kw)
+    assert a.stats["n_scat"] > 1e6
+    assert np.array_equal(a.spectrum, b.spectrum)
+    assert np.array_equal(np.asarray(a.raw_X).view(np.uint32), np.asarray(b.raw_X).view(np.uint32))
+    assert np.array_equal(np.asarray(a.raw_nscat), np.asarray(b.raw_nscat))
+    assert np.array_equal(np.asarray(a.raw_status), np.asarray(b.raw_status))
+    for k in ("n_escaped", "n_absorbed", "n_capped", "n_scat", "n_dust_scat", "n_upar_iters", "n_steps", "sum_scat2"):
+        assert a.stats[k] == b.stats[k], k
+
+
 def test_tail_compaction_does_not_change_results(ctx):
     """Tail compaction re-packs survivors between launches; every photon's history is
     keyed by its id, so the tallies must be bit-identical with it on and off."""
