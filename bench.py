@@ -440,6 +440,8 @@ def run_probe(args):
     tail of the shell run."""
     from paper_2507_11603_gb300 import thor
     ctx = thor.Context(0)
+    if args.no_tail_share:
+        ctx.set_tail_share(False)
     n = args.probe_photons
     first = args.probe_first_id
     if first < 0 and args.probe_model == "shell":

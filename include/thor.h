@@ -102,7 +102,8 @@ int thor_ctx_set_bursts(thor_ctx_t ctx, int pipe_lanes, int burst_lanes);
  * for a packet that a warp with several live packets gives away, and runs it alone, so
  * the longest histories of a run run at a lone lane's latency as soon as there is room.
  * Packets move with their complete state (as tail compaction saves them), so results do
- * not depend on this setting.  Applies when tail compaction is off (thor_ctx_set_tail). */
+ * not depend on this setting.  Applies when tail compaction is off (thor_ctx_set_tail) and
+ * the run has more photons than the launch has warps (otherwise each photon has a warp). */
 int thor_ctx_set_tail_share(thor_ctx_t ctx, int share);
 /* Event-based execution of the grid photon loop (the propagate / interact split that
  * Sec. 7.2.2 proposes against divergence).  With slots > 0, thor_run on a grid keeps up to

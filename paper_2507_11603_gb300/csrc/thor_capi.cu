@@ -586,7 +586,7 @@ extern "C" int thor_run(thor_ctx_t ctx, thor_geom_t g, const thor_source* src, u
     if (ctx->spill_below <= 0) {
       // work sharing in the tail: a pool of one record per photon, its ready flags, counters
       Compact sh{};
-      const bool share = ctx->share_tail != 0;
+      const bool share = ctx->share_tail != 0 && n_photons > warps0;  // else every photon has a warp already
       if (share) {
         auto r256 = [](size_t b) { return (b + 255) & ~(size_t)255; };
         const size_t b_pool = r256((size_t)n_photons * sizeof(PhotonRec)), b_ready = r256((size_t)n_photons * 4);
@@ -651,7 +651,7 @@ extern "C" int thor_run(thor_ctx_t ctx, thor_geom_t g, const thor_source* src, u
       for (int phase = 0;; ++phase) {
         const bool last = phase + 1 >= ctx->max_phases || (phase > 0 && n_in <= (unsigned long long)ctx->final_below);
         if ((rc = ctx->cuda(cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned long long), s), "clear counters"))) break;
-        Compact c;
+        Compact c{};
         c.resume = in;
         c.n_resume = n_in;
         c.resume_next = ctr;

@@ -103,24 +103,24 @@ struct PhotonRec {
 // lanes saves them to `spill` and exits, and the next launch repacks the survivors
 // `per_warp` to a warp.  Also carries per_warp for the first launch (few photons spread
 // over all warps).
-struct Compact {
-  const PhotonRec* resume;
-  unsigned long long n_resume;
-  unsigned long long* resume_next;
-  PhotonRec* spill;
-  unsigned long long* n_spill;
-  int32_t spill_below;  // 0: run to completion
-  int32_t per_warp;     // lanes per warp that take packets (1..32): few packets spread over all schedulers
-  int32_t core_lanes;   // warps with at most this many live packets run pipelined events (0 = never)
-  int32_t burst_lanes;  // ... and, with at most this many, core bursts (0 = never)
+struct Compact {  // every field defaults to off / empty
+  const PhotonRec* resume = nullptr;
+  unsigned long long n_resume = 0;
+  unsigned long long* resume_next = nullptr;
+  PhotonRec* spill = nullptr;
+  unsigned long long* n_spill = nullptr;
+  int32_t spill_below = 0;  // 0: run to completion
+  int32_t per_warp = 32;    // lanes per warp that take packets (1..32): few packets spread over all schedulers
+  int32_t core_lanes = 32;  // warps with at most this many live packets run pipelined events (0 = never)
+  int32_t burst_lanes = 1;  // ... and, with at most this many, core bursts (0 = never)
   // Work sharing in the tail of a one-launch run (pool = NULL: off).  Once the queue is
   // drained, a warp whose lanes are all done waits for a packet that a warp with several
   // live packets gives away, and runs it alone.
-  PhotonRec* pool;              // given-away packets (one entry per photon at most)
-  uint32_t* ready;              // pool entry i written (1), set after the record
-  unsigned long long* share;    // [0] entries reserved, [1] taken, [2] empty warps waiting,
-                                // [3] photons finished, [4] a taken entry never became ready
-  unsigned long long n_total;   // photons of the run
+  PhotonRec* pool = nullptr;            // given-away packets (one entry per photon at most)
+  uint32_t* ready = nullptr;            // pool entry i written (1), set after the record
+  unsigned long long* share = nullptr;  // [0] entries reserved, [1] taken, [2] empty warps waiting,
+                                        // [3] photons finished, [4] a taken entry never became ready
+  unsigned long long n_total = 0;       // photons of the run
 };
 
 // Resident packet state for time-sliced (served) execution, SoA, one slot per thread.
