@@ -314,6 +314,9 @@ def run_shell_bench(args):
                      "simt_efficiency": simt,
                      "lane_frac": lane_achieved / (32.0 * peak_issue),
                      "lane_per_unit": f"{thread_inst_per_scat:g} thread instructions per scattering (ncu)",
+                     "lane_note": "the idle lanes of a cooperative burst form Philox blocks and evaluate throw-away "
+                                  "events; their instructions count as executed, so the lane figures overstate "
+                                  "useful lane work",
                      "tail": {"longest_photon_events": [c for c, _ in longest],
                               "lone_event_us": us_per_event, "lone_events_timed": lone_events,
                               "tail_frac": tail_frac,
@@ -675,12 +678,14 @@ def main():
     ap.add_argument("--burst-lanes", type=int, default=-1,
                     help="core bursts in warps with at most this many live packets (-1 = library default)")
     ap.add_argument("--blocks-per-sm", type=int, default=0)
-    ap.add_argument("--inst-per-scat", type=float, default=374.0,
-                    help="warp instructions per scattering of the shell photon loop (ncu, bench workload)")
-    ap.add_argument("--thread-inst-per-scat", type=float, default=702.0,
-                    help="thread instructions per scattering of the shell photon loop (ncu, bench workload)")
-    ap.add_argument("--launch-dram-bytes", type=float, default=858112.0,
-                    help="DRAM bytes read + written by one bench launch of the shell kernel (ncu)")
+    ap.add_argument("--inst-per-scat", type=float, default=365.0,
+                    help="warp instructions per scattering of the shell photon loop (ncu, photons 0..19999 of the "
+                         "bench workload)")
+    ap.add_argument("--thread-inst-per-scat", type=float, default=9276.0,
+                    help="thread instructions per scattering of the shell photon loop (ncu, same capture)")
+    ap.add_argument("--launch-dram-bytes", type=float, default=974592.0,
+                    help="DRAM bytes read + written by one launch of the shell kernel (ncu, same capture; fixed per "
+                         "launch: code, constants, tables)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
