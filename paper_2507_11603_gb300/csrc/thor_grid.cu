@@ -160,6 +160,11 @@ __device__ __forceinline__ int64_t cell_index(const GridModel& m, int ix, int iy
 // memory once per four cells; the optical depth is summed in the same order as one at a
 // time.  Walks at most max_cells cells (all when max_cells <= 0).  Returns true when the walk
 // is over (tau > tau_cut, or the box face reached).
+// H(a, x) for the peel-off rays, out of line: the six first-cell segments of a scattering's
+// rays and the walk share one copy (the photon's own steps keep theirs inline).
+__device__ __noinline__ float peel_voigt(float a, float x, const float* __restrict__ Ktab) {
+  return voigt<false>(a, x, Ktab);
+}
 struct PeelWalk {
   int i;     // next cell along the axis
   double t;  // distance from the ray's start to that cell's entry face
@@ -190,7 +195,7 @@ __device__ __noinline__ WalkOut peel_walk_cells(const GridCell* __restrict__ cel
       const double tn = __dadd_rn((double)(w.i + 1), -pa);
       const float v = (axis == 0) ? g[k].vx : (axis == 1) ? g[k].vy : g[k].vz;
       const float x = (Xp - v) * g[k].inv_vth;
-      w.tau = __fmaf_rn(__fmaf_rn(g[k].kap0, voigt<false>(g[k].a, x, Ktab), g[k].kd), (float)(tn - w.t), w.tau);
+      w.tau = __fmaf_rn(__fmaf_rn(g[k].kap0, peel_voigt(g[k].a, x, Ktab), g[k].kd), (float)(tn - w.t), w.tau);
       ++o.cells;
       ++w.i;
       c += stride;
@@ -305,7 +310,7 @@ __device__ __forceinline__ void peel_from_cell(const GridModel& m, const GPhoton
   const float v = (ax == 0) ? g.vx : (ax == 1) ? g.vy : g.vz;
   const float x = (Xp - v) * g.inv_vth;
   const float d = (ax == 0) ? ph.fhi[0] - ph.o[0] : (ax == 1) ? ph.fhi[1] - ph.o[1] : ph.fhi[2] - ph.o[2];
-  float tau = __fmaf_rn(g.kap0, voigt<false>(g.a, x, Ktab), g.kd) * fmaxf(d, 0.0f);
+  float tau = __fmaf_rn(g.kap0, peel_voigt(g.a, x, Ktab), g.kd) * fmaxf(d, 0.0f);
   ++pr;
   ++pc;
   if (tau > m.tau_cut) return;  // blocked inside the current cell: no FP64, no gather
@@ -631,7 +636,7 @@ __global__ void grid_slab_sum_kernel(GridModel m, GridSlots S) {
 // refilled from the photon queue (warp-aggregated).  kResume: lanes first take the packets
 // on the resume list of S (the tail handed over by the event-based loop).
 template <bool kResume>
-__global__ void __launch_bounds__(256) grid_run_kernel(GridModel m, WorkQueue q, const float* __restrict__ gK,
+__global__ void __launch_bounds__(256, 2) grid_run_kernel(GridModel m, WorkQueue q, const float* __restrict__ gK,
                                                        GridSlots S) {
   __shared__ __align__(16) float sK[THOR_VOIGT_NINT * THOR_VOIGT_NCOEF];
   load_ktab(sK, gK);
