@@ -388,6 +388,7 @@ extern "C" int thor_server_create(thor_ctx_t ctx, const thor_server_config* cfg,
       cap = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
       if (!cap) break;
       cudaMemcpyAsync(s->d_queue, s->h_queue, L.bytes, cudaMemcpyHostToDevice, cs);
+      cudaMemsetAsync(&s->st_in.live[4], 0, 8, cs);  // regular warps done this round
       launch_shell_slice(s->d_models, wq, s->st_in, s->st_out, (uint32_t)s->cfg.events_per_round, ctx->d_ktab,
                          s->grid, s->block, v == 1, cs);
       // the survivors become the next round's list: sorted by frequency bucket (pre-sorting),

@@ -18,7 +18,8 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kServedPipeLanes = 32;  // served rounds: pipelined events in every warp
 constexpr int kServedBurstLanes = 1;  // served rounds: core bursts for lone packets
-constexpr uint32_t kLongLived = 1u << 14;  // served rounds: packets past this many events run one per warp
+constexpr uint32_t kLongLived = 1u << 14;
+constexpr uint32_t kPriBudget = 16;  // served rounds: budget multiple of a priority warp (one packet)  // served rounds: packets past this many events run one per warp
 
 struct Photon {
   double px, py, pz;  // FP64 anchor; the position is anchor + offset
@@ -947,6 +948,13 @@ __global__ void __launch_bounds__(256, 1) shell_slice_kernel(const ShellModel* _
   const int64_t n_rest_warps = n_warps - n_pw;
   const bool pri_warp = warp < n_pw;
   if (pri_warp) per_warp = 1;
+  // A priority warp holds one packet and runs at a lone lane's latency, several times the
+  // events a crowded warp runs in the same time: past the round's budget it goes on, up to
+  // kPriBudget times the budget, while other warps of the round are still running (live[4]
+  // counts those that finished), so the round lasts no longer for it.
+  const int64_t n_regular = n_warps - n_pw;
+  const uint32_t base_budget = budget;
+  if (pri_warp) budget *= kPriBudget;
   int64_t slot = -1;
   if (pri_warp) {
     if (lane == 0) slot = in.n_slots - 1 - warp;
@@ -980,7 +988,8 @@ __global__ void __launch_bounds__(256, 1) shell_slice_kernel(const ShellModel* _
     active = true;
   }
   uint32_t ev = 0;  // event iterations of this launch (warp-uniform)
-  while (ev < budget) {
+  auto others_done = [&]() { return pri_warp && ev >= base_budget && (int64_t)vload(&in.live[4]) >= n_regular; };
+  while (ev < budget && !others_done()) {
     const unsigned idle = __ballot_sync(kFull, !active && !done);
     const int room = per_warp - __popc(__ballot_sync(kFull, active));
     const bool take = ((idle >> lane) & 1u) && (int)__popc(idle & ((1u << lane) - 1u)) < room;
@@ -1045,8 +1054,9 @@ __global__ void __launch_bounds__(256, 1) shell_slice_kernel(const ShellModel* _
         if (r) { finish_global(mr, ph, r); active = false; fin = true; }
       }
       ev += 1u + __reduce_max_sync(kFull, nb);  // a burst is charged its events
-    } while (ev < budget && !__any_sync(kFull, fin));
+    } while (ev < budget && !__any_sync(kFull, fin) && !others_done());
   }
+  if (!pri_warp && lane == 0) atomicAdd(&in.live[4], 1ull);  // this regular warp's round is over
   if (active && prepared) pipe_unprepare(ph);  // saved packets hold their last completed event
   // append the packets still in flight to the next list (one atomic per warp and list):
   // priority packets from the back, the others from the front.  Priority: packets of the
