@@ -723,6 +723,16 @@ def test_invalid_arguments_are_rejected(ctx):
                    ds_cm=1.0, dv_cell=2.0, n_bins=7, dv_bin=1.0)
     with pytest.raises(thor.ThorError):
         ctx.shell(T=float("inf"), tau0=1.0)
+    # execution settings out of range leave the context as it was
+    for slots, handoff in ((-1, 0), (1 << 27, 0), (100, 101)):
+        with pytest.raises(thor.ThorError):
+            ctx.set_grid_exec(slots, handoff)
+    assert ctx.L.thor_ctx_set_tail_share(ctx.h, 2) == thor.ERR_INVALID_ARG
+    for pipe, burst in ((-1, 1), (33, 1), (32, 33)):
+        with pytest.raises(thor.ThorError):
+            ctx.set_bursts(pipe, burst)
+    r = ctx.run(g, n_photons=64, seed=1)
+    assert r.stats["n_escaped"] + r.stats["n_absorbed"] + r.stats["n_capped"] == 64
     # unusable grid cells are found on the device, for host and device fields alike
     import torch
     f = _small_grid(n=8, seed=2)
