@@ -138,6 +138,51 @@ struct Rng {
 };
 
 // ------------------------------------------------------------------------------
+// Work sharing in the tail of a one-launch photon loop (shell and grid): warps that ran
+// dry wait for packets that crowded warps give away.  share: [0] pool entries reserved,
+// [1] taken, [2] warps waiting, [3] photons finished, [4] a taken entry never became ready;
+// ready[i] is set (after a fence) once entry i is written.
+// Lane 0 of a warp whose lanes are all done (queue drained) takes the next pool entry
+// (compare-and-swap on the taken counter), or gives up once every photon of the run has
+// finished or after kPollMax polls (a packet still in the pool then is resumed by the
+// host).  Between polls it sleeps, backing off to 32 us, so that a thousand waiting warps
+// load the counters' cache lines little.  Returns the pool index, or -1.
+constexpr uint32_t kPollMax = 1u << 24;
+__device__ __forceinline__ unsigned long long vload(const unsigned long long* p) {
+  return *(volatile const unsigned long long*)p;
+}
+static __device__ __noinline__ long long pool_take(unsigned long long* share, const uint32_t* ready,
+                                                   unsigned long long n_total) {
+  atomicAdd(&share[2], 1ull);
+  long long got = -1;
+  unsigned ns = 64;
+  for (uint32_t it = 0; it < kPollMax; ++it) {
+    const unsigned long long t = vload(&share[1]), n = vload(&share[0]);
+    if (t < n) {
+      if (atomicCAS(&share[1], t, t + 1ull) == t) { got = (long long)t; break; }
+      continue;
+    }
+    if (vload(&share[3]) >= n_total) break;
+    __nanosleep(ns);
+    ns = ns < 32768u ? 2u * ns : 32768u;
+  }
+  atomicAdd(&share[2], ~0ull);  // -1
+  if (got >= 0) {  // the giver writes the record, then the flag: wait for the flag (short)
+    uint32_t it = 0;
+    while (*(volatile const uint32_t*)&ready[got] == 0u && ++it < kPollMax) __nanosleep(32);
+    if (it >= kPollMax) { atomicAdd(&share[4], 1ull); return -1; }
+    __threadfence();
+  }
+  return got;
+}
+// How many packets a warp with `live` packets gives away: all but one, up to the warps
+// waiting beyond the entries already in the pool.
+__device__ __forceinline__ long long pool_give_count(const unsigned long long* share, int live) {
+  const long long waiting = (long long)vload(&share[2]) - (long long)(vload(&share[0]) - vload(&share[1]));
+  return min((long long)(live - 1), waiting);
+}
+
+// ------------------------------------------------------------------------------
 // Voigt function H(a, x) in FP32 (App. A.3 defines the truth Re w(x + i a)).
 //   |x| >= 6 : wing, H = (a/sqrt(pi)) t g(t), t = 1/(x^2 + a^2), g = 2 x^2 K(x) fitted by a
 //              degree-4 polynomial in t (the asymptotic series sum_k ((2k+1)!!/2^k) t^k,

@@ -636,7 +636,7 @@ __global__ void grid_slab_sum_kernel(GridModel m, GridSlots S) {
 // refilled from the photon queue (warp-aggregated).  kResume: lanes first take the packets
 // on the resume list of S (the tail handed over by the event-based loop).
 template <bool kResume>
-__global__ void __launch_bounds__(256, 2) grid_run_kernel(GridModel m, WorkQueue q, const float* __restrict__ gK,
+__global__ void __launch_bounds__(256) grid_run_kernel(GridModel m, WorkQueue q, const float* __restrict__ gK,
                                                        GridSlots S) {
   __shared__ __align__(16) float sK[THOR_VOIGT_NINT * THOR_VOIGT_NCOEF];
   load_ktab(sK, gK);

@@ -716,40 +716,9 @@ __device__ __forceinline__ void load_rec(const ShellModel& m, const PhotonRec& r
   ph.rng.event = r.event;
 }
 
-// ---- work sharing in the tail of a one-launch run -----------------------------------------
-// Lane 0 of a warp whose lanes are all done (queue drained) waits for a given-away packet:
-// takes the next pool entry (compare-and-swap on the taken counter), or gives up once every
-// photon of the run has finished or after kPollMax polls (a packet still in the pool then is
-// resumed by the host).  Between polls it sleeps, backing off to 32 us, so that a thousand
-// waiting warps load the counters' cache lines little.  Returns the pool index, or -1.
-constexpr uint32_t kPollMax = 1u << 24;
+// ---- work sharing in the tail of a one-launch run (pool_take in thor_device.cuh) ----------
 constexpr uint32_t kShareEvents = 512;  // a warp with several live packets checks for waiting warps this often
-__device__ __forceinline__ unsigned long long vload(const unsigned long long* p) {
-  return *(volatile const unsigned long long*)p;
-}
-__device__ long long share_take(const Compact& c) {
-  atomicAdd(&c.share[2], 1ull);
-  long long got = -1;
-  unsigned ns = 64;
-  for (uint32_t it = 0; it < kPollMax; ++it) {
-    const unsigned long long t = vload(&c.share[1]), n = vload(&c.share[0]);
-    if (t < n) {
-      if (atomicCAS(&c.share[1], t, t + 1ull) == t) { got = (long long)t; break; }
-      continue;
-    }
-    if (vload(&c.share[3]) >= c.n_total) break;
-    __nanosleep(ns);
-    ns = ns < 32768u ? 2u * ns : 32768u;
-  }
-  atomicAdd(&c.share[2], ~0ull);  // -1
-  if (got >= 0) {  // the giver writes the record, then the flag: wait for the flag (short)
-    uint32_t it = 0;
-    while (*(volatile const uint32_t*)&c.ready[got] == 0u && ++it < kPollMax) __nanosleep(32);
-    if (it >= kPollMax) { atomicAdd(&c.share[4], 1ull); return -1; }
-    __threadfence();
-  }
-  return got;
-}
+__device__ __forceinline__ long long share_take(const Compact& c) { return pool_take(c.share, c.ready, c.n_total); }
 
 // Run-to-completion: all queue entries belong to one model (thor_run).  With kCompact,
 // lanes first resume saved packets, and a warp whose sources are empty and whose live
@@ -830,11 +799,7 @@ __global__ void __launch_bounds__(256, 1) shell_run_kernel(const ShellModel* __r
       if (__popc(live) >= 2) {  // give packets away while empty warps wait, keeping the lowest lane's
         const int leader = __ffs(live) - 1;
         long long give = 0;
-        if ((int)lane == leader) {
-          const long long waiting = (long long)vload(&c.share[2]) -
-                                    (long long)(vload(&c.share[0]) - vload(&c.share[1]));
-          give = min((long long)(__popc(live) - 1), waiting);
-        }
+        if ((int)lane == leader) give = pool_give_count(c.share, __popc(live));
         give = __shfl_sync(kFull, give, leader);
         if (give > 0) {
           // the `give` highest live lanes: their rank from the top
