@@ -683,7 +683,7 @@ def main():
                          "bench workload)")
     ap.add_argument("--thread-inst-per-scat", type=float, default=9276.0,
                     help="thread instructions per scattering of the shell photon loop (ncu, same capture)")
-    ap.add_argument("--launch-dram-bytes", type=float, default=974592.0,
+    ap.add_argument("--launch-dram-bytes", type=float, default=798976.0,
                     help="DRAM bytes read + written by one launch of the shell kernel (ncu, same capture; fixed per "
                          "launch: code, constants, tables)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -5,8 +5,10 @@ the number of resident blocks per SM (register pressure versus latency hiding) a
 for served rounds, the number of events a lane runs per launch.  ``tune_run`` times a
 short representative run for each candidate shape through the C ABI and keeps the
 fastest; ``tune_server`` does the same for ``events_per_round`` on a small burst of
-requests.  Results are cached per device name and workload key in a JSON file next to
-the built library.
+requests.  ``tune_modes`` times the execution modes that change no result -- for a grid,
+the one-kernel loop against the event-based loop with a few slot counts; for a shell, the
+lanes that run pipelined events and core bursts -- and keeps the fastest.  Results are
+cached per device name and workload key in a JSON file next to the built library.
 """
 from __future__ import annotations
 
@@ -86,4 +88,39 @@ def tune_server(ctx, requests, key, candidates=(32, 64, 128, 256, 512, 1024), **
     best = dict(best, table=results)
     cache[dk] = best
     _save(cache)
+    return best
+
+
+GRID_MODES = ((0, 0), (1 << 16, 1 << 13), (1 << 18, 1 << 15))  # (slots, handoff); 0 = one kernel
+SHELL_MODES = ((32, 1), (32, 2), (32, 4), (8, 1))              # (pipe_lanes, burst_lanes)
+
+
+def tune_modes(ctx, geom, key, n_photons=20000, repeats=2, candidates=None, grid=False, **run_kw):
+    """Pick the execution mode of thor_run on `geom` (grid: thor_ctx_set_grid_exec; shell:
+    thor_ctx_set_bursts) from timed runs; returns the best and sets it."""
+    cache = _load()
+    dk = f"{_device_name()}|mode|{key}|{n_photons}"
+    cands = list(candidates or (GRID_MODES if grid else SHELL_MODES))
+
+    def apply(c):
+        if grid:
+            ctx.set_grid_exec(*c)
+        else:
+            ctx.set_bursts(*c)
+
+    if dk in cache:
+        apply(tuple(cache[dk]["mode"]))
+        return cache[dk]
+    results = []
+    for c in cands:
+        apply(c)
+        ctx.run(geom, n_photons=n_photons, seed=99, **run_kw)  # warm-up
+        ms = min(ctx.run(geom, n_photons=n_photons, seed=100 + r, **run_kw).stats["elapsed_ms"]
+                 for r in range(repeats))
+        results.append({"mode": list(c), "ms": ms})
+    best = min(results, key=lambda t: t["ms"])
+    best = dict(best, table=results)
+    cache[dk] = best
+    _save(cache)
+    apply(tuple(best["mode"]))
     return best

@@ -898,6 +898,19 @@ def test_autotuner_picks_a_measured_shape(ctx, tmp_path, monkeypatch):
     srv = autotune.tune_server(ctx, [dict(N_HI=1e18, T=1e4, v_max=100.0, n_photons=2000, seed=s) for s in (1, 2)],
                                "two-requests", candidates=(64, 256), R_in=0.9, phase="dipole", sigma=50.0)
     assert srv["events_per_round"] in (64, 256)
+    # execution modes: grid loop (one kernel or event-based), shell bursts
+    f = _small_grid(n=8, seed=4)
+    gg = ctx.grid(f["n_HI"], f["T"], f["v"], f["kd"], 100 * 3.0856775814913673e18, phase="dipole")
+    gkw = dict(n_bins=32, X_min=-400.0, X_max=400.0)
+    m = autotune.tune_modes(ctx, gg, "grid8", n_photons=3000, candidates=[(0, 0), (4096, 512)], grid=True, **gkw)
+    assert len(m["table"]) == 2 and m["ms"] == min(t["ms"] for t in m["table"])
+    r1 = ctx.run(gg, n_photons=2000, seed=5, **gkw)
+    ctx.set_grid_exec(0, 0)
+    r0 = ctx.run(gg, n_photons=2000, seed=5, **gkw)
+    assert np.array_equal(r0.spectrum, r1.spectrum) and r0.stats["n_scat"] == r1.stats["n_scat"]
+    sm = autotune.tune_modes(ctx, g, "sphere-1e4", n_photons=2000, candidates=[(32, 1), (32, 4)], **kw)
+    assert sm["mode"] in ([32, 1], [32, 4])
+    ctx.set_bursts(32, 1)
 
 
 def test_server_mixes_power_law_and_homologous_requests(ctx):
