@@ -154,7 +154,9 @@ def test_dda_bit_exact(ctx, orc, dims):
 # ------------------------------------------------------------------ samplers
 @pytest.mark.parametrize("x,a", [(0.0, 4.7e-4), (1.3, 4.7e-4), (2.5, 1e-3), (3.0, 1e-2), (6.0, 1e-3),
                                  (-14.0, 4.7e-4), (3.5, 1e-4), (4.0, 1e-5), (4.0, 4.7e-4), (50.0, 4.7e-4),
-                                 (-200.0, 1e-3)])
+                                 (-200.0, 1e-3),
+                                 # near line centre u0 = 0: w1 from the series in a/x (a <= x/20) or atan2
+                                 (0.02, 4.7e-4), (-0.005, 4.7e-4)])
 def test_upar_sampler(ctx, orc, x, a):
     n = 100000
     u, it = ctx.sample_upar(x, a, n, seed=21)
