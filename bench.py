@@ -337,7 +337,7 @@ def run_shell_bench(args):
 
 
 def stream_bench(ctx, n_requests=256, seed=2, load=0.75, events_per_round=256, nhi_max=1e21, core_skip=True,
-                 priority=True, presort=True):
+                 priority=True, presort=False):
     """Served shell-model stream (Sec. 5.1 parameter grid): requests with Poisson arrivals at
     `load` x the measured batched capacity, continuous batching on the device.  Baseline,
     also live: the same requests at the same arrival times served one launch per model
@@ -427,7 +427,7 @@ def run_stream_bench(args):
     with ClockSampler(0) as clk:
         s = stream_bench(ctx, n_requests=args.stream_requests, nhi_max=args.stream_nhi_max,
                          core_skip=not args.no_core_skip, priority=not args.no_priority,
-                         presort=not args.no_presort)
+                         presort=args.presort)
     print(json.dumps({"metric": METRIC, "value": s["batched"]["scatterings_per_s"], "unit": "scatterings/s",
                       "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
                       "config": {"workload": "served shell-model stream"}, "stream": s, "clocks": clk.summary()}))
@@ -667,7 +667,7 @@ def main():
     ap.add_argument("--stream-nhi-max", type=float, default=1e21)
     ap.add_argument("--no-core-skip", action="store_true")
     ap.add_argument("--no-priority", action="store_true", help="served stream without age priority")
-    ap.add_argument("--no-presort", action="store_true", help="served stream without frequency pre-sorting")
+    ap.add_argument("--presort", action="store_true", help="served stream with frequency pre-sorting between rounds")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--lone-events", type=int, default=200000,
                     help="events of the longest photon run alone to time the lone-lane event latency")

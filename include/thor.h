@@ -321,7 +321,9 @@ typedef struct {
                                 their packets in flight fit in half of the warps, run their packets
                                 one per warp), -1 = off (every packet shares warps) */
   int32_t presort;           /* frequency pre-sorting of the packets in flight between rounds, so a
-                                warp's packets are of one kind: 0 = on, -1 = off */
+                                warp's packets are of one kind: 1 = on, 0 = off (the default; on the
+                                measured stream it did not pay, the pipelined core events already
+                                keep core packets in step) */
   int32_t reserved;
 } thor_server_config;
 

@@ -393,7 +393,7 @@ extern "C" int thor_server_create(thor_ctx_t ctx, const thor_server_config* cfg,
                          s->grid, s->block, v == 1, cs);
       // the survivors become the next round's list: sorted by frequency bucket (pre-sorting),
       // or copied as they are
-      if (s->cfg.presort >= 0) launch_slot_presort(s->st_out, s->st_in, s->st_in.live + 8, cs);
+      if (s->cfg.presort > 0) launch_slot_presort(s->st_out, s->st_in, s->st_in.live + 8, cs);
       else cudaMemcpyAsync(s->d_slots, (char*)s->d_slots + s->slot_bytes, s->slot_bytes, cudaMemcpyDeviceToDevice, cs);
       cudaMemcpyAsync(&s->st_in.live[0], &s->st_in.live[1], 8, cudaMemcpyDeviceToDevice, cs);
       cudaMemsetAsync(&s->st_in.live[1], 0, 8, cs);

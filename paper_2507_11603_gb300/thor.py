@@ -493,11 +493,11 @@ class Context:
         return out
 
     def server(self, *, max_requests=256, events_per_round=256, n_slots=0, mem_budget_bytes=0, block_size=0,
-               priority=True, presort=True):
+               priority=True, presort=False):
         """thor_server_create; priority: age priority (the oldest requests' packets one per warp);
         presort: frequency pre-sorting of the packets in flight between rounds."""
         return Server(self, ServerConfig(max_requests, events_per_round, n_slots, mem_budget_bytes, block_size,
-                                         0 if priority else -1, 0 if presort else -1, 0))
+                                         0 if priority else -1, 1 if presort else 0, 0))
 
 
 class Geometry:
