@@ -286,7 +286,8 @@ int thor_reweight(thor_ctx_t ctx, int64_t n, const float* X0, const float* X, co
  * allocate device memory when they need a run -- code running under an external memory
  * pool with nothing to spare, a process whose GPU quota its own buffers already use up,
  * or a host callback in which cudaMalloc is not allowed.  It runs the same shell photon
- * loop as thor_run (identical results for identical arguments) on the current device and
+ * loop as thor_run (identical results for identical arguments; the context defaults of
+ * thor_ctx_set_bursts, no tail work sharing) on the current device and
  * `stream` (a cudaStream_t, NULL = legacy default stream), with no context and no
  * cudaMalloc / cudaFree: its scratch (model record, tallies, queue, and a staging copy of
  * a host spectrum) lives in a fixed file-scope device array that every GPU loading the
