@@ -114,7 +114,7 @@ def test_line_parameters(orc):
 # ------------------------------------------------------------------ samplers
 @pytest.mark.parametrize("sampler", ["eq10", "envelope"])
 @pytest.mark.parametrize("a", [1e-2, 1e-3, 1e-4])
-@pytest.mark.parametrize("x", [0.0, 1.0, 2.0, 3.0, 4.0, 6.0, 10.0, -2.5, 50.0, -200.0])
+@pytest.mark.parametrize("x", [0.0, 0.005, -0.02, 1.0, 2.0, 3.0, 4.0, 6.0, 10.0, -2.5, 50.0, -200.0])
 def test_upar_distribution_matches_eq6(orc, x, a, sampler):
     """Both exact samplers of the oracle against the Eq. 6 CDF by quadrature."""
     n = 40000
